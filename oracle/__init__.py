@@ -1,0 +1,262 @@
+"""FP64 brute-force ray-cast oracle (TEST INFRASTRUCTURE ONLY).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may import this package. The product renderer (``paper_2503_01471_gb300``)
+never imports it, and the two share no code.
+
+The C library ``oracle.c`` implements the method of the Aerial Gym Simulator
+paper, Sec. III-D.1 (per-object rigid transform of the base meshes, one ray
+per pixel or beam, nearest hit against every triangle, depth vs range, segment
+IDs) in double precision. This module compiles it with gcc on first use and
+wraps it with ctypes. The only non-C step here is gathering a sub-mesh's
+transformed vertices by its triangle indices (numpy fancy indexing).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_HDR = os.path.join(_HERE, "oracle.h")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+
+MAX_CAND = 4
+F_COUNTED = 1
+F_SILHOUETTE = 2
+F_NEAR_TIE = 4
+F_RANGE_EDGE = 8
+F_GRAZING = 16
+F_OVERFLOW = 32
+F_MISS_OK = 64
+
+PINHOLE = 0
+LIDAR = 1
+NEAR_CLAMP = 0
+NEAR_INVALID = 1
+
+# Error bands of the float32 renderer being judged: world vertex coordinates
+# within VERT_REL * max(|x|, 1) of exact (4 units in the last place), ray
+# directions within DIR_REL (relative), and intersection arithmetic that moves
+# the ray sideways by at most ARITH_REL times the distance to the vertices.
+VERT_REL = 4.0 * 2.0 ** -23
+DIR_REL = 1e-6
+ARITH_REL = 4.0 * 2.0 ** -24
+
+
+def build(force: bool = False, extra_flags: tuple[str, ...] = (), out: str | None = None) -> str:
+    """Compile oracle.c into a shared library (gcc, OpenMP, no FP contraction)."""
+    out = out or _LIB
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= newest:
+        return out
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+           "-shared", "-fPIC", *extra_flags, _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
+class _Sensor(ctypes.Structure):
+    _fields_ = [
+        ("type", ctypes.c_int32), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+        ("near_mode", ctypes.c_int32), ("hfov", ctypes.c_double), ("vfov_min", ctypes.c_double),
+        ("vfov_max", ctypes.c_double), ("min_range", ctypes.c_double),
+        ("max_range", ctypes.c_double), ("vert_rel", ctypes.c_double),
+        ("dir_rel", ctypes.c_double), ("arith_rel", ctypes.c_double),
+    ]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [
+        ("v", ctypes.c_double), ("seg", ctypes.c_int32), ("tri", ctypes.c_int32),
+        ("flags", ctypes.c_int32), ("n_cand", ctypes.c_int32),
+        ("cand_seg", ctypes.c_int32 * MAX_CAND), ("cand_lo", ctypes.c_double * MAX_CAND),
+        ("cand_hi", ctypes.c_double * MAX_CAND),
+    ]
+
+
+RESULT_DTYPE = np.dtype({
+    "names": ["v", "seg", "tri", "flags", "n_cand", "cand_seg", "cand_lo", "cand_hi"],
+    "formats": ["<f8", "<i4", "<i4", "<i4", "<i4", ("<i4", MAX_CAND), ("<f8", MAX_CAND),
+                ("<f8", MAX_CAND)],
+    "offsets": [_Result.v.offset, _Result.seg.offset, _Result.tri.offset, _Result.flags.offset,
+                _Result.n_cand.offset, _Result.cand_seg.offset, _Result.cand_lo.offset,
+                _Result.cand_hi.offset],
+    "itemsize": ctypes.sizeof(_Result),
+})
+
+_lock = threading.Lock()
+_libs: dict[str, ctypes.CDLL] = {}
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load (building if needed) the oracle library; ``path`` selects a variant build."""
+    with _lock:
+        key = path or _LIB
+        if key in _libs:
+            return _libs[key]
+        if path is None:
+            build()
+        lib = ctypes.CDLL(key)
+        dp = ctypes.POINTER(ctypes.c_double)
+        lib.orc_rotation.argtypes = [dp, dp]
+        lib.orc_rotation.restype = None
+        lib.orc_transform.argtypes = [dp, ctypes.c_int64, dp, dp]
+        lib.orc_transform.restype = None
+        lib.orc_ray.argtypes = [ctypes.POINTER(_Sensor), dp, ctypes.c_int64, ctypes.c_int64, dp, dp, dp]
+        lib.orc_ray.restype = ctypes.c_int
+        lib.orc_render.argtypes = [dp, ctypes.POINTER(ctypes.c_int32), ctypes.c_int64,
+                                   ctypes.POINTER(_Sensor), dp, ctypes.POINTER(ctypes.c_int64),
+                                   ctypes.c_int64, ctypes.c_void_p]
+        lib.orc_render.restype = ctypes.c_int
+        lib.orc_num_threads.argtypes = []
+        lib.orc_num_threads.restype = ctypes.c_int
+        _libs[key] = lib
+        return lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+@dataclass
+class Sensor:
+    """Sensor model of the oracle (angles in radians, ranges in metres)."""
+    type: int
+    width: int
+    height: int
+    hfov: float
+    min_range: float
+    max_range: float
+    vfov_min: float = 0.0
+    vfov_max: float = 0.0
+    near_mode: int = NEAR_CLAMP
+    vert_rel: float = VERT_REL
+    dir_rel: float = DIR_REL
+    arith_rel: float = ARITH_REL
+
+    def _c(self) -> _Sensor:
+        return _Sensor(self.type, self.width, self.height, self.near_mode, self.hfov,
+                       self.vfov_min, self.vfov_max, self.min_range, self.max_range,
+                       self.vert_rel, self.dir_rel, self.arith_rel)
+
+
+def rotation(q, lib=None) -> np.ndarray:
+    lib = lib or load()
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    R = np.zeros(9, np.float64)
+    lib.orc_rotation(_dp(q), _dp(R))
+    return R.reshape(3, 3)
+
+
+def transform(v, pose, lib=None) -> np.ndarray:
+    """World coordinates v' = R(q) v + p of object-frame points v [n,3]."""
+    lib = lib or load()
+    v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1, 3)
+    pose = np.ascontiguousarray(pose, dtype=np.float64).reshape(7)
+    out = np.empty_like(v)
+    lib.orc_transform(_dp(v), v.shape[0], _dp(pose), _dp(out))
+    return out
+
+
+def ray(sensor: Sensor, pose, row: int, col: int, lib=None):
+    """(origin, unit direction, value scale) of one pixel/beam."""
+    lib = lib or load()
+    pose = np.ascontiguousarray(pose, dtype=np.float64).reshape(7)
+    o = np.zeros(3)
+    d = np.zeros(3)
+    sc = np.zeros(1)
+    s = sensor._c()
+    rc = lib.orc_ray(ctypes.byref(s), _dp(pose), row, col, _dp(o), _dp(d), _dp(sc))
+    if rc != 0:
+        raise ValueError("orc_ray: bad sensor or pixel")
+    return o, d, float(sc[0])
+
+
+def world_triangles(vertices_list, indices_list, poses, segs):
+    """FP64 world-space triangles [F,9] and segment IDs [F] of one environment.
+
+    ``vertices_list[j]`` [n_j,3] and ``indices_list[j]`` [m_j,3] are sub-mesh j
+    in its object frame, ``poses[j]`` its (p, q) pose and ``segs[j]`` its ID.
+    """
+    lib = load()
+    tris, seg = [], []
+    for v, idx, pose, s in zip(vertices_list, indices_list, poses, segs):
+        w = transform(np.asarray(v, np.float64), np.asarray(pose, np.float64), lib)
+        idx = np.asarray(idx, np.int64)
+        tris.append(w[idx].reshape(-1, 9))
+        seg.append(np.full(idx.shape[0], int(s), np.int32))
+    if not tris:
+        return np.zeros((0, 9)), np.zeros(0, np.int32)
+    return np.ascontiguousarray(np.concatenate(tris)), np.ascontiguousarray(np.concatenate(seg))
+
+
+def render(tris, seg, sensor: Sensor, pose, rays=None, lib=None) -> np.ndarray:
+    """Oracle result for each listed ray (flat index row*width+col; all if None)."""
+    lib = lib or load()
+    tris = np.ascontiguousarray(tris, dtype=np.float64).reshape(-1, 9)
+    seg = np.ascontiguousarray(seg, dtype=np.int32).reshape(-1)
+    if seg.shape[0] != tris.shape[0]:
+        raise ValueError("seg and tris disagree")
+    pose = np.ascontiguousarray(pose, dtype=np.float64).reshape(7)
+    if rays is None:
+        rays = np.arange(sensor.width * sensor.height, dtype=np.int64)
+    rays = np.ascontiguousarray(rays, dtype=np.int64).reshape(-1)
+    out = np.zeros(rays.shape[0], RESULT_DTYPE)
+    s = sensor._c()
+    rc = lib.orc_render(_dp(tris), seg.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                        tris.shape[0], ctypes.byref(s), _dp(pose),
+                        rays.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), rays.shape[0],
+                        out.ctypes.data)
+    if rc != 0:
+        raise ValueError("orc_render: bad input")
+    return out
+
+
+def num_threads(lib=None) -> int:
+    return int((lib or load()).orc_num_threads())
+
+
+def tol(v):
+    """Depth/range tolerance |dv| <= 1e-5 v + 1e-6 m."""
+    return 1e-5 * np.abs(v) + 1e-6
+
+
+def check(res: np.ndarray, v_gpu, seg_gpu, max_range: float):
+    """Element-wise acceptance of renderer outputs against oracle results.
+
+    Returns (ok mask, counted mask). A miss must be bit-exact (float32
+    max_range, segment -1) and allowed; a hit must fall in a candidate group of
+    the same segment within tolerance; uncounted rays must also match the exact
+    answer within tolerance.
+    """
+    v = np.asarray(v_gpu, np.float64).reshape(-1)
+    s = np.asarray(seg_gpu, np.int64).reshape(-1)
+    miss_val = float(np.float32(max_range))
+    is_miss = s == -1
+    miss_ok = (res["flags"] & F_MISS_OK) != 0
+    ok = np.zeros(v.shape[0], bool)
+    ok |= is_miss & (v == miss_val) & miss_ok
+    hit_ok = np.zeros(v.shape[0], bool)
+    for k in range(MAX_CAND):
+        valid = res["n_cand"] > k
+        lo = res["cand_lo"][:, k]
+        hi = res["cand_hi"][:, k]
+        m = valid & (res["cand_seg"][:, k] == s) & (v >= lo - tol(lo)) & (v <= hi + tol(hi))
+        hit_ok |= m
+    ok |= (~is_miss) & hit_ok
+    counted = (res["flags"] & F_COUNTED) != 0
+    exact = np.where(res["seg"] == -1, (v == miss_val) & is_miss,
+                     (s == res["seg"]) & (np.abs(v - res["v"]) <= tol(res["v"])))
+    ok &= counted | exact
+    ok &= (res["flags"] & F_OVERFLOW) == 0
+    return ok, counted

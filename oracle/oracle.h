@@ -1,0 +1,98 @@
+/*
+ * FP64 brute-force ray-cast oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may load
+ * this library. The product (the CUDA renderer behind include/ags.h) never
+ * calls it and shares no code, header or constant with it.
+ *
+ * What it computes (Aerial Gym Simulator, Sec. III-D.1 "Exteroceptive Sensors"):
+ *   - the per-object rigid transform of each base sub-mesh into the world
+ *     (the "T o M^base" composition, read as v' = R(q) v + p);
+ *   - one ray per pixel (pinhole camera) or per channel/azimuth bin (3-D LiDAR);
+ *   - the nearest intersection of that ray with every triangle of the
+ *     environment (no acceleration structure: the plain definition);
+ *   - the reported value: range (distance sensor -> hit) for LiDAR, depth
+ *     (distance of the hit from the image plane) for the camera, and the
+ *     segment ID of the object hit; misses report max_range and -1.
+ * On top of the exact answer it classifies each ray's tolerance-ambiguous
+ * outcomes (edge/silhouette, near-tie, range boundary, grazing) so that a
+ * single-precision implementation can be judged element by element.
+ */
+#ifndef AGS_ORACLE_H
+#define AGS_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_PINHOLE 0
+#define ORC_LIDAR 1
+#define ORC_NEAR_CLAMP 0
+#define ORC_NEAR_INVALID 1
+
+/* maximum number of distinct-segment outcome groups reported per ray */
+#define ORC_MAX_CAND 4
+
+/* flag bits of orc_result.flags */
+#define ORC_F_COUNTED 1      /* more than one outcome is acceptable */
+#define ORC_F_SILHOUETTE 2   /* a candidate lies within eps of a triangle edge */
+#define ORC_F_NEAR_TIE 4     /* two surely-hit triangles of different segments within tol */
+#define ORC_F_RANGE_EDGE 8   /* a candidate lies within tol of a range limit */
+#define ORC_F_GRAZING 16     /* a candidate has |n.d| < 1e-3 */
+#define ORC_F_OVERFLOW 32    /* more than ORC_MAX_CAND segment groups (test must fail) */
+#define ORC_F_MISS_OK 64     /* "miss" (max_range, -1) is an acceptable outcome */
+
+typedef struct {
+  int32_t type;        /* ORC_PINHOLE or ORC_LIDAR */
+  int32_t width;       /* camera columns, or LiDAR azimuth bins */
+  int32_t height;      /* camera rows, or LiDAR channels */
+  int32_t near_mode;   /* ORC_NEAR_CLAMP or ORC_NEAR_INVALID */
+  double hfov;         /* camera: horizontal field of view; LiDAR: azimuth span (rad) */
+  double vfov_min;     /* LiDAR: lowest channel elevation (rad); unused by the camera */
+  double vfov_max;     /* LiDAR: highest channel elevation (rad) */
+  double min_range;    /* metres; applies to depth (camera) or range (LiDAR) */
+  double max_range;
+  /* error bands of the single-precision renderer being judged (see orc_render) */
+  double vert_rel;     /* world vertex coordinate error, relative to max(|coord|, 1) */
+  double dir_rel;      /* ray direction error, relative */
+  double arith_rel;    /* intersection arithmetic error, relative to the vertex distance */
+} orc_sensor;
+
+typedef struct {
+  double v;            /* exact reported value (depth or range), metres */
+  int32_t seg;         /* exact segment ID, -1 on miss */
+  int32_t tri;         /* env-local triangle index of the exact nearest hit, -1 on miss */
+  int32_t flags;       /* ORC_F_* */
+  int32_t n_cand;      /* number of valid candidate groups */
+  int32_t cand_seg[ORC_MAX_CAND];
+  double cand_lo[ORC_MAX_CAND];   /* acceptable reported-value interval per segment */
+  double cand_hi[ORC_MAX_CAND];
+} orc_result;
+
+/* Rotation matrix of the unit quaternion q/|q| (x, y, z, w order), row-major. */
+void orc_rotation(const double q[4], double R[9]);
+
+/* v' = R(q) v + p for n points; pose = (px, py, pz, qx, qy, qz, qw). */
+void orc_transform(const double* v, int64_t n, const double pose[7], double* out);
+
+/* The ray of pixel/beam (row, col): origin o, unit direction d, and the factor
+ * that turns distance along d into the reported value (d.f for a camera whose
+ * optical axis is f = R(q) (1,0,0); 1 for LiDAR). Returns 0, or -1 on bad input. */
+int orc_ray(const orc_sensor* s, const double pose[7], int64_t row, int64_t col,
+            double o[3], double d[3], double* scale);
+
+/* Nearest hit for each listed ray (flat index row*width+col) against all F
+ * triangles tris[F][9] (x0 y0 z0 x1 y1 z1 x2 y2 z2), segment IDs seg[F].
+ * Parallel over rays with OpenMP. Returns 0, or -1 on bad input. */
+int orc_render(const double* tris, const int32_t* seg, int64_t F,
+               const orc_sensor* s, const double pose[7],
+               const int64_t* rays, int64_t n_rays, orc_result* out);
+
+/* Number of OpenMP threads the oracle uses. */
+int orc_num_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

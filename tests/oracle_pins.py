@@ -1,0 +1,393 @@
+"""Checks that pin the FP64 oracle to facts outside itself.
+
+Each ``pin_*`` function takes a loaded oracle library (so the same checks can
+run against deliberately broken builds in test_oracle_mutants.py) and raises
+AssertionError when the oracle disagrees with:
+  - scipy's quaternion rotation (a library routine, for the transform);
+  - closed forms of the camera / LiDAR ray geometry;
+  - closed-form depths and ranges (wall, cylinder facets, icosphere bounds);
+  - hand-worked cases stored in tests/golden/hand_worked.json;
+  - a numpy.linalg.solve brute force on tiny random scenes;
+  - invariants (exact misses, translation/rotation of the whole scene).
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import numpy as np
+
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "hand_worked.json")
+
+
+def _sensor_from(d):
+    return O.Sensor(
+        type=d["type"], width=d["width"], height=d["height"], hfov=math.radians(d["hfov_deg"]),
+        min_range=d["min_range"], max_range=d["max_range"],
+        vfov_min=math.radians(d.get("vfov_min_deg", 0.0)),
+        vfov_max=math.radians(d.get("vfov_max_deg", 0.0)), near_mode=d.get("near_mode", 0))
+
+
+def _rot_scipy(q):
+    from scipy.spatial.transform import Rotation
+    return Rotation.from_quat(np.asarray(q, np.float64)).as_matrix()
+
+
+def _quat_from_matrix_scipy(R):
+    from scipy.spatial.transform import Rotation
+    return Rotation.from_matrix(R).as_quat()
+
+
+IDENT = np.array([0, 0, 0, 0, 0, 0, 1.0])
+
+
+# ---------------------------------------------------------------- a1 transform
+def pin_rotation_vs_scipy(lib):
+    rng = np.random.default_rng(11)
+    for _ in range(200):
+        q = rng.normal(size=4) * rng.uniform(0.1, 5.0)  # not normalised on purpose
+        R = O.rotation(q, lib)
+        assert np.allclose(R, _rot_scipy(q), atol=1e-13, rtol=0), (q, R)
+
+
+def pin_transform_vs_scipy(lib):
+    rng = np.random.default_rng(12)
+    for _ in range(50):
+        q = rng.normal(size=4)
+        p = rng.uniform(-10, 10, 3)
+        v = rng.uniform(-3, 3, (40, 3))
+        out = O.transform(v, np.concatenate([p, q]), lib)
+        ref = v @ _rot_scipy(q).T + p
+        assert np.allclose(out, ref, atol=1e-12, rtol=0)
+
+
+def pin_transform_identity_exact(lib):
+    rng = np.random.default_rng(13)
+    v = rng.uniform(-100, 100, (1000, 3))
+    out = O.transform(v, IDENT, lib)
+    assert np.array_equal(out, v)
+
+
+# ---------------------------------------------------------------- a3 rays
+def pin_camera_centre_and_corner(lib):
+    rng = np.random.default_rng(14)
+    for _ in range(20):
+        W, H = 2 * int(rng.integers(1, 40)) + 1, 2 * int(rng.integers(1, 30)) + 1
+        hfov = rng.uniform(0.3, 2.5)
+        s = O.Sensor(O.PINHOLE, W, H, hfov, 0.1, 10.0)
+        q = rng.normal(size=4)
+        pose = np.concatenate([rng.uniform(-5, 5, 3), q])
+        R = _rot_scipy(q)
+        fwd = R[:, 0]
+        o, d, sc = O.ray(s, pose, H // 2, W // 2, lib)
+        assert np.allclose(o, pose[:3], atol=0)
+        assert np.allclose(d, fwd, atol=1e-14), "centre pixel looks along the optical axis"
+        assert abs(sc - 1.0) < 1e-14
+        f = (W / 2) / math.tan(hfov / 2)
+        a, b = (W / 2 - 0.5) / f, (H / 2 - 0.5) / f
+        o, d, sc = O.ray(s, pose, 0, 0, lib)
+        ang = math.acos(min(1.0, float(d @ fwd)))
+        assert abs(ang - math.atan(math.hypot(a, b))) < 1e-12
+        # top-left pixel looks left (+y body) and up (+z body)
+        local = R.T @ d
+        assert local[1] > 0 and local[2] > 0
+        assert abs(sc - 1.0 / math.sqrt(1 + a * a + b * b)) < 1e-13
+        assert abs(np.linalg.norm(d) - 1) < 1e-14
+
+
+def pin_camera_column_angles(lib):
+    W, H, hfov = 16, 4, math.radians(87)
+    s = O.Sensor(O.PINHOLE, W, H, hfov, 0.1, 10.0)
+    f = (W / 2) / math.tan(hfov / 2)
+    for c in range(W):
+        o, d, _ = O.ray(s, IDENT, 1, c, lib)
+        az = math.atan2(d[1], d[0])
+        assert abs(az - math.atan((W / 2 - c - 0.5) / f)) < 1e-13
+    # mirrored columns mirror the direction in y
+    for c in range(W):
+        _, d1, _ = O.ray(s, IDENT, 0, c, lib)
+        _, d2, _ = O.ray(s, IDENT, 0, W - 1 - c, lib)
+        assert np.allclose(d1 * [1, -1, 1], d2, atol=1e-15)
+
+
+def pin_lidar_angles(lib):
+    C, A = 7, 12
+    vmin, vmax = math.radians(-22.5), math.radians(22.5)
+    s = O.Sensor(O.LIDAR, A, C, 2 * math.pi, 0.3, 50.0, vmin, vmax)
+    for k in range(C):
+        for j in range(A):
+            o, d, sc = O.ray(s, IDENT, k, j, lib)
+            assert abs(np.linalg.norm(d) - 1) < 1e-14 and sc == 1.0
+            el = math.asin(d[2])
+            assert abs(el - (vmax - k * (vmax - vmin) / (C - 1))) < 1e-13
+            az = math.atan2(d[1], d[0]) % (2 * math.pi)
+            want = (2 * math.pi * j / A) % (2 * math.pi)
+            assert min(abs(az - want), 2 * math.pi - abs(az - want)) < 1e-13
+    # yaw by +90 deg turns azimuth 0 into +y
+    q = np.array([0, 0, math.sin(math.pi / 4), math.cos(math.pi / 4)])
+    _, d, _ = O.ray(s, np.concatenate([[1, 2, 3], q]), (C - 1) // 2, 0, lib)
+    assert np.allclose(d, [0, 1, 0], atol=1e-15)
+
+
+# ---------------------------------------------------------------- a4-a6 closed forms
+def _quad(x, half, seg, tris, segs):
+    tris += [[x, -half, -half, x, half, -half, x, half, half], [x, -half, -half, x, half, half, x, -half, half]]
+    segs += [seg, seg]
+
+
+def pin_wall_depth_constant(lib):
+    """Camera facing a huge wall at distance D: depth = D everywhere, range = D / cos."""
+    rng = np.random.default_rng(15)
+    for _ in range(6):
+        D = rng.uniform(0.5, 9.0)
+        q = rng.normal(size=4)
+        R = _rot_scipy(q)
+        p = rng.uniform(-3, 3, 3)
+        # wall in the camera frame at x = D, moved to the world by the same pose
+        local = np.array([[D, -60, -60], [D, 60, -60], [D, 60, 60], [D, -60, 60]])
+        wv = local @ R.T + p
+        tris = np.array([np.concatenate([wv[0], wv[1], wv[2]]), np.concatenate([wv[0], wv[2], wv[3]])])
+        seg = np.array([3, 3], np.int32)
+        s = O.Sensor(O.PINHOLE, 24, 18, math.radians(87), 0.1, 10.0)
+        pose = np.concatenate([p, q])
+        r = O.render(tris, seg, s, pose, lib=lib)
+        assert np.all(np.abs(r["v"] - D) <= 1e-9 * D)
+        assert np.all(r["seg"] == 3)
+        sl = O.Sensor(O.LIDAR, 16, 5, 2 * math.pi, 0.1, 1e5, -0.4, 0.4)
+        rl = O.render(tris, seg, sl, pose, lib=lib)
+        for idx in range(16 * 5):
+            k, j = divmod(idx, 16)
+            _, d, _ = O.ray(sl, pose, k, j, lib)
+            cos = float(d @ R[:, 0])
+            if cos > 1e-3:
+                assert abs(rl["v"][idx] - D / cos) <= 1e-9 * D / cos
+                assert rl["seg"][idx] == 3
+            elif cos < 0:
+                assert rl["seg"][idx] == -1 and rl["v"][idx] == 1e5
+
+
+def pin_lidar_cylinder_facets(lib):
+    """LiDAR on the axis of a closed 32-gon prism: range = r cos(pi/n) / cos(psi - facet normal) / cos(phi)."""
+    n, r, h = 32, 2.0, 40.0
+    th = 2 * np.pi * np.arange(n) / n
+    ring = np.stack([np.cos(th), np.sin(th)], 1) * r
+    tris, segs = [], []
+    for k in range(n):
+        k1 = (k + 1) % n
+        a0, a1 = ring[k], ring[k1]
+        v0, v1 = [a0[0], a0[1], -h / 2], [a1[0], a1[1], -h / 2]
+        v2, v3 = [a1[0], a1[1], h / 2], [a0[0], a0[1], h / 2]
+        tris += [v0 + v1 + v2, v0 + v2 + v3]
+        segs += [k, k]
+    tris = np.array(tris, float)
+    seg = np.array(segs, np.int32)
+    C, A = 9, 100
+    s = O.Sensor(O.LIDAR, A, C, 2 * math.pi, 0.1, 50.0, math.radians(-22.5), math.radians(22.5))
+    pose = np.array([0, 0, 0.0, 0, 0, 0, 1])
+    res = O.render(tris, seg, s, pose, lib=lib)
+    for idx in range(C * A):
+        k, j = divmod(idx, A)
+        phi = math.radians(22.5) - k * math.radians(45) / (C - 1)
+        psi = 2 * math.pi * j / A
+        f = int(psi // (2 * math.pi / n)) % n
+        normal = (th[f] + math.pi / n)
+        want = r * math.cos(math.pi / n) / math.cos(psi - normal) / math.cos(phi)
+        if res["flags"][idx] & O.F_SILHOUETTE:
+            continue  # beam along a facet edge: either facet is right
+        assert abs(res["v"][idx] - want) < 1e-10 * want, (idx, res["v"][idx], want)
+        assert res["seg"][idx] == f
+
+
+def pin_icosphere_bounds(lib):
+    """Rays at an icosphere: the hit lies between the analytic spheres of radius r and r_in."""
+    from paper_2503_01471_gb300.scenes import icosphere_unit
+    v, f = icosphere_unit(2)
+    r, L = 0.8, 4.0
+    c = np.array([L, 0.3, -0.2])
+    verts = v * r + c
+    tris = verts[f].reshape(-1, 9)
+    # inscribed radius: smallest distance from the centre to a face plane
+    a, b, cc = verts[f[:, 0]], verts[f[:, 1]], verts[f[:, 2]]
+    nrm = np.cross(b - a, cc - a)
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    r_in = float(np.min(np.abs(np.sum((a - c) * nrm, 1))))
+    assert r_in < r
+    seg = np.full(len(tris), 6, np.int32)
+    s = O.Sensor(O.LIDAR, 64, 16, 0.6, 0.1, 50.0, -0.25, 0.25)
+    q = _quat_from_matrix_scipy(np.eye(3))
+    pose = np.concatenate([[0, 0, 0.0], q])
+    # aim the azimuth fan at the sphere: rotate by -0.3 rad about z
+    from scipy.spatial.transform import Rotation
+    pose[3:] = Rotation.from_euler("z", math.atan2(c[1], c[0]) - 0.3).as_quat()
+    res = O.render(tris, seg, s, pose, lib=lib)
+    n_hit = 0
+    for idx in range(64 * 16):
+        k, j = divmod(idx, 64)
+        o, d, _ = O.ray(s, pose, k, j, lib)
+        m = float(d @ (c - o))
+        b2 = float((c - o) @ (c - o)) - m * m
+        if b2 < r_in * r_in * 0.999:
+            lo, hi = m - math.sqrt(r * r - b2), m - math.sqrt(r_in * r_in - b2)
+            assert res["seg"][idx] == 6
+            assert lo - 1e-12 <= res["v"][idx] <= hi + 1e-12, (idx, lo, res["v"][idx], hi)
+            n_hit += 1
+        elif b2 > r * r * 1.001:
+            assert res["seg"][idx] == -1 and res["v"][idx] == 50.0
+    assert n_hit > 50
+    # the centre ray: t in [L' - r, L' - r_in]
+    s1 = O.Sensor(O.PINHOLE, 1, 1, 0.5, 0.1, 50.0)
+    d0 = c / np.linalg.norm(c)
+    from scipy.spatial.transform import Rotation as Rot
+    rot, _ = Rot.align_vectors([d0], [[1, 0, 0]])
+    res = O.render(tris, seg, s1, np.concatenate([[0, 0, 0], rot.as_quat()]), lib=lib)
+    Lc = float(np.linalg.norm(c))
+    assert Lc - r - 1e-12 <= res["v"][0] <= Lc - r_in + 1e-12
+
+
+def pin_hand_worked(lib):
+    with open(GOLDEN) as fh:
+        cases = json.load(fh)["cases"]
+    for case in cases:
+        s = _sensor_from(case["sensor"])
+        tris = np.array(case["triangles"], float)
+        seg = np.array(case["segs"], np.int32)
+        res = O.render(tris, seg, s, IDENT, lib=lib)
+        depth = np.array(case["depth"], float).reshape(-1)
+        want_seg = np.array(case["seg"]).reshape(-1)
+        counted = np.zeros(depth.shape, bool)
+        if "counted" in case:
+            counted = np.array(case["counted"]).reshape(-1).astype(bool)
+            assert np.array_equal((res["flags"] & O.F_COUNTED) != 0, counted), case["name"]
+        for i in range(depth.shape[0]):
+            if not counted[i]:
+                assert abs(res["v"][i] - depth[i]) <= 1e-12, (case["name"], i, res["v"][i], depth[i])
+                assert res["seg"][i] == want_seg[i], (case["name"], i, res["seg"][i], want_seg[i])
+                continue
+            # several outcomes are right (an exact edge or range tie): the
+            # hand-worked one must be among the accepted outcomes
+            ok, _ = O.check(res[i:i + 1], [depth[i]], [want_seg[i]], s.max_range)
+            assert ok[0], (case["name"], i, res[i])
+
+
+def _brute_solve(tris, seg, o, d, t_far):
+    """Nearest hit by solving o + t d = v0 + u e1 + w e2 with numpy.linalg.solve."""
+    best_t, best_i = math.inf, -1
+    for i, tri in enumerate(tris):
+        v0, v1, v2 = tri[:3], tri[3:6], tri[6:]
+        M = np.stack([d, v0 - v1, v0 - v2], 1)
+        if abs(np.linalg.det(M)) < 1e-12:
+            continue
+        t, u, w = np.linalg.solve(M, v0 - o)
+        if u >= 0 and w >= 0 and u + w <= 1 and 0 <= t <= t_far and t < best_t:
+            best_t, best_i = t, i
+    return best_t, best_i
+
+
+def pin_brute_force_linear_solve(lib):
+    rng = np.random.default_rng(16)
+    checked = 0
+    for trial in range(12):
+        F = int(rng.integers(1, 9))
+        tris = rng.uniform(-4, 4, (F, 9))
+        seg = rng.integers(0, 5, F).astype(np.int32)
+        s = O.Sensor(O.PINHOLE, 12, 9, math.radians(100), 0.05, 20.0)
+        q = rng.normal(size=4)
+        pose = np.concatenate([rng.uniform(-1, 1, 3), q])
+        res = O.render(tris, seg, s, pose, lib=lib)
+        for idx in range(12 * 9):
+            if res["flags"][idx] & (O.F_SILHOUETTE | O.F_NEAR_TIE | O.F_RANGE_EDGE):
+                continue
+            k, j = divmod(idx, 12)
+            o, d, sc = O.ray(s, pose, k, j, lib)
+            t, i = _brute_solve(tris, seg, o, d, 20.0 / sc)
+            if i < 0:
+                assert res["seg"][idx] == -1 and res["v"][idx] == 20.0
+            else:
+                v = max(t * sc, 0.05)
+                assert abs(res["v"][idx] - v) < 1e-9, (trial, idx, res["v"][idx], v)
+                assert res["seg"][idx] == seg[i] and res["tri"][idx] == i
+            checked += 1
+    assert checked > 800
+
+
+# ---------------------------------------------------------------- invariants
+def _room_scene():
+    from paper_2503_01471_gb300 import scenes as S
+    sc, spec, poses = S.tiny_room()
+    vs, ix, ps, sg = sc.env_submeshes(0)
+    return vs, ix, ps, sg, spec, poses
+
+
+def pin_miss_exact(lib):
+    """Rays leaving an open scene report exactly max_range and segment -1."""
+    tris = np.array([[3, -1, -1, 3, 1, -1, 3, 0, 1.0]])
+    seg = np.array([2], np.int32)
+    s = O.Sensor(O.LIDAR, 36, 9, 2 * math.pi, 0.3, 37.5, -0.3, 0.3)
+    res = O.render(tris, seg, s, IDENT, lib=lib)
+    miss = res["seg"] == -1
+    assert miss.sum() > 300
+    assert np.all(res["v"][miss] == 37.5)
+    assert np.all(res["flags"][miss] & O.F_MISS_OK)
+    assert np.all(res["n_cand"][miss] == 0)
+
+
+def pin_translation_rotation_invariance(lib):
+    vs, ix, ps, sg, spec, poses = _room_scene()
+    s = O.Sensor(O.PINHOLE, spec.width, spec.height, spec.hfov, spec.min_range, spec.max_range)
+    tris, seg = O.world_triangles(vs, ix, ps, sg)
+    rng = np.random.default_rng(17)
+    for p in poses[:4].astype(np.float64):
+        base = O.render(tris, seg, s, p, lib=lib)
+        off = rng.uniform(-50, 50, 3)
+        t2 = tris + np.tile(off, 3)
+        p2 = p.copy()
+        p2[:3] += off
+        moved = O.render(t2, seg, s, p2, lib=lib)
+        amb = O.F_SILHOUETTE | O.F_NEAR_TIE
+        ok = ((base["flags"] | moved["flags"]) & amb) == 0
+        assert ok.mean() > 0.9
+        assert np.array_equal(base["seg"][ok], moved["seg"][ok])
+        assert np.all(np.abs(base["v"][ok] - moved["v"][ok]) <= O.tol(base["v"][ok]))
+        # common rotation about the sensor
+        from scipy.spatial.transform import Rotation
+        rot = Rotation.from_quat(rng.normal(size=4))
+        t3 = (rot.apply((tris.reshape(-1, 3) - p[:3])) + p[:3]).reshape(-1, 9)
+        p3 = p.copy()
+        p3[3:] = (rot * Rotation.from_quat(p[3:])).as_quat()
+        rotd = O.render(t3, seg, s, p3, lib=lib)
+        ok = ((base["flags"] | rotd["flags"]) & amb) == 0
+        assert np.array_equal(base["seg"][ok], rotd["seg"][ok])
+        assert np.all(np.abs(base["v"][ok] - rotd["v"][ok]) <= O.tol(base["v"][ok]))
+
+
+def pin_degenerate_never_hits(lib):
+    tris = np.array([[3, -1, -1, 3, 1, 1, 3, 0, 0.0], [3, 0, 0, 3, 0, 0, 3, 0, 0.0]])  # collinear, point
+    seg = np.array([1, 2], np.int32)
+    s = O.Sensor(O.PINHOLE, 1, 1, 1.0, 0.1, 10.0)
+    res = O.render(tris, seg, s, IDENT, lib=lib)
+    assert res["seg"][0] == -1 and res["v"][0] == 10.0
+    # the ray runs exactly through both: still no acceptable hit outcome
+    assert res["n_cand"][0] == 0 and (res["flags"][0] & O.F_COUNTED) == 0
+
+
+def pin_tie_break(lib):
+    """Coincident triangles: equal distance goes to the smaller index; both are acceptable."""
+    t = [4, -2, -2, 4, 2, -2, 4, 0, 2.0]
+    s = O.Sensor(O.PINHOLE, 1, 1, 1.0, 0.1, 10.0)
+    for segs, want in (([5, 8], 5), ([8, 5], 8)):
+        res = O.render(np.array([t, t]), np.array(segs, np.int32), s, IDENT, lib=lib)
+        assert res["seg"][0] == want and res["tri"][0] == 0 and res["v"][0] == 4.0
+        assert res["flags"][0] & O.F_NEAR_TIE and res["flags"][0] & O.F_COUNTED
+        assert sorted(res["cand_seg"][0][:res["n_cand"][0]]) == [5, 8]
+
+
+ALL_PINS = [
+    pin_rotation_vs_scipy, pin_transform_vs_scipy, pin_transform_identity_exact,
+    pin_camera_centre_and_corner, pin_camera_column_angles, pin_lidar_angles,
+    pin_wall_depth_constant, pin_lidar_cylinder_facets, pin_icosphere_bounds, pin_hand_worked,
+    pin_brute_force_linear_solve, pin_miss_exact, pin_translation_rotation_invariance,
+    pin_degenerate_never_hits, pin_tie_break,
+]

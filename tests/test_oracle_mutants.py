@@ -1,0 +1,68 @@
+"""Plant plausible mistakes in the oracle (on the CPU) and check that a pin catches each.
+
+Every mutant is a one-line textual change of oracle/oracle.c compiled into a
+temporary library; the pins of oracle_pins.py must reject all of them. This
+shows the pins constrain every step the oracle takes (transform, ray
+generation, intersection, nearest-hit resolution, reported value).
+"""
+import os
+import subprocess
+
+import pytest
+
+import oracle as O
+from oracle_pins import ALL_PINS
+
+SRC = os.path.join(os.path.dirname(O.__file__), "oracle.c")
+
+MUTANTS = {
+    "rotation_sign": ("R[1] = 2.0 * (x * y - z * w);", "R[1] = 2.0 * (x * y + z * w);"),
+    "rotation_transposed": ("b[r] = R[3 * r + 0] * a[0] + R[3 * r + 1] * a[1] + R[3 * r + 2] * a[2] + pose[r];",
+                            "b[r] = R[r] * a[0] + R[3 + r] * a[1] + R[6 + r] * a[2] + pose[r];"),
+    "no_translation": ("R[3 * r + 2] * a[2] + pose[r];", "R[3 * r + 2] * a[2];"),
+    "no_normalise": ("double x = q[0] / n, y = q[1] / n, z = q[2] / n, w = q[3] / n;",
+                     "double x = q[0], y = q[1], z = q[2], w = q[3]; (void)n;"),
+    "pixel_corner_not_centre": ("local[1] = -(((double)col + 0.5) - W / 2.0) / f;",
+                                "local[1] = -(((double)col) - W / 2.0) / f;"),
+    "row_flipped": ("local[2] = -(((double)row + 0.5) - H / 2.0) / f;",
+                    "local[2] = (((double)row + 0.5) - H / 2.0) / f;"),
+    "depth_reported_as_range": ("*scale = dot3(d, fwd);", "*scale = 1.0;"),
+    "lidar_rows_upside_down": ("s->vfov_max - (double)row * (s->vfov_max - s->vfov_min) / (C - 1.0)",
+                               "s->vfov_min + (double)row * (s->vfov_max - s->vfov_min) / (C - 1.0)"),
+    "lidar_azimuth_clockwise": ("local[1] = cos(phi) * sin(psi);", "local[1] = -cos(phi) * sin(psi);"),
+    "backface_culling": ("if (area2 != 0.0 && ((e0 >= 0 && e1 >= 0 && e2 >= 0) || (e0 <= 0 && e1 <= 0 && e2 <= 0))) {",
+                         "if (area2 != 0.0 && ((e0 >= 0 && e1 >= 0 && e2 >= 0))) {"),
+    "open_edges": ("if (area2 != 0.0 && ((e0 >= 0 && e1 >= 0 && e2 >= 0) || (e0 <= 0 && e1 <= 0 && e2 <= 0))) {",
+                   "if (area2 != 0.0 && ((e0 > 0 && e1 > 0 && e2 > 0) || (e0 < 0 && e1 < 0 && e2 < 0))) {"),
+    "t_wrong_vertex": ("    double t = (e0 * za + e1 * zb + e2 * zc) / area2;",
+                       "    double t = (e0 * za + e1 * zc + e2 * zb) / area2;"),
+    "farthest_not_nearest": ("if (ev.exact_hit && (ev.t_exact < best_t ||", "if (ev.exact_hit && (ev.t_exact > -best_t ||"),
+    "tie_to_larger_index": ("(ev.t_exact == best_t && i < best_i)", "(ev.t_exact == best_t && (i > best_i || best_i < 0))"),
+    "no_near_clamp": ("        res->v = s->min_range;\n", "        res->v = v;\n"),
+    "miss_value_zero": ("  } else {\n    res->v = s->max_range;", "  } else {\n    res->v = 0.0;"),
+    "max_applies_to_range": ("double t_far = s->max_range / scale;", "double t_far = s->max_range;"),
+    "hits_behind_sensor": ("    if (t >= 0.0 && t <= t_far) {", "    if (t <= t_far) {"),
+    "degenerate_hits": ("  if (nn == 0.0) return; /* zero-area triangle: never hit */", "  if (nn < 0.0) return;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation site of {name} not found"
+    mutated = src.replace(old, new, 1)
+    cpath = tmp_path / "oracle.c"
+    cpath.write_text(mutated)
+    hdr = os.path.join(os.path.dirname(SRC), "oracle.h")
+    (tmp_path / "oracle.h").write_text(open(hdr).read())
+    lib_path = str(tmp_path / "libmut.so")
+    subprocess.run(["gcc", "-O1", "-std=c11", "-fopenmp", "-ffp-contract=off", "-shared", "-fPIC",
+                    str(cpath), "-o", lib_path, "-lm"], check=True)
+    lib = O.load(lib_path)
+    for pin in ALL_PINS:
+        try:
+            pin(lib)
+        except (AssertionError, ValueError, FloatingPointError, IndexError):
+            return  # caught
+    pytest.fail(f"no pin catches mutant {name}")
