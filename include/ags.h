@@ -1,0 +1,196 @@
+/*
+ * ags.h -- C ABI of the GB300 batched ray-cast sensor renderer.
+ *
+ * The operation (Aerial Gym Simulator, Kulkarni, Rehberg, Alexis, IEEE RA-L
+ * 2025, Sec. III-D.1 "Exteroceptive Sensors"): every environment i holds a
+ * base triangle mesh made of n_i sub-meshes, one per object; each sub-mesh j
+ * is moved into the world by its own transform T_j (here a position and a
+ * unit quaternion); a bounding volume hierarchy is built over the moved mesh;
+ * then one ray per pixel (pinhole camera) or per beam (3-D LiDAR) is cast from
+ * each sensor and the nearest intersection reports depth (distance of the hit
+ * from the image plane, cameras) or range (distance from the sensor to the
+ * hit, LiDAR / time-of-flight), plus the segment ID of the object hit.
+ *
+ * Conventions (readings of points the paper leaves open):
+ *   - pose = (px, py, pz, qx, qy, qz, qw), float32; q need not be unit length
+ *     (it is normalised); world vertex v' = R(q) v + p.
+ *   - sensor body frame: +x forward (optical axis), +y left, +z up. Camera row
+ *     0 is the top row, column 0 the left column; rays pass through pixel
+ *     centres; focal length f = (W/2) / tan(hfov/2), square pixels.
+ *   - LiDAR: row k = channel at elevation vfov_max - k (vfov_max - vfov_min) /
+ *     (H - 1) (row 0 = vfov_max; a single channel sits at vfov_max); column j
+ *     = azimuth hfov * j / W counter-clockwise from +x.
+ *   - two-sided triangles with closed edges (watertight); nearest hit wins;
+ *     equal float32 distance goes to the smaller triangle index within the
+ *     environment (sub-meshes concatenated in order).
+ *   - min/max range apply to the reported value (depth for cameras, range for
+ *     LiDAR); a hit at exactly max_range counts. Misses report exactly
+ *     max_range and segment -1. Hits nearer than min_range report min_range
+ *     (AGS_NEAR_CLAMP, segment kept) or max_range and -1 (AGS_NEAR_INVALID).
+ *
+ * Memory: device pointers are CUDA device addresses on the context's device;
+ * host pointers are ordinary (pageable or pinned) host memory. Inputs stay
+ * owned by the caller. Scenes are owned by the library until
+ * ags_scene_destroy. Output buffers are owned by the caller.
+ *
+ * Errors: every call returns an ags_status and never aborts the process.
+ * ags_last_error() returns a thread-local message for the last failure.
+ * Kernels never trap: limits hit on the device (traversal stack or iteration
+ * cap) set a device status word, returned by ags_stream_status.
+ * Thread safety: one context per host thread, or external locking.
+ */
+#ifndef AGS_H
+#define AGS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  AGS_OK = 0,
+  AGS_ERR_INVALID_ARG = 1,    /* bad pointer, size, index, pose or spec */
+  AGS_ERR_OUT_OF_MEMORY = 2,  /* device or host allocation failed */
+  AGS_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+  AGS_ERR_TRAVERSAL_LIMIT = 4,/* a ray hit the stack or iteration limit; its output is NaN */
+  AGS_ERR_NOT_READY = 5,
+  AGS_ERR_BUSY = 6
+} ags_status;
+
+typedef struct ags_context ags_context;
+typedef struct ags_scene ags_scene;
+
+/* One object (sub-mesh M_j of Sec. III-D.1). Host pointers. */
+typedef struct {
+  const float* vertices;    /* [n_vertices][3] object frame, metres */
+  int32_t n_vertices;
+  const int32_t* indices;   /* [n_triangles][3], each in [0, n_vertices) */
+  int32_t n_triangles;
+  int32_t segment_id;       /* reported for rays that hit this object; >= 0 */
+} ags_submesh;
+
+/* One environment: its objects in order. */
+typedef struct {
+  const ags_submesh* submeshes;
+  int32_t n_submeshes;
+} ags_env_mesh;
+
+typedef enum { AGS_PINHOLE = 0, AGS_LIDAR = 1 } ags_sensor_type;
+typedef enum { AGS_NEAR_CLAMP = 0, AGS_NEAR_INVALID = 1 } ags_near_mode;
+
+typedef struct {
+  int32_t type;          /* ags_sensor_type */
+  int32_t width;         /* camera columns / LiDAR azimuth bins, 1..16384 */
+  int32_t height;        /* camera rows / LiDAR channels, 1..16384 */
+  float hfov_rad;        /* camera horizontal FOV in (0, pi); LiDAR azimuth span in (0, 2 pi] */
+  float vfov_min_rad;    /* LiDAR lowest channel elevation (rad), >= -pi/2 */
+  float vfov_max_rad;    /* LiDAR highest channel elevation (rad), <= pi/2 */
+  float min_range;       /* >= 0 */
+  float max_range;       /* > min_range, finite */
+  int32_t near_mode;     /* ags_near_mode */
+  uint32_t flags;        /* reserved, must be 0 */
+} ags_sensor_spec;
+
+/* Build flags: node format of the wide BVH. */
+#define AGS_BVH_FP32 0u
+
+/* Create a context on CUDA device `device`. */
+ags_status ags_context_create(int device, ags_context** out);
+void ags_context_destroy(ags_context* ctx);
+
+/*
+ * ags_scene_build -- Sec. III-D.1: transform every sub-mesh by its pose and
+ * build one BVH per environment ("a bounding volume hierarchy is calculated
+ * for M_{i,t}"). envs[n_envs] describe the meshes (host memory);
+ * obstacle_poses is host float32 [sum_i n_submeshes(i)][7] in environment
+ * order, then sub-mesh order. The call validates every input before any
+ * device work (indices in range, finite vertices and poses, non-zero
+ * quaternions, segment IDs >= 0), copies everything to the device, runs the
+ * build kernels on an internal stream and returns once the scene is
+ * resident. Limits: 1 <= n_envs <= 65536; total triangles < 2^31 - 1.
+ * Environments may be empty (every ray misses).
+ */
+ags_status ags_scene_build(ags_context* ctx, const ags_env_mesh* envs, int32_t n_envs,
+                           const float* obstacle_poses, uint32_t build_flags, ags_scene** out);
+void ags_scene_destroy(ags_scene* scene);
+
+/*
+ * ags_render -- Sec. III-D.1: cast one ray per pixel / beam of `spec` from
+ * each environment's sensor pose and report the nearest hit.
+ * sensor_poses_dev: device float32 [n_envs][7]. out_depth_dev: device float32
+ * [n_envs][height][width] (depth for cameras, range for LiDAR), row-major.
+ * out_seg_dev: device int32, same shape. cuda_stream: a cudaStream_t (NULL =
+ * legacy default stream). Asynchronous: returns after enqueueing; the outputs
+ * are ready when the stream reaches that point. Host-side argument errors are
+ * returned immediately with nothing enqueued.
+ */
+ags_status ags_render(ags_context* ctx, const ags_scene* scene, const ags_sensor_spec* spec,
+                      const float* sensor_poses_dev, float* out_depth_dev, int32_t* out_seg_dev,
+                      void* cuda_stream);
+
+/*
+ * ags_render_envs -- as ags_render for the n environments listed in
+ * env_ids_dev (device int32 [n], each in [0, n_envs)); sensor_poses_dev is
+ * [n][7] and the outputs are [n][height][width], in list order.
+ */
+ags_status ags_render_envs(ags_context* ctx, const ags_scene* scene, const ags_sensor_spec* spec,
+                           const int32_t* env_ids_dev, int32_t n, const float* sensor_poses_dev,
+                           float* out_depth_dev, int32_t* out_seg_dev, void* cuda_stream);
+
+/*
+ * ags_render_host -- ags_render with HOST buffers: copies sensor_poses_host
+ * [n_envs][7] to the device, renders into context-owned device buffers and
+ * copies depth/range and segment IDs back into out_depth_host and
+ * out_seg_host ([n_envs][height][width]). Synchronous; returns the device
+ * status of this render as ags_stream_status would.
+ */
+ags_status ags_render_host(ags_context* ctx, const ags_scene* scene, const ags_sensor_spec* spec,
+                           const float* sensor_poses_host, float* out_depth_host,
+                           int32_t* out_seg_host);
+
+/*
+ * ags_render_count -- the traversal of ags_render instrumented to count, over
+ * all rays, the wide BVH nodes visited and triangles tested (no outputs are
+ * written). counts_host receives {rays, nodes visited, triangles tested}.
+ * Synchronous. Used to state the algorithmic bytes per ray.
+ */
+ags_status ags_render_count(ags_context* ctx, const ags_scene* scene, const ags_sensor_spec* spec,
+                            const float* sensor_poses_dev, uint64_t counts_host[3]);
+
+/* Synchronise `cuda_stream`, then read and clear the context's device status
+ * word: AGS_OK, or AGS_ERR_TRAVERSAL_LIMIT if any ray since the last call hit
+ * a limit, or AGS_ERR_CUDA. */
+ags_status ags_stream_status(ags_context* ctx, void* cuda_stream);
+
+/* Thread-local text of the last error ("" if none). */
+const char* ags_last_error(void);
+
+/* Number of environments of a scene, or -1 for NULL. */
+int32_t ags_scene_n_envs(const ags_scene* scene);
+
+/*
+ * ags_scene_get_world_triangles -- debug/test: the float32 world-space
+ * triangles of environment `env` as the renderer sees them, in input order
+ * (sub-mesh after sub-mesh): out_host [n][9] (x0 y0 z0 x1 y1 z1 x2 y2 z2) and
+ * out_seg [n]; `capacity` is the number of rows the buffers hold, n the
+ * environment's triangle count (ags_scene_stats).
+ */
+ags_status ags_scene_get_world_triangles(const ags_scene* scene, int32_t env, float* out_host,
+                                         int32_t* out_seg, int64_t capacity);
+
+/*
+ * ags_scene_stats -- triangles, wide BVH nodes and resident bytes (nodes +
+ * packed triangles) of environment `env`, or of the whole scene if env == -1.
+ * Any output pointer may be NULL.
+ */
+ags_status ags_scene_stats(const ags_scene* scene, int32_t env, int64_t* n_tris, int64_t* n_nodes,
+                           int64_t* bytes);
+
+/* Size in bytes of one wide BVH node of the scene's format. */
+int32_t ags_scene_node_bytes(const ags_scene* scene);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AGS_H */

@@ -1,1 +1,267 @@
-"""GB300-native batched ray-cast depth / LiDAR renderer (placeholder; the binding lands with the CUDA library)."""
+"""GB300-native batched ray-cast sensor renderer (Aerial Gym Simulator, Sec. III-D.1).
+
+Thin ctypes binding of the C ABI in ``include/ags.h``: the functions below
+carry the same names and only marshal arguments (numpy arrays on the host,
+torch CUDA tensors or raw device pointers on the device). Every step of the
+method runs in the CUDA library ``_build/libags.so``; there is no CPU or
+PyTorch fallback: if the library is missing or fails to load, the import of
+``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import scenes  # noqa: F401  (input generators)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libags.so")
+
+AGS_OK = 0
+AGS_ERR_INVALID_ARG = 1
+AGS_ERR_OUT_OF_MEMORY = 2
+AGS_ERR_CUDA = 3
+AGS_ERR_TRAVERSAL_LIMIT = 4
+AGS_ERR_NOT_READY = 5
+AGS_ERR_BUSY = 6
+STATUS_NAMES = {0: "AGS_OK", 1: "AGS_ERR_INVALID_ARG", 2: "AGS_ERR_OUT_OF_MEMORY", 3: "AGS_ERR_CUDA",
+                4: "AGS_ERR_TRAVERSAL_LIMIT", 5: "AGS_ERR_NOT_READY", 6: "AGS_ERR_BUSY"}
+
+AGS_PINHOLE = 0
+AGS_LIDAR = 1
+AGS_NEAR_CLAMP = 0
+AGS_NEAR_INVALID = 1
+AGS_BVH_FP32 = 0
+
+# every symbol declared in include/ags.h
+EXPORTS = [
+    "ags_context_create", "ags_context_destroy", "ags_scene_build", "ags_scene_destroy", "ags_render",
+    "ags_render_envs", "ags_render_host", "ags_render_count", "ags_stream_status", "ags_last_error",
+    "ags_scene_n_envs", "ags_scene_get_world_triangles", "ags_scene_stats", "ags_scene_node_bytes",
+]
+
+
+class AgsError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class ags_submesh(ctypes.Structure):
+    _fields_ = [("vertices", ctypes.c_void_p), ("n_vertices", ctypes.c_int32), ("indices", ctypes.c_void_p),
+                ("n_triangles", ctypes.c_int32), ("segment_id", ctypes.c_int32)]
+
+
+class ags_env_mesh(ctypes.Structure):
+    _fields_ = [("submeshes", ctypes.c_void_p), ("n_submeshes", ctypes.c_int32)]
+
+
+class ags_sensor_spec(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("hfov_rad", ctypes.c_float), ("vfov_min_rad", ctypes.c_float), ("vfov_max_rad", ctypes.c_float),
+                ("min_range", ctypes.c_float), ("max_range", ctypes.c_float), ("near_mode", ctypes.c_int32),
+                ("flags", ctypes.c_uint32)]
+
+
+_SUB_DTYPE = np.dtype({"names": ["vertices", "n_vertices", "indices", "n_triangles", "segment_id"],
+                       "formats": ["<u8", "<i4", "<u8", "<i4", "<i4"],
+                       "offsets": [ags_submesh.vertices.offset, ags_submesh.n_vertices.offset,
+                                   ags_submesh.indices.offset, ags_submesh.n_triangles.offset,
+                                   ags_submesh.segment_id.offset],
+                       "itemsize": ctypes.sizeof(ags_submesh)})
+_ENV_DTYPE = np.dtype({"names": ["submeshes", "n_submeshes"], "formats": ["<u8", "<i4"],
+                       "offsets": [ags_env_mesh.submeshes.offset, ags_env_mesh.n_submeshes.offset],
+                       "itemsize": ctypes.sizeof(ags_env_mesh)})
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA renderer library not built: {LIB_PATH} (run paper_2503_01471_gb300/build.py)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, u32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64
+    sig = {
+        "ags_context_create": (i32, [ctypes.c_int, ctypes.POINTER(vp)]),
+        "ags_context_destroy": (None, [vp]),
+        "ags_scene_build": (i32, [vp, vp, i32, vp, u32, ctypes.POINTER(vp)]),
+        "ags_scene_destroy": (None, [vp]),
+        "ags_render": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), vp, vp, vp, vp]),
+        "ags_render_envs": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), vp, i32, vp, vp, vp, vp]),
+        "ags_render_host": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), vp, vp, vp]),
+        "ags_render_count": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), vp, ctypes.POINTER(ctypes.c_uint64)]),
+        "ags_stream_status": (i32, [vp, vp]),
+        "ags_last_error": (ctypes.c_char_p, []),
+        "ags_scene_n_envs": (i32, [vp]),
+        "ags_scene_get_world_triangles": (i32, [vp, i32, vp, vp, i64]),
+        "ags_scene_stats": (i32, [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+        "ags_scene_node_bytes": (i32, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int, where: str):
+    if status != AGS_OK:
+        msg = lib().ags_last_error()
+        raise AgsError(status, where, msg.decode() if msg else "")
+
+
+def _ptr(x) -> int:
+    """Device or host address of a torch tensor, a numpy array or an int."""
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:  # pragma: no cover
+            return 0
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def make_spec(spec) -> ags_sensor_spec:
+    """ags_sensor_spec from a ``scenes.SensorSpec`` (or anything with those fields)."""
+    return ags_sensor_spec(int(spec.type), int(spec.width), int(spec.height), float(spec.hfov),
+                           float(getattr(spec, "vfov_min", 0.0)), float(getattr(spec, "vfov_max", 0.0)),
+                           float(spec.min_range), float(spec.max_range), int(getattr(spec, "near_mode", 0)),
+                           int(getattr(spec, "flags", 0)))
+
+
+# ---------------------------------------------------------------- context
+def ags_context_create(device: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().ags_context_create(int(device), ctypes.byref(h)), "ags_context_create")
+    return h.value
+
+
+def ags_context_destroy(ctx: int) -> None:
+    lib().ags_context_destroy(ctx)
+
+
+# ---------------------------------------------------------------- scene
+def ags_scene_build(ctx: int, batch, build_flags: int = AGS_BVH_FP32) -> int:
+    """Build per-environment BVHs from a ``scenes.SceneBatch`` (host arrays)."""
+    verts = np.ascontiguousarray(batch.vertices, np.float32)
+    idx = np.ascontiguousarray(batch.indices, np.int32)
+    poses = np.ascontiguousarray(batch.poses, np.float32)
+    J = int(batch.sub_seg.shape[0])
+    subs = np.zeros(max(J, 1), _SUB_DTYPE)
+    vbase, ibase = verts.ctypes.data, idx.ctypes.data
+    sv, st = np.asarray(batch.sub_vert, np.int64), np.asarray(batch.sub_tri, np.int64)
+    subs["vertices"][:J] = vbase + sv[:J] * 12
+    subs["n_vertices"][:J] = sv[1:] - sv[:-1]
+    subs["indices"][:J] = ibase + st[:J] * 12
+    subs["n_triangles"][:J] = st[1:] - st[:-1]
+    subs["segment_id"][:J] = batch.sub_seg
+    E = batch.n_envs
+    env_sub = np.asarray(batch.env_sub, np.int64)
+    envs = np.zeros(E, _ENV_DTYPE)
+    envs["submeshes"] = subs.ctypes.data + env_sub[:E] * _SUB_DTYPE.itemsize
+    envs["n_submeshes"] = env_sub[1:] - env_sub[:-1]
+    h = ctypes.c_void_p()
+    _check(lib().ags_scene_build(ctx, envs.ctypes.data, E, poses.ctypes.data if J else None, int(build_flags),
+                                 ctypes.byref(h)), "ags_scene_build")
+    return h.value
+
+
+def ags_scene_destroy(scene: int) -> None:
+    lib().ags_scene_destroy(scene)
+
+
+def ags_scene_n_envs(scene: int) -> int:
+    return int(lib().ags_scene_n_envs(scene))
+
+
+def ags_scene_node_bytes(scene: int) -> int:
+    return int(lib().ags_scene_node_bytes(scene))
+
+
+def ags_scene_stats(scene: int, env: int = -1):
+    t, n, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().ags_scene_stats(scene, int(env), ctypes.byref(t), ctypes.byref(n), ctypes.byref(b)),
+           "ags_scene_stats")
+    return t.value, n.value, b.value
+
+
+def ags_scene_get_world_triangles(scene: int, env: int):
+    n, _, _ = ags_scene_stats(scene, env)
+    out = np.zeros((n, 9), np.float32)
+    seg = np.zeros(n, np.int32)
+    _check(lib().ags_scene_get_world_triangles(scene, int(env), out.ctypes.data, seg.ctypes.data, n),
+           "ags_scene_get_world_triangles")
+    return out, seg
+
+
+# ---------------------------------------------------------------- render
+def ags_render(ctx: int, scene: int, spec, sensor_poses, out_depth, out_seg, stream=None) -> None:
+    """Enqueue a render of every environment; tensors are CUDA tensors (or device pointers)."""
+    s = make_spec(spec)
+    _check(lib().ags_render(ctx, scene, ctypes.byref(s), _ptr(sensor_poses), _ptr(out_depth), _ptr(out_seg),
+                            _stream(stream)), "ags_render")
+
+
+def ags_render_envs(ctx: int, scene: int, spec, env_ids, sensor_poses, out_depth, out_seg, stream=None) -> None:
+    s = make_spec(spec)
+    n = int(env_ids.numel() if hasattr(env_ids, "numel") else len(env_ids))
+    _check(lib().ags_render_envs(ctx, scene, ctypes.byref(s), _ptr(env_ids), n, _ptr(sensor_poses), _ptr(out_depth),
+                                 _ptr(out_seg), _stream(stream)), "ags_render_envs")
+
+
+def ags_render_host(ctx: int, scene: int, spec, sensor_poses_host, out_depth_host=None, out_seg_host=None):
+    """Render with host buffers (numpy or pinned torch CPU tensors); returns (depth, seg)."""
+    s = make_spec(spec)
+    E = ags_scene_n_envs(scene)
+    if out_depth_host is None:
+        out_depth_host = np.zeros((E, spec.height, spec.width), np.float32)
+    if out_seg_host is None:
+        out_seg_host = np.zeros((E, spec.height, spec.width), np.int32)
+    _check(lib().ags_render_host(ctx, scene, ctypes.byref(s), _ptr(sensor_poses_host), _ptr(out_depth_host),
+                                 _ptr(out_seg_host)), "ags_render_host")
+    return out_depth_host, out_seg_host
+
+
+def ags_render_count(ctx: int, scene: int, spec, sensor_poses):
+    """(rays, wide nodes visited, triangles tested) of one render."""
+    s = make_spec(spec)
+    c = (ctypes.c_uint64 * 3)()
+    _check(lib().ags_render_count(ctx, scene, ctypes.byref(s), _ptr(sensor_poses), c), "ags_render_count")
+    return int(c[0]), int(c[1]), int(c[2])
+
+
+def ags_stream_status(ctx: int, stream=None) -> int:
+    """Synchronise the stream and return the device status (raises on errors)."""
+    st = lib().ags_stream_status(ctx, _stream(stream))
+    _check(st, "ags_stream_status")
+    return st
+
+
+def ags_last_error() -> str:
+    m = lib().ags_last_error()
+    return m.decode() if m else ""

@@ -1,0 +1,700 @@
+// Scene build: object-to-world transform (Sec. III-D.1, M_{i,t} from the
+// per-object transforms T_{j,t}) and one BVH per environment ("a bounding
+// volume hierarchy is calculated for M_{i,t}"), as an LBVH (Morton codes,
+// radix sort, Karras-style radix tree, bottom-up bounds refit) collapsed into
+// 8-wide nodes. All environments are built together, in one pass per stage.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "internal.cuh"
+
+namespace ags {
+
+namespace {
+
+#define AGS_CHECK(call)                                     \
+  do {                                                      \
+    cudaError_t _e = (call);                                \
+    if (_e != cudaSuccess) return cuda_fail(_e, #call);     \
+  } while (0)
+
+// ---------------------------------------------------------------- float-float
+// Transform arithmetic in unevaluated float pairs (hi + lo) built from
+// error-free products (fma) and sums, so the float32 world vertex is within
+// one unit in the last place of the exact value without any double math.
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff ff_fast_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float e = __fsub_rn(b, __fsub_rn(s, a));
+  return {s, e};
+}
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  ff s = ff_two_sum(a.hi, b.hi);
+  float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return ff_fast_sum(s.hi, e);
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return ff_fast_sum(p, e);
+}
+__device__ __forceinline__ ff ff_of(float a) { return {a, 0.0f}; }
+__device__ __forceinline__ ff ff_div(ff a, ff b) {
+  float q1 = __fdiv_rn(a.hi, b.hi);
+  ff r = ff_add(a, ff_neg(ff_mul(ff_of(q1), b)));
+  float q2 = __fdiv_rn(r.hi, b.hi);
+  return ff_fast_sum(q1, q2);
+}
+
+// Rotation of the (not necessarily unit) quaternion q: R = I + s K with
+// s = 2 / |q|^2, so no square root is needed.
+__global__ void k_submesh_rotations(const float* __restrict__ poses, int32_t J, float* __restrict__ rot_ff) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= J) return;
+  const float* P = poses + 7 * (int64_t)j;
+  ff x = ff_of(P[3]), y = ff_of(P[4]), z = ff_of(P[5]), w = ff_of(P[6]);
+  ff xx = ff_mul(x, x), yy = ff_mul(y, y), zz = ff_mul(z, z), ww = ff_mul(w, w);
+  ff n2 = ff_add(ff_add(xx, yy), ff_add(zz, ww));
+  ff s = ff_div(ff_of(2.0f), n2);
+  ff xy = ff_mul(x, y), xz = ff_mul(x, z), yz = ff_mul(y, z);
+  ff xw = ff_mul(x, w), yw = ff_mul(y, w), zw = ff_mul(z, w);
+  ff one = ff_of(1.0f);
+  ff R[9];
+  R[0] = ff_add(one, ff_neg(ff_mul(s, ff_add(yy, zz))));
+  R[1] = ff_mul(s, ff_add(xy, ff_neg(zw)));
+  R[2] = ff_mul(s, ff_add(xz, yw));
+  R[3] = ff_mul(s, ff_add(xy, zw));
+  R[4] = ff_add(one, ff_neg(ff_mul(s, ff_add(xx, zz))));
+  R[5] = ff_mul(s, ff_add(yz, ff_neg(xw)));
+  R[6] = ff_mul(s, ff_add(xz, ff_neg(yw)));
+  R[7] = ff_mul(s, ff_add(yz, xw));
+  R[8] = ff_add(one, ff_neg(ff_mul(s, ff_add(xx, yy))));
+  float* o = rot_ff + 18 * (int64_t)j;
+  for (int k = 0; k < 9; ++k) {
+    o[2 * k] = R[k].hi;
+    o[2 * k + 1] = R[k].lo;
+  }
+}
+
+__device__ __forceinline__ int32_t upper_bound_i32(const int32_t* a, int32_t n, int32_t x) {
+  // first index k in [0, n) with a[k] > x  (a sorted ascending)
+  int32_t lo = 0, hi = n;
+  while (lo < hi) {
+    int32_t mid = (lo + hi) >> 1;
+    if (__ldg(a + mid) <= x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// a1: v' = R(q_j) v + p_j for every vertex of sub-mesh j.
+__global__ void k_transform_vertices(const float* __restrict__ base, int32_t V, const int32_t* __restrict__ sub_vert_off,
+                                     int32_t J, const float* __restrict__ rot_ff, const float* __restrict__ poses,
+                                     float4* __restrict__ world) {
+  int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= V) return;
+  int32_t j = upper_bound_i32(sub_vert_off + 1, J, v);  // sub_vert_off[j] <= v < sub_vert_off[j+1]
+  const float* r = rot_ff + 18 * (int64_t)j;
+  const float* P = poses + 7 * (int64_t)j;
+  ff b[3] = {ff_of(base[3 * (int64_t)v]), ff_of(base[3 * (int64_t)v + 1]), ff_of(base[3 * (int64_t)v + 2])};
+  float out[3];
+#pragma unroll
+  for (int row = 0; row < 3; ++row) {
+    ff acc = ff_of(P[row]);
+    acc = ff_add(acc, ff_mul({r[6 * row + 0], r[6 * row + 1]}, b[0]));
+    acc = ff_add(acc, ff_mul({r[6 * row + 2], r[6 * row + 3]}, b[1]));
+    acc = ff_add(acc, ff_mul({r[6 * row + 4], r[6 * row + 5]}, b[2]));
+    out[row] = __fadd_rn(acc.hi, acc.lo);
+  }
+  world[v] = make_float4(out[0], out[1], out[2], 0.0f);
+}
+
+// Packed triangles in input order; also the environment of each triangle.
+__global__ void k_pack_triangles(const int32_t* __restrict__ vidx, int32_t F, const float4* __restrict__ world,
+                                 const int32_t* __restrict__ sub_tri_off, int32_t J,
+                                 const int32_t* __restrict__ sub_seg, const int32_t* __restrict__ sub_env,
+                                 const int32_t* __restrict__ env_tri_off, float4* __restrict__ packed,
+                                 int32_t* __restrict__ tri_env) {
+  int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= F) return;
+  int32_t j = upper_bound_i32(sub_tri_off + 1, J, t);
+  int32_t e = sub_env[j];
+  float4 a = world[vidx[3 * (int64_t)t]];
+  float4 b = world[vidx[3 * (int64_t)t + 1]];
+  float4 c = world[vidx[3 * (int64_t)t + 2]];
+  a.w = __int_as_float(sub_seg[j]);
+  b.w = __int_as_float(t - env_tri_off[e]);
+  c.w = 0.0f;
+  packed[3 * (int64_t)t] = a;
+  packed[3 * (int64_t)t + 1] = b;
+  packed[3 * (int64_t)t + 2] = c;
+  tri_env[t] = e;
+}
+
+// order-preserving float <-> int mapping for atomic min/max
+__device__ __forceinline__ int32_t f2ord(float f) {
+  int32_t i = __float_as_int(f);
+  return i >= 0 ? i : (i ^ 0x7FFFFFFF);
+}
+__device__ __forceinline__ float ord2f(int32_t i) { return __int_as_float(i >= 0 ? i : (i ^ 0x7FFFFFFF)); }
+
+__global__ void k_init_bounds(int32_t* b, int32_t E) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  for (int k = 0; k < 3; ++k) {
+    b[6 * e + k] = 0x7FFFFFFF;
+    b[6 * e + 3 + k] = (int32_t)0x80000000;
+  }
+}
+
+__device__ __forceinline__ float3 centroid(const float4* packed, int64_t t) {
+  float4 a = packed[3 * t], b = packed[3 * t + 1], c = packed[3 * t + 2];
+  return make_float3((a.x + b.x + c.x) * (1.0f / 3.0f), (a.y + b.y + c.y) * (1.0f / 3.0f),
+                     (a.z + b.z + c.z) * (1.0f / 3.0f));
+}
+
+// per-environment bounds of triangle centroids (warp-aggregated atomics when
+// the whole warp belongs to one environment, per-lane atomics otherwise)
+__global__ void k_env_bounds(const float4* __restrict__ packed, const int32_t* __restrict__ tri_env, int32_t F,
+                             int32_t* __restrict__ bounds) {
+  int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  bool valid = t < F;
+  int32_t e = valid ? tri_env[t] : -1;
+  float3 c = valid ? centroid(packed, t) : make_float3(0, 0, 0);
+  int32_t v[6] = {f2ord(c.x), f2ord(c.y), f2ord(c.z), f2ord(c.x), f2ord(c.y), f2ord(c.z)};
+  unsigned peers = __match_any_sync(0xffffffffu, e);
+  if (peers == 0xffffffffu) {  // uniform branch: every lane sees the same mask
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      int32_t x = v[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        int32_t y = __shfl_xor_sync(0xffffffffu, x, o);
+        x = (k < 3) ? min(x, y) : max(x, y);
+      }
+      v[k] = x;
+    }
+    if (!valid || (threadIdx.x & 31) != 0) return;
+  } else if (!valid) {
+    return;
+  }
+  int32_t* b = bounds + 6 * (int64_t)e;
+  for (int k = 0; k < 3; ++k) atomicMin(b + k, v[k]);
+  for (int k = 3; k < 6; ++k) atomicMax(b + k, v[k]);
+}
+
+__device__ __forceinline__ uint64_t spread3(uint64_t x) {
+  // bits of x (up to 21) moved to every third position
+  x &= 0x1fffffull;
+  x = (x | (x << 32)) & 0x1f00000000ffffull;
+  x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+  x = (x | (x << 8)) & 0x100f00f00f00f00full;
+  x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+
+__global__ void k_morton(const float4* __restrict__ packed, const int32_t* __restrict__ tri_env, int32_t F,
+                         const int32_t* __restrict__ bounds, int bits, uint64_t* __restrict__ keys,
+                         uint32_t* __restrict__ vals) {
+  int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= F) return;
+  int32_t e = tri_env[t];
+  const int32_t* b = bounds + 6 * (int64_t)e;
+  float3 c = centroid(packed, t);
+  float cc[3] = {c.x, c.y, c.z};
+  uint64_t q[3];
+  const float scale = (float)(1u << bits);
+  for (int k = 0; k < 3; ++k) {
+    float lo = ord2f(b[k]), hi = ord2f(b[3 + k]);
+    float ext = hi - lo;
+    float u = ext > 0.0f ? (cc[k] - lo) / ext : 0.0f;
+    float s = fminf(fmaxf(u * scale, 0.0f), scale - 1.0f);
+    q[k] = (uint64_t)s;
+  }
+  uint64_t m = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
+  keys[t] = ((uint64_t)e << (3 * bits)) | m;
+  vals[t] = (uint32_t)t;
+}
+
+// ---------------------------------------------------------------- Karras tree
+// Inner node li of environment e has global index env_tri_off[e] + li; its
+// children are inner nodes (>= 0) or leaves (~sorted position, < 0).
+__device__ __forceinline__ int delta(const uint64_t* keys, int64_t base, int32_t n, int32_t a, int32_t b) {
+  if (b < 0 || b >= n) return -1;
+  uint64_t ka = keys[base + a], kb = keys[base + b];
+  if (ka == kb) return 64 + __clz((uint32_t)a ^ (uint32_t)b);
+  return __clzll(ka ^ kb);
+}
+
+__global__ void k_karras(const uint64_t* __restrict__ keys, int32_t F, int key_shift,
+                         const int32_t* __restrict__ env_tri_off, int32_t* __restrict__ left,
+                         int32_t* __restrict__ right, int32_t* __restrict__ parent_inner,
+                         int32_t* __restrict__ parent_leaf, int32_t* __restrict__ first,
+                         int32_t* __restrict__ last) {
+  int32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= F) return;
+  int32_t e = (int32_t)(keys[g] >> key_shift);
+  int64_t base = env_tri_off[e];
+  int32_t n = env_tri_off[e + 1] - (int32_t)base;
+  int32_t i = g - (int32_t)base;
+  if (i == 0) {
+    if (n == 1) parent_leaf[g] = -1;
+    else parent_inner[g] = -1;  // root of this environment
+  }
+  if (i >= n - 1) return;
+  int d = (delta(keys, base, n, i, i + 1) - delta(keys, base, n, i, i - 1)) >= 0 ? 1 : -1;
+  int dmin = delta(keys, base, n, i, i - d);
+  int32_t lmax = 2;
+  while (delta(keys, base, n, i, i + lmax * d) > dmin) lmax <<= 1;
+  int32_t l = 0;
+  for (int32_t t = lmax >> 1; t >= 1; t >>= 1)
+    if (delta(keys, base, n, i, i + (l + t) * d) > dmin) l += t;
+  int32_t j = i + l * d;
+  int dnode = delta(keys, base, n, i, j);
+  int32_t s = 0;
+  int32_t t = l;
+  do {
+    t = (t + 1) >> 1;
+    if (delta(keys, base, n, i, i + (s + t) * d) > dnode) s += t;
+  } while (t > 1);
+  int32_t gamma = i + s * d + min(d, 0);
+  int32_t lo = min(i, j), hi = max(i, j);
+  int32_t lc, rc;
+  if (lo == gamma) {
+    lc = ~(int32_t)(base + gamma);
+    parent_leaf[base + gamma] = g;
+  } else {
+    lc = (int32_t)(base + gamma);
+    parent_inner[base + gamma] = g;
+  }
+  if (hi == gamma + 1) {
+    rc = ~(int32_t)(base + gamma + 1);
+    parent_leaf[base + gamma + 1] = g;
+  } else {
+    rc = (int32_t)(base + gamma + 1);
+    parent_inner[base + gamma + 1] = g;
+  }
+  left[g] = lc;
+  right[g] = rc;
+  first[g] = (int32_t)base + lo;
+  last[g] = (int32_t)base + hi;
+}
+
+__device__ __forceinline__ Box tri_box(const float4* packed, int64_t t) {
+  float4 a = packed[3 * t], b = packed[3 * t + 1], c = packed[3 * t + 2];
+  Box x;
+  x.lox = fminf(a.x, fminf(b.x, c.x));
+  x.loy = fminf(a.y, fminf(b.y, c.y));
+  x.loz = fminf(a.z, fminf(b.z, c.z));
+  x.hix = fmaxf(a.x, fmaxf(b.x, c.x));
+  x.hiy = fmaxf(a.y, fmaxf(b.y, c.y));
+  x.hiz = fmaxf(a.z, fmaxf(b.z, c.z));
+  return x;
+}
+
+__device__ __forceinline__ Box load_box_cg(const Box* p) {
+  const float* f = reinterpret_cast<const float*>(p);
+  Box b;
+  b.lox = __ldcg(f);
+  b.loy = __ldcg(f + 1);
+  b.loz = __ldcg(f + 2);
+  b.hix = __ldcg(f + 3);
+  b.hiy = __ldcg(f + 4);
+  b.hiz = __ldcg(f + 5);
+  return b;
+}
+
+__device__ __forceinline__ Box box_union(const Box& a, const Box& b) {
+  return {fminf(a.lox, b.lox), fminf(a.loy, b.loy), fminf(a.loz, b.loz),
+          fmaxf(a.hix, b.hix), fmaxf(a.hiy, b.hiy), fmaxf(a.hiz, b.hiz)};
+}
+
+__device__ __forceinline__ void store_box_cg(Box* p, const Box& b) {
+  float* f = reinterpret_cast<float*>(p);
+  __stcg(f, b.lox);
+  __stcg(f + 1, b.loy);
+  __stcg(f + 2, b.loz);
+  __stcg(f + 3, b.hix);
+  __stcg(f + 4, b.hiy);
+  __stcg(f + 5, b.hiz);
+}
+
+// Bottom-up refit: the second child to arrive at a node computes its box.
+__global__ void k_refit(const float4* __restrict__ packed, const uint32_t* __restrict__ vals, int32_t F,
+                        const int32_t* __restrict__ left, const int32_t* __restrict__ right,
+                        const int32_t* __restrict__ parent_inner, const int32_t* __restrict__ parent_leaf,
+                        Box* __restrict__ leaf_box, Box* __restrict__ inner_box, int32_t* __restrict__ visits) {
+  int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= F) return;
+  Box b = tri_box(packed, vals[i]);
+  store_box_cg(leaf_box + i, b);
+  int32_t p = parent_leaf[i];
+  int guard = 0;
+  while (p >= 0 && guard++ < 4096) {
+    __threadfence();
+    if (atomicAdd(visits + p, 1) == 0) return;
+    __threadfence();
+    int32_t l = left[p], r = right[p];
+    Box bl = l >= 0 ? load_box_cg(inner_box + l) : load_box_cg(leaf_box + ~l);
+    Box br = r >= 0 ? load_box_cg(inner_box + r) : load_box_cg(leaf_box + ~r);
+    store_box_cg(inner_box + p, box_union(bl, br));
+    p = parent_inner[p];
+  }
+}
+
+// ---------------------------------------------------------------- collapse
+struct QueueItem {
+  int32_t ref;  // inner node (>= 0) or ~leaf (single-triangle environment root)
+  int32_t env;
+};
+
+__device__ __forceinline__ int32_t ref_count(int32_t ref, const int32_t* first, const int32_t* last) {
+  return ref >= 0 ? last[ref] - first[ref] + 1 : 1;
+}
+
+__device__ __forceinline__ float box_area(const Box& b) {
+  float dx = b.hix - b.lox, dy = b.hiy - b.loy, dz = b.hiz - b.loz;
+  return dx * dy + dy * dz + dz * dx;
+}
+
+constexpr int32_t kSlotEmpty = (int32_t)0x80000000;
+
+// Phase A: open the binary subtree below each queued node into up to 8
+// slots (largest surface area first), classify them and count.
+__global__ void k_collapse_expand(const QueueItem* __restrict__ items, int32_t n_items,
+                                  const int32_t* __restrict__ left, const int32_t* __restrict__ right,
+                                  const int32_t* __restrict__ first, const int32_t* __restrict__ last,
+                                  const Box* __restrict__ inner_box, int leaf_max, int32_t* __restrict__ slots,
+                                  int32_t* __restrict__ n_inner, int32_t* __restrict__ n_leaf_tris) {
+  int32_t it = blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= n_items) return;
+  int32_t ref = items[it].ref;
+  int32_t s[8];
+  int ns = 0;
+  if (ref >= 0) {
+    s[0] = left[ref];
+    s[1] = right[ref];
+    ns = 2;
+  } else {
+    s[0] = ref;
+    ns = 1;
+  }
+  while (ns < 8) {
+    int best = -1;
+    float best_area = -1.0f;
+    for (int k = 0; k < ns; ++k) {
+      int32_t r = s[k];
+      if (r >= 0 && ref_count(r, first, last) > leaf_max) {
+        float a = box_area(inner_box[r]);
+        if (a > best_area) {
+          best_area = a;
+          best = k;
+        }
+      }
+    }
+    if (best < 0) break;
+    int32_t r = s[best];
+    s[best] = left[r];
+    s[ns++] = right[r];
+  }
+  int ni = 0, nt = 0;
+  for (int k = 0; k < 8; ++k) {
+    int32_t r = k < ns ? s[k] : kSlotEmpty;
+    slots[8 * (int64_t)it + k] = r;
+    if (k >= ns) continue;
+    int32_t c = ref_count(r, first, last);
+    if (r >= 0 && c > leaf_max) ++ni;
+    else nt += c;
+  }
+  n_inner[it] = ni;
+  n_leaf_tris[it] = nt;
+}
+
+// Phase C: write the wide nodes of this level, the next level's queue and
+// the leaf-order triangle permutation.
+__global__ void k_collapse_emit(const QueueItem* __restrict__ items, int32_t n_items,
+                                const int32_t* __restrict__ slots, const int32_t* __restrict__ inner_off,
+                                const int32_t* __restrict__ tri_off, int32_t level_base, int32_t next_base,
+                                int32_t tri_base_level, const int32_t* __restrict__ first,
+                                const int32_t* __restrict__ last, const Box* __restrict__ inner_box,
+                                const Box* __restrict__ leaf_box, int leaf_max, WideNode* __restrict__ nodes,
+                                QueueItem* __restrict__ next_items, int32_t* __restrict__ perm,
+                                unsigned long long* __restrict__ env_nodes) {
+  int32_t it = blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= n_items) return;
+  QueueItem q = items[it];
+  WideNode nd;
+  nd.child_base = next_base + inner_off[it];
+  nd.tri_base = tri_base_level + tri_off[it];
+  uint32_t meta[2] = {0, 0};
+  int rank = 0, toff = 0;
+  for (int k = 0; k < 8; ++k) {
+    int32_t r = slots[8 * (int64_t)it + k];
+    uint32_t m;
+    Box b;
+    if (r == kSlotEmpty) {
+      m = kMetaEmpty;
+      b = {kEmptyBoxCoord, kEmptyBoxCoord, kEmptyBoxCoord, kEmptyBoxCoord, kEmptyBoxCoord, kEmptyBoxCoord};
+    } else {
+      int32_t c = ref_count(r, first, last);
+      b = r >= 0 ? inner_box[r] : leaf_box[~r];
+      if (r >= 0 && c > leaf_max) {
+        m = 0x80u | (uint32_t)rank;
+        next_items[inner_off[it] + rank] = {r, q.env};
+        ++rank;
+      } else {
+        int32_t f0 = r >= 0 ? first[r] : ~r;
+        m = ((uint32_t)toff << 2) | (uint32_t)(c - 1);
+        for (int32_t x = 0; x < c; ++x) perm[nd.tri_base + toff + x] = f0 + x;
+        toff += c;
+      }
+    }
+    meta[k >> 2] |= (m & 0xFFu) << (8 * (k & 3));
+    nd.lox[k] = b.lox;
+    nd.hix[k] = b.hix;
+    nd.loy[k] = b.loy;
+    nd.hiy[k] = b.hiy;
+    nd.loz[k] = b.loz;
+    nd.hiz[k] = b.hiz;
+  }
+  nd.meta_lo = meta[0];
+  nd.meta_hi = meta[1];
+  nodes[level_base + it] = nd;
+  atomicAdd(env_nodes + q.env, 1ull);
+}
+
+__global__ void k_gather_tris(const float4* __restrict__ packed, const uint32_t* __restrict__ vals,
+                              const int32_t* __restrict__ perm, int32_t F, float4* __restrict__ out) {
+  int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= F) return;
+  int64_t t = vals[perm[k]];
+  out[3 * (int64_t)k] = packed[3 * t];
+  out[3 * (int64_t)k + 1] = packed[3 * t + 1];
+  out[3 * (int64_t)k + 2] = packed[3 * t + 2];
+}
+
+unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+// device allocations released on scope exit
+struct DevBufs {
+  std::vector<void*> ptrs;
+  ~DevBufs() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <class T>
+  cudaError_t alloc(T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e == cudaSuccess) {
+      ptrs.push_back(q);
+      *p = static_cast<T*>(q);
+    }
+    return e;
+  }
+};
+
+}  // namespace
+
+ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_h, const int32_t* tri_vidx_h,
+                       const int32_t* sub_vert_off_h, const float* poses_h, const int32_t* sub_env_h) {
+  cudaStream_t s = ctx->stream;
+  const int32_t E = sc->n_envs;
+  const int32_t F = (int32_t)sc->n_tris;
+  const int32_t V = (int32_t)sc->n_verts;
+  const int32_t J = (int32_t)sc->n_subs;
+  DevBufs tmp;
+
+  // persistent buffers (owned by the scene)
+  AGS_CHECK(cudaMalloc(&sc->d.world_verts, std::max<int64_t>(V, 1) * sizeof(float4)));
+  AGS_CHECK(cudaMalloc(&sc->d.tri_vidx, std::max<int64_t>(3 * (int64_t)F, 1) * sizeof(int32_t)));
+  AGS_CHECK(cudaMalloc(&sc->d.env_root, std::max<int32_t>(E, 1) * sizeof(int32_t)));
+  AGS_CHECK(cudaMalloc(&sc->d.tris, std::max<int64_t>(3 * (int64_t)F, 1) * sizeof(float4)));
+
+  float *d_base = nullptr, *d_poses = nullptr, *d_rot = nullptr;
+  int32_t *d_sub_vert = nullptr, *d_sub_tri = nullptr, *d_sub_seg = nullptr, *d_sub_env = nullptr,
+          *d_env_tri = nullptr;
+  AGS_CHECK(tmp.alloc(&d_base, 3 * (size_t)V));
+  AGS_CHECK(tmp.alloc(&d_poses, 7 * (size_t)J));
+  AGS_CHECK(tmp.alloc(&d_rot, 18 * (size_t)J));
+  AGS_CHECK(tmp.alloc(&d_sub_vert, (size_t)J + 1));
+  AGS_CHECK(tmp.alloc(&d_sub_tri, (size_t)J + 1));
+  AGS_CHECK(tmp.alloc(&d_sub_seg, (size_t)J));
+  AGS_CHECK(tmp.alloc(&d_sub_env, (size_t)J));
+  AGS_CHECK(tmp.alloc(&d_env_tri, (size_t)E + 1));
+
+  std::vector<int32_t> sub_tri32(J + 1), env_tri32(E + 1);
+  for (int32_t j = 0; j <= J; ++j) sub_tri32[j] = (int32_t)sc->sub_tri_off[j];
+  for (int32_t e = 0; e <= E; ++e) env_tri32[e] = (int32_t)sc->env_tri_off[e];
+
+  AGS_CHECK(cudaMemcpyAsync(d_base, base_verts_h, 3 * (size_t)V * sizeof(float), cudaMemcpyHostToDevice, s));
+  AGS_CHECK(cudaMemcpyAsync(d_poses, poses_h, 7 * (size_t)J * sizeof(float), cudaMemcpyHostToDevice, s));
+  AGS_CHECK(cudaMemcpyAsync(d_sub_vert, sub_vert_off_h, ((size_t)J + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  AGS_CHECK(cudaMemcpyAsync(d_sub_tri, sub_tri32.data(), ((size_t)J + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  AGS_CHECK(cudaMemcpyAsync(d_sub_seg, sc->sub_seg.data(), (size_t)J * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  AGS_CHECK(cudaMemcpyAsync(d_sub_env, sub_env_h, (size_t)J * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  AGS_CHECK(cudaMemcpyAsync(d_env_tri, env_tri32.data(), ((size_t)E + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  AGS_CHECK(cudaMemcpyAsync(sc->d.tri_vidx, tri_vidx_h, 3 * (size_t)F * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+
+  // a1: transform
+  if (J > 0) k_submesh_rotations<<<blocks_for(J, 128), 128, 0, s>>>(d_poses, J, d_rot);
+  if (V > 0)
+    k_transform_vertices<<<blocks_for(V, 256), 256, 0, s>>>(d_base, V, d_sub_vert, J, d_rot, d_poses,
+                                                            sc->d.world_verts);
+  AGS_CHECK(cudaGetLastError());
+
+  // roots and level-0 queue (host side: environments with at least one triangle)
+  std::vector<int32_t> env_root(E, -1);
+  std::vector<QueueItem> q0;
+  for (int32_t e = 0; e < E; ++e) {
+    int64_t n = sc->env_tri_off[e + 1] - sc->env_tri_off[e];
+    if (n <= 0) continue;
+    env_root[e] = (int32_t)q0.size();
+    int32_t base = (int32_t)sc->env_tri_off[e];
+    q0.push_back({n >= 2 ? base : ~base, e});
+  }
+  AGS_CHECK(cudaMemcpyAsync(sc->d.env_root, env_root.data(), (size_t)std::max(E, 1) * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, s));
+  sc->env_nodes.assign(E, 0);
+  if (F == 0) {
+    AGS_CHECK(cudaMalloc(&sc->d.nodes, sizeof(WideNode)));
+    sc->n_nodes = 0;
+    AGS_CHECK(cudaStreamSynchronize(s));
+    return AGS_OK;
+  }
+
+  // packed triangles in input order
+  float4* d_packed = nullptr;
+  int32_t* d_tri_env = nullptr;
+  AGS_CHECK(tmp.alloc(&d_packed, 3 * (size_t)F));
+  AGS_CHECK(tmp.alloc(&d_tri_env, (size_t)F));
+  k_pack_triangles<<<blocks_for(F, 256), 256, 0, s>>>(sc->d.tri_vidx, F, sc->d.world_verts, d_sub_tri, J, d_sub_seg,
+                                                      d_sub_env, d_env_tri, d_packed, d_tri_env);
+
+  // a2: Morton codes over each environment's centroid bounds
+  int64_t max_env_tris = 0;
+  for (int32_t e = 0; e < E; ++e) max_env_tris = std::max(max_env_tris, sc->env_tri_off[e + 1] - sc->env_tri_off[e]);
+  int env_bits = 0;
+  while ((1ll << env_bits) < E) ++env_bits;
+  int bits = 10;
+  if (max_env_tris > (1ll << 20)) bits = std::min(21, (64 - env_bits) / 3);
+  bits = std::min(bits, (64 - env_bits) / 3);
+  int key_shift = 3 * bits;
+  int end_bit = key_shift + env_bits;
+
+  int32_t* d_bounds = nullptr;
+  AGS_CHECK(tmp.alloc(&d_bounds, 6 * (size_t)E));
+  k_init_bounds<<<blocks_for(E, 128), 128, 0, s>>>(d_bounds, E);
+  k_env_bounds<<<blocks_for(F, 256), 256, 0, s>>>(d_packed, d_tri_env, F, d_bounds);
+  uint64_t *d_keys = nullptr, *d_keys2 = nullptr;
+  uint32_t *d_vals = nullptr, *d_vals2 = nullptr;
+  AGS_CHECK(tmp.alloc(&d_keys, (size_t)F));
+  AGS_CHECK(tmp.alloc(&d_keys2, (size_t)F));
+  AGS_CHECK(tmp.alloc(&d_vals, (size_t)F));
+  AGS_CHECK(tmp.alloc(&d_vals2, (size_t)F));
+  k_morton<<<blocks_for(F, 256), 256, 0, s>>>(d_packed, d_tri_env, F, d_bounds, bits, d_keys, d_vals);
+  AGS_CHECK(cudaGetLastError());
+  void* d_sort_tmp = nullptr;
+  AGS_CHECK(tmp.alloc(reinterpret_cast<char**>(&d_sort_tmp), sort_temp_bytes(F)));
+  AGS_CHECK(sort_pairs(d_keys, d_vals, d_keys2, d_vals2, F, end_bit, d_sort_tmp, s));
+
+  // binary radix tree per environment
+  int32_t *d_left, *d_right, *d_pin, *d_pleaf, *d_first, *d_last, *d_visits;
+  AGS_CHECK(tmp.alloc(&d_left, (size_t)F));
+  AGS_CHECK(tmp.alloc(&d_right, (size_t)F));
+  AGS_CHECK(tmp.alloc(&d_pin, (size_t)F));
+  AGS_CHECK(tmp.alloc(&d_pleaf, (size_t)F));
+  AGS_CHECK(tmp.alloc(&d_first, (size_t)F));
+  AGS_CHECK(tmp.alloc(&d_last, (size_t)F));
+  AGS_CHECK(tmp.alloc(&d_visits, (size_t)F));
+  AGS_CHECK(cudaMemsetAsync(d_visits, 0, (size_t)F * sizeof(int32_t), s));
+  k_karras<<<blocks_for(F, 256), 256, 0, s>>>(d_keys, F, key_shift, d_env_tri, d_left, d_right, d_pin, d_pleaf,
+                                              d_first, d_last);
+  Box *d_leaf_box, *d_inner_box;
+  AGS_CHECK(tmp.alloc(&d_leaf_box, (size_t)F));
+  AGS_CHECK(tmp.alloc(&d_inner_box, (size_t)F));
+  k_refit<<<blocks_for(F, 256), 256, 0, s>>>(d_packed, d_vals, F, d_left, d_right, d_pin, d_pleaf, d_leaf_box,
+                                             d_inner_box, d_visits);
+  AGS_CHECK(cudaGetLastError());
+
+  // collapse into 8-wide nodes, level by level
+  int64_t node_cap = (int64_t)(0.4 * (double)F) + 2 * (int64_t)E + 64;
+  WideNode* d_nodes_tmp = nullptr;
+  AGS_CHECK(tmp.alloc(&d_nodes_tmp, (size_t)node_cap));
+  QueueItem *d_q = nullptr, *d_q2 = nullptr;
+  int64_t q_cap = node_cap;
+  AGS_CHECK(tmp.alloc(&d_q, (size_t)q_cap));
+  AGS_CHECK(tmp.alloc(&d_q2, (size_t)q_cap));
+  int32_t *d_slots, *d_ninner, *d_ntris, *d_perm, *d_tot;
+  AGS_CHECK(tmp.alloc(&d_slots, 8 * (size_t)q_cap));
+  AGS_CHECK(tmp.alloc(&d_ninner, (size_t)q_cap));
+  AGS_CHECK(tmp.alloc(&d_ntris, (size_t)q_cap));
+  AGS_CHECK(tmp.alloc(&d_perm, (size_t)F));
+  AGS_CHECK(tmp.alloc(&d_tot, 2));
+  void* d_scan_tmp = nullptr;
+  AGS_CHECK(tmp.alloc(reinterpret_cast<char**>(&d_scan_tmp), scan_temp_bytes(q_cap)));
+  unsigned long long* d_env_nodes = nullptr;
+  AGS_CHECK(tmp.alloc(&d_env_nodes, (size_t)E));
+  AGS_CHECK(cudaMemsetAsync(d_env_nodes, 0, (size_t)E * sizeof(unsigned long long), s));
+  AGS_CHECK(cudaMemcpyAsync(d_q, q0.data(), q0.size() * sizeof(QueueItem), cudaMemcpyHostToDevice, s));
+
+  int32_t n_items = (int32_t)q0.size();
+  int32_t level_base = 0, tri_level_base = 0;
+  int levels = 0;
+  while (n_items > 0) {
+    if (++levels > 4096) {
+      set_error("BVH collapse did not terminate");
+      return AGS_ERR_CUDA;
+    }
+    k_collapse_expand<<<blocks_for(n_items, 128), 128, 0, s>>>(d_q, n_items, d_left, d_right, d_first, d_last,
+                                                              d_inner_box, kMaxLeafTris, d_slots, d_ninner, d_ntris);
+    AGS_CHECK(cudaGetLastError());
+    AGS_CHECK(exclusive_scan(d_ninner, n_items, d_tot, d_scan_tmp, s));
+    AGS_CHECK(exclusive_scan(d_ntris, n_items, d_tot + 1, d_scan_tmp, s));
+    int32_t tot[2];
+    AGS_CHECK(cudaMemcpyAsync(tot, d_tot, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    AGS_CHECK(cudaStreamSynchronize(s));
+    int32_t next_base = level_base + n_items;
+    if ((int64_t)next_base + tot[0] > node_cap) {
+      set_error("BVH node capacity exceeded");
+      return AGS_ERR_CUDA;
+    }
+    k_collapse_emit<<<blocks_for(n_items, 128), 128, 0, s>>>(
+        d_q, n_items, d_slots, d_ninner, d_ntris, level_base, next_base, tri_level_base, d_first, d_last,
+        d_inner_box, d_leaf_box, kMaxLeafTris, d_nodes_tmp, d_q2, d_perm, d_env_nodes);
+    AGS_CHECK(cudaGetLastError());
+    std::swap(d_q, d_q2);
+    level_base = next_base;
+    tri_level_base += tot[1];
+    n_items = tot[0];
+  }
+  if (tri_level_base != F) {
+    set_error("BVH collapse lost triangles");
+    return AGS_ERR_CUDA;
+  }
+  sc->n_nodes = level_base;
+  AGS_CHECK(cudaMalloc(&sc->d.nodes, std::max<int64_t>(sc->n_nodes, 1) * sizeof(WideNode)));
+  AGS_CHECK(cudaMemcpyAsync(sc->d.nodes, d_nodes_tmp, (size_t)sc->n_nodes * sizeof(WideNode),
+                            cudaMemcpyDeviceToDevice, s));
+  k_gather_tris<<<blocks_for(F, 256), 256, 0, s>>>(d_packed, d_vals, d_perm, F, sc->d.tris);
+  AGS_CHECK(cudaGetLastError());
+  std::vector<unsigned long long> env_nodes(E);
+  AGS_CHECK(cudaMemcpyAsync(env_nodes.data(), d_env_nodes, (size_t)E * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, s));
+  AGS_CHECK(cudaStreamSynchronize(s));
+  for (int32_t e = 0; e < E; ++e) sc->env_nodes[e] = (int64_t)env_nodes[e];
+  return AGS_OK;
+}
+
+}  // namespace ags

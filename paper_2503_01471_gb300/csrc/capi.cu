@@ -1,0 +1,452 @@
+// C ABI of the renderer (include/ags.h): argument validation, context and
+// scene lifetime, kernel launches. No torch types, no exceptions across the
+// boundary; every failure is an ags_status plus a thread-local message.
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+
+#include "internal.cuh"
+
+namespace ags {
+
+namespace {
+thread_local std::string g_last_error;
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int d) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != d) cudaSetDevice(d);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+ags_status invalid(const std::string& msg) {
+  set_error(msg);
+  return AGS_ERR_INVALID_ARG;
+}
+
+bool finite3(const float* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+ags_status check_spec(const ags_sensor_spec* s) {
+  if (!s) return invalid("spec is NULL");
+  if (s->type != AGS_PINHOLE && s->type != AGS_LIDAR) return invalid("spec.type must be AGS_PINHOLE or AGS_LIDAR");
+  if (s->width < 1 || s->width > 16384 || s->height < 1 || s->height > 16384)
+    return invalid("spec.width/height must be in [1, 16384]");
+  if (!std::isfinite(s->min_range) || !std::isfinite(s->max_range) || s->min_range < 0.0f ||
+      !(s->max_range > s->min_range))
+    return invalid("spec ranges must satisfy 0 <= min_range < max_range < inf");
+  if (s->near_mode != AGS_NEAR_CLAMP && s->near_mode != AGS_NEAR_INVALID) return invalid("spec.near_mode invalid");
+  if (s->flags != 0) return invalid("spec.flags must be 0");
+  const double pi = 3.14159265358979323846;
+  if (s->type == AGS_PINHOLE) {
+    if (!(s->hfov_rad > 0.0f) || !(s->hfov_rad < (float)pi)) return invalid("camera hfov must be in (0, pi)");
+  } else {
+    if (!(s->hfov_rad > 0.0f) || !(s->hfov_rad <= (float)(2.0 * pi) + 1e-6f))
+      return invalid("LiDAR azimuth span must be in (0, 2 pi]");
+    if (!std::isfinite(s->vfov_min_rad) || !std::isfinite(s->vfov_max_rad) || s->vfov_min_rad < -(float)(pi / 2) - 1e-6f ||
+        s->vfov_max_rad > (float)(pi / 2) + 1e-6f || s->vfov_min_rad > s->vfov_max_rad)
+      return invalid("LiDAR elevations must satisfy -pi/2 <= vfov_min <= vfov_max <= pi/2");
+  }
+  return AGS_OK;
+}
+
+unsigned int* tile_counter(ags_context* ctx, cudaStream_t s) {
+  auto it = ctx->tile_counters.find(s);
+  if (it != ctx->tile_counters.end()) return it->second;
+  unsigned int* p = nullptr;
+  if (cudaMalloc(&p, sizeof(unsigned int)) != cudaSuccess) return nullptr;
+  ctx->tile_counters[s] = p;
+  return p;
+}
+
+ags_status fill_trace_args(ags_context* ctx, const ags_scene* sc, const ags_sensor_spec* spec, int32_t n,
+                           const int32_t* env_ids, const float* poses, float* depth, int32_t* seg, TraceArgs& a) {
+  a.nodes = sc->d.nodes;
+  a.tris = sc->d.tris;
+  a.env_root = sc->d.env_root;
+  a.env_ids = env_ids;
+  a.poses = poses;
+  a.out_depth = depth;
+  a.out_seg = seg;
+  a.n = n;
+  a.W = spec->width;
+  a.H = spec->height;
+  a.type = spec->type;
+  a.near_mode = spec->near_mode;
+  a.inv_f = (float)(std::tan(0.5 * (double)spec->hfov_rad) / (0.5 * (double)spec->width));
+  a.hfov = spec->hfov_rad;
+  a.vmax = spec->vfov_max_rad;
+  a.dv = spec->height > 1 ? (float)(((double)spec->vfov_max_rad - (double)spec->vfov_min_rad) / (spec->height - 1)) : 0.0f;
+  a.min_range = spec->min_range;
+  a.max_range = spec->max_range;
+  a.tiles_x = (spec->width + 7) / 8;
+  int64_t tiles_y = (spec->height + 3) / 4;
+  int64_t per_env = (int64_t)a.tiles_x * tiles_y;
+  int64_t total = per_env * n;
+  if (total >= (1ll << 31)) return invalid("too many rays in one render call (tiles >= 2^31)");
+  a.tiles_per_env = (int32_t)per_env;
+  a.total_tiles = total;
+  a.status = ctx->d_status;
+  a.counts = ctx->d_counts;
+  return AGS_OK;
+}
+
+ags_status launch(ags_context* ctx, TraceArgs& a, cudaStream_t s, bool count) {
+  unsigned int* counter = tile_counter(ctx, s);
+  if (!counter) {
+    set_error("cannot allocate the tile counter");
+    return AGS_ERR_OUT_OF_MEMORY;
+  }
+  a.tile_counter = counter;
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(tile counter)");
+  if (a.total_tiles == 0) return AGS_OK;
+  e = launch_trace(a, count ? ctx->trace_count_blocks : ctx->trace_blocks, count, s);
+  if (e != cudaSuccess) return cuda_fail(e, "k_trace launch");
+  return AGS_OK;
+}
+
+}  // namespace
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+ags_status cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? AGS_ERR_OUT_OF_MEMORY : AGS_ERR_CUDA;
+}
+
+}  // namespace ags
+
+using namespace ags;
+
+#define AGS_API_BEGIN try {
+#define AGS_API_END                                   \
+  }                                                   \
+  catch (const std::bad_alloc&) {                     \
+    set_error("host allocation failed");              \
+    return AGS_ERR_OUT_OF_MEMORY;                     \
+  }                                                   \
+  catch (...) {                                       \
+    set_error("unexpected host exception");           \
+    return AGS_ERR_CUDA;                              \
+  }
+
+extern "C" {
+
+const char* ags_last_error(void) { return g_last_error.c_str(); }
+
+ags_status ags_context_create(int device, ags_context** out) {
+  AGS_API_BEGIN
+  if (!out) return invalid("out is NULL");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= n) return invalid("device index out of range");
+  DeviceGuard g(device);
+  ags_context* ctx = new ags_context();
+  ctx->device = device;
+  cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if ((e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaMalloc(&ctx->d_status, sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&ctx->d_counts, 3 * sizeof(unsigned long long))) != cudaSuccess ||
+      (e = cudaMemset(ctx->d_status, 0, sizeof(int))) != cudaSuccess) {
+    ags_status st = cuda_fail(e, "context setup");
+    ags_context_destroy(ctx);
+    return st;
+  }
+  ctx->trace_blocks = ctx->sm_count * trace_blocks_per_sm(false);
+  ctx->trace_count_blocks = ctx->sm_count * trace_blocks_per_sm(true);
+  *out = ctx;
+  return AGS_OK;
+  AGS_API_END
+}
+
+void ags_context_destroy(ags_context* ctx) {
+  if (!ctx) return;
+  DeviceGuard g(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto& kv : ctx->tile_counters) cudaFree(kv.second);
+  cudaFree(ctx->d_status);
+  cudaFree(ctx->d_counts);
+  cudaFree(ctx->stage);
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+ags_status ags_scene_build(ags_context* ctx, const ags_env_mesh* envs, int32_t n_envs, const float* obstacle_poses,
+                           uint32_t build_flags, ags_scene** out) {
+  AGS_API_BEGIN
+  if (!out) return invalid("out is NULL");
+  *out = nullptr;
+  if (!ctx) return invalid("ctx is NULL");
+  if (!envs) return invalid("envs is NULL");
+  if (n_envs < 1 || n_envs > 65536) return invalid("n_envs must be in [1, 65536]");
+  if (build_flags != AGS_BVH_FP32) return invalid("unsupported build_flags");
+  // sizes
+  int64_t J = 0, V = 0, F = 0;
+  for (int32_t e = 0; e < n_envs; ++e) {
+    if (envs[e].n_submeshes < 0) return invalid("env " + std::to_string(e) + ": n_submeshes < 0");
+    if (envs[e].n_submeshes > 0 && !envs[e].submeshes) return invalid("env " + std::to_string(e) + ": submeshes NULL");
+    for (int32_t j = 0; j < envs[e].n_submeshes; ++j) {
+      const ags_submesh& m = envs[e].submeshes[j];
+      if (m.n_vertices < 0 || m.n_triangles < 0)
+        return invalid("env " + std::to_string(e) + " submesh " + std::to_string(j) + ": negative size");
+      V += m.n_vertices;
+      F += m.n_triangles;
+    }
+    J += envs[e].n_submeshes;
+  }
+  if (F >= (1ll << 31) - 1 || V >= (1ll << 31) - 1 || J >= (1ll << 31) - 1)
+    return invalid("scene too large (2^31 - 1 triangles, vertices or sub-meshes)");
+  if (J > 0 && !obstacle_poses) return invalid("obstacle_poses is NULL");
+
+  std::unique_ptr<ags_scene> sc(new ags_scene());
+  sc->ctx = ctx;
+  sc->n_envs = n_envs;
+  sc->n_tris = F;
+  sc->n_verts = V;
+  sc->n_subs = J;
+  sc->flags = build_flags;
+  sc->env_tri_off.assign(n_envs + 1, 0);
+  sc->env_vert_off.assign(n_envs + 1, 0);
+  sc->env_sub_off.assign(n_envs + 1, 0);
+  sc->sub_tri_off.assign(J + 1, 0);
+  sc->sub_seg.assign(J, 0);
+  std::vector<float> base(3 * V);
+  std::vector<int32_t> vidx(3 * F), sub_vert(J + 1, 0), sub_env(J);
+  int64_t j_all = 0, v_all = 0, f_all = 0;
+  for (int32_t e = 0; e < n_envs; ++e) {
+    for (int32_t j = 0; j < envs[e].n_submeshes; ++j, ++j_all) {
+      const ags_submesh& m = envs[e].submeshes[j];
+      std::string where = "env " + std::to_string(e) + " submesh " + std::to_string(j);
+      if (m.n_vertices > 0 && !m.vertices) return invalid(where + ": vertices NULL");
+      if (m.n_triangles > 0 && !m.indices) return invalid(where + ": indices NULL");
+      if (m.segment_id < 0) return invalid(where + ": segment_id < 0");
+      for (int32_t v = 0; v < m.n_vertices; ++v)
+        if (!finite3(m.vertices + 3 * (int64_t)v)) return invalid(where + ": non-finite vertex");
+      for (int64_t k = 0; k < 3 * (int64_t)m.n_triangles; ++k) {
+        int32_t x = m.indices[k];
+        if (x < 0 || x >= m.n_vertices) return invalid(where + ": triangle index out of range");
+        vidx[3 * f_all + k] = (int32_t)v_all + x;
+      }
+      const float* p = obstacle_poses + 7 * j_all;
+      for (int k = 0; k < 7; ++k)
+        if (!std::isfinite(p[k])) return invalid(where + ": non-finite pose");
+      double qn = (double)p[3] * p[3] + (double)p[4] * p[4] + (double)p[5] * p[5] + (double)p[6] * p[6];
+      if (!(qn > 1e-12) || !std::isfinite(qn)) return invalid(where + ": quaternion has zero length");
+      if (m.n_vertices > 0) std::memcpy(base.data() + 3 * v_all, m.vertices, 3 * (size_t)m.n_vertices * sizeof(float));
+      sub_env[j_all] = e;
+      sc->sub_seg[j_all] = m.segment_id;
+      v_all += m.n_vertices;
+      f_all += m.n_triangles;
+      sub_vert[j_all + 1] = (int32_t)v_all;
+      sc->sub_tri_off[j_all + 1] = f_all;
+    }
+    sc->env_tri_off[e + 1] = f_all;
+    sc->env_vert_off[e + 1] = v_all;
+    sc->env_sub_off[e + 1] = j_all;
+  }
+  DeviceGuard g(ctx->device);
+  ags_status st = build_scene(ctx, sc.get(), base.data(), vidx.data(), sub_vert.data(), obstacle_poses,
+                              sub_env.data());
+  if (st != AGS_OK) {
+    cudaStreamSynchronize(ctx->stream);
+    ags_scene_destroy(sc.release());
+    return st;
+  }
+  *out = sc.release();
+  return AGS_OK;
+  AGS_API_END
+}
+
+void ags_scene_destroy(ags_scene* sc) {
+  if (!sc) return;
+  DeviceGuard g(sc->ctx->device);
+  cudaFree(sc->d.world_verts);
+  cudaFree(sc->d.tri_vidx);
+  cudaFree(sc->d.nodes);
+  cudaFree(sc->d.tris);
+  cudaFree(sc->d.env_root);
+  delete sc;
+}
+
+int32_t ags_scene_n_envs(const ags_scene* sc) { return sc ? sc->n_envs : -1; }
+
+int32_t ags_scene_node_bytes(const ags_scene* sc) { return sc ? (int32_t)sizeof(WideNode) : -1; }
+
+ags_status ags_render(ags_context* ctx, const ags_scene* sc, const ags_sensor_spec* spec, const float* poses,
+                      float* depth, int32_t* seg, void* stream) {
+  AGS_API_BEGIN
+  if (!ctx || !sc) return invalid("ctx or scene is NULL");
+  if (sc->ctx != ctx) return invalid("scene belongs to another context");
+  ags_status st = check_spec(spec);
+  if (st != AGS_OK) return st;
+  if (!poses || !depth || !seg) return invalid("poses/depth/seg pointer is NULL");
+  DeviceGuard g(ctx->device);
+  TraceArgs a{};
+  if ((st = fill_trace_args(ctx, sc, spec, sc->n_envs, nullptr, poses, depth, seg, a)) != AGS_OK) return st;
+  return launch(ctx, a, static_cast<cudaStream_t>(stream), false);
+  AGS_API_END
+}
+
+ags_status ags_render_envs(ags_context* ctx, const ags_scene* sc, const ags_sensor_spec* spec, const int32_t* env_ids,
+                           int32_t n, const float* poses, float* depth, int32_t* seg, void* stream) {
+  AGS_API_BEGIN
+  if (!ctx || !sc) return invalid("ctx or scene is NULL");
+  if (sc->ctx != ctx) return invalid("scene belongs to another context");
+  ags_status st = check_spec(spec);
+  if (st != AGS_OK) return st;
+  if (n < 0) return invalid("n < 0");
+  if (n > 0 && (!env_ids || !poses || !depth || !seg)) return invalid("env_ids/poses/depth/seg pointer is NULL");
+  DeviceGuard g(ctx->device);
+  TraceArgs a{};
+  if ((st = fill_trace_args(ctx, sc, spec, n, env_ids, poses, depth, seg, a)) != AGS_OK) return st;
+  return launch(ctx, a, static_cast<cudaStream_t>(stream), false);
+  AGS_API_END
+}
+
+ags_status ags_stream_status(ags_context* ctx, void* stream) {
+  AGS_API_BEGIN
+  if (!ctx) return invalid("ctx is NULL");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  int word = 0;
+  if ((e = cudaMemcpyAsync(&word, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
+    return cuda_fail(e, "status word");
+  if (word != 0) {
+    set_error(std::string("device traversal limit hit:") + ((word & kStatusStackOverflow) ? " stack" : "") +
+              ((word & kStatusIterationCap) ? " iterations" : ""));
+    return AGS_ERR_TRAVERSAL_LIMIT;
+  }
+  return AGS_OK;
+  AGS_API_END
+}
+
+ags_status ags_render_host(ags_context* ctx, const ags_scene* sc, const ags_sensor_spec* spec, const float* poses_h,
+                           float* depth_h, int32_t* seg_h) {
+  AGS_API_BEGIN
+  if (!ctx || !sc) return invalid("ctx or scene is NULL");
+  if (sc->ctx != ctx) return invalid("scene belongs to another context");
+  ags_status st = check_spec(spec);
+  if (st != AGS_OK) return st;
+  if (!poses_h || !depth_h || !seg_h) return invalid("poses/depth/seg pointer is NULL");
+  DeviceGuard g(ctx->device);
+  const int64_t n = sc->n_envs, pix = (int64_t)spec->width * spec->height;
+  const size_t pose_b = ((size_t)n * 7 * sizeof(float) + 255) & ~size_t(255);
+  const size_t out_b = ((size_t)(n * pix) * sizeof(float) + 255) & ~size_t(255);
+  const size_t need = pose_b + 2 * out_b;
+  cudaError_t e;
+  if (ctx->stage_bytes < need) {
+    cudaFree(ctx->stage);
+    ctx->stage = nullptr;
+    ctx->stage_bytes = 0;
+    if ((e = cudaMalloc(&ctx->stage, need)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(staging)");
+    ctx->stage_bytes = need;
+  }
+  char* base = static_cast<char*>(ctx->stage);
+  float* d_pose = reinterpret_cast<float*>(base);
+  float* d_depth = reinterpret_cast<float*>(base + pose_b);
+  int32_t* d_seg = reinterpret_cast<int32_t*>(base + pose_b + out_b);
+  cudaStream_t s = ctx->stream;
+  if ((e = cudaMemcpyAsync(d_pose, poses_h, (size_t)n * 7 * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemcpyAsync(poses)");
+  TraceArgs a{};
+  if ((st = fill_trace_args(ctx, sc, spec, (int32_t)n, nullptr, d_pose, d_depth, d_seg, a)) != AGS_OK) return st;
+  if ((st = launch(ctx, a, s, false)) != AGS_OK) return st;
+  if ((e = cudaMemcpyAsync(depth_h, d_depth, (size_t)(n * pix) * sizeof(float), cudaMemcpyDeviceToHost, s)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(seg_h, d_seg, (size_t)(n * pix) * sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemcpyAsync(outputs)");
+  return ags_stream_status(ctx, s);
+  AGS_API_END
+}
+
+ags_status ags_render_count(ags_context* ctx, const ags_scene* sc, const ags_sensor_spec* spec, const float* poses,
+                            uint64_t counts_host[3]) {
+  AGS_API_BEGIN
+  if (!ctx || !sc) return invalid("ctx or scene is NULL");
+  if (sc->ctx != ctx) return invalid("scene belongs to another context");
+  ags_status st = check_spec(spec);
+  if (st != AGS_OK) return st;
+  if (!poses || !counts_host) return invalid("poses/counts pointer is NULL");
+  DeviceGuard g(ctx->device);
+  TraceArgs a{};
+  if ((st = fill_trace_args(ctx, sc, spec, sc->n_envs, nullptr, poses, nullptr, nullptr, a)) != AGS_OK) return st;
+  cudaStream_t s = ctx->stream;
+  cudaError_t e = cudaMemsetAsync(ctx->d_counts, 0, 3 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counts)");
+  if ((st = launch(ctx, a, s, true)) != AGS_OK) return st;
+  unsigned long long c[3];
+  if ((e = cudaMemcpyAsync(c, ctx->d_counts, sizeof(c), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(e, "cudaMemcpyAsync(counts)");
+  st = ags_stream_status(ctx, s);
+  for (int k = 0; k < 3; ++k) counts_host[k] = c[k];
+  return st;
+  AGS_API_END
+}
+
+ags_status ags_scene_get_world_triangles(const ags_scene* sc, int32_t env, float* out, int32_t* out_seg,
+                                         int64_t capacity) {
+  AGS_API_BEGIN
+  if (!sc) return invalid("scene is NULL");
+  if (env < 0 || env >= sc->n_envs) return invalid("env out of range");
+  int64_t f0 = sc->env_tri_off[env], f1 = sc->env_tri_off[env + 1];
+  int64_t v0 = sc->env_vert_off[env], v1 = sc->env_vert_off[env + 1];
+  int64_t n = f1 - f0;
+  if (capacity < n) return invalid("capacity smaller than the environment's triangle count");
+  if (n == 0) return AGS_OK;
+  if (!out || !out_seg) return invalid("output pointer is NULL");
+  DeviceGuard g(sc->ctx->device);
+  std::vector<float4> verts(v1 - v0);
+  std::vector<int32_t> idx(3 * n);
+  cudaStream_t s = sc->ctx->stream;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(verts.data(), sc->d.world_verts + v0, verts.size() * sizeof(float4), cudaMemcpyDeviceToHost,
+                           s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(idx.data(), sc->d.tri_vidx + 3 * f0, idx.size() * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                           s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cuda_fail(e, "world triangle readback");
+  for (int64_t t = 0; t < n; ++t)
+    for (int c = 0; c < 3; ++c) {
+      const float4& v = verts[idx[3 * t + c] - v0];
+      out[9 * t + 3 * c] = v.x;
+      out[9 * t + 3 * c + 1] = v.y;
+      out[9 * t + 3 * c + 2] = v.z;
+    }
+  for (int64_t j = sc->env_sub_off[env]; j < sc->env_sub_off[env + 1]; ++j)
+    for (int64_t t = sc->sub_tri_off[j]; t < sc->sub_tri_off[j + 1]; ++t) out_seg[t - f0] = sc->sub_seg[j];
+  return AGS_OK;
+  AGS_API_END
+}
+
+ags_status ags_scene_stats(const ags_scene* sc, int32_t env, int64_t* n_tris, int64_t* n_nodes, int64_t* bytes) {
+  AGS_API_BEGIN
+  if (!sc) return invalid("scene is NULL");
+  if (env < -1 || env >= sc->n_envs) return invalid("env out of range");
+  int64_t t, nd;
+  if (env == -1) {
+    t = sc->n_tris;
+    nd = sc->n_nodes;
+  } else {
+    t = sc->env_tri_off[env + 1] - sc->env_tri_off[env];
+    nd = sc->env_nodes[env];
+  }
+  if (n_tris) *n_tris = t;
+  if (n_nodes) *n_nodes = nd;
+  if (bytes) *bytes = nd * (int64_t)sizeof(WideNode) + t * kTriFloat4 * (int64_t)sizeof(float4);
+  return AGS_OK;
+  AGS_API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,133 @@
+// Internal declarations of the GB300 ray-cast renderer (product code only).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/ags.h"
+
+namespace ags {
+
+// ----------------------------------------------------------------- wide BVH
+// 8-wide node, float32 child boxes in structure-of-arrays order so a thread
+// reads a whole node with 13 aligned 16-byte loads. Children that are inner
+// nodes are stored contiguously from child_base; the triangles of all leaf
+// children are stored contiguously from tri_base.
+// meta[k] (byte k of meta_lo/meta_hi): 0xFF empty slot; 0x80 | r inner child
+// child_base + r; otherwise a leaf of (meta & 3) + 1 triangles starting at
+// tri_base + (meta >> 2).
+struct __align__(16) WideNode {
+  int32_t child_base;
+  int32_t tri_base;
+  uint32_t meta_lo;
+  uint32_t meta_hi;
+  float lox[8], hix[8], loy[8], hiy[8], loz[8], hiz[8];
+};
+static_assert(sizeof(WideNode) == 208, "WideNode layout");
+
+constexpr int kMaxLeafTris = 4;  // triangles per wide-BVH leaf (2-bit count field)
+constexpr uint8_t kMetaEmpty = 0xFF;
+constexpr float kEmptyBoxCoord = 1e30f;  // empty slots hold a far-away point box
+
+// Packed triangle: three float4, xyz = world vertex; w of the first holds the
+// segment ID bits, w of the second the triangle's index within its
+// environment (tie-break key), w of the third is unused.
+constexpr int kTriFloat4 = 3;
+
+// device status word bits
+constexpr int kStatusStackOverflow = 1;
+constexpr int kStatusIterationCap = 2;
+
+// ----------------------------------------------------------------- scene
+struct SceneDevice {
+  float4* world_verts = nullptr;   // [V] xyz world, w 0
+  int32_t* tri_vidx = nullptr;     // [3F] global vertex indices (input order)
+  WideNode* nodes = nullptr;       // [n_nodes]
+  float4* tris = nullptr;          // [3F] packed, BVH leaf order
+  int32_t* env_root = nullptr;     // [E] root node index, -1 if empty
+};
+
+struct Box {
+  float lox, loy, loz, hix, hiy, hiz;
+};
+
+}  // namespace ags
+
+struct ags_context {
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t stream = nullptr;       // internal stream for builds and host renders
+  int* d_status = nullptr;             // device status word
+  unsigned long long* d_counts = nullptr;  // [3] counters for ags_render_count
+  std::map<cudaStream_t, unsigned int*> tile_counters;
+  int trace_blocks = 0;                // persistent grid size
+  int trace_count_blocks = 0;
+  // staging for ags_render_host
+  void* stage = nullptr;
+  size_t stage_bytes = 0;
+};
+
+struct ags_scene {
+  ags_context* ctx = nullptr;
+  int32_t n_envs = 0;
+  int64_t n_tris = 0, n_verts = 0, n_subs = 0, n_nodes = 0;
+  uint32_t flags = 0;
+  ags::SceneDevice d;
+  std::vector<int64_t> env_tri_off;    // [E+1]
+  std::vector<int64_t> env_vert_off;   // [E+1]
+  std::vector<int64_t> env_sub_off;    // [E+1]
+  std::vector<int64_t> sub_tri_off;    // [J+1]
+  std::vector<int32_t> sub_seg;        // [J]
+  std::vector<int64_t> env_nodes;      // [E]
+};
+
+namespace ags {
+
+void set_error(const std::string& msg);
+ags_status cuda_fail(cudaError_t e, const char* what);
+
+// radix_sort.cu: stable LSD sort of (key, value) pairs over bits [0, end_bit).
+// keys/vals hold the input and receive the output; alt_* are scratch of the
+// same size. temp must hold sort_temp_bytes(n) bytes.
+size_t sort_temp_bytes(int64_t n);
+cudaError_t sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* alt_keys, uint32_t* alt_vals,
+                       int64_t n, int end_bit, void* temp, cudaStream_t s);
+// exclusive scan of n int32 values in place; returns the total in *total_dev (device int)
+size_t scan_temp_bytes(int64_t n);
+cudaError_t exclusive_scan(int32_t* data, int64_t n, int32_t* total_dev, void* temp, cudaStream_t s);
+
+// build.cu
+ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_h,
+                       const int32_t* tri_vidx_h, const int32_t* sub_vert_off_h,
+                       const float* poses_h, const int32_t* sub_env_h);
+
+// trace.cu
+struct TraceArgs {
+  const WideNode* nodes;
+  const float4* tris;
+  const int32_t* env_root;
+  const int32_t* env_ids;    // nullable
+  const float* poses;        // [n][7]
+  float* out_depth;          // [n][H][W]
+  int32_t* out_seg;
+  int32_t n;                 // environments rendered
+  int32_t W, H;
+  int32_t type;
+  int32_t near_mode;
+  float inv_f;               // camera: 1/f
+  float hfov, vmax, dv;      // LiDAR: azimuth span, top elevation, elevation step
+  float min_range, max_range;
+  int32_t tiles_x, tiles_per_env;
+  int64_t total_tiles;
+  unsigned int* tile_counter;
+  int* status;
+  unsigned long long* counts;
+};
+cudaError_t launch_trace(const TraceArgs& a, int blocks, bool count, cudaStream_t s);
+int trace_blocks_per_sm(bool count);
+
+}  // namespace ags

@@ -1,0 +1,63 @@
+"""The C-ABI library loads and exports every symbol include/ags.h declares (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2503_01471_gb300 as ags
+from paper_2503_01471_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^[A-Za-z_][\w\s\*]*?\b(ags_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return ags.lib()
+
+
+def test_header_declares_the_binding_names():
+    assert declared_functions() == sorted(ags.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_struct_layouts_match_the_header():
+    assert ctypes.sizeof(ags.ags_submesh) == 32
+    assert ctypes.sizeof(ags.ags_env_mesh) == 16
+    assert ctypes.sizeof(ags.ags_sensor_spec) == 40
+
+
+def test_null_arguments_are_rejected_without_a_device(lib):
+    spec = ags.ags_sensor_spec(0, 4, 4, 1.0, 0, 0, 0.1, 10.0, 0, 0)
+    assert lib.ags_render(None, None, ctypes.byref(spec), None, None, None, None) == ags.AGS_ERR_INVALID_ARG
+    assert "NULL" in ags.ags_last_error()
+    h = ctypes.c_void_p()
+    assert lib.ags_scene_build(None, None, 1, None, 0, ctypes.byref(h)) == ags.AGS_ERR_INVALID_ARG
+    assert lib.ags_scene_n_envs(None) == -1
+
+
+def test_context_on_a_missing_device_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    st = lib.ags_context_create(0, ctypes.byref(h))
+    assert st in (ags.AGS_ERR_CUDA, ags.AGS_ERR_INVALID_ARG)
+    assert h.value is None
+    assert ags.ags_last_error() != ""

@@ -1,0 +1,253 @@
+"""CUDA renderer vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerance (from the benchmark spec of the method's accuracy): |depth - oracle|
+<= 1e-5 * depth + 1e-6 m on every ray whose outcome is unique; misses exactly
+max_range with segment -1; segment IDs exact. Rays where several outcomes are
+correct within the float32 error bands (edges, near ties, range limits) must
+match one of the outcomes the oracle lists for them, and are counted.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_2503_01471_gb300 as ags
+from paper_2503_01471_gb300 import build as B
+from paper_2503_01471_gb300 import scenes as S
+
+from helpers import compare_env, describe_failures, oracle_env
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    B.build()
+    c = ags.ags_context_create(0)
+    yield c
+    ags.ags_context_destroy(c)
+
+
+def render(ctx, scene, spec, poses):
+    E = poses.shape[0]
+    p = torch.as_tensor(np.ascontiguousarray(poses, np.float32)).cuda()
+    depth = torch.empty((E, spec.height, spec.width), dtype=torch.float32, device="cuda")
+    seg = torch.empty((E, spec.height, spec.width), dtype=torch.int32, device="cuda")
+    ags.ags_render(ctx, scene, spec, p, depth, seg)
+    ags.ags_stream_status(ctx)
+    return depth.cpu().numpy(), seg.cpu().numpy()
+
+
+def check_all(batch, spec, poses, depth, seg, envs=None, rays=None):
+    envs = range(batch.n_envs) if envs is None else envs
+    n_ok = n_cnt = n = 0
+    for e in envs:
+        ok, counted, res = compare_env(batch, e, spec, poses[e], depth[e], seg[e], rays)
+        rr = np.arange(spec.width * spec.height) if rays is None else rays
+        assert ok.all(), f"env {e}: {int((~ok).sum())} rays off\n" + describe_failures(
+            ok, res, depth[e].reshape(-1)[rr], seg[e].reshape(-1)[rr], rr)
+        n += ok.size
+        n_cnt += int(counted.sum())
+    return n, n_cnt
+
+
+# ---------------------------------------------------------------- a1
+def test_transform_within_one_ulp(ctx):
+    rng = np.random.default_rng(5)
+    envs = []
+    for e in range(3):
+        objs = []
+        for k in range(20):
+            v = rng.uniform(-3, 3, (30, 3)).astype(np.float32)
+            f = rng.integers(0, 30, (10, 3)).astype(np.int32)
+            q = rng.normal(size=4) * rng.uniform(0.2, 3.0)  # non-unit on purpose
+            p = rng.uniform(-20, 20, 3)
+            objs.append((v, f, np.concatenate([p, q]).astype(np.float32), k))
+        objs.append((rng.uniform(-9, 9, (5, 3)).astype(np.float32), np.array([[0, 1, 2], [2, 3, 4]], np.int32),
+                     S.IDENTITY_POSE, 99))
+        envs.append(objs)
+    batch = S.scene_from_lists(envs)
+    scene = ags.ags_scene_build(ctx, batch)
+    try:
+        for e in range(batch.n_envs):
+            gpu, gseg = ags.ags_scene_get_world_triangles(scene, e)
+            ref, rseg = oracle_env(batch, e)
+            assert np.array_equal(gseg, rseg)
+            ulp = np.spacing(np.maximum(np.abs(ref), 1.0).astype(np.float32)).astype(np.float64)
+            err = np.abs(gpu.astype(np.float64) - ref) / ulp
+            assert err.max() <= 1.0, err.max()
+            # identity pose: bit-exact
+            assert np.array_equal(gpu[-2:], ref[-2:].astype(np.float32))
+    finally:
+        ags.ags_scene_destroy(scene)
+
+
+# ---------------------------------------------------------------- tiny room: every ray
+def test_tiny_room_all_rays(ctx):
+    batch, spec, poses = S.tiny_room()
+    scene = ags.ags_scene_build(ctx, batch)
+    try:
+        n = cnt = 0
+        for k in range(poses.shape[0]):
+            d, s = render(ctx, scene, spec, poses[k:k + 1])
+            a, b = check_all(batch, spec, poses[k:k + 1], d, s)
+            n += a
+            cnt += b
+        assert n == 16 * 64 * 48
+        print(f"tiny room: {n} rays, {cnt} counted")
+    finally:
+        ags.ags_scene_destroy(scene)
+
+
+# ---------------------------------------------------------------- obstacle rooms: every ray, ragged tiles
+@pytest.mark.parametrize("W,H", [(96, 72), (13, 7), (1, 1)])
+def test_obstacle_rooms_all_rays(ctx, W, H):
+    batch, spec, poses = S.obstacle_rooms(4, steps=2, width=W, height=H)
+    scene = ags.ags_scene_build(ctx, batch)
+    try:
+        for step in range(2):
+            d, s = render(ctx, scene, spec, poses[step])
+            n, cnt = check_all(batch, spec, poses[step], d, s)
+            print(f"rooms {W}x{H} step {step}: {n} rays, {cnt} counted")
+    finally:
+        ags.ags_scene_destroy(scene)
+
+
+# ---------------------------------------------------------------- LiDAR forest
+def test_lidar_forest_all_rays(ctx):
+    batch, spec, poses = S.lidar_forests(2, steps=1, trees=(6, 10), tris=(2000, 3000))
+    spec.width = 256
+    scene = ags.ags_scene_build(ctx, batch)
+    try:
+        d, s = render(ctx, scene, spec, poses[0])
+        n, cnt = check_all(batch, spec, poses[0], d, s)
+        hit = (s >= 0).mean()
+        assert hit > 0.3
+        print(f"lidar: {n} rays, {cnt} counted, hit fraction {hit:.2f}")
+    finally:
+        ags.ags_scene_destroy(scene)
+
+
+# ---------------------------------------------------------------- full size, sampled
+def test_full_size_1024_envs_sampled(ctx):
+    """1024 rooms x 270x480 in the launch configuration the benchmark times; oracle on samples."""
+    batch, spec, poses = S.obstacle_rooms(1024, steps=1)
+    scene = ags.ags_scene_build(ctx, batch)
+    try:
+        d, s = render(ctx, scene, spec, poses[0])
+        assert np.isfinite(d).all()
+        rng = np.random.default_rng(99)
+        n_pix = spec.width * spec.height
+        total = cnt = 0
+        for e in range(batch.n_envs):
+            k = 256 if e in (0, 511, 1023) else 8
+            rays = np.sort(rng.choice(n_pix, k, replace=False)).astype(np.int64)
+            a, b = check_all(batch, spec, poses[0], d, s, envs=[e], rays=rays)
+            total += a
+            cnt += b
+        print(f"full size: {total} sampled rays, {cnt} counted")
+        # properties that hold for every ray
+        assert (d[s == -1] == np.float32(spec.max_range)).all()
+        assert ((d >= np.float32(spec.min_range)) & (d <= np.float32(spec.max_range))).all()
+    finally:
+        ags.ags_scene_destroy(scene)
+
+
+# ---------------------------------------------------------------- edge cases
+def test_empty_and_single_triangle_envs(ctx):
+    tri = (np.array([[3, -3, -3], [3, 3, -3], [3, 0, 3]], np.float32), np.array([[0, 1, 2]], np.int32),
+           S.IDENTITY_POSE, 7)
+    batch = S.scene_from_lists([[], [tri], [tri, tri]])
+    spec = S.pinhole(3, 3, 90.0, 0.1, 10.0)
+    poses = np.tile(S.IDENTITY_POSE, (3, 1))
+    scene = ags.ags_scene_build(ctx, batch)
+    try:
+        d, s = render(ctx, scene, spec, poses)
+        assert (s[0] == -1).all() and (d[0] == np.float32(10.0)).all()
+        want = np.array([[-1, 7, -1], [-1, 7, -1], [7, 7, 7]])
+        assert np.array_equal(s[1], want) and np.array_equal(s[2], want)
+        assert np.allclose(d[1][want == 7], 3.0, rtol=1e-6)
+        check_all(batch, spec, poses, d, s, envs=[1, 2])
+        t, n, b = ags.ags_scene_stats(scene, 0)
+        assert (t, n, b) == (0, 0, 0)
+    finally:
+        ags.ags_scene_destroy(scene)
+
+
+def test_near_modes_and_host_path(ctx):
+    batch, spec, poses = S.obstacle_rooms(3, steps=1, width=40, height=30)
+    scene = ags.ags_scene_build(ctx, batch)
+    try:
+        for mode, mn in ((ags.AGS_NEAR_CLAMP, 1.5), (ags.AGS_NEAR_INVALID, 1.5)):
+            spec.near_mode, spec.min_range = mode, mn
+            d, s = render(ctx, scene, spec, poses[0])
+            check_all(batch, spec, poses[0], d, s)
+            hd, hs = ags.ags_render_host(ctx, scene, spec, np.ascontiguousarray(poses[0]))
+            assert np.array_equal(hd, d) and np.array_equal(hs, s)
+    finally:
+        ags.ags_scene_destroy(scene)
+
+
+def test_subset_render_matches_full(ctx):
+    batch, spec, poses = S.obstacle_rooms(6, steps=1, width=32, height=24)
+    scene = ags.ags_scene_build(ctx, batch)
+    try:
+        d, s = render(ctx, scene, spec, poses[0])
+        ids = torch.tensor([4, 1, 1, 5], dtype=torch.int32, device="cuda")
+        p = torch.as_tensor(poses[0][[4, 1, 1, 5]]).cuda()
+        dd = torch.empty((4, 24, 32), device="cuda")
+        ss = torch.empty((4, 24, 32), dtype=torch.int32, device="cuda")
+        ags.ags_render_envs(ctx, scene, spec, ids, p, dd, ss)
+        ags.ags_stream_status(ctx)
+        assert np.array_equal(dd.cpu().numpy(), d[[4, 1, 1, 5]])
+        assert np.array_equal(ss.cpu().numpy(), s[[4, 1, 1, 5]])
+        rays, nodes, tris = ags.ags_render_count(ctx, scene, spec, torch.as_tensor(poses[0]).cuda())
+        assert rays == 6 * 24 * 32 and nodes >= rays and tris > 0
+    finally:
+        ags.ags_scene_destroy(scene)
+
+
+def test_deterministic_repeat(ctx):
+    batch, spec, poses = S.obstacle_rooms(8, steps=1, width=64, height=48)
+    scene = ags.ags_scene_build(ctx, batch)
+    try:
+        a = render(ctx, scene, spec, poses[0])
+        b = render(ctx, scene, spec, poses[0])
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        scene2 = ags.ags_scene_build(ctx, batch)
+        c = render(ctx, scene2, spec, poses[0])
+        ags.ags_scene_destroy(scene2)
+        assert np.array_equal(a[0], c[0]) and np.array_equal(a[1], c[1])
+    finally:
+        ags.ags_scene_destroy(scene)
+
+
+def test_host_validation_errors(ctx):
+    v = np.zeros((3, 3), np.float32)
+    bad_idx = S.scene_from_lists([[(v, np.array([[0, 1, 3]], np.int32), S.IDENTITY_POSE, 0)]])
+    with pytest.raises(ags.AgsError, match="out of range"):
+        ags.ags_scene_build(ctx, bad_idx)
+    nan_pose = S.IDENTITY_POSE.copy()
+    nan_pose[0] = np.nan
+    with pytest.raises(ags.AgsError, match="non-finite pose"):
+        ags.ags_scene_build(ctx, S.scene_from_lists([[(v, np.array([[0, 1, 2]], np.int32), nan_pose, 0)]]))
+    zq = np.zeros(7, np.float32)
+    with pytest.raises(ags.AgsError, match="zero length"):
+        ags.ags_scene_build(ctx, S.scene_from_lists([[(v, np.array([[0, 1, 2]], np.int32), zq, 0)]]))
+    with pytest.raises(ags.AgsError, match="segment_id"):
+        ags.ags_scene_build(ctx, S.scene_from_lists([[(v, np.array([[0, 1, 2]], np.int32), S.IDENTITY_POSE, -3)]]))
+    batch, spec, poses = S.obstacle_rooms(1, steps=1, width=8, height=8)
+    scene = ags.ags_scene_build(ctx, batch)
+    try:
+        p = torch.as_tensor(poses[0]).cuda()
+        out = torch.empty((1, 8, 8), device="cuda")
+        seg = torch.empty((1, 8, 8), dtype=torch.int32, device="cuda")
+        for field, val in (("width", 0), ("max_range", 0.1), ("hfov", 4.0), ("type", 7)):
+            bad = S.pinhole(8, 8)
+            setattr(bad, field, val)
+            with pytest.raises(ags.AgsError) as ei:
+                ags.ags_render(ctx, scene, bad, p, out, seg)
+            assert ei.value.status == ags.AGS_ERR_INVALID_ARG
+        assert ags.ags_stream_status(ctx) == ags.AGS_OK
+    finally:
+        ags.ags_scene_destroy(scene)
