@@ -53,7 +53,8 @@ typedef enum {
   AGS_ERR_INVALID_ARG = 1,    /* bad pointer, size, index, pose or spec */
   AGS_ERR_OUT_OF_MEMORY = 2,  /* device or host allocation failed */
   AGS_ERR_CUDA = 3,           /* a CUDA runtime call failed */
-  AGS_ERR_TRAVERSAL_LIMIT = 4,/* a ray hit the stack or iteration limit; its output is NaN */
+  AGS_ERR_TRAVERSAL_LIMIT = 4,/* a ray hit the stack or iteration limit, or met an out-of-range
+                                 index; that ray's output is NaN */
   AGS_ERR_NOT_READY = 5,
   AGS_ERR_BUSY = 6
 } ags_status;

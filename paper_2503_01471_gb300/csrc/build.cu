@@ -377,10 +377,21 @@ __global__ void k_collapse_expand(const QueueItem* __restrict__ items, int32_t n
                                   const int32_t* __restrict__ left, const int32_t* __restrict__ right,
                                   const int32_t* __restrict__ first, const int32_t* __restrict__ last,
                                   const Box* __restrict__ inner_box, int leaf_max, int32_t* __restrict__ slots,
-                                  int32_t* __restrict__ n_inner, int32_t* __restrict__ n_leaf_tris) {
+                                  int32_t* __restrict__ n_inner, int32_t* __restrict__ n_leaf_tris, int32_t F,
+                                  int* __restrict__ err) {
   int32_t it = blockIdx.x * blockDim.x + threadIdx.x;
   if (it >= n_items) return;
   int32_t ref = items[it].ref;
+  // every reference must name a node or leaf of this build; anything else is
+  // reported instead of being followed
+  auto bad = [&](int32_t r) { return r >= 0 ? r >= F : ~r >= F; };
+  if (bad(ref)) {
+    atomicOr(err, 1);
+    slots[8 * (int64_t)it] = kSlotEmpty;
+    n_inner[it] = 0;
+    n_leaf_tris[it] = 0;
+    return;
+  }
   int32_t s[8];
   int ns = 0;
   if (ref >= 0) {
@@ -390,6 +401,10 @@ __global__ void k_collapse_expand(const QueueItem* __restrict__ items, int32_t n
   } else {
     s[0] = ref;
     ns = 1;
+  }
+  if (bad(s[0]) || (ns == 2 && bad(s[1]))) {
+    atomicOr(err, 1);
+    ns = 0;
   }
   while (ns < 8) {
     int best = -1;
@@ -406,6 +421,10 @@ __global__ void k_collapse_expand(const QueueItem* __restrict__ items, int32_t n
     }
     if (best < 0) break;
     int32_t r = s[best];
+    if (bad(left[r]) || bad(right[r])) {
+      atomicOr(err, 1);
+      break;
+    }
     s[best] = left[r];
     s[ns++] = right[r];
   }
@@ -637,6 +656,9 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
   AGS_CHECK(tmp.alloc(&d_q, (size_t)q_cap));
   AGS_CHECK(tmp.alloc(&d_q2, (size_t)q_cap));
   int32_t *d_slots, *d_ninner, *d_ntris, *d_perm, *d_tot;
+  int* d_err = nullptr;
+  AGS_CHECK(tmp.alloc(&d_err, 1));
+  AGS_CHECK(cudaMemsetAsync(d_err, 0, sizeof(int), s));
   AGS_CHECK(tmp.alloc(&d_slots, 8 * (size_t)q_cap));
   AGS_CHECK(tmp.alloc(&d_ninner, (size_t)q_cap));
   AGS_CHECK(tmp.alloc(&d_ntris, (size_t)q_cap));
@@ -658,13 +680,23 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
       return AGS_ERR_CUDA;
     }
     k_collapse_expand<<<blocks_for(n_items, 128), 128, 0, s>>>(d_q, n_items, d_left, d_right, d_first, d_last,
-                                                              d_inner_box, kMaxLeafTris, d_slots, d_ninner, d_ntris);
+                                                              d_inner_box, kMaxLeafTris, d_slots, d_ninner, d_ntris,
+                                                              F, d_err);
     AGS_CHECK(cudaGetLastError());
     AGS_CHECK(exclusive_scan(d_ninner, n_items, d_tot, d_scan_tmp, s));
     AGS_CHECK(exclusive_scan(d_ntris, n_items, d_tot + 1, d_scan_tmp, s));
-    int32_t tot[2];
+    int32_t tot[3];
     AGS_CHECK(cudaMemcpyAsync(tot, d_tot, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    AGS_CHECK(cudaMemcpyAsync(tot + 2, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     AGS_CHECK(cudaStreamSynchronize(s));
+    if (tot[2] != 0) {
+      set_error("BVH collapse met an out-of-range node reference");
+      return AGS_ERR_CUDA;
+    }
+    if (tot[0] < 0 || tot[1] < 0 || (int64_t)tri_level_base + tot[1] > F) {
+      set_error("BVH collapse produced inconsistent counts");
+      return AGS_ERR_CUDA;
+    }
     int32_t next_base = level_base + n_items;
     if ((int64_t)next_base + tot[0] > node_cap) {
       set_error("BVH node capacity exceeded");

@@ -69,6 +69,9 @@ ags_status fill_trace_args(ags_context* ctx, const ags_scene* sc, const ags_sens
   a.nodes = sc->d.nodes;
   a.tris = sc->d.tris;
   a.env_root = sc->d.env_root;
+  a.n_nodes = (int32_t)sc->n_nodes;
+  a.n_tris = (int32_t)sc->n_tris;
+  a.n_scene_envs = sc->n_envs;
   a.env_ids = env_ids;
   a.poses = poses;
   a.out_depth = depth;
@@ -325,7 +328,8 @@ ags_status ags_stream_status(ags_context* ctx, void* stream) {
     return cuda_fail(e, "status word");
   if (word != 0) {
     set_error(std::string("device traversal limit hit:") + ((word & kStatusStackOverflow) ? " stack" : "") +
-              ((word & kStatusIterationCap) ? " iterations" : ""));
+              ((word & kStatusIterationCap) ? " iterations" : "") +
+              ((word & kStatusBadIndex) ? " out-of-range index" : ""));
     return AGS_ERR_TRAVERSAL_LIMIT;
   }
   return AGS_OK;

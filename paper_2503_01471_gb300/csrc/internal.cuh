@@ -41,6 +41,7 @@ constexpr int kTriFloat4 = 3;
 // device status word bits
 constexpr int kStatusStackOverflow = 1;
 constexpr int kStatusIterationCap = 2;
+constexpr int kStatusBadIndex = 4;
 
 // ----------------------------------------------------------------- scene
 struct SceneDevice {
@@ -110,6 +111,9 @@ struct TraceArgs {
   const WideNode* nodes;
   const float4* tris;
   const int32_t* env_root;
+  int32_t n_nodes;           // bounds for the node and triangle indices read
+  int32_t n_tris;
+  int32_t n_scene_envs;
   const int32_t* env_ids;    // nullable
   const float* poses;        // [n][7]
   float* out_depth;          // [n][H][W]

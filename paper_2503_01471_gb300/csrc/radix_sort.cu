@@ -153,11 +153,11 @@ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 size_t scan_temp_bytes(int64_t n) {
   size_t bytes = 256;  // last value copy
-  int64_t m = n;
-  while (m > 1) {
+  int64_t m = n > 0 ? n : 1;
+  do {
     m = ceil_div(m, kScanTile);
     bytes += ((size_t)m * sizeof(int32_t) + 255) & ~size_t(255);
-  }
+  } while (m > 1);
   return bytes + 256;
 }
 
@@ -168,17 +168,18 @@ cudaError_t exclusive_scan(int32_t* data, int64_t n, int32_t* total_dev, void* t
   t += 256;
   cudaError_t e = cudaMemcpyAsync(last_copy, data + n - 1, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return e;
-  // levels of tile sums
+  // levels of tile sums; every level is scanned, down to a single tile
   std::vector<int32_t*> lv_data{data};
   std::vector<int64_t> lv_n{n};
-  while (lv_n.back() > 1) {
-    int64_t tiles = ceil_div(lv_n.back(), kScanTile);
+  int64_t tiles;
+  do {
+    tiles = ceil_div(lv_n.back(), kScanTile);
     int32_t* sums = reinterpret_cast<int32_t*>(t);
     t += ((size_t)tiles * sizeof(int32_t) + 255) & ~size_t(255);
     k_scan_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(lv_data.back(), lv_n.back(), sums);
     lv_data.push_back(sums);
     lv_n.push_back(tiles);
-  }
+  } while (tiles > 1);
   for (size_t l = lv_data.size() - 1; l-- > 1;) {
     // lv_data[l] scanned (exclusive) including its own tile sums added; add to level l-1
     k_scan_add<<<(unsigned)ceil_div(lv_n[l - 1], kScanTile), kScanThreads, 0, s>>>(lv_data[l - 1], lv_n[l - 1],

@@ -125,6 +125,10 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(const TraceArgs a) {
     const int32_t slot = (int32_t)(tile / (unsigned)a.tiles_per_env);
     const int32_t t_in = (int32_t)(tile - (unsigned)slot * (unsigned)a.tiles_per_env);
     const int32_t env = a.env_ids ? __ldg(a.env_ids + slot) : slot;
+    if ((unsigned)env >= (unsigned)a.n_scene_envs) {
+      if (lane == 0) atomicOr(a.status, kStatusBadIndex);
+      continue;
+    }
     const int32_t col = (t_in % a.tiles_x) * kTileW + (lane & (kTileW - 1));
     const int32_t row = (t_in / a.tiles_x) * kTileH + (lane >> 3);
     if (col >= a.W || row >= a.H) continue;
@@ -172,6 +176,11 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(const TraceArgs a) {
         failed = true;
         break;
       }
+      if (node >= a.n_nodes) {
+        atomicOr(status, kStatusBadIndex);
+        failed = true;
+        break;
+      }
       if (kCount) ++n_nodes;
       const float4* np = reinterpret_cast<const float4*>(a.nodes + node);
       const float4 h = __ldg(np);
@@ -211,9 +220,15 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(const TraceArgs a) {
         const uint32_t m = ((k < 4 ? meta_lo : meta_hi) >> (8 * (k & 3))) & 0xFFu;
         const int32_t start = tri_base + (int32_t)(m >> 2);
         const int32_t cnt = (int32_t)(m & 3u) + 1;
+        if (start < 0 || start + cnt > a.n_tris) {
+          atomicOr(status, kStatusBadIndex);
+          failed = true;
+          break;
+        }
         for (int32_t x = 0; x < cnt; ++x) test_triangle(r, a.tris, start + x, t_best, best_id, best_seg);
         if (kCount) n_tris += cnt;
       }
+      if (failed) break;
       // inner children, nearest first (sorting network on packed keys)
 #define AGS_CSWAP(i, j)                      \
   {                                          \
