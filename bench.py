@@ -278,6 +278,7 @@ def bench_ours(args, rank, world, local):
     pin_depth = torch.empty((E, spec.height, spec.width), dtype=torch.float32).pin_memory()
     pin_seg = torch.empty((E, spec.height, spec.width), dtype=torch.int32).pin_memory()
     host_poses = poses
+    pin_pose.numpy()[:] = host_poses[0]
     ags.ags_render_host(ctx, scene, spec, pin_pose.numpy(), pin_depth.numpy(), pin_seg.numpy())  # warm staging
     if dist is not None:
         dist.barrier()

@@ -160,9 +160,16 @@ ags_status ags_render_count(ags_context* ctx, const ags_scene* scene, const ags_
                             const float* sensor_poses_dev, uint64_t counts_host[3]);
 
 /* Synchronise `cuda_stream`, then read and clear the context's device status
- * word: AGS_OK, or AGS_ERR_TRAVERSAL_LIMIT if any ray since the last call hit
- * a limit, or AGS_ERR_CUDA. */
+ * word: AGS_OK; AGS_ERR_INVALID_ARG if a device sensor pose was non-finite or
+ * had a zero quaternion (those rays report NaN, segment -1);
+ * AGS_ERR_TRAVERSAL_LIMIT if any ray since the last call hit a limit; or
+ * AGS_ERR_CUDA. */
 ags_status ags_stream_status(ags_context* ctx, void* cuda_stream);
+
+/* Cap on the BVH nodes one ray may visit (default 1048576). A ray that reaches
+ * it stops, reports NaN / segment -1 and makes the next ags_stream_status
+ * return AGS_ERR_TRAVERSAL_LIMIT. Values below 1 are rejected. */
+ags_status ags_context_set_traversal_cap(ags_context* ctx, int32_t max_node_visits);
 
 /* Thread-local text of the last error ("" if none). */
 const char* ags_last_error(void);

@@ -42,11 +42,13 @@ NEAR_CLAMP = 0
 NEAR_INVALID = 1
 
 # Error bands of the float32 renderer being judged: world vertex coordinates
-# within VERT_REL * max(|x|, 1) of exact (4 units in the last place), ray
-# directions within DIR_REL (relative), and intersection arithmetic that moves
-# the ray sideways by at most ARITH_REL times the distance to the vertices.
-VERT_REL = 4.0 * 2.0 ** -23
-DIR_REL = 1e-6
+# within VERT_REL * max(|x|, 1) of exact (one unit in the last place, the bound
+# the transform test holds the renderer to), ray directions within DIR_REL
+# (relative; a float32 rotation of the pixel direction is good to ~4e-7), and
+# intersection arithmetic that moves the ray sideways by at most ARITH_REL
+# times the distance to the vertices.
+VERT_REL = 2.0 ** -23
+DIR_REL = 6e-7
 ARITH_REL = 4.0 * 2.0 ** -24
 
 

@@ -40,6 +40,7 @@ EXPORTS = [
     "ags_context_create", "ags_context_destroy", "ags_scene_build", "ags_scene_destroy", "ags_render",
     "ags_render_envs", "ags_render_host", "ags_render_count", "ags_stream_status", "ags_last_error",
     "ags_scene_n_envs", "ags_scene_get_world_triangles", "ags_scene_stats", "ags_scene_node_bytes",
+    "ags_context_set_traversal_cap",
 ]
 
 
@@ -102,6 +103,7 @@ def lib() -> ctypes.CDLL:
         "ags_scene_get_world_triangles": (i32, [vp, i32, vp, vp, i64]),
         "ags_scene_stats": (i32, [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "ags_scene_node_bytes": (i32, [vp]),
+        "ags_context_set_traversal_cap": (i32, [vp, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -163,6 +165,10 @@ def ags_context_create(device: int = 0) -> int:
 
 def ags_context_destroy(ctx: int) -> None:
     lib().ags_context_destroy(ctx)
+
+
+def ags_context_set_traversal_cap(ctx: int, max_node_visits: int) -> None:
+    _check(lib().ags_context_set_traversal_cap(ctx, int(max_node_visits)), "ags_context_set_traversal_cap")
 
 
 # ---------------------------------------------------------------- scene

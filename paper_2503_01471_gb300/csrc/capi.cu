@@ -96,6 +96,7 @@ ags_status fill_trace_args(ags_context* ctx, const ags_scene* sc, const ags_sens
   a.total_tiles = total;
   a.status = ctx->d_status;
   a.counts = ctx->d_counts;
+  a.max_visits = ctx->max_node_visits;
   return AGS_OK;
 }
 
@@ -180,6 +181,13 @@ void ags_context_destroy(ags_context* ctx) {
   cudaFree(ctx->stage);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
+}
+
+ags_status ags_context_set_traversal_cap(ags_context* ctx, int32_t max_node_visits) {
+  if (!ctx) return invalid("ctx is NULL");
+  if (max_node_visits < 1) return invalid("max_node_visits must be >= 1");
+  ctx->max_node_visits = max_node_visits;
+  return AGS_OK;
 }
 
 ags_status ags_scene_build(ags_context* ctx, const ags_env_mesh* envs, int32_t n_envs, const float* obstacle_poses,
@@ -326,6 +334,10 @@ ags_status ags_stream_status(ags_context* ctx, void* stream) {
       (e = cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
     return cuda_fail(e, "status word");
+  if (word & kStatusBadPose) {
+    set_error("a sensor pose was not finite or had a zero-length quaternion; its rays are NaN");
+    return AGS_ERR_INVALID_ARG;
+  }
   if (word != 0) {
     set_error(std::string("device traversal limit hit:") + ((word & kStatusStackOverflow) ? " stack" : "") +
               ((word & kStatusIterationCap) ? " iterations" : "") +

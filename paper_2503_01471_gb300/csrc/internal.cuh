@@ -42,6 +42,7 @@ constexpr int kTriFloat4 = 3;
 constexpr int kStatusStackOverflow = 1;
 constexpr int kStatusIterationCap = 2;
 constexpr int kStatusBadIndex = 4;
+constexpr int kStatusBadPose = 8;
 
 // ----------------------------------------------------------------- scene
 struct SceneDevice {
@@ -66,6 +67,7 @@ struct ags_context {
   unsigned long long* d_counts = nullptr;  // [3] counters for ags_render_count
   std::map<cudaStream_t, unsigned int*> tile_counters;
   int trace_blocks = 0;                // persistent grid size
+  int32_t max_node_visits = 1 << 20;   // per-ray traversal cap
   int trace_count_blocks = 0;
   // staging for ags_render_host
   void* stage = nullptr;
@@ -127,6 +129,7 @@ struct TraceArgs {
   float min_range, max_range;
   int32_t tiles_x, tiles_per_env;
   int64_t total_tiles;
+  int32_t max_visits;
   unsigned int* tile_counter;
   int* status;
   unsigned long long* counts;

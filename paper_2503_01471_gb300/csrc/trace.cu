@@ -14,7 +14,6 @@ namespace {
 constexpr int kTraceThreads = 128;
 constexpr int kStackSize = 64;
 constexpr int kTileW = 8, kTileH = 4;
-constexpr int kMaxNodeVisits = 1 << 20;
 // Box culling is made conservative against float32 rounding: the slab exit
 // is scaled up by (1 + 2 gamma_3) and the current nearest hit by (1 + 2^-12),
 // so a box holding the eventual nearest triangle is never skipped.
@@ -137,7 +136,18 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(const TraceArgs a) {
     const float* P = a.poses + 7 * (int64_t)slot;
     const float px = __ldg(P), py = __ldg(P + 1), pz = __ldg(P + 2);
     const float qx = __ldg(P + 3), qy = __ldg(P + 4), qz = __ldg(P + 5), qw = __ldg(P + 6);
-    const float s = 2.0f / (qx * qx + qy * qy + qz * qz + qw * qw);
+    const float n2 = qx * qx + qy * qy + qz * qz + qw * qw;
+    if (!(n2 >= 1e-30f) || !isfinite(n2) || !isfinite(px + py + pz)) {
+      // a pose the method cannot use: flag it and report NaN for this ray
+      atomicOr(status, kStatusBadPose);
+      if (!kCount) {
+        const int64_t o = ((int64_t)slot * a.H + row) * a.W + col;
+        a.out_depth[o] = __int_as_float(0x7fc00000);
+        a.out_seg[o] = -1;
+      }
+      continue;
+    }
+    const float s = 2.0f / n2;
     const float R00 = 1.0f - s * (qy * qy + qz * qz), R01 = s * (qx * qy - qz * qw), R02 = s * (qx * qz + qy * qw);
     const float R10 = s * (qx * qy + qz * qw), R11 = 1.0f - s * (qx * qx + qz * qz), R12 = s * (qy * qz - qx * qw);
     const float R20 = s * (qx * qz - qy * qw), R21 = s * (qy * qz + qx * qw), R22 = 1.0f - s * (qx * qx + qy * qy);
@@ -171,7 +181,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(const TraceArgs a) {
     int sp = 0, visits = 0;
     bool failed = false;
     while (node >= 0) {
-      if (++visits > kMaxNodeVisits) {
+      if (++visits > a.max_visits) {
         atomicOr(status, kStatusIterationCap);
         failed = true;
         break;
@@ -208,7 +218,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(const TraceArgs a) {
           const float tmax = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1)) * kSlabSlack;
           const bool hit = tmin <= fminf(tmax, t_cull);
           const uint32_t m = (meta >> (8 * q)) & 0xFFu;
-          const bool inner = (m & 0x80u) != 0u;
+          const bool inner = (m & 0xF8u) == 0x80u;  // 0x80..0x87; 0xFF is an empty slot
           keys[k] = (hit && inner) ? ((__float_as_uint(tmin) & ~7u) | (m & 7u)) : 0xFFFFFFFFu;
           if (hit && !inner) leaf_mask |= 1u << k;
         }

@@ -251,3 +251,34 @@ def test_host_validation_errors(ctx):
         assert ags.ags_stream_status(ctx) == ags.AGS_OK
     finally:
         ags.ags_scene_destroy(scene)
+
+
+def test_device_limits_report_status_without_faulting(ctx):
+    """A tiny traversal cap and an unusable device pose end in an error status, not a fault."""
+    batch, spec, poses = S.obstacle_rooms(2, steps=1, width=16, height=12)
+    scene = ags.ags_scene_build(ctx, batch)
+    try:
+        ags.ags_context_set_traversal_cap(ctx, 1)
+        p = torch.as_tensor(poses[0]).cuda()
+        d = torch.empty((2, 12, 16), device="cuda")
+        s = torch.empty((2, 12, 16), dtype=torch.int32, device="cuda")
+        ags.ags_render(ctx, scene, spec, p, d, s)
+        with pytest.raises(ags.AgsError) as ei:
+            ags.ags_stream_status(ctx)
+        assert ei.value.status == ags.AGS_ERR_TRAVERSAL_LIMIT
+        assert torch.isnan(d).any()
+        ags.ags_context_set_traversal_cap(ctx, 1 << 20)
+        # context still usable; a zero quaternion is reported as invalid input
+        bad = p.clone()
+        bad[1, 3:] = 0.0
+        ags.ags_render(ctx, scene, spec, bad, d, s)
+        with pytest.raises(ags.AgsError) as ei:
+            ags.ags_stream_status(ctx)
+        assert ei.value.status == ags.AGS_ERR_INVALID_ARG
+        assert torch.isnan(d[1]).all() and (s[1] == -1).all() and not torch.isnan(d[0]).any()
+        ags.ags_render(ctx, scene, spec, p, d, s)
+        assert ags.ags_stream_status(ctx) == ags.AGS_OK
+        check_all(batch, spec, poses[0], d.cpu().numpy(), s.cpu().numpy())
+    finally:
+        ags.ags_context_set_traversal_cap(ctx, 1 << 20)
+        ags.ags_scene_destroy(scene)
