@@ -174,9 +174,10 @@ def cpu_baseline(batch, spec, poses, budget_s=12.0):
 
 
 # ---------------------------------------------------------------- workload
-def make_workload(args, rank):
+def make_workload(args, rank, world=1):
     from paper_2503_01471_gb300 import scenes as S
-    envs = range(rank * args.envs, (rank + 1) * args.envs)
+    from paper_2503_01471_gb300 import shard
+    envs = shard.weak_shard(args.envs, rank, max(world, rank + 1))
     batch, spec, poses = S.obstacle_rooms(args.envs, steps=args.walk, width=args.width, height=args.height,
                                           envs=list(envs) if rank else None)
     return batch, spec, poses
@@ -225,7 +226,7 @@ def bench_ours(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
 
-    batch, spec, poses = make_workload(args, rank)
+    batch, spec, poses = make_workload(args, rank, world)
     E = batch.n_envs
     ctx = ags.ags_context_create(local)
     t0 = time.perf_counter()
