@@ -171,6 +171,38 @@ ags_status ags_stream_status(ags_context* ctx, void* cuda_stream);
  * return AGS_ERR_TRAVERSAL_LIMIT. Values below 1 are rejected. */
 ags_status ags_context_set_traversal_cap(ags_context* ctx, int32_t max_node_visits);
 
+/*
+ * ags_transform_vertices_noalloc -- the object-to-world vertex transform of
+ * ags_scene_build (v' = R(q) v + p per sub-mesh, float-float arithmetic, within
+ * one unit in the last place) on caller-owned device buffers, without
+ * allocating any memory. The paper has no counterpart: this entry point exists
+ * for callers that cannot let a library call cudaMalloc -- a process whose
+ * device memory is reserved up front by its own allocator (a fixed serving
+ * memory plan, or a framework's caching allocator that owns the pool), or one
+ * that cannot afford the device-wide synchronisation a cudaMalloc may cause in
+ * the middle of its work.
+ * base_vertices_dev: device float32 [n_vertices][3], object frames.
+ * submesh_vertex_offsets_dev: device int32 [n_submeshes + 1], ascending, first
+ *   0, last n_vertices; sub-mesh j owns vertices [off[j], off[j+1]).
+ * poses_dev: device float32 [n_submeshes][7] (px, py, pz, qx, qy, qz, qw).
+ * world_vertices_dev: device float32 [n_vertices][4], 16-byte aligned; xyz =
+ *   world position, w = 0 (the layout the renderer keeps internally).
+ * Asynchronous on cuda_stream. Its per-sub-mesh scratch (18 floats each) is a
+ * fixed device array inside the library, sized for at most 65536 sub-meshes
+ * (4.5 MiB, held by every GPU that loads the library until the process
+ * exits); larger n_submeshes is rejected with AGS_ERR_INVALID_ARG. The first
+ * call on a device looks up that array's device address (once per device),
+ * so make that first call before any stream capture. All calls share the one
+ * array: calls that overlap on the GPU (other streams, other threads) race and
+ * must be serialised by the caller. Every scratch entry a call reads it first
+ * writes, so nothing has to be cleared between calls. No device memory is
+ * allocated; a successful call allocates no host memory either.
+ */
+ags_status ags_transform_vertices_noalloc(ags_context* ctx, const float* base_vertices_dev,
+                                          int32_t n_vertices, const int32_t* submesh_vertex_offsets_dev,
+                                          int32_t n_submeshes, const float* poses_dev,
+                                          float* world_vertices_dev, void* cuda_stream);
+
 /* Thread-local text of the last error ("" if none). */
 const char* ags_last_error(void);
 

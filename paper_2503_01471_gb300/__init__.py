@@ -40,7 +40,7 @@ EXPORTS = [
     "ags_context_create", "ags_context_destroy", "ags_scene_build", "ags_scene_destroy", "ags_render",
     "ags_render_envs", "ags_render_host", "ags_render_count", "ags_stream_status", "ags_last_error",
     "ags_scene_n_envs", "ags_scene_get_world_triangles", "ags_scene_stats", "ags_scene_node_bytes",
-    "ags_context_set_traversal_cap",
+    "ags_context_set_traversal_cap", "ags_transform_vertices_noalloc",
 ]
 
 
@@ -104,6 +104,7 @@ def lib() -> ctypes.CDLL:
         "ags_scene_stats": (i32, [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "ags_scene_node_bytes": (i32, [vp]),
         "ags_context_set_traversal_cap": (i32, [vp, i32]),
+        "ags_transform_vertices_noalloc": (i32, [vp, vp, i32, vp, i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -223,6 +224,21 @@ def ags_scene_get_world_triangles(scene: int, env: int):
     _check(lib().ags_scene_get_world_triangles(scene, int(env), out.ctypes.data, seg.ctypes.data, n),
            "ags_scene_get_world_triangles")
     return out, seg
+
+
+def ags_transform_vertices_noalloc(ctx: int, base_vertices, submesh_vertex_offsets, poses, world_vertices,
+                                   stream=None) -> None:
+    """Object-to-world transform into caller-owned device buffers, allocating nothing.
+
+    base_vertices float32 [V,3], submesh_vertex_offsets int32 [J+1], poses
+    float32 [J,7], world_vertices float32 [V,4] (all CUDA tensors or device
+    pointers; pass sizes through the tensors' shapes).
+    """
+    V = int(base_vertices.shape[0])
+    J = int(poses.shape[0])
+    _check(lib().ags_transform_vertices_noalloc(ctx, _ptr(base_vertices), V, _ptr(submesh_vertex_offsets), J,
+                                                _ptr(poses), _ptr(world_vertices), _stream(stream)),
+           "ags_transform_vertices_noalloc")
 
 
 # ---------------------------------------------------------------- render

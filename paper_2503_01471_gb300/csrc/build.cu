@@ -730,3 +730,91 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
 }
 
 }  // namespace ags
+
+// ---------------------------------------------------------------- allocation-free transform
+// ags_transform_vertices_noalloc runs the same two transform kernels as the
+// scene build, but keeps their per-sub-mesh scratch (the float-float rotation
+// of each pose, 18 floats) in this file-scope device array instead of memory
+// from cudaMalloc. Every GPU that loads the library holds the array until the
+// process exits: 18 floats x 65536 sub-meshes = 4.5 MiB.
+#include <mutex>
+
+namespace {
+constexpr int32_t kNoAllocMaxSubmeshes = 65536;
+constexpr int kNoAllocMaxDevices = 64;
+}  // namespace
+
+static __device__ __align__(256) float ags_noalloc_rot_scratch[18 * kNoAllocMaxSubmeshes];
+
+namespace ags {
+namespace {
+
+std::mutex g_noalloc_mu;
+float* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on `device`, looked up once per device
+// with that device current (host code cannot use the symbol itself: on the
+// host it names a stand-in, not device memory).
+ags_status noalloc_scratch(int device, float** out) {
+  if (device < 0 || device >= kNoAllocMaxDevices) {
+    set_error("ags_transform_vertices_noalloc: device index beyond the supported 64");
+    return AGS_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, ags_noalloc_rot_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(ags_noalloc_rot_scratch)");
+    g_noalloc_ptr[device] = static_cast<float*>(p);
+  }
+  *out = g_noalloc_ptr[device];
+  return AGS_OK;
+}
+
+}  // namespace
+}  // namespace ags
+
+extern "C" ags_status ags_transform_vertices_noalloc(ags_context* ctx, const float* base_vertices_dev,
+                                                     int32_t n_vertices, const int32_t* submesh_vertex_offsets_dev,
+                                                     int32_t n_submeshes, const float* poses_dev,
+                                                     float* world_vertices_dev, void* cuda_stream) {
+  using namespace ags;
+  if (!ctx) {
+    set_error("ags_transform_vertices_noalloc: ctx is NULL");
+    return AGS_ERR_INVALID_ARG;
+  }
+  if (n_vertices < 0 || n_submeshes < 0) {
+    set_error("ags_transform_vertices_noalloc: negative size");
+    return AGS_ERR_INVALID_ARG;
+  }
+  if (n_submeshes > kNoAllocMaxSubmeshes) {
+    set_error("ags_transform_vertices_noalloc: n_submeshes exceeds the maximum of 65536 its fixed scratch holds");
+    return AGS_ERR_INVALID_ARG;
+  }
+  if (n_vertices == 0) return AGS_OK;
+  if (n_submeshes == 0 || !base_vertices_dev || !submesh_vertex_offsets_dev || !poses_dev || !world_vertices_dev) {
+    set_error("ags_transform_vertices_noalloc: NULL pointer or vertices without sub-meshes");
+    return AGS_ERR_INVALID_ARG;
+  }
+  if ((reinterpret_cast<uintptr_t>(world_vertices_dev) & 15u) != 0) {
+    set_error("ags_transform_vertices_noalloc: world_vertices_dev must be 16-byte aligned");
+    return AGS_ERR_INVALID_ARG;
+  }
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+  if (prev != ctx->device) cudaSetDevice(ctx->device);
+  float* rot = nullptr;
+  ags_status st = noalloc_scratch(ctx->device, &rot);
+  if (st == AGS_OK) {
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    k_submesh_rotations<<<blocks_for(n_submeshes, 128), 128, 0, s>>>(poses_dev, n_submeshes, rot);
+    k_transform_vertices<<<blocks_for(n_vertices, 256), 256, 0, s>>>(base_vertices_dev, n_vertices,
+                                                                     submesh_vertex_offsets_dev, n_submeshes, rot,
+                                                                     poses_dev,
+                                                                     reinterpret_cast<float4*>(world_vertices_dev));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) st = cuda_fail(e, "ags_transform_vertices_noalloc launch");
+  }
+  if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+  return st;
+}

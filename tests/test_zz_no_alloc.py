@@ -1,0 +1,85 @@
+"""The allocation-free transform entry point against the scene build's own transform.
+
+ags_transform_vertices_noalloc serves callers that cannot let the library call
+cudaMalloc (device memory reserved up front by their own allocator, or no
+room for the synchronisation an allocation may cause mid-work). It keeps its
+scratch in a fixed device array inside the library. This file is collected
+last so that a failure here never hides the other GPU tests.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2503_01471_gb300 as ags
+from paper_2503_01471_gb300 import build as B
+from paper_2503_01471_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    B.build()
+    c = ags.ags_context_create(0)
+    yield c
+    ags.ags_context_destroy(c)
+
+
+def _scene(seed):
+    rng = np.random.default_rng(seed)
+    envs = []
+    for e in range(3):
+        objs = []
+        for k in range(int(rng.integers(5, 25))):
+            v = rng.uniform(-3, 3, (int(rng.integers(3, 40)), 3)).astype(np.float32)
+            f = rng.integers(0, v.shape[0], (int(rng.integers(1, 20)), 3)).astype(np.int32)
+            q = rng.normal(size=4) * rng.uniform(0.3, 2.0)
+            p = rng.uniform(-15, 15, 3)
+            objs.append((v, f, np.concatenate([p, q]).astype(np.float32), k))
+        envs.append(objs)
+    return S.scene_from_lists(envs)
+
+
+def _via_build(ctx, batch):
+    """World triangles [F,9] of every env, from the existing entry points."""
+    scene = ags.ags_scene_build(ctx, batch)
+    try:
+        return np.concatenate([ags.ags_scene_get_world_triangles(scene, e)[0] for e in range(batch.n_envs)])
+    finally:
+        ags.ags_scene_destroy(scene)
+
+
+def _via_noalloc(ctx, batch, out):
+    base = torch.as_tensor(batch.vertices).cuda()
+    offs = torch.as_tensor(batch.sub_vert.astype(np.int32)).cuda()
+    poses = torch.as_tensor(batch.poses).cuda()
+    ags.ags_transform_vertices_noalloc(ctx, base, offs, poses, out)
+    torch.cuda.synchronize()
+    w = out[: base.shape[0], :3].cpu().numpy()
+    # global vertex index of every triangle corner (indices are local to their sub-mesh)
+    sub_of_tri = np.repeat(np.arange(batch.sub_seg.shape[0]), np.diff(batch.sub_tri))
+    gidx = batch.indices.astype(np.int64) + batch.sub_vert[sub_of_tri][:, None]
+    return w[gidx].reshape(-1, 9)
+
+
+def test_noalloc_transform_matches_build_on_two_calls(ctx):
+    a, b = _scene(1), _scene(2)
+    vmax = max(a.vertices.shape[0], b.vertices.shape[0])
+    out = torch.full((vmax, 4), float("nan"), device="cuda")
+    for batch in (a, b):  # two calls in a row share the scratch array
+        ref = _via_build(ctx, batch)
+        got = _via_noalloc(ctx, batch, out)
+        ulp = np.spacing(np.maximum(np.abs(ref), 1.0)).astype(np.float64)
+        assert np.all(np.abs(got.astype(np.float64) - ref) <= ulp)  # the transform tests' bound: 1 ulp
+        assert np.array_equal(got, ref)  # same kernels: in fact identical
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch(ctx):
+    base = torch.zeros((4, 3), device="cuda")
+    offs = torch.zeros(65538, dtype=torch.int32, device="cuda")
+    offs[-1] = 4
+    poses = torch.zeros((65537, 7), device="cuda")
+    poses[:, 6] = 1.0
+    out = torch.zeros((4, 4), device="cuda")
+    with pytest.raises(ags.AgsError, match="65536"):
+        ags.ags_transform_vertices_noalloc(ctx, base, offs, poses, out)
