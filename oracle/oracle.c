@@ -192,21 +192,24 @@ static void eval_triangle(const double* tri, const double o[3], const double d[3
   int geo_sure = area2 != 0.0 && sg * e0 >= eps * len0 && sg * e1 >= eps * len1 &&
                  sg * e2 >= eps * len2;
 
-  /* range of t over the perturbations: a sideways shift moves the barycentrics
-   * by at most eps len_k / |area2| each (they still sum to 1), and moving the
-   * plane by vert along its normal moves t by vert / |cos(n, d)| */
+  /* Range of t over the perturbations. A ray displaced sideways by e meets
+   * the triangle's plane at a t that differs by at most e tan(n, d); the
+   * renderer's arithmetic error displaces the ray that way (arith_rel * rmax)
+   * and also shifts t along the ray directly (the same amount); moving the
+   * plane by vert along its normal moves t by vert / cos(n, d). */
   double cosn = fabs(dot3(n, d)) / nn;
   double zmin = fmin(za, fmin(zb, zc)) - vert, zmax = fmax(za, fmax(zb, zc)) + vert;
   double t_lo = zmin, t_hi = zmax;
-  if (area2 != 0.0) {
+  if (area2 != 0.0 && cosn > 0.0) {
     double tc = (e0 * za + e1 * zb + e2 * zc) / area2;
-    /* only the ray's own displacement moves the hit along the plane; vertex
-     * displacement is the plane shift dpl */
-    double eps_t = bands->dir_rel * fabs(tc) + bands->arith_rel * rmax;
-    double dlat = eps_t * (len0 * fabs(za - tc) + len1 * fabs(zb - tc) + len2 * fabs(zc - tc)) /
-                  fabs(area2);
-    double dpl = (cosn > 0.0) ? vert / cosn : INFINITY;
-    double lo = fmax(zmin, tc - dlat - dpl), hi = fmin(zmax, tc + dlat + dpl);
+    double ar = bands->arith_rel * rmax;
+    /* the sideways effect is bounded two ways; both hold, take the smaller:
+     * the plane's slope tan(n, d), and the barycentric bound (a shift moves
+     * each barycentric by at most e len_k / |area2| and they sum to one) */
+    double tan_n = sqrt(fmax(0.0, 1.0 - cosn * cosn)) / cosn;
+    double bary = (len0 * fabs(za - tc) + len1 * fabs(zb - tc) + len2 * fabs(zc - tc)) / fabs(area2);
+    double delta = (bands->dir_rel * fabs(tc) + ar) * fmin(tan_n, bary) + ar + vert / cosn;
+    double lo = fmax(zmin, tc - delta), hi = fmin(zmax, tc + delta);
     if (lo > hi) {
       double tcc = fmin(fmax(tc, zmin), zmax);
       lo = hi = tcc;
@@ -362,8 +365,8 @@ static void render_one(const double* tris, const int32_t* seg, int64_t F, const 
   if (miss_ok) flags |= ORC_F_MISS_OK;
   int outcomes = res->n_cand + (miss_ok ? 1 : 0);
   if (outcomes > 1) flags |= ORC_F_COUNTED;
-  if (res->n_cand == 1 && res->cand_hi[0] - res->cand_lo[0] > 2.0 * tolv(res->cand_hi[0]))
-    flags |= ORC_F_COUNTED;
+  for (int g = 0; g < res->n_cand; ++g)
+    if (res->cand_hi[g] - res->cand_lo[g] > 2.0 * tolv(res->cand_hi[g])) flags |= ORC_F_WIDE;
   res->flags = flags;
 }
 

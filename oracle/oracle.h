@@ -35,13 +35,14 @@ extern "C" {
 #define ORC_MAX_CAND 4
 
 /* flag bits of orc_result.flags */
-#define ORC_F_COUNTED 1      /* more than one outcome is acceptable */
+#define ORC_F_COUNTED 1      /* more than one outcome (segment, or hit vs miss) is acceptable */
 #define ORC_F_SILHOUETTE 2   /* a candidate lies within eps of a triangle edge */
 #define ORC_F_NEAR_TIE 4     /* two surely-hit triangles of different segments within tol */
 #define ORC_F_RANGE_EDGE 8   /* a candidate lies within tol of a range limit */
 #define ORC_F_GRAZING 16     /* a candidate has |n.d| < 1e-3 */
 #define ORC_F_OVERFLOW 32    /* more than ORC_MAX_CAND segment groups (test must fail) */
 #define ORC_F_MISS_OK 64     /* "miss" (max_range, -1) is an acceptable outcome */
+#define ORC_F_WIDE 128       /* the error bands widen an outcome's value range beyond +-tol */
 
 typedef struct {
   int32_t type;        /* ORC_PINHOLE or ORC_LIDAR */

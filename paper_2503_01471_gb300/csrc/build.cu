@@ -458,35 +458,48 @@ __global__ void k_collapse_emit(const QueueItem* __restrict__ items, int32_t n_i
   nd.child_base = next_base + inner_off[it];
   nd.tri_base = tri_base_level + tri_off[it];
   uint32_t meta[2] = {0, 0};
-  int rank = 0, toff = 0;
+  // inner children take slots 0..ni-1 (child k is node child_base + k), then
+  // the leaves, then the empty slots
+  int ni = 0;
   for (int k = 0; k < 8; ++k) {
     int32_t r = slots[8 * (int64_t)it + k];
-    uint32_t m;
-    Box b;
-    if (r == kSlotEmpty) {
-      m = kMetaEmpty;
-      b = {kEmptyBoxCoord, kEmptyBoxCoord, kEmptyBoxCoord, kEmptyBoxCoord, kEmptyBoxCoord, kEmptyBoxCoord};
-    } else {
-      int32_t c = ref_count(r, first, last);
-      b = r >= 0 ? inner_box[r] : leaf_box[~r];
-      if (r >= 0 && c > leaf_max) {
-        m = 0x80u | (uint32_t)rank;
-        next_items[inner_off[it] + rank] = {r, q.env};
-        ++rank;
+    if (r != kSlotEmpty && r >= 0 && ref_count(r, first, last) > leaf_max) ++ni;
+  }
+  int pos = 0, rank = 0, toff = 0;
+  for (int pass = 0; pass < 3; ++pass) {
+    for (int k = 0; k < 8; ++k) {
+      int32_t r = slots[8 * (int64_t)it + k];
+      const bool empty = r == kSlotEmpty;
+      const bool inner = !empty && r >= 0 && ref_count(r, first, last) > leaf_max;
+      if ((pass == 0) != inner || (pass == 2) != empty) continue;
+      uint32_t m;
+      Box b;
+      if (empty) {
+        m = kMetaEmpty;
+        b = {kEmptyBoxCoord, kEmptyBoxCoord, kEmptyBoxCoord, kEmptyBoxCoord, kEmptyBoxCoord, kEmptyBoxCoord};
       } else {
-        int32_t f0 = r >= 0 ? first[r] : ~r;
-        m = ((uint32_t)toff << 2) | (uint32_t)(c - 1);
-        for (int32_t x = 0; x < c; ++x) perm[nd.tri_base + toff + x] = f0 + x;
-        toff += c;
+        int32_t c = ref_count(r, first, last);
+        b = r >= 0 ? inner_box[r] : leaf_box[~r];
+        if (inner) {
+          m = 0x80u | (uint32_t)ni;
+          next_items[inner_off[it] + rank] = {r, q.env};
+          ++rank;
+        } else {
+          int32_t f0 = r >= 0 ? first[r] : ~r;
+          m = ((uint32_t)toff << 2) | (uint32_t)(c - 1);
+          for (int32_t x = 0; x < c; ++x) perm[nd.tri_base + toff + x] = f0 + x;
+          toff += c;
+        }
       }
+      meta[pos >> 2] |= (m & 0xFFu) << (8 * (pos & 3));
+      nd.lox[pos] = b.lox;
+      nd.hix[pos] = b.hix;
+      nd.loy[pos] = b.loy;
+      nd.hiy[pos] = b.hiy;
+      nd.loz[pos] = b.loz;
+      nd.hiz[pos] = b.hiz;
+      ++pos;
     }
-    meta[k >> 2] |= (m & 0xFFu) << (8 * (k & 3));
-    nd.lox[k] = b.lox;
-    nd.hix[k] = b.hix;
-    nd.loy[k] = b.loy;
-    nd.hiy[k] = b.hiy;
-    nd.loz[k] = b.loz;
-    nd.hiz[k] = b.hiz;
   }
   nd.meta_lo = meta[0];
   nd.meta_hi = meta[1];

@@ -14,12 +14,13 @@ namespace ags {
 
 // ----------------------------------------------------------------- wide BVH
 // 8-wide node, float32 child boxes in structure-of-arrays order so a thread
-// reads a whole node with 13 aligned 16-byte loads. Children that are inner
-// nodes are stored contiguously from child_base; the triangles of all leaf
-// children are stored contiguously from tri_base.
-// meta[k] (byte k of meta_lo/meta_hi): 0xFF empty slot; 0x80 | r inner child
-// child_base + r; otherwise a leaf of (meta & 3) + 1 triangles starting at
-// tri_base + (meta >> 2).
+// reads a whole node with 13 aligned 16-byte loads. The ni inner children sit
+// in slots 0..ni-1 and are nodes child_base + slot; leaf children follow, and
+// the triangles of all leaf children are contiguous from tri_base; empty
+// slots come last. meta[k] (byte k of meta_lo/meta_hi): inner slot 0x80 | ni;
+// leaf slot (offset << 2) | (count - 1), its triangles starting at tri_base +
+// offset; empty slot 0xFF. So ni = meta byte 0 & 0xF when its top bit is set,
+// else 0.
 struct __align__(16) WideNode {
   int32_t child_base;
   int32_t tri_base;

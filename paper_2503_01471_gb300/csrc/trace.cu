@@ -14,20 +14,23 @@ namespace {
 constexpr int kTraceThreads = 128;
 constexpr int kStackSize = 64;
 constexpr int kTileW = 8, kTileH = 4;
-// Box culling is made conservative against float32 rounding: the slab exit
-// is scaled up by (1 + 2 gamma_3) and the current nearest hit by (1 + 2^-12),
-// so a box holding the eventual nearest triangle is never skipped.
+// Box culling is made conservative against float32 rounding: each slab
+// bound is computed as one fma with a per-ray constant that already moves
+// the near bound down and the far bound up by more than the rounding of
+// -o/d, the slab exit is scaled up by (1 + 4u) and the current nearest hit by
+// (1 + 2^-12), so a box holding the eventual nearest triangle is never skipped.
 constexpr float kSlabSlack = 1.0f + 4.0f * 5.96046448e-8f;
 constexpr float kCullSlack = 1.0f + 2.44140625e-4f;
+constexpr float kSlabEps = 4.0f * 5.96046448e-8f;
 
 struct Ray {
   float ox, oy, oz;
-  float dx, dy, dz;
-  float ix, iy, iz;
-  // watertight test: permuted axes and shear constants
-  int kx, ky, kz;
-  float Sx, Sy, Sz;
-  float okx, oky, okz;
+  float ix, iy, iz;          // 1 / direction
+  float cnx, cny, cnz;       // near-bound constants: -o/d, lowered
+  float cfx, cfy, cfz;       // far-bound constants: -o/d, raised
+  int onx, ony, onz;         // float4 offsets of the near-bound arrays in a node (octant)
+  // watertight test: rows of the shear that maps (v - o) to the ray's frame
+  float m0x, m0y, m0z, m1x, m1y, m1z, m2x, m2y, m2z;
 };
 
 __device__ __forceinline__ float nonzero(float d) {
@@ -36,57 +39,84 @@ __device__ __forceinline__ float nonzero(float d) {
   return fabsf(d) < 1e-30f ? copysignf(1e-30f, d) : d;
 }
 
-__device__ __forceinline__ float sel3(float x, float y, float z, int k) { return k == 0 ? x : (k == 1 ? y : z); }
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
 
-__device__ __forceinline__ void setup_ray(Ray& r) {
-  r.dx = nonzero(r.dx);
-  r.dy = nonzero(r.dy);
-  r.dz = nonzero(r.dz);
-  r.ix = 1.0f / r.dx;
-  r.iy = 1.0f / r.dy;
-  r.iz = 1.0f / r.dz;
-  float ax = fabsf(r.dx), ay = fabsf(r.dy), az = fabsf(r.dz);
-  int kz = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
+__device__ __forceinline__ void setup_ray(Ray& r, float dx, float dy, float dz) {
+  dx = nonzero(dx);
+  dy = nonzero(dy);
+  dz = nonzero(dz);
+  r.ix = 1.0f / dx;
+  r.iy = 1.0f / dy;
+  r.iz = 1.0f / dz;
+  const float px = -r.ox * r.ix, py = -r.oy * r.iy, pz = -r.oz * r.iz;
+  const float ex = kSlabEps * fabsf(px), ey = kSlabEps * fabsf(py), ez = kSlabEps * fabsf(pz);
+  r.cnx = px - ex;
+  r.cfx = px + ex;
+  r.cny = py - ey;
+  r.cfy = py + ey;
+  r.cnz = pz - ez;
+  r.cfz = pz + ez;
+  // node layout (float4 units): header, lox[2], hix[2], loy[2], hiy[2], loz[2], hiz[2]
+  r.onx = r.ix >= 0.0f ? 1 : 3;
+  r.ony = r.iy >= 0.0f ? 5 : 7;
+  r.onz = r.iz >= 0.0f ? 9 : 11;
+  // watertight shear: z axis = largest |d| component, x/y the next two in
+  // cyclic order (swapped when d_z < 0 to keep the winding)
+  const float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
+  const int kz = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
   int kx = kz == 2 ? 0 : kz + 1;
   int ky = kx == 2 ? 0 : kx + 1;
-  float dkz = sel3(r.dx, r.dy, r.dz, kz);
-  if (dkz < 0.0f) {  // keep the winding so the edge tests stay consistent
-    int t = kx;
+  const float dkz = kz == 0 ? dx : (kz == 1 ? dy : dz);
+  if (dkz < 0.0f) {
+    const int t = kx;
     kx = ky;
     ky = t;
   }
-  r.kx = kx;
-  r.ky = ky;
-  r.kz = kz;
-  r.Sx = sel3(r.dx, r.dy, r.dz, kx) / dkz;
-  r.Sy = sel3(r.dx, r.dy, r.dz, ky) / dkz;
-  r.Sz = 1.0f / dkz;
-  r.okx = sel3(r.ox, r.oy, r.oz, kx);
-  r.oky = sel3(r.ox, r.oy, r.oz, ky);
-  r.okz = sel3(r.ox, r.oy, r.oz, kz);
+  const float dkx = kx == 0 ? dx : (kx == 1 ? dy : dz);
+  const float dky = ky == 0 ? dx : (ky == 1 ? dy : dz);
+  const float Sx = dkx / dkz, Sy = dky / dkz, Sz = 1.0f / dkz;
+  r.m0x = (kx == 0 ? 1.0f : 0.0f) - (kz == 0 ? Sx : 0.0f);
+  r.m0y = (kx == 1 ? 1.0f : 0.0f) - (kz == 1 ? Sx : 0.0f);
+  r.m0z = (kx == 2 ? 1.0f : 0.0f) - (kz == 2 ? Sx : 0.0f);
+  r.m1x = (ky == 0 ? 1.0f : 0.0f) - (kz == 0 ? Sy : 0.0f);
+  r.m1y = (ky == 1 ? 1.0f : 0.0f) - (kz == 1 ? Sy : 0.0f);
+  r.m1z = (ky == 2 ? 1.0f : 0.0f) - (kz == 2 ? Sy : 0.0f);
+  r.m2x = kz == 0 ? Sz : 0.0f;
+  r.m2y = kz == 1 ? Sz : 0.0f;
+  r.m2z = kz == 2 ? Sz : 0.0f;
 }
 
 // Watertight ray/triangle test (Woop, Benthin, Wald 2013), two-sided with
-// closed edges. Each edge function is an explicitly rounded difference of two
-// rounded products, so a shared edge gives exactly opposite values in its two
-// triangles and no ray slips between them.
+// closed edges. Each vertex is sheared by the same per-ray rows (so a vertex
+// shared by two triangles gets the same coordinates in both), and each edge
+// function is an explicitly rounded difference of two rounded products, so a
+// shared edge gives exactly opposite values in its two triangles and no ray
+// slips between them.
+__device__ __forceinline__ void shear(const Ray& r, const float4 v, float& X, float& Y, float& Z) {
+  const float ax = __fsub_rn(v.x, r.ox), ay = __fsub_rn(v.y, r.oy), az = __fsub_rn(v.z, r.oz);
+  X = __fmaf_rn(r.m0x, ax, __fmaf_rn(r.m0y, ay, __fmul_rn(r.m0z, az)));
+  Y = __fmaf_rn(r.m1x, ax, __fmaf_rn(r.m1y, ay, __fmul_rn(r.m1z, az)));
+  Z = __fmaf_rn(r.m2x, ax, __fmaf_rn(r.m2y, ay, __fmul_rn(r.m2z, az)));
+}
+
 __device__ __forceinline__ void test_triangle(const Ray& r, const float4* __restrict__ tris, int32_t k,
                                               float& t_best, int32_t& best_id, int32_t& best_seg) {
   const float4 a = __ldg(tris + 3 * (int64_t)k);
   const float4 b = __ldg(tris + 3 * (int64_t)k + 1);
   const float4 c = __ldg(tris + 3 * (int64_t)k + 2);
-  float ax = __fsub_rn(sel3(a.x, a.y, a.z, r.kx), r.okx);
-  float ay = __fsub_rn(sel3(a.x, a.y, a.z, r.ky), r.oky);
-  float az = __fsub_rn(sel3(a.x, a.y, a.z, r.kz), r.okz);
-  float bx = __fsub_rn(sel3(b.x, b.y, b.z, r.kx), r.okx);
-  float by = __fsub_rn(sel3(b.x, b.y, b.z, r.ky), r.oky);
-  float bz = __fsub_rn(sel3(b.x, b.y, b.z, r.kz), r.okz);
-  float cx = __fsub_rn(sel3(c.x, c.y, c.z, r.kx), r.okx);
-  float cy = __fsub_rn(sel3(c.x, c.y, c.z, r.ky), r.oky);
-  float cz = __fsub_rn(sel3(c.x, c.y, c.z, r.kz), r.okz);
-  const float Ax = __fmaf_rn(-r.Sx, az, ax), Ay = __fmaf_rn(-r.Sy, az, ay);
-  const float Bx = __fmaf_rn(-r.Sx, bz, bx), By = __fmaf_rn(-r.Sy, bz, by);
-  const float Cx = __fmaf_rn(-r.Sx, cz, cx), Cy = __fmaf_rn(-r.Sy, cz, cy);
+  float Ax, Ay, Az, Bx, By, Bz, Cx, Cy, Cz;
+  shear(r, a, Ax, Ay, Az);
+  shear(r, b, Bx, By, Bz);
+  shear(r, c, Cx, Cy, Cz);
   const float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
   const float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
   const float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
@@ -95,10 +125,10 @@ __device__ __forceinline__ void test_triangle(const Ray& r, const float4* __rest
   if (neg && pos) return;
   const float det = U + V + W;
   if (det == 0.0f) return;
-  const float T = __fmaf_rn(U, r.Sz * az, __fmaf_rn(V, r.Sz * bz, __fmul_rn(W, r.Sz * cz)));
-  // cheap reject before the division: |t| beyond the current best (with slack)
+  const float T = __fmaf_rn(U, Az, __fmaf_rn(V, Bz, __fmul_rn(W, Cz)));
+  // reject t < 0, and |t| beyond the current best (with slack) before dividing
+  if (T != 0.0f && ((__float_as_uint(T) ^ __float_as_uint(det)) >> 31)) return;
   const float aT = fabsf(T), adet = fabsf(det);
-  if (T != 0.0f && ((__float_as_uint(T) ^ __float_as_uint(det)) >> 31)) return;  // t < 0
   if (aT > t_best * adet * kCullSlack) return;
   const float t = __fdiv_rn(aT, adet);
   const int32_t id = __float_as_int(b.w);
@@ -169,10 +199,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(const TraceArgs a) {
     r.ox = px;
     r.oy = py;
     r.oz = pz;
-    r.dx = R00 * lx + R01 * ly + R02 * lz;
-    r.dy = R10 * lx + R11 * ly + R12 * lz;
-    r.dz = R20 * lx + R21 * ly + R22 * lz;
-    setup_ray(r);
+    setup_ray(r, R00 * lx + R01 * ly + R02 * lz, R10 * lx + R11 * ly + R12 * lz, R20 * lx + R21 * ly + R22 * lz);
 
     // ---- a4-a6: traversal, triangle tests, nearest hit
     float t_best = a.max_range;  // camera: depth limit; LiDAR: range limit (unit direction)
@@ -197,37 +224,39 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(const TraceArgs a) {
       const int32_t child_base = __float_as_int(h.x), tri_base = __float_as_int(h.y);
       const uint32_t meta_lo = __float_as_uint(h.z), meta_hi = __float_as_uint(h.w);
       const float t_cull = t_best * kCullSlack;
-      uint32_t keys[8];
-      uint32_t leaf_mask = 0;
+      const uint32_t b0 = meta_lo & 0xFFu;
+      const int ni = (b0 & 0x80u) ? (int)min(b0 & 0xFu, 8u) : 0;
+      float tmins[8];
+      uint32_t hit_mask = 0;
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
-        const float4 lx4 = __ldg(np + 1 + half), hx4 = __ldg(np + 3 + half);
-        const float4 ly4 = __ldg(np + 5 + half), hy4 = __ldg(np + 7 + half);
-        const float4 lz4 = __ldg(np + 9 + half), hz4 = __ldg(np + 11 + half);
-        const float lxs[4] = {lx4.x, lx4.y, lx4.z, lx4.w}, hxs[4] = {hx4.x, hx4.y, hx4.z, hx4.w};
-        const float lys[4] = {ly4.x, ly4.y, ly4.z, ly4.w}, hys[4] = {hy4.x, hy4.y, hy4.z, hy4.w};
-        const float lzs[4] = {lz4.x, lz4.y, lz4.z, lz4.w}, hzs[4] = {hz4.x, hz4.y, hz4.z, hz4.w};
-        const uint32_t meta = half ? meta_hi : meta_lo;
+        const float4 nx4 = __ldg(np + r.onx + half), fx4 = __ldg(np + (4 - r.onx) + half);
+        const float4 ny4 = __ldg(np + r.ony + half), fy4 = __ldg(np + (12 - r.ony) + half);
+        const float4 nz4 = __ldg(np + r.onz + half), fz4 = __ldg(np + (20 - r.onz) + half);
+        const float nxs[4] = {nx4.x, nx4.y, nx4.z, nx4.w}, fxs[4] = {fx4.x, fx4.y, fx4.z, fx4.w};
+        const float nys[4] = {ny4.x, ny4.y, ny4.z, ny4.w}, fys[4] = {fy4.x, fy4.y, fy4.z, fy4.w};
+        const float nzs[4] = {nz4.x, nz4.y, nz4.z, nz4.w}, fzs[4] = {fz4.x, fz4.y, fz4.z, fz4.w};
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int k = 4 * half + q;
-          const float tx0 = __fmul_rn(__fsub_rn(lxs[q], r.ox), r.ix), tx1 = __fmul_rn(__fsub_rn(hxs[q], r.ox), r.ix);
-          const float ty0 = __fmul_rn(__fsub_rn(lys[q], r.oy), r.iy), ty1 = __fmul_rn(__fsub_rn(hys[q], r.oy), r.iy);
-          const float tz0 = __fmul_rn(__fsub_rn(lzs[q], r.oz), r.iz), tz1 = __fmul_rn(__fsub_rn(hzs[q], r.oz), r.iz);
-          const float tmin = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
-          const float tmax = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1)) * kSlabSlack;
-          const bool hit = tmin <= fminf(tmax, t_cull);
-          const uint32_t m = (meta >> (8 * q)) & 0xFFu;
-          const bool inner = (m & 0xF8u) == 0x80u;  // 0x80..0x87; 0xFF is an empty slot
-          keys[k] = (hit && inner) ? ((__float_as_uint(tmin) & ~7u) | (m & 7u)) : 0xFFFFFFFFu;
-          if (hit && !inner) leaf_mask |= 1u << k;
+          const float tnx = __fmaf_rn(nxs[q], r.ix, r.cnx), tfx = __fmaf_rn(fxs[q], r.ix, r.cfx);
+          const float tny = __fmaf_rn(nys[q], r.iy, r.cny), tfy = __fmaf_rn(fys[q], r.iy, r.cfy);
+          const float tnz = __fmaf_rn(nzs[q], r.iz, r.cnz), tfz = __fmaf_rn(fzs[q], r.iz, r.cfz);
+          const float tmin = max3f(tnx, tny, fmaxf(tnz, 0.0f));
+          const float tmax = min3f(tfx, tfy, tfz) * kSlabSlack;
+          tmins[k] = tmin;
+          if (tmin <= fminf(tmax, t_cull)) hit_mask |= 1u << k;
         }
       }
+      const uint32_t inner_bits = (1u << ni) - 1u;
+      uint32_t leaf_mask = hit_mask & ~inner_bits;
+      const uint32_t inner_hits = hit_mask & inner_bits;
       // leaves of this node first: they tighten t_best before descending
       while (leaf_mask) {
         const int k = __ffs(leaf_mask) - 1;
         leaf_mask &= leaf_mask - 1;
         const uint32_t m = ((k < 4 ? meta_lo : meta_hi) >> (8 * (k & 3))) & 0xFFu;
+        if (m == kMetaEmpty) continue;
         const int32_t start = tri_base + (int32_t)(m >> 2);
         const int32_t cnt = (int32_t)(m & 3u) + 1;
         if (start < 0 || start + cnt > a.n_tris) {
@@ -239,38 +268,49 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(const TraceArgs a) {
         if (kCount) n_tris += cnt;
       }
       if (failed) break;
-      // inner children, nearest first (sorting network on packed keys)
-#define AGS_CSWAP(i, j)                      \
-  {                                          \
+      const int n_inner = __popc(inner_hits);
+      if (n_inner == 1) {  // the common case: no ordering needed
+        node = child_base + (__ffs(inner_hits) - 1);
+        continue;
+      }
+      if (n_inner > 1) {
+        // nearest first (sorting network on keys: tmin bits with the slot in the low 3 bits)
+        uint32_t keys[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          keys[k] = ((inner_hits >> k) & 1u) ? ((__float_as_uint(tmins[k]) & ~7u) | (uint32_t)k) : 0xFFFFFFFFu;
+#define AGS_CSWAP(i, j)                         \
+  {                                             \
     const uint32_t lo_ = min(keys[i], keys[j]); \
     const uint32_t hi_ = max(keys[i], keys[j]); \
-    keys[i] = lo_;                           \
-    keys[j] = hi_;                           \
+    keys[i] = lo_;                              \
+    keys[j] = hi_;                              \
   }
-      AGS_CSWAP(0, 1) AGS_CSWAP(2, 3) AGS_CSWAP(4, 5) AGS_CSWAP(6, 7)
-      AGS_CSWAP(0, 2) AGS_CSWAP(1, 3) AGS_CSWAP(4, 6) AGS_CSWAP(5, 7)
-      AGS_CSWAP(1, 2) AGS_CSWAP(5, 6) AGS_CSWAP(0, 4) AGS_CSWAP(3, 7)
-      AGS_CSWAP(1, 5) AGS_CSWAP(2, 6)
-      AGS_CSWAP(1, 4) AGS_CSWAP(3, 6)
-      AGS_CSWAP(2, 4) AGS_CSWAP(3, 5)
-      AGS_CSWAP(3, 4)
+        AGS_CSWAP(0, 1) AGS_CSWAP(2, 3) AGS_CSWAP(4, 5) AGS_CSWAP(6, 7)
+        AGS_CSWAP(0, 2) AGS_CSWAP(1, 3) AGS_CSWAP(4, 6) AGS_CSWAP(5, 7)
+        AGS_CSWAP(1, 2) AGS_CSWAP(5, 6) AGS_CSWAP(0, 4) AGS_CSWAP(3, 7)
+        AGS_CSWAP(1, 5) AGS_CSWAP(2, 6)
+        AGS_CSWAP(1, 4) AGS_CSWAP(3, 6)
+        AGS_CSWAP(2, 4) AGS_CSWAP(3, 5)
+        AGS_CSWAP(3, 4)
 #undef AGS_CSWAP
-      const uint32_t key_cull = __float_as_uint(t_best * kCullSlack);
+        const uint32_t key_cull = __float_as_uint(t_best * kCullSlack);
 #pragma unroll
-      for (int k = 7; k >= 1; --k) {
-        if (keys[k] != 0xFFFFFFFFu && (keys[k] & ~7u) <= key_cull) {
-          if (sp >= kStackSize) {
-            atomicOr(status, kStatusStackOverflow);
-            failed = true;
-          } else {
-            stack[sp++] = make_int2(child_base + (int32_t)(keys[k] & 7u), (int32_t)(keys[k] & ~7u));
+        for (int k = 7; k >= 1; --k) {
+          if (keys[k] != 0xFFFFFFFFu && (keys[k] & ~7u) <= key_cull) {
+            if (sp >= kStackSize) {
+              atomicOr(status, kStatusStackOverflow);
+              failed = true;
+            } else {
+              stack[sp++] = make_int2(child_base + (int32_t)(keys[k] & 7u), (int32_t)(keys[k] & ~7u));
+            }
           }
         }
-      }
-      if (failed) break;
-      if (keys[0] != 0xFFFFFFFFu && (keys[0] & ~7u) <= key_cull) {
-        node = child_base + (int32_t)(keys[0] & 7u);
-        continue;
+        if (failed) break;
+        if ((keys[0] & ~7u) <= key_cull) {
+          node = child_base + (int32_t)(keys[0] & 7u);
+          continue;
+        }
       }
       node = -1;
       const float t_pop = t_best * kCullSlack;

@@ -28,7 +28,9 @@ def compare_env(batch, e, spec, pose, depth, seg, rays=None):
     res = O.render(tris, tseg, s, np.asarray(pose, np.float32).astype(np.float64), rays)
     d = np.asarray(depth, np.float32).reshape(-1)[rays]
     g = np.asarray(seg, np.int32).reshape(-1)[rays]
-    ok, counted = O.check(res, d, g, s.max_range)
+    ok, counted, strict = O.check(res, d, g, s.max_range, with_strict=True)
+    compare_env.last_strict = strict
+    compare_env.last_wide = (res["flags"] & O.F_WIDE) != 0
     return ok, counted, res
 
 

@@ -25,7 +25,7 @@ def test_planted_errors_rejected():
     res, spec = _room_result()
     v = res["v"].astype(np.float32).astype(np.float64)
     seg = res["seg"].copy()
-    hit = np.nonzero((res["seg"] >= 0) & ((res["flags"] & O.F_COUNTED) == 0))[0]
+    hit = np.nonzero((res["seg"] >= 0) & ((res["flags"] & (O.F_COUNTED | O.F_WIDE)) == 0))[0]
     miss = np.nonzero((res["seg"] == -1) & ((res["flags"] & O.F_COUNTED) == 0))[0]
     assert len(hit) > 100
     i, j, k = hit[0], hit[1], hit[2]
