@@ -93,8 +93,10 @@ typedef struct {
   uint32_t flags;        /* reserved, must be 0 */
 } ags_sensor_spec;
 
-/* Build flags: node format of the wide BVH. */
+/* Build flags: node format of the wide BVH (bits 0-7) and the largest number
+ * of triangles in one BVH leaf (bits 8-11: 1..4; 0 selects 4). */
 #define AGS_BVH_FP32 0u
+#define AGS_LEAF_SIZE(n) (((uint32_t)(n) & 0xFu) << 8)
 
 /* Create a context on CUDA device `device`. */
 ags_status ags_context_create(int device, ags_context** out);

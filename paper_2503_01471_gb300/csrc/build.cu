@@ -661,7 +661,12 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
   AGS_CHECK(cudaGetLastError());
 
   // collapse into 8-wide nodes, level by level
-  int64_t node_cap = (int64_t)(0.4 * (double)F) + 2 * (int64_t)E + 64;
+  // wide nodes: at most F/(L+1) + E without inner children (each covers more
+  // than L triangles, or is a root), and every node with inner children has
+  // 8 slots, which bounds those by (F + F/(L+1) + E)/7
+  const int leaf_cap = ((sc->flags >> 8) & 0xFu) ? (int)((sc->flags >> 8) & 0xFu) : kMaxLeafTris;
+  const double leafonly = (double)F / (leaf_cap + 1) + E;
+  int64_t node_cap = (int64_t)(leafonly + ((double)F + leafonly) / 7.0) + 2 * (int64_t)E + 64;
   WideNode* d_nodes_tmp = nullptr;
   AGS_CHECK(tmp.alloc(&d_nodes_tmp, (size_t)node_cap));
   QueueItem *d_q = nullptr, *d_q2 = nullptr;
@@ -684,6 +689,7 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
   AGS_CHECK(cudaMemsetAsync(d_env_nodes, 0, (size_t)E * sizeof(unsigned long long), s));
   AGS_CHECK(cudaMemcpyAsync(d_q, q0.data(), q0.size() * sizeof(QueueItem), cudaMemcpyHostToDevice, s));
 
+  const int leaf_max = ((sc->flags >> 8) & 0xFu) ? (int)((sc->flags >> 8) & 0xFu) : kMaxLeafTris;
   int32_t n_items = (int32_t)q0.size();
   int32_t level_base = 0, tri_level_base = 0;
   int levels = 0;
@@ -693,7 +699,7 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
       return AGS_ERR_CUDA;
     }
     k_collapse_expand<<<blocks_for(n_items, 128), 128, 0, s>>>(d_q, n_items, d_left, d_right, d_first, d_last,
-                                                              d_inner_box, kMaxLeafTris, d_slots, d_ninner, d_ntris,
+                                                              d_inner_box, leaf_max, d_slots, d_ninner, d_ntris,
                                                               F, d_err);
     AGS_CHECK(cudaGetLastError());
     AGS_CHECK(exclusive_scan(d_ninner, n_items, d_tot, d_scan_tmp, s));
@@ -717,7 +723,7 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
     }
     k_collapse_emit<<<blocks_for(n_items, 128), 128, 0, s>>>(
         d_q, n_items, d_slots, d_ninner, d_ntris, level_base, next_base, tri_level_base, d_first, d_last,
-        d_inner_box, d_leaf_box, kMaxLeafTris, d_nodes_tmp, d_q2, d_perm, d_env_nodes);
+        d_inner_box, d_leaf_box, leaf_max, d_nodes_tmp, d_q2, d_perm, d_env_nodes);
     AGS_CHECK(cudaGetLastError());
     std::swap(d_q, d_q2);
     level_base = next_base;

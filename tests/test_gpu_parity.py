@@ -294,3 +294,19 @@ def test_device_limits_report_status_without_faulting(ctx):
     finally:
         ags.ags_context_set_traversal_cap(ctx, 1 << 20)
         ags.ags_scene_destroy(scene)
+
+
+def test_bit_exact_across_bvh_variants(ctx):
+    """Culling is conservative and the triangle test and tie-break do not depend on the tree, so every
+    BVH variant gives bit-identical depth and segments."""
+    batch, spec, poses = S.obstacle_rooms(6, steps=1, width=120, height=90)
+    outs = []
+    for flags in (ags.AGS_LEAF_SIZE(1), ags.AGS_LEAF_SIZE(2), ags.AGS_LEAF_SIZE(3), ags.AGS_LEAF_SIZE(4)):
+        scene = ags.ags_scene_build(ctx, batch, flags)
+        try:
+            outs.append(render(ctx, scene, spec, poses[0]))
+        finally:
+            ags.ags_scene_destroy(scene)
+    for d, s in outs[1:]:
+        assert np.array_equal(d, outs[0][0]) and np.array_equal(s, outs[0][1])
+    check_all(batch, spec, poses[0], outs[0][0], outs[0][1], tag="BVH variants 120x90")
