@@ -93,10 +93,16 @@ typedef struct {
   uint32_t flags;        /* reserved, must be 0 */
 } ags_sensor_spec;
 
-/* Build flags: node format of the wide BVH (bits 0-7) and the largest number
- * of triangles in one BVH leaf (bits 8-11: 1..4; 0 selects 4). */
+/* Build flags: node format of the wide BVH (bits 0-7); the largest number of
+ * triangles in one BVH leaf (bits 8-11: 1..4; 0 selects 2); and the splitting
+ * of large triangles into several BVH references (bits 12-19): 0 selects 16
+ * cells across an environment's largest extent, 1 turns splitting off, n >= 2
+ * uses n cells. A triangle larger than a cell is referenced from up to 8
+ * cells per axis (64 in all), each boxed by the triangle clipped to the cell;
+ * results are identical with or without splitting. */
 #define AGS_BVH_FP32 0u
 #define AGS_LEAF_SIZE(n) (((uint32_t)(n) & 0xFu) << 8)
+#define AGS_SPLIT_CELLS(n) (((uint32_t)(n) & 0xFFu) << 12)
 
 /* Create a context on CUDA device `device`. */
 ags_status ags_context_create(int device, ags_context** out);
@@ -223,7 +229,8 @@ ags_status ags_scene_get_world_triangles(const ags_scene* scene, int32_t env, fl
 
 /*
  * ags_scene_stats -- triangles, wide BVH nodes and resident bytes (nodes +
- * packed triangles) of environment `env`, or of the whole scene if env == -1.
+ * packed triangles, one 48-byte copy per BVH reference) of environment `env`,
+ * or of the whole scene if env == -1.
  * Any output pointer may be NULL.
  */
 ags_status ags_scene_stats(const ags_scene* scene, int32_t env, int64_t* n_tris, int64_t* n_nodes,

@@ -39,6 +39,10 @@ AGS_BVH_FP32 = 0
 def AGS_LEAF_SIZE(n: int) -> int:
     return (int(n) & 0xF) << 8
 
+
+def AGS_SPLIT_CELLS(n: int) -> int:
+    return (int(n) & 0xFF) << 12
+
 # every symbol declared in include/ags.h
 EXPORTS = [
     "ags_context_create", "ags_context_destroy", "ags_scene_build", "ags_scene_destroy", "ags_render",

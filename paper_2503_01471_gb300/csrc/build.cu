@@ -158,20 +158,19 @@ __global__ void k_init_bounds(int32_t* b, int32_t E) {
   }
 }
 
-__device__ __forceinline__ float3 centroid(const float4* packed, int64_t t) {
-  float4 a = packed[3 * t], b = packed[3 * t + 1], c = packed[3 * t + 2];
-  return make_float3((a.x + b.x + c.x) * (1.0f / 3.0f), (a.y + b.y + c.y) * (1.0f / 3.0f),
-                     (a.z + b.z + c.z) * (1.0f / 3.0f));
+
+__device__ __forceinline__ float3 box_center(const Box& b) {
+  return make_float3(0.5f * (b.lox + b.hix), 0.5f * (b.loy + b.hiy), 0.5f * (b.loz + b.hiz));
 }
 
-// per-environment bounds of triangle centroids (warp-aggregated atomics when
-// the whole warp belongs to one environment, per-lane atomics otherwise)
-__global__ void k_env_bounds(const float4* __restrict__ packed, const int32_t* __restrict__ tri_env, int32_t F,
+// per-environment bounds of reference-box centres (warp-aggregated atomics
+// when the whole warp belongs to one environment, per-lane atomics otherwise)
+__global__ void k_env_bounds(const Box* __restrict__ boxes, const int32_t* __restrict__ env_of, int32_t n,
                              int32_t* __restrict__ bounds) {
   int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  bool valid = t < F;
-  int32_t e = valid ? tri_env[t] : -1;
-  float3 c = valid ? centroid(packed, t) : make_float3(0, 0, 0);
+  bool valid = t < n;
+  int32_t e = valid ? env_of[t] : -1;
+  float3 c = valid ? box_center(boxes[t]) : make_float3(0, 0, 0);
   int32_t v[6] = {f2ord(c.x), f2ord(c.y), f2ord(c.z), f2ord(c.x), f2ord(c.y), f2ord(c.z)};
   unsigned peers = __match_any_sync(0xffffffffu, e);
   if (peers == 0xffffffffu) {  // uniform branch: every lane sees the same mask
@@ -205,14 +204,14 @@ __device__ __forceinline__ uint64_t spread3(uint64_t x) {
   return x;
 }
 
-__global__ void k_morton(const float4* __restrict__ packed, const int32_t* __restrict__ tri_env, int32_t F,
+__global__ void k_morton(const Box* __restrict__ boxes, const int32_t* __restrict__ env_of, int32_t n,
                          const int32_t* __restrict__ bounds, int bits, uint64_t* __restrict__ keys,
                          uint32_t* __restrict__ vals) {
   int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= F) return;
-  int32_t e = tri_env[t];
+  if (t >= n) return;
+  int32_t e = env_of[t];
   const int32_t* b = bounds + 6 * (int64_t)e;
-  float3 c = centroid(packed, t);
+  float3 c = box_center(boxes[t]);
   float cc[3] = {c.x, c.y, c.z};
   uint64_t q[3];
   const float scale = (float)(1u << bits);
@@ -220,12 +219,188 @@ __global__ void k_morton(const float4* __restrict__ packed, const int32_t* __res
     float lo = ord2f(b[k]), hi = ord2f(b[3 + k]);
     float ext = hi - lo;
     float u = ext > 0.0f ? (cc[k] - lo) / ext : 0.0f;
-    float s = fminf(fmaxf(u * scale, 0.0f), scale - 1.0f);
-    q[k] = (uint64_t)s;
+    float sc = fminf(fmaxf(u * scale, 0.0f), scale - 1.0f);
+    q[k] = (uint64_t)sc;
   }
   uint64_t m = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
   keys[t] = ((uint64_t)e << (3 * bits)) | m;
   vals[t] = (uint32_t)t;
+}
+
+__device__ __forceinline__ Box tri_box(const float4* packed, int64_t t) {
+  float4 a = packed[3 * t], b = packed[3 * t + 1], c = packed[3 * t + 2];
+  Box x;
+  x.lox = fminf(a.x, fminf(b.x, c.x));
+  x.loy = fminf(a.y, fminf(b.y, c.y));
+  x.loz = fminf(a.z, fminf(b.z, c.z));
+  x.hix = fmaxf(a.x, fmaxf(b.x, c.x));
+  x.hiy = fmaxf(a.y, fmaxf(b.y, c.y));
+  x.hiz = fmaxf(a.z, fmaxf(b.z, c.z));
+  return x;
+}
+
+__global__ void k_tri_boxes(const float4* __restrict__ packed, int32_t F, Box* __restrict__ out) {
+  int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < F) out[t] = tri_box(packed, t);
+}
+
+// ---------------------------------------------------------------- reference splitting
+// A triangle much larger than its environment's cell size gets several BVH
+// references: its box is cut into a grid of up to 8 cells per axis (64 in
+// all) and each cell that the triangle reaches becomes a reference whose box
+// is the triangle clipped to that cell. All references point at the same
+// packed triangle, so ray results do not change; the boxes are tighter, so
+// traversal enters fewer nodes. Clipped boxes are widened by 2^-19 of the
+// coordinate magnitude (beyond the clipping's rounding) and cut back to the
+// triangle's exact box, so together they always cover the whole triangle.
+constexpr int kSplitMaxPerAxis = 8;
+constexpr int kDefaultSplitCells = 16;  // cells across an environment's largest extent
+constexpr int kSplitMaxRefs = 64;
+
+struct SplitGrid {
+  int n[3];
+  float lo[3], hi[3];
+};
+
+__device__ __forceinline__ SplitGrid split_grid(const Box& tb, float cell, int max_refs) {
+  SplitGrid g;
+  g.lo[0] = tb.lox; g.lo[1] = tb.loy; g.lo[2] = tb.loz;
+  g.hi[0] = tb.hix; g.hi[1] = tb.hiy; g.hi[2] = tb.hiz;
+  for (int a = 0; a < 3; ++a) {
+    float ext = g.hi[a] - g.lo[a];
+    int k = 1;
+    if (cell > 0.0f && ext > cell) k = (int)fminf(ceilf(ext / cell), (float)kSplitMaxPerAxis);
+    g.n[a] = max(k, 1);
+  }
+  while (g.n[0] * g.n[1] * g.n[2] > max_refs) {
+    int a = (g.n[0] >= g.n[1] && g.n[0] >= g.n[2]) ? 0 : (g.n[1] >= g.n[2] ? 1 : 2);
+    g.n[a] = (g.n[a] + 1) / 2;
+  }
+  return g;
+}
+
+__device__ __forceinline__ float grid_bound(const SplitGrid& g, int a, int i) {
+  if (i <= 0) return g.lo[a];
+  if (i >= g.n[a]) return g.hi[a];
+  return g.lo[a] + (g.hi[a] - g.lo[a]) * ((float)i / (float)g.n[a]);
+}
+
+// Clip triangle (a, b, c) to the cell [lo, hi] (Sutherland-Hodgman against
+// its six planes); false if nothing is left, else the clipped polygon's box.
+__device__ bool clip_to_cell(const float4& a, const float4& b, const float4& c, const float lo[3],
+                             const float hi[3], Box& out) {
+  float P[9][3], Q[9][3];
+  P[0][0] = a.x; P[0][1] = a.y; P[0][2] = a.z;
+  P[1][0] = b.x; P[1][1] = b.y; P[1][2] = b.z;
+  P[2][0] = c.x; P[2][1] = c.y; P[2][2] = c.z;
+  int n = 3;
+  for (int plane = 0; plane < 6; ++plane) {
+    const int ax = plane >> 1;
+    const bool upper = plane & 1;
+    const float bound = upper ? hi[ax] : lo[ax];
+    int m = 0;
+    for (int i = 0; i < n; ++i) {
+      const float* cur = P[i];
+      const float* nxt = P[(i + 1) % n];
+      const float dc = upper ? bound - cur[ax] : cur[ax] - bound;
+      const float dn = upper ? bound - nxt[ax] : nxt[ax] - bound;
+      if (dc >= 0.0f && m < 9) {
+        Q[m][0] = cur[0]; Q[m][1] = cur[1]; Q[m][2] = cur[2];
+        ++m;
+      }
+      if (((dc > 0.0f && dn < 0.0f) || (dc < 0.0f && dn > 0.0f)) && m < 9) {
+        const float t = dc / (dc - dn);
+        for (int k = 0; k < 3; ++k) Q[m][k] = cur[k] + t * (nxt[k] - cur[k]);
+        Q[m][ax] = bound;
+        ++m;
+      }
+    }
+    n = m;
+    if (n == 0) return false;
+    for (int i = 0; i < n; ++i)
+      for (int k = 0; k < 3; ++k) P[i][k] = Q[i][k];
+  }
+  Box bx = {P[0][0], P[0][1], P[0][2], P[0][0], P[0][1], P[0][2]};
+  for (int i = 1; i < n; ++i) {
+    bx.lox = fminf(bx.lox, P[i][0]); bx.hix = fmaxf(bx.hix, P[i][0]);
+    bx.loy = fminf(bx.loy, P[i][1]); bx.hiy = fmaxf(bx.hiy, P[i][1]);
+    bx.loz = fminf(bx.loz, P[i][2]); bx.hiz = fmaxf(bx.hiz, P[i][2]);
+  }
+  out = bx;
+  return true;
+}
+
+__device__ __forceinline__ float widen_dn(float x) { return x - 1.9073486328125e-6f * fmaxf(fabsf(x), 1.0f); }
+__device__ __forceinline__ float widen_up(float x) { return x + 1.9073486328125e-6f * fmaxf(fabsf(x), 1.0f); }
+
+// One pass per triangle: count (out_box == nullptr) or emit its references.
+template <bool kEmit>
+__global__ void k_split(const float4* __restrict__ packed, const int32_t* __restrict__ tri_env, int32_t F,
+                        const int32_t* __restrict__ bounds, float cells, int max_refs,
+                        int32_t* __restrict__ counts,
+                        const int32_t* __restrict__ ref_off, int32_t* __restrict__ ref_tri,
+                        Box* __restrict__ ref_box, int32_t* __restrict__ ref_env) {
+  int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= F) return;
+  const int32_t e = tri_env[t];
+  const Box tb = tri_box(packed, t);
+  float cell = 0.0f;
+  if (cells > 0.0f) {
+    const int32_t* b = bounds + 6 * (int64_t)e;
+    float ext = fmaxf(fmaxf(ord2f(b[3]) - ord2f(b[0]), ord2f(b[4]) - ord2f(b[1])), ord2f(b[5]) - ord2f(b[2]));
+    cell = ext / cells;
+  }
+  const SplitGrid g = split_grid(tb, cell, max_refs);
+  int32_t out = kEmit ? ref_off[t] : 0;
+  int32_t count = 0;
+  if (g.n[0] * g.n[1] * g.n[2] == 1) {
+    count = 1;
+    if (kEmit) {
+      ref_tri[out] = t;
+      ref_box[out] = tb;
+      ref_env[out] = e;
+    }
+  } else {
+    const float4 A = packed[3 * (int64_t)t], B = packed[3 * (int64_t)t + 1], C = packed[3 * (int64_t)t + 2];
+    for (int i = 0; i < g.n[0]; ++i)
+      for (int j = 0; j < g.n[1]; ++j)
+        for (int k = 0; k < g.n[2]; ++k) {
+          const float lo[3] = {grid_bound(g, 0, i), grid_bound(g, 1, j), grid_bound(g, 2, k)};
+          const float hi[3] = {grid_bound(g, 0, i + 1), grid_bound(g, 1, j + 1), grid_bound(g, 2, k + 1)};
+          // clip against the cell widened by the same margin, so rounding at
+          // the cell faces cannot drop a sliver of the triangle
+          const float wlo[3] = {widen_dn(lo[0]), widen_dn(lo[1]), widen_dn(lo[2])};
+          const float whi[3] = {widen_up(hi[0]), widen_up(hi[1]), widen_up(hi[2])};
+          Box cb;
+          if (!clip_to_cell(A, B, C, wlo, whi, cb)) continue;
+          if (kEmit) {
+            Box r = {fmaxf(widen_dn(cb.lox), tb.lox), fmaxf(widen_dn(cb.loy), tb.loy), fmaxf(widen_dn(cb.loz), tb.loz),
+                     fminf(widen_up(cb.hix), tb.hix), fminf(widen_up(cb.hiy), tb.hiy), fminf(widen_up(cb.hiz), tb.hiz)};
+            ref_tri[out + count] = t;
+            ref_box[out + count] = r;
+            ref_env[out + count] = e;
+          }
+          ++count;
+        }
+    if (count == 0) {  // cannot happen for a finite triangle; keep it referenced regardless
+      count = 1;
+      if (kEmit) {
+        ref_tri[out] = t;
+        ref_box[out] = tb;
+        ref_env[out] = e;
+      }
+    }
+  }
+  if (!kEmit) counts[t] = count;
+}
+
+// reference offset of each environment's first triangle
+__global__ void k_env_ref_off(const int32_t* __restrict__ ref_off, const int32_t* __restrict__ env_tri_off,
+                              int32_t E, int32_t F, const int32_t* __restrict__ total, int32_t* __restrict__ out) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e > E) return;
+  int32_t t = env_tri_off[e];
+  out[e] = t < F ? ref_off[t] : *total;
 }
 
 // ---------------------------------------------------------------- Karras tree
@@ -292,17 +467,6 @@ __global__ void k_karras(const uint64_t* __restrict__ keys, int32_t F, int key_s
   last[g] = (int32_t)base + hi;
 }
 
-__device__ __forceinline__ Box tri_box(const float4* packed, int64_t t) {
-  float4 a = packed[3 * t], b = packed[3 * t + 1], c = packed[3 * t + 2];
-  Box x;
-  x.lox = fminf(a.x, fminf(b.x, c.x));
-  x.loy = fminf(a.y, fminf(b.y, c.y));
-  x.loz = fminf(a.z, fminf(b.z, c.z));
-  x.hix = fmaxf(a.x, fmaxf(b.x, c.x));
-  x.hiy = fmaxf(a.y, fmaxf(b.y, c.y));
-  x.hiz = fmaxf(a.z, fmaxf(b.z, c.z));
-  return x;
-}
 
 __device__ __forceinline__ Box load_box_cg(const Box* p) {
   const float* f = reinterpret_cast<const float*>(p);
@@ -332,13 +496,13 @@ __device__ __forceinline__ void store_box_cg(Box* p, const Box& b) {
 }
 
 // Bottom-up refit: the second child to arrive at a node computes its box.
-__global__ void k_refit(const float4* __restrict__ packed, const uint32_t* __restrict__ vals, int32_t F,
+__global__ void k_refit(const Box* __restrict__ ref_box, const uint32_t* __restrict__ vals, int32_t F,
                         const int32_t* __restrict__ left, const int32_t* __restrict__ right,
                         const int32_t* __restrict__ parent_inner, const int32_t* __restrict__ parent_leaf,
                         Box* __restrict__ leaf_box, Box* __restrict__ inner_box, int32_t* __restrict__ visits) {
   int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= F) return;
-  Box b = tri_box(packed, vals[i]);
+  Box b = ref_box[vals[i]];
   store_box_cg(leaf_box + i, b);
   int32_t p = parent_leaf[i];
   int guard = 0;
@@ -507,11 +671,12 @@ __global__ void k_collapse_emit(const QueueItem* __restrict__ items, int32_t n_i
   atomicAdd(env_nodes + q.env, 1ull);
 }
 
-__global__ void k_gather_tris(const float4* __restrict__ packed, const uint32_t* __restrict__ vals,
-                              const int32_t* __restrict__ perm, int32_t F, float4* __restrict__ out) {
+__global__ void k_gather_tris(const float4* __restrict__ packed, const int32_t* __restrict__ ref_tri,
+                              const uint32_t* __restrict__ vals, const int32_t* __restrict__ perm, int32_t R,
+                              float4* __restrict__ out) {
   int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= F) return;
-  int64_t t = vals[perm[k]];
+  if (k >= R) return;
+  int64_t t = ref_tri[vals[perm[k]]];
   out[3 * (int64_t)k] = packed[3 * t];
   out[3 * (int64_t)k + 1] = packed[3 * t + 1];
   out[3 * (int64_t)k + 2] = packed[3 * t + 2];
@@ -552,7 +717,6 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
   AGS_CHECK(cudaMalloc(&sc->d.world_verts, std::max<int64_t>(V, 1) * sizeof(float4)));
   AGS_CHECK(cudaMalloc(&sc->d.tri_vidx, std::max<int64_t>(3 * (int64_t)F, 1) * sizeof(int32_t)));
   AGS_CHECK(cudaMalloc(&sc->d.env_root, std::max<int32_t>(E, 1) * sizeof(int32_t)));
-  AGS_CHECK(cudaMalloc(&sc->d.tris, std::max<int64_t>(3 * (int64_t)F, 1) * sizeof(float4)));
 
   float *d_base = nullptr, *d_poses = nullptr, *d_rot = nullptr;
   int32_t *d_sub_vert = nullptr, *d_sub_tri = nullptr, *d_sub_seg = nullptr, *d_sub_env = nullptr,
@@ -586,22 +750,15 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
                                                             sc->d.world_verts);
   AGS_CHECK(cudaGetLastError());
 
-  // roots and level-0 queue (host side: environments with at least one triangle)
-  std::vector<int32_t> env_root(E, -1);
-  std::vector<QueueItem> q0;
-  for (int32_t e = 0; e < E; ++e) {
-    int64_t n = sc->env_tri_off[e + 1] - sc->env_tri_off[e];
-    if (n <= 0) continue;
-    env_root[e] = (int32_t)q0.size();
-    int32_t base = (int32_t)sc->env_tri_off[e];
-    q0.push_back({n >= 2 ? base : ~base, e});
-  }
-  AGS_CHECK(cudaMemcpyAsync(sc->d.env_root, env_root.data(), (size_t)std::max(E, 1) * sizeof(int32_t),
-                            cudaMemcpyHostToDevice, s));
   sc->env_nodes.assign(E, 0);
+  sc->env_ref_off.assign(E + 1, 0);
   if (F == 0) {
+    std::vector<int32_t> env_root(E, -1);
+    AGS_CHECK(cudaMemcpyAsync(sc->d.env_root, env_root.data(), (size_t)std::max(E, 1) * sizeof(int32_t),
+                              cudaMemcpyHostToDevice, s));
     AGS_CHECK(cudaMalloc(&sc->d.nodes, sizeof(WideNode)));
     sc->n_nodes = 0;
+    sc->n_refs = 0;
     AGS_CHECK(cudaStreamSynchronize(s));
     return AGS_OK;
   }
@@ -614,59 +771,113 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
   k_pack_triangles<<<blocks_for(F, 256), 256, 0, s>>>(sc->d.tri_vidx, F, sc->d.world_verts, d_sub_tri, J, d_sub_seg,
                                                       d_sub_env, d_env_tri, d_packed, d_tri_env);
 
-  // a2: Morton codes over each environment's centroid bounds
-  int64_t max_env_tris = 0;
-  for (int32_t e = 0; e < E; ++e) max_env_tris = std::max(max_env_tris, sc->env_tri_off[e + 1] - sc->env_tri_off[e]);
+  // per-environment bounds of triangle boxes' centres: split cell size and Morton frame
+  Box* d_tbox = nullptr;
+  int32_t* d_bounds = nullptr;
+  AGS_CHECK(tmp.alloc(&d_tbox, (size_t)F));
+  AGS_CHECK(tmp.alloc(&d_bounds, 6 * (size_t)E));
+  k_tri_boxes<<<blocks_for(F, 256), 256, 0, s>>>(d_packed, F, d_tbox);
+  k_init_bounds<<<blocks_for(E, 128), 128, 0, s>>>(d_bounds, E);
+  k_env_bounds<<<blocks_for(F, 256), 256, 0, s>>>(d_tbox, d_tri_env, F, d_bounds);
+
+  // references: large triangles split into clipped cells
+  const uint32_t split_code = (sc->flags >> 12) & 0xFFu;
+  const float cells = split_code == 1 ? 0.0f : (split_code == 0 ? (float)kDefaultSplitCells : (float)split_code);
+  int32_t *d_ref_count = nullptr, *d_ref_tot = nullptr, *d_env_ref = nullptr;
+  AGS_CHECK(tmp.alloc(&d_ref_count, (size_t)F));
+  AGS_CHECK(tmp.alloc(&d_ref_tot, 1));
+  AGS_CHECK(tmp.alloc(&d_env_ref, (size_t)E + 1));
+  void* d_scan_f = nullptr;
+  AGS_CHECK(tmp.alloc(reinterpret_cast<char**>(&d_scan_f), scan_temp_bytes(F)));
+  // references per triangle are capped so that their total stays below 2^31
+  const int max_refs = (int)std::max<int64_t>(1, std::min<int64_t>(kSplitMaxRefs, ((1ll << 31) - 2 - F) / F + 1));
+  k_split<false><<<blocks_for(F, 128), 128, 0, s>>>(d_packed, d_tri_env, F, d_bounds, cells, max_refs, d_ref_count,
+                                                   nullptr, nullptr, nullptr, nullptr);
+  AGS_CHECK(cudaGetLastError());
+  AGS_CHECK(exclusive_scan(d_ref_count, F, d_ref_tot, d_scan_f, s));
+  k_env_ref_off<<<blocks_for((int64_t)E + 1, 128), 128, 0, s>>>(d_ref_count, d_env_tri, E, F, d_ref_tot, d_env_ref);
+  std::vector<int32_t> env_ref32(E + 1);
+  AGS_CHECK(cudaMemcpyAsync(env_ref32.data(), d_env_ref, ((size_t)E + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  AGS_CHECK(cudaStreamSynchronize(s));
+  const int32_t R = env_ref32[E];
+  if (R < F) {
+    set_error("reference splitting produced too few references");
+    return AGS_ERR_CUDA;
+  }
+  for (int32_t e = 0; e <= E; ++e) sc->env_ref_off[e] = env_ref32[e];
+  sc->n_refs = R;
+  int32_t *d_ref_tri = nullptr, *d_ref_env = nullptr;
+  Box* d_ref_box = nullptr;
+  AGS_CHECK(tmp.alloc(&d_ref_tri, (size_t)R));
+  AGS_CHECK(tmp.alloc(&d_ref_env, (size_t)R));
+  AGS_CHECK(tmp.alloc(&d_ref_box, (size_t)R));
+  k_split<true><<<blocks_for(F, 128), 128, 0, s>>>(d_packed, d_tri_env, F, d_bounds, cells, max_refs, nullptr,
+                                                  d_ref_count, d_ref_tri, d_ref_box, d_ref_env);
+  AGS_CHECK(cudaGetLastError());
+
+  // roots and level-0 queue (environments with at least one reference)
+  std::vector<int32_t> env_root(E, -1);
+  std::vector<QueueItem> q0;
+  int64_t max_env_refs = 0;
+  for (int32_t e = 0; e < E; ++e) {
+    int64_t n = sc->env_ref_off[e + 1] - sc->env_ref_off[e];
+    max_env_refs = std::max(max_env_refs, n);
+    if (n <= 0) continue;
+    env_root[e] = (int32_t)q0.size();
+    int32_t base = (int32_t)sc->env_ref_off[e];
+    q0.push_back({n >= 2 ? base : ~base, e});
+  }
+  AGS_CHECK(cudaMemcpyAsync(sc->d.env_root, env_root.data(), (size_t)std::max(E, 1) * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, s));
+
+  // a2: Morton codes of reference centres over each environment's bounds
   int env_bits = 0;
   while ((1ll << env_bits) < E) ++env_bits;
   int bits = 10;
-  if (max_env_tris > (1ll << 20)) bits = std::min(21, (64 - env_bits) / 3);
+  if (max_env_refs > (1ll << 20)) bits = std::min(21, (64 - env_bits) / 3);
   bits = std::min(bits, (64 - env_bits) / 3);
   int key_shift = 3 * bits;
   int end_bit = key_shift + env_bits;
-
-  int32_t* d_bounds = nullptr;
-  AGS_CHECK(tmp.alloc(&d_bounds, 6 * (size_t)E));
   k_init_bounds<<<blocks_for(E, 128), 128, 0, s>>>(d_bounds, E);
-  k_env_bounds<<<blocks_for(F, 256), 256, 0, s>>>(d_packed, d_tri_env, F, d_bounds);
+  k_env_bounds<<<blocks_for(R, 256), 256, 0, s>>>(d_ref_box, d_ref_env, R, d_bounds);
   uint64_t *d_keys = nullptr, *d_keys2 = nullptr;
   uint32_t *d_vals = nullptr, *d_vals2 = nullptr;
-  AGS_CHECK(tmp.alloc(&d_keys, (size_t)F));
-  AGS_CHECK(tmp.alloc(&d_keys2, (size_t)F));
-  AGS_CHECK(tmp.alloc(&d_vals, (size_t)F));
-  AGS_CHECK(tmp.alloc(&d_vals2, (size_t)F));
-  k_morton<<<blocks_for(F, 256), 256, 0, s>>>(d_packed, d_tri_env, F, d_bounds, bits, d_keys, d_vals);
+  AGS_CHECK(tmp.alloc(&d_keys, (size_t)R));
+  AGS_CHECK(tmp.alloc(&d_keys2, (size_t)R));
+  AGS_CHECK(tmp.alloc(&d_vals, (size_t)R));
+  AGS_CHECK(tmp.alloc(&d_vals2, (size_t)R));
+  k_morton<<<blocks_for(R, 256), 256, 0, s>>>(d_ref_box, d_ref_env, R, d_bounds, bits, d_keys, d_vals);
   AGS_CHECK(cudaGetLastError());
   void* d_sort_tmp = nullptr;
-  AGS_CHECK(tmp.alloc(reinterpret_cast<char**>(&d_sort_tmp), sort_temp_bytes(F)));
-  AGS_CHECK(sort_pairs(d_keys, d_vals, d_keys2, d_vals2, F, end_bit, d_sort_tmp, s));
+  AGS_CHECK(tmp.alloc(reinterpret_cast<char**>(&d_sort_tmp), sort_temp_bytes(R)));
+  AGS_CHECK(sort_pairs(d_keys, d_vals, d_keys2, d_vals2, R, end_bit, d_sort_tmp, s));
 
-  // binary radix tree per environment
+  // binary radix tree per environment (over its references)
   int32_t *d_left, *d_right, *d_pin, *d_pleaf, *d_first, *d_last, *d_visits;
-  AGS_CHECK(tmp.alloc(&d_left, (size_t)F));
-  AGS_CHECK(tmp.alloc(&d_right, (size_t)F));
-  AGS_CHECK(tmp.alloc(&d_pin, (size_t)F));
-  AGS_CHECK(tmp.alloc(&d_pleaf, (size_t)F));
-  AGS_CHECK(tmp.alloc(&d_first, (size_t)F));
-  AGS_CHECK(tmp.alloc(&d_last, (size_t)F));
-  AGS_CHECK(tmp.alloc(&d_visits, (size_t)F));
-  AGS_CHECK(cudaMemsetAsync(d_visits, 0, (size_t)F * sizeof(int32_t), s));
-  k_karras<<<blocks_for(F, 256), 256, 0, s>>>(d_keys, F, key_shift, d_env_tri, d_left, d_right, d_pin, d_pleaf,
+  AGS_CHECK(tmp.alloc(&d_left, (size_t)R));
+  AGS_CHECK(tmp.alloc(&d_right, (size_t)R));
+  AGS_CHECK(tmp.alloc(&d_pin, (size_t)R));
+  AGS_CHECK(tmp.alloc(&d_pleaf, (size_t)R));
+  AGS_CHECK(tmp.alloc(&d_first, (size_t)R));
+  AGS_CHECK(tmp.alloc(&d_last, (size_t)R));
+  AGS_CHECK(tmp.alloc(&d_visits, (size_t)R));
+  AGS_CHECK(cudaMemsetAsync(d_visits, 0, (size_t)R * sizeof(int32_t), s));
+  k_karras<<<blocks_for(R, 256), 256, 0, s>>>(d_keys, R, key_shift, d_env_ref, d_left, d_right, d_pin, d_pleaf,
                                               d_first, d_last);
   Box *d_leaf_box, *d_inner_box;
-  AGS_CHECK(tmp.alloc(&d_leaf_box, (size_t)F));
-  AGS_CHECK(tmp.alloc(&d_inner_box, (size_t)F));
-  k_refit<<<blocks_for(F, 256), 256, 0, s>>>(d_packed, d_vals, F, d_left, d_right, d_pin, d_pleaf, d_leaf_box,
+  AGS_CHECK(tmp.alloc(&d_leaf_box, (size_t)R));
+  AGS_CHECK(tmp.alloc(&d_inner_box, (size_t)R));
+  k_refit<<<blocks_for(R, 256), 256, 0, s>>>(d_ref_box, d_vals, R, d_left, d_right, d_pin, d_pleaf, d_leaf_box,
                                              d_inner_box, d_visits);
   AGS_CHECK(cudaGetLastError());
 
   // collapse into 8-wide nodes, level by level
-  // wide nodes: at most F/(L+1) + E without inner children (each covers more
-  // than L triangles, or is a root), and every node with inner children has
-  // 8 slots, which bounds those by (F + F/(L+1) + E)/7
-  const int leaf_cap = ((sc->flags >> 8) & 0xFu) ? (int)((sc->flags >> 8) & 0xFu) : kMaxLeafTris;
-  const double leafonly = (double)F / (leaf_cap + 1) + E;
-  int64_t node_cap = (int64_t)(leafonly + ((double)F + leafonly) / 7.0) + 2 * (int64_t)E + 64;
+  // wide nodes: at most R/(L+1) + E without inner children (each covers more
+  // than L references, or is a root), and every node with inner children has
+  // 8 slots, which bounds those by (R + R/(L+1) + E)/7
+  const int leaf_max = ((sc->flags >> 8) & 0xFu) ? (int)((sc->flags >> 8) & 0xFu) : kDefaultLeafTris;
+  const double leafonly = (double)R / (leaf_max + 1) + E;
+  int64_t node_cap = (int64_t)(leafonly + ((double)R + leafonly) / 7.0) + 2 * (int64_t)E + 64;
   WideNode* d_nodes_tmp = nullptr;
   AGS_CHECK(tmp.alloc(&d_nodes_tmp, (size_t)node_cap));
   QueueItem *d_q = nullptr, *d_q2 = nullptr;
@@ -680,7 +891,7 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
   AGS_CHECK(tmp.alloc(&d_slots, 8 * (size_t)q_cap));
   AGS_CHECK(tmp.alloc(&d_ninner, (size_t)q_cap));
   AGS_CHECK(tmp.alloc(&d_ntris, (size_t)q_cap));
-  AGS_CHECK(tmp.alloc(&d_perm, (size_t)F));
+  AGS_CHECK(tmp.alloc(&d_perm, (size_t)R));
   AGS_CHECK(tmp.alloc(&d_tot, 2));
   void* d_scan_tmp = nullptr;
   AGS_CHECK(tmp.alloc(reinterpret_cast<char**>(&d_scan_tmp), scan_temp_bytes(q_cap)));
@@ -689,7 +900,6 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
   AGS_CHECK(cudaMemsetAsync(d_env_nodes, 0, (size_t)E * sizeof(unsigned long long), s));
   AGS_CHECK(cudaMemcpyAsync(d_q, q0.data(), q0.size() * sizeof(QueueItem), cudaMemcpyHostToDevice, s));
 
-  const int leaf_max = ((sc->flags >> 8) & 0xFu) ? (int)((sc->flags >> 8) & 0xFu) : kMaxLeafTris;
   int32_t n_items = (int32_t)q0.size();
   int32_t level_base = 0, tri_level_base = 0;
   int levels = 0;
@@ -700,7 +910,7 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
     }
     k_collapse_expand<<<blocks_for(n_items, 128), 128, 0, s>>>(d_q, n_items, d_left, d_right, d_first, d_last,
                                                               d_inner_box, leaf_max, d_slots, d_ninner, d_ntris,
-                                                              F, d_err);
+                                                              R, d_err);
     AGS_CHECK(cudaGetLastError());
     AGS_CHECK(exclusive_scan(d_ninner, n_items, d_tot, d_scan_tmp, s));
     AGS_CHECK(exclusive_scan(d_ntris, n_items, d_tot + 1, d_scan_tmp, s));
@@ -712,7 +922,7 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
       set_error("BVH collapse met an out-of-range node reference");
       return AGS_ERR_CUDA;
     }
-    if (tot[0] < 0 || tot[1] < 0 || (int64_t)tri_level_base + tot[1] > F) {
+    if (tot[0] < 0 || tot[1] < 0 || (int64_t)tri_level_base + tot[1] > R) {
       set_error("BVH collapse produced inconsistent counts");
       return AGS_ERR_CUDA;
     }
@@ -730,15 +940,16 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
     tri_level_base += tot[1];
     n_items = tot[0];
   }
-  if (tri_level_base != F) {
-    set_error("BVH collapse lost triangles");
+  if (tri_level_base != R) {
+    set_error("BVH collapse lost references");
     return AGS_ERR_CUDA;
   }
   sc->n_nodes = level_base;
   AGS_CHECK(cudaMalloc(&sc->d.nodes, std::max<int64_t>(sc->n_nodes, 1) * sizeof(WideNode)));
   AGS_CHECK(cudaMemcpyAsync(sc->d.nodes, d_nodes_tmp, (size_t)sc->n_nodes * sizeof(WideNode),
                             cudaMemcpyDeviceToDevice, s));
-  k_gather_tris<<<blocks_for(F, 256), 256, 0, s>>>(d_packed, d_vals, d_perm, F, sc->d.tris);
+  AGS_CHECK(cudaMalloc(&sc->d.tris, std::max<int64_t>(3 * (int64_t)R, 1) * sizeof(float4)));
+  k_gather_tris<<<blocks_for(R, 256), 256, 0, s>>>(d_packed, d_ref_tri, d_vals, d_perm, R, sc->d.tris);
   AGS_CHECK(cudaGetLastError());
   std::vector<unsigned long long> env_nodes(E);
   AGS_CHECK(cudaMemcpyAsync(env_nodes.data(), d_env_nodes, (size_t)E * sizeof(unsigned long long),

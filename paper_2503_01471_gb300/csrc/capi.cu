@@ -70,7 +70,7 @@ ags_status fill_trace_args(ags_context* ctx, const ags_scene* sc, const ags_sens
   a.tris = sc->d.tris;
   a.env_root = sc->d.env_root;
   a.n_nodes = (int32_t)sc->n_nodes;
-  a.n_tris = (int32_t)sc->n_tris;
+  a.n_tris = (int32_t)sc->n_refs;
   a.n_scene_envs = sc->n_envs;
   a.env_ids = env_ids;
   a.poses = poses;
@@ -199,7 +199,7 @@ ags_status ags_scene_build(ags_context* ctx, const ags_env_mesh* envs, int32_t n
   if (!envs) return invalid("envs is NULL");
   if (n_envs < 1 || n_envs > 65536) return invalid("n_envs must be in [1, 65536]");
   if ((build_flags & 0xFFu) != AGS_BVH_FP32) return invalid("unsupported BVH node format in build_flags");
-  if ((build_flags & ~0xFFFu) != 0) return invalid("unknown bits in build_flags");
+  if ((build_flags & ~0xFFFFFu) != 0) return invalid("unknown bits in build_flags");
   if (((build_flags >> 8) & 0xFu) > (uint32_t)kMaxLeafTris) return invalid("leaf size must be 1..4");
   // sizes
   int64_t J = 0, V = 0, F = 0;
@@ -452,17 +452,19 @@ ags_status ags_scene_stats(const ags_scene* sc, int32_t env, int64_t* n_tris, in
   AGS_API_BEGIN
   if (!sc) return invalid("scene is NULL");
   if (env < -1 || env >= sc->n_envs) return invalid("env out of range");
-  int64_t t, nd;
+  int64_t t, nd, refs;
   if (env == -1) {
     t = sc->n_tris;
     nd = sc->n_nodes;
+    refs = sc->n_refs;
   } else {
     t = sc->env_tri_off[env + 1] - sc->env_tri_off[env];
     nd = sc->env_nodes[env];
+    refs = sc->env_ref_off.empty() ? 0 : sc->env_ref_off[env + 1] - sc->env_ref_off[env];
   }
   if (n_tris) *n_tris = t;
   if (n_nodes) *n_nodes = nd;
-  if (bytes) *bytes = nd * (int64_t)sizeof(WideNode) + t * kTriFloat4 * (int64_t)sizeof(float4);
+  if (bytes) *bytes = nd * (int64_t)sizeof(WideNode) + refs * kTriFloat4 * (int64_t)sizeof(float4);
   return AGS_OK;
   AGS_API_END
 }

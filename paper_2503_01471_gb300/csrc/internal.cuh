@@ -30,7 +30,8 @@ struct __align__(16) WideNode {
 };
 static_assert(sizeof(WideNode) == 208, "WideNode layout");
 
-constexpr int kMaxLeafTris = 4;  // triangles per wide-BVH leaf (2-bit count field)
+constexpr int kMaxLeafTris = 4;      // largest wide-BVH leaf (2-bit count field)
+constexpr int kDefaultLeafTris = 2;  // default leaf size (fewest instructions per ray on room scenes)
 constexpr uint8_t kMetaEmpty = 0xFF;
 constexpr float kEmptyBoxCoord = 1e30f;  // empty slots hold a far-away point box
 
@@ -50,7 +51,7 @@ struct SceneDevice {
   float4* world_verts = nullptr;   // [V] xyz world, w 0
   int32_t* tri_vidx = nullptr;     // [3F] global vertex indices (input order)
   WideNode* nodes = nullptr;       // [n_nodes]
-  float4* tris = nullptr;          // [3F] packed, BVH leaf order
+  float4* tris = nullptr;          // [3R] packed, one per BVH reference, leaf order
   int32_t* env_root = nullptr;     // [E] root node index, -1 if empty
 };
 
@@ -79,6 +80,7 @@ struct ags_scene {
   ags_context* ctx = nullptr;
   int32_t n_envs = 0;
   int64_t n_tris = 0, n_verts = 0, n_subs = 0, n_nodes = 0;
+  int64_t n_refs = 0;                  // BVH references (triangles, some split into several)
   uint32_t flags = 0;
   ags::SceneDevice d;
   std::vector<int64_t> env_tri_off;    // [E+1]
@@ -87,6 +89,7 @@ struct ags_scene {
   std::vector<int64_t> sub_tri_off;    // [J+1]
   std::vector<int32_t> sub_seg;        // [J]
   std::vector<int64_t> env_nodes;      // [E]
+  std::vector<int64_t> env_ref_off;    // [E+1]
 };
 
 namespace ags {

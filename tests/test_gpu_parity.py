@@ -301,7 +301,9 @@ def test_bit_exact_across_bvh_variants(ctx):
     BVH variant gives bit-identical depth and segments."""
     batch, spec, poses = S.obstacle_rooms(6, steps=1, width=120, height=90)
     outs = []
-    for flags in (ags.AGS_LEAF_SIZE(1), ags.AGS_LEAF_SIZE(2), ags.AGS_LEAF_SIZE(3), ags.AGS_LEAF_SIZE(4)):
+    variants = [ags.AGS_LEAF_SIZE(n) for n in (1, 2, 3, 4)]
+    variants += [ags.AGS_SPLIT_CELLS(1), ags.AGS_SPLIT_CELLS(64) | ags.AGS_LEAF_SIZE(2), ags.AGS_SPLIT_CELLS(4)]
+    for flags in variants:
         scene = ags.ags_scene_build(ctx, batch, flags)
         try:
             outs.append(render(ctx, scene, spec, poses[0]))
@@ -310,3 +312,25 @@ def test_bit_exact_across_bvh_variants(ctx):
     for d, s in outs[1:]:
         assert np.array_equal(d, outs[0][0]) and np.array_equal(s, outs[0][1])
     check_all(batch, spec, poses[0], outs[0][0], outs[0][1], tag="BVH variants 120x90")
+
+
+def test_reference_splitting_keeps_results_and_adds_references(ctx):
+    """Large triangles (the room's walls, a forest's ground) get several BVH references; the scene's
+    triangles and every ray's result stay the same."""
+    batch, spec, poses = S.obstacle_rooms(3, steps=1, width=64, height=48)
+    off = ags.ags_scene_build(ctx, batch, ags.AGS_SPLIT_CELLS(1))
+    on = ags.ags_scene_build(ctx, batch)
+    try:
+        t0, n0, b0 = ags.ags_scene_stats(off)
+        t1, n1, b1 = ags.ags_scene_stats(on)
+        assert t0 == t1 == int(batch.env_tri_counts().sum())
+        assert b1 > b0  # more references, each a 48-byte triangle copy
+        a = render(ctx, off, spec, poses[0])
+        b = render(ctx, on, spec, poses[0])
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        for e in range(3):
+            assert np.array_equal(ags.ags_scene_get_world_triangles(off, e)[0],
+                                  ags.ags_scene_get_world_triangles(on, e)[0])
+    finally:
+        ags.ags_scene_destroy(off)
+        ags.ags_scene_destroy(on)
