@@ -29,6 +29,11 @@ if ROOT not in sys.path:
 
 METRIC = "Mrays/s at 1024 envs x 270x480 depth+seg vs plain; p50/p99 served latency"
 UNIT = "Mrays/s"
+# other workloads of the method, measured with the same harness (--workload)
+WORKLOADS = {
+    "rooms": {"envs": 1024, "metric": METRIC},
+    "forest": {"envs": 256, "metric": "Mrays/s at 256 LiDAR forests x 64x512 range+seg"},
+}
 PAPER_MRAYS = 340.5  # Table II, 1024 envs x 270x480 (RTX 3090; context)
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 
@@ -39,14 +44,22 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--envs", type=int, default=1024)
-    ap.add_argument("--width", type=int, default=480)
-    ap.add_argument("--height", type=int, default=270)
+    ap.add_argument("--workload", default="rooms", choices=sorted(WORKLOADS))
+    ap.add_argument("--envs", type=int, default=None, help="environments per GPU (workload default)")
+    ap.add_argument("--width", type=int, default=None, help="camera columns (rooms only)")
+    ap.add_argument("--height", type=int, default=None, help="camera rows (rooms only)")
     ap.add_argument("--walk", type=int, default=100, help="length of the sensor-pose random walk")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
-    return ap.parse_args()
+    ap.add_argument("--build-flags", type=int, default=0, help="ags_scene_build flags")
+    args = ap.parse_args()
+    if args.envs is None:
+        args.envs = WORKLOADS[args.workload]["envs"]
+    if args.workload == "rooms":
+        args.width = args.width or 480
+        args.height = args.height or 270
+    return args
 
 
 def dist_info():
@@ -178,9 +191,16 @@ def make_workload(args, rank, world=1):
     from paper_2503_01471_gb300 import scenes as S
     from paper_2503_01471_gb300 import shard
     envs = shard.weak_shard(args.envs, rank, max(world, rank + 1))
-    batch, spec, poses = S.obstacle_rooms(args.envs, steps=args.walk, width=args.width, height=args.height,
-                                          envs=list(envs) if rank else None)
-    return batch, spec, poses
+    ids = list(envs) if rank else None
+    if args.workload == "forest":
+        return S.lidar_forests(args.envs, steps=args.walk, envs=ids)
+    return S.obstacle_rooms(args.envs, steps=args.walk, width=args.width, height=args.height, envs=ids)
+
+
+def workload_name(args, spec, E):
+    if args.workload == "forest":
+        return f"LiDAR forests, {E} envs (50-200 trees of 2k-10k triangles), {spec.height}x{spec.width} LiDAR"
+    return f"obstacle rooms, {E} envs x {spec.height}x{spec.width} depth+seg camera"
 
 
 def bench_reference(args, rank, world):
@@ -199,11 +219,10 @@ def bench_reference(args, rank, world):
     t_tot = sum(dt for _, dt in times)
     value = n_tot / t_tot / 1e6
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "impl": "reference", "metric": WORKLOADS[args.workload]["metric"], "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"obstacle rooms, {E} envs x {args.height}x{args.width} depth+seg camera",
-                   "envs": E, "width": args.width, "height": args.height},
+        "config": {"workload": workload_name(args, spec, E), "envs": E, "width": spec.width, "height": spec.height},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"each step: {rays_per_step} random rays of one env (env cycles), FP64 brute "
                                    f"force over every triangle"},
@@ -230,7 +249,7 @@ def bench_ours(args, rank, world, local):
     E = batch.n_envs
     ctx = ags.ags_context_create(local)
     t0 = time.perf_counter()
-    scene = ags.ags_scene_build(ctx, batch)
+    scene = ags.ags_scene_build(ctx, batch, args.build_flags)
     build_s = time.perf_counter() - t0
     n_tris = int(batch.env_tri_counts().sum())
     poses_d = torch.as_tensor(poses).to(dev)  # [walk, E, 7]
@@ -324,16 +343,18 @@ def bench_ours(args, rank, world, local):
 
     hbm, peak_kind = peaks()
     achieved_gbs = b_ray * rays_per_step / (ms_step * 1e-3) / 1e9
-    workload = f"obstacle rooms, {E} envs x {spec.height}x{spec.width} depth+seg camera"
-    traffic = profiled_traffic(f"{E}x{spec.height}x{spec.width}")
+    workload = workload_name(args, spec, E)
+    traffic = profiled_traffic(f"{args.workload}:{E}x{spec.height}x{spec.width}")
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": WORKLOADS[args.workload]["metric"], "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": value / PAPER_MRAYS if (E == 1024 and spec.width == 480 and spec.height == 270) else None,
+        "vs_baseline": value / PAPER_MRAYS if (args.workload == "rooms" and E == 1024 and spec.width == 480
+                                                and spec.height == 270) else None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload, "envs_per_gpu": E, "width": spec.width, "height": spec.height,
                    "tris_per_gpu": n_tris, "rays_per_step": rays_per_step * world, "walk_steps": walk,
-                   "l2": "not flushed: per step the BVHs (~1.1 GB) and outputs (1.06 GB) exceed the 129 MB L2",
+                   "l2": "not flushed: per step the resident BVHs and the outputs exceed the 129 MB L2",
+                   "bvh_bytes": ags.ags_scene_stats(scene)[2], "build_flags": args.build_flags,
                    "parallelism": f"env-sharded x{world}, no collective on the data path"},
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
                      "frac": achieved_gbs / hbm, "traffic": traffic,
