@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--build-flags", type=int, default=0, help="ags_scene_build flags")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
     args = ap.parse_args()
     if args.envs is None:
         args.envs = WORKLOADS[args.workload]["envs"]
@@ -262,6 +263,9 @@ def bench_ours(args, rank, world, local):
     def step(i):
         ags.ags_render(ctx, scene, spec, poses_d[i % walk], depth, seg, stream)
 
+    tuned = None
+    if not args.no_autotune:  # untimed set-up, like the scene build
+        tuned = ags.ags_autotune(ctx, scene, spec, poses_d[0], depth, seg, 2).as_dict()
     for i in range(args.warmup):
         step(i)
     ags.ags_stream_status(ctx, stream)
@@ -364,6 +368,7 @@ def bench_ours(args, rank, world, local):
         "clocks": clk.summary(),
         "e2e": e2e,
         "gpu_launches": args.steps,
+        "launch_config": ags.ags_get_launch_config(ctx, scene, spec), "autotuned": tuned is not None,
         "build_ms": build_s * 1e3,
         "build_mtris_per_s": n_tris / build_s / 1e6,
     }

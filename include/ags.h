@@ -104,6 +104,17 @@ typedef struct {
 #define AGS_LEAF_SIZE(n) (((uint32_t)(n) & 0xFu) << 8)
 #define AGS_SPLIT_CELLS(n) (((uint32_t)(n) & 0xFFu) << 12)
 
+/* Launch shape of the persistent render kernel for one (scene, sensor shape):
+ * each warp repeatedly takes a tile of tile_w x (32 * rays_per_lane / tile_w)
+ * pixels (or beams) of one environment, each lane tracing rays_per_lane rays
+ * of it; the grid holds blocks_per_sm blocks per SM (0: as many as fit). */
+typedef struct {
+  int32_t tile_w;         /* with rays_per_lane, one of the compiled shapes: */
+  int32_t rays_per_lane;  /* (8,1) 8x4, (4,1) 4x8, (8,2) 8x8, (16,2) 16x4, (16,4) 16x8 */
+  int32_t blocks_per_sm;  /* 0, or 1 .. the kernel's occupancy limit */
+  float ms;               /* ags_autotune: measured time of one render; else 0 */
+} ags_launch_config;
+
 /* Create a context on CUDA device `device`. */
 ags_status ags_context_create(int device, ags_context** out);
 void ags_context_destroy(ags_context* ctx);
@@ -166,6 +177,29 @@ ags_status ags_render_host(ags_context* ctx, const ags_scene* scene, const ags_s
  */
 ags_status ags_render_count(ags_context* ctx, const ags_scene* scene, const ags_sensor_spec* spec,
                             const float* sensor_poses_dev, uint64_t counts_host[3]);
+
+/*
+ * ags_autotune -- time the render of `scene` with `spec` under each compiled
+ * launch shape (tiles 8x4, 4x8, 8x8, 16x4, 16x8; full or reduced grid),
+ * `repeats` timed renders each after one warm-up, on the context's
+ * stream, writing into the caller's buffers (as ags_render). The fastest shape
+ * is stored with the scene for this sensor shape (type, width, height) and
+ * used by every later ags_render / ags_render_envs of that shape; it is also
+ * returned in *best. Synchronous. The paper has no counterpart (its renderer
+ * is Warp's); the shape does not change any output bit.
+ */
+ags_status ags_autotune(ags_context* ctx, const ags_scene* scene, const ags_sensor_spec* spec,
+                        const float* sensor_poses_dev, float* out_depth_dev, int32_t* out_seg_dev,
+                        int32_t repeats, ags_launch_config* best);
+
+/* Set (or, with config == NULL, clear) the launch shape used for `scene` with
+ * sensors of spec's type, width and height. */
+ags_status ags_set_launch_config(ags_context* ctx, const ags_scene* scene, const ags_sensor_spec* spec,
+                                 const ags_launch_config* config);
+
+/* The launch shape ags_render would use for `scene` and `spec`. */
+ags_status ags_get_launch_config(ags_context* ctx, const ags_scene* scene, const ags_sensor_spec* spec,
+                                 ags_launch_config* config);
 
 /* Synchronise `cuda_stream`, then read and clear the context's device status
  * word: AGS_OK; AGS_ERR_INVALID_ARG if a device sensor pose was non-finite or

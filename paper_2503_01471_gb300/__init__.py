@@ -48,7 +48,8 @@ EXPORTS = [
     "ags_context_create", "ags_context_destroy", "ags_scene_build", "ags_scene_destroy", "ags_render",
     "ags_render_envs", "ags_render_host", "ags_render_count", "ags_stream_status", "ags_last_error",
     "ags_scene_n_envs", "ags_scene_get_world_triangles", "ags_scene_stats", "ags_scene_node_bytes",
-    "ags_context_set_traversal_cap", "ags_transform_vertices_noalloc",
+    "ags_context_set_traversal_cap", "ags_transform_vertices_noalloc", "ags_autotune",
+    "ags_set_launch_config", "ags_get_launch_config",
 ]
 
 
@@ -65,6 +66,15 @@ class ags_submesh(ctypes.Structure):
 
 class ags_env_mesh(ctypes.Structure):
     _fields_ = [("submeshes", ctypes.c_void_p), ("n_submeshes", ctypes.c_int32)]
+
+
+class ags_launch_config(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int32), ("rays_per_lane", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {"tile_w": self.tile_w, "tile_h": 32 * self.rays_per_lane // self.tile_w,
+                "rays_per_lane": self.rays_per_lane, "blocks_per_sm": self.blocks_per_sm, "ms": self.ms}
 
 
 class ags_sensor_spec(ctypes.Structure):
@@ -113,6 +123,10 @@ def lib() -> ctypes.CDLL:
         "ags_scene_node_bytes": (i32, [vp]),
         "ags_context_set_traversal_cap": (i32, [vp, i32]),
         "ags_transform_vertices_noalloc": (i32, [vp, vp, i32, vp, i32, vp, vp, vp]),
+        "ags_autotune": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), vp, vp, vp, i32,
+                               ctypes.POINTER(ags_launch_config)]),
+        "ags_set_launch_config": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), ctypes.POINTER(ags_launch_config)]),
+        "ags_get_launch_config": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), ctypes.POINTER(ags_launch_config)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -283,6 +297,30 @@ def ags_render_count(ctx: int, scene: int, spec, sensor_poses):
     c = (ctypes.c_uint64 * 3)()
     _check(lib().ags_render_count(ctx, scene, ctypes.byref(s), _ptr(sensor_poses), c), "ags_render_count")
     return int(c[0]), int(c[1]), int(c[2])
+
+
+def ags_autotune(ctx: int, scene: int, spec, sensor_poses, out_depth, out_seg, repeats: int = 3):
+    """Pick (and remember for this scene and sensor shape) the fastest launch shape; returns it."""
+    s = make_spec(spec)
+    best = ags_launch_config()
+    _check(lib().ags_autotune(ctx, scene, ctypes.byref(s), _ptr(sensor_poses), _ptr(out_depth), _ptr(out_seg),
+                              int(repeats), ctypes.byref(best)), "ags_autotune")
+    return best
+
+
+def ags_set_launch_config(ctx: int, scene: int, spec, tile_w=None, rays_per_lane=1, blocks_per_sm=0) -> None:
+    """Set the launch shape for this scene and sensor shape (tile_w None clears it)."""
+    s = make_spec(spec)
+    cfg = None if tile_w is None else ctypes.byref(ags_launch_config(int(tile_w), int(rays_per_lane),
+                                                                     int(blocks_per_sm), 0.0))
+    _check(lib().ags_set_launch_config(ctx, scene, ctypes.byref(s), cfg), "ags_set_launch_config")
+
+
+def ags_get_launch_config(ctx: int, scene: int, spec) -> dict:
+    s = make_spec(spec)
+    c = ags_launch_config()
+    _check(lib().ags_get_launch_config(ctx, scene, ctypes.byref(s), ctypes.byref(c)), "ags_get_launch_config")
+    return c.as_dict()
 
 
 def ags_stream_status(ctx: int, stream=None) -> int:

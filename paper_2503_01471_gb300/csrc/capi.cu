@@ -64,8 +64,27 @@ unsigned int* tile_counter(ags_context* ctx, cudaStream_t s) {
   return p;
 }
 
+ags_launch_config default_config() { return {8, 1, 0, 0.0f}; }
+
+ags_launch_config lookup_config(const ags_scene* sc, const ags_sensor_spec* spec) {
+  auto it = sc->launch.find({spec->type, spec->width, spec->height});
+  return it != sc->launch.end() ? it->second : default_config();
+}
+
+int max_blocks_per_sm(ags_context* ctx) { return ctx->sm_count > 0 ? ctx->trace_blocks / ctx->sm_count : 1; }
+
+ags_status check_config(ags_context* ctx, const ags_launch_config* c) {
+  if (!c) return invalid("launch config is NULL");
+  if (!trace_shape_supported(c->tile_w, c->rays_per_lane))
+    return invalid("unsupported launch shape: (tile_w, rays_per_lane) must be one of (8,1) (4,1) (8,2) (16,2) (16,4)");
+  if (c->blocks_per_sm < 0 || c->blocks_per_sm > max_blocks_per_sm(ctx))
+    return invalid("blocks_per_sm must be 0 .. the kernel's occupancy limit");
+  return AGS_OK;
+}
+
 ags_status fill_trace_args(ags_context* ctx, const ags_scene* sc, const ags_sensor_spec* spec, int32_t n,
-                           const int32_t* env_ids, const float* poses, float* depth, int32_t* seg, TraceArgs& a) {
+                           const int32_t* env_ids, const float* poses, float* depth, int32_t* seg, TraceArgs& a,
+                           const ags_launch_config& cfg) {
   a.nodes = sc->d.nodes;
   a.tris = sc->d.tris;
   a.env_root = sc->d.env_root;
@@ -87,8 +106,13 @@ ags_status fill_trace_args(ags_context* ctx, const ags_scene* sc, const ags_sens
   a.dv = spec->height > 1 ? (float)(((double)spec->vfov_max_rad - (double)spec->vfov_min_rad) / (spec->height - 1)) : 0.0f;
   a.min_range = spec->min_range;
   a.max_range = spec->max_range;
-  a.tiles_x = (spec->width + 7) / 8;
-  int64_t tiles_y = (spec->height + 3) / 4;
+  int lw = 0;
+  while ((1 << lw) < cfg.tile_w) ++lw;
+  a.log2_tile_w = lw;
+  a.rays_per_lane = cfg.rays_per_lane;
+  a.tile_h = 32 * cfg.rays_per_lane / cfg.tile_w;
+  a.tiles_x = (spec->width + cfg.tile_w - 1) / cfg.tile_w;
+  int64_t tiles_y = (spec->height + a.tile_h - 1) / a.tile_h;
   int64_t per_env = (int64_t)a.tiles_x * tiles_y;
   int64_t total = per_env * n;
   if (total >= (1ll << 31)) return invalid("too many rays in one render call (tiles >= 2^31)");
@@ -100,7 +124,7 @@ ags_status fill_trace_args(ags_context* ctx, const ags_scene* sc, const ags_sens
   return AGS_OK;
 }
 
-ags_status launch(ags_context* ctx, TraceArgs& a, cudaStream_t s, bool count) {
+ags_status launch(ags_context* ctx, TraceArgs& a, cudaStream_t s, bool count, int blocks_per_sm = 0) {
   unsigned int* counter = tile_counter(ctx, s);
   if (!counter) {
     set_error("cannot allocate the tile counter");
@@ -110,7 +134,9 @@ ags_status launch(ags_context* ctx, TraceArgs& a, cudaStream_t s, bool count) {
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(tile counter)");
   if (a.total_tiles == 0) return AGS_OK;
-  e = launch_trace(a, count ? ctx->trace_count_blocks : ctx->trace_blocks, count, s);
+  const int blocks = count ? ctx->trace_count_blocks
+                           : (blocks_per_sm > 0 ? ctx->sm_count * blocks_per_sm : ctx->trace_blocks);
+  e = launch_trace(a, blocks, count, s);
   if (e != cudaSuccess) return cuda_fail(e, "k_trace launch");
   return AGS_OK;
 }
@@ -303,8 +329,9 @@ ags_status ags_render(ags_context* ctx, const ags_scene* sc, const ags_sensor_sp
   if (!poses || !depth || !seg) return invalid("poses/depth/seg pointer is NULL");
   DeviceGuard g(ctx->device);
   TraceArgs a{};
-  if ((st = fill_trace_args(ctx, sc, spec, sc->n_envs, nullptr, poses, depth, seg, a)) != AGS_OK) return st;
-  return launch(ctx, a, static_cast<cudaStream_t>(stream), false);
+  const ags_launch_config cfg = lookup_config(sc, spec);
+  if ((st = fill_trace_args(ctx, sc, spec, sc->n_envs, nullptr, poses, depth, seg, a, cfg)) != AGS_OK) return st;
+  return launch(ctx, a, static_cast<cudaStream_t>(stream), false, cfg.blocks_per_sm);
   AGS_API_END
 }
 
@@ -319,8 +346,9 @@ ags_status ags_render_envs(ags_context* ctx, const ags_scene* sc, const ags_sens
   if (n > 0 && (!env_ids || !poses || !depth || !seg)) return invalid("env_ids/poses/depth/seg pointer is NULL");
   DeviceGuard g(ctx->device);
   TraceArgs a{};
-  if ((st = fill_trace_args(ctx, sc, spec, n, env_ids, poses, depth, seg, a)) != AGS_OK) return st;
-  return launch(ctx, a, static_cast<cudaStream_t>(stream), false);
+  const ags_launch_config cfg = lookup_config(sc, spec);
+  if ((st = fill_trace_args(ctx, sc, spec, n, env_ids, poses, depth, seg, a, cfg)) != AGS_OK) return st;
+  return launch(ctx, a, static_cast<cudaStream_t>(stream), false, cfg.blocks_per_sm);
   AGS_API_END
 }
 
@@ -379,8 +407,9 @@ ags_status ags_render_host(ags_context* ctx, const ags_scene* sc, const ags_sens
   if ((e = cudaMemcpyAsync(d_pose, poses_h, (size_t)n * 7 * sizeof(float), cudaMemcpyHostToDevice, s)) != cudaSuccess)
     return cuda_fail(e, "cudaMemcpyAsync(poses)");
   TraceArgs a{};
-  if ((st = fill_trace_args(ctx, sc, spec, (int32_t)n, nullptr, d_pose, d_depth, d_seg, a)) != AGS_OK) return st;
-  if ((st = launch(ctx, a, s, false)) != AGS_OK) return st;
+  const ags_launch_config cfg = lookup_config(sc, spec);
+  if ((st = fill_trace_args(ctx, sc, spec, (int32_t)n, nullptr, d_pose, d_depth, d_seg, a, cfg)) != AGS_OK) return st;
+  if ((st = launch(ctx, a, s, false, cfg.blocks_per_sm)) != AGS_OK) return st;
   if ((e = cudaMemcpyAsync(depth_h, d_depth, (size_t)(n * pix) * sizeof(float), cudaMemcpyDeviceToHost, s)) !=
           cudaSuccess ||
       (e = cudaMemcpyAsync(seg_h, d_seg, (size_t)(n * pix) * sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
@@ -399,7 +428,9 @@ ags_status ags_render_count(ags_context* ctx, const ags_scene* sc, const ags_sen
   if (!poses || !counts_host) return invalid("poses/counts pointer is NULL");
   DeviceGuard g(ctx->device);
   TraceArgs a{};
-  if ((st = fill_trace_args(ctx, sc, spec, sc->n_envs, nullptr, poses, nullptr, nullptr, a)) != AGS_OK) return st;
+  if ((st = fill_trace_args(ctx, sc, spec, sc->n_envs, nullptr, poses, nullptr, nullptr, a, default_config())) !=
+      AGS_OK)
+    return st;
   cudaStream_t s = ctx->stream;
   cudaError_t e = cudaMemsetAsync(ctx->d_counts, 0, 3 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counts)");
@@ -465,6 +496,90 @@ ags_status ags_scene_stats(const ags_scene* sc, int32_t env, int64_t* n_tris, in
   if (n_tris) *n_tris = t;
   if (n_nodes) *n_nodes = nd;
   if (bytes) *bytes = nd * (int64_t)sizeof(WideNode) + refs * kTriFloat4 * (int64_t)sizeof(float4);
+  return AGS_OK;
+  AGS_API_END
+}
+
+ags_status ags_set_launch_config(ags_context* ctx, const ags_scene* sc, const ags_sensor_spec* spec,
+                                 const ags_launch_config* config) {
+  AGS_API_BEGIN
+  if (!ctx || !sc) return invalid("ctx or scene is NULL");
+  if (sc->ctx != ctx) return invalid("scene belongs to another context");
+  ags_status st = check_spec(spec);
+  if (st != AGS_OK) return st;
+  if (!config) {
+    sc->launch.erase({spec->type, spec->width, spec->height});
+    return AGS_OK;
+  }
+  if ((st = check_config(ctx, config)) != AGS_OK) return st;
+  sc->launch[{spec->type, spec->width, spec->height}] = *config;
+  return AGS_OK;
+  AGS_API_END
+}
+
+ags_status ags_get_launch_config(ags_context* ctx, const ags_scene* sc, const ags_sensor_spec* spec,
+                                 ags_launch_config* config) {
+  AGS_API_BEGIN
+  if (!ctx || !sc || !config) return invalid("ctx, scene or config is NULL");
+  ags_status st = check_spec(spec);
+  if (st != AGS_OK) return st;
+  *config = lookup_config(sc, spec);
+  return AGS_OK;
+  AGS_API_END
+}
+
+ags_status ags_autotune(ags_context* ctx, const ags_scene* sc, const ags_sensor_spec* spec, const float* poses,
+                        float* depth, int32_t* seg, int32_t repeats, ags_launch_config* best) {
+  AGS_API_BEGIN
+  if (!ctx || !sc) return invalid("ctx or scene is NULL");
+  if (sc->ctx != ctx) return invalid("scene belongs to another context");
+  ags_status st = check_spec(spec);
+  if (st != AGS_OK) return st;
+  if (!poses || !depth || !seg || !best) return invalid("poses/depth/seg/best pointer is NULL");
+  if (repeats < 1 || repeats > 1000) return invalid("repeats must be in [1, 1000]");
+  DeviceGuard g(ctx->device);
+
+  const int full = max_blocks_per_sm(ctx);
+  const int grids[2] = {0, full > 2 ? full - 2 : 0};
+  cudaStream_t s = ctx->stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return cuda_fail(e, "cudaEventCreate");
+  }
+  ags_launch_config top = default_config();
+  top.ms = -1.0f;
+  st = AGS_OK;
+  for (int gi = 0; gi < 2 && st == AGS_OK; ++gi) {
+    if (gi == 1 && grids[1] == 0) break;
+    for (int k = 0; k < kTraceShapes && st == AGS_OK; ++k) {
+      ags_launch_config c = {kTraceShape[k][0], kTraceShape[k][1], grids[gi], 0.0f};
+      TraceArgs a{};
+      if ((st = fill_trace_args(ctx, sc, spec, sc->n_envs, nullptr, poses, depth, seg, a, c)) != AGS_OK) break;
+      if ((st = launch(ctx, a, s, false, c.blocks_per_sm)) != AGS_OK) break;
+      if ((e = cudaEventRecord(e0, s)) != cudaSuccess) {
+        st = cuda_fail(e, "cudaEventRecord");
+        break;
+      }
+      for (int r = 0; r < repeats && st == AGS_OK; ++r) st = launch(ctx, a, s, false, c.blocks_per_sm);
+      if (st != AGS_OK) break;
+      float ms = 0.0f;
+      if ((e = cudaEventRecord(e1, s)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+          (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) {
+        st = cuda_fail(e, "autotune timing");
+        break;
+      }
+      c.ms = ms / repeats;
+      if (top.ms < 0.0f || c.ms < top.ms) top = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != AGS_OK) return st;
+  if ((st = ags_stream_status(ctx, s)) != AGS_OK) return st;
+  sc->launch[{spec->type, spec->width, spec->height}] = top;
+  *best = top;
   return AGS_OK;
   AGS_API_END
 }

@@ -76,6 +76,13 @@ struct ags_context {
   size_t stage_bytes = 0;
 };
 
+struct LaunchKey {
+  int32_t type, width, height;
+  bool operator<(const LaunchKey& o) const {
+    return type != o.type ? type < o.type : (width != o.width ? width < o.width : height < o.height);
+  }
+};
+
 struct ags_scene {
   ags_context* ctx = nullptr;
   int32_t n_envs = 0;
@@ -90,6 +97,7 @@ struct ags_scene {
   std::vector<int32_t> sub_seg;        // [J]
   std::vector<int64_t> env_nodes;      // [E]
   std::vector<int64_t> env_ref_off;    // [E+1]
+  mutable std::map<LaunchKey, ags_launch_config> launch;  // tuned or set launch shapes per sensor shape
 };
 
 namespace ags {
@@ -131,6 +139,7 @@ struct TraceArgs {
   float inv_f;               // camera: 1/f
   float hfov, vmax, dv;      // LiDAR: azimuth span, top elevation, elevation step
   float min_range, max_range;
+  int32_t log2_tile_w, tile_h, rays_per_lane;  // a warp's tile: (1 << log2_tile_w) x tile_h pixels
   int32_t tiles_x, tiles_per_env;
   int64_t total_tiles;
   int32_t max_visits;
@@ -139,6 +148,10 @@ struct TraceArgs {
   unsigned long long* counts;
 };
 cudaError_t launch_trace(const TraceArgs& a, int blocks, bool count, cudaStream_t s);
+// compiled launch shapes of the render kernel: {tile width, rays per lane}
+constexpr int kTraceShapes = 5;
+constexpr int kTraceShape[kTraceShapes][2] = {{8, 1}, {4, 1}, {8, 2}, {16, 2}, {16, 4}};
+bool trace_shape_supported(int tile_w, int rays_per_lane);
 int trace_blocks_per_sm(bool count);
 
 }  // namespace ags

@@ -12,8 +12,11 @@ namespace ags {
 namespace {
 
 constexpr int kTraceThreads = 128;
+#ifndef AGS_TRACE_MIN_BLOCKS
+#define AGS_TRACE_MIN_BLOCKS 7
+#endif
+constexpr int kTraceMinBlocks = AGS_TRACE_MIN_BLOCKS;  // resident blocks per SM the register budget targets
 constexpr int kStackSize = 64;
-constexpr int kTileW = 8, kTileH = 4;
 // Box culling is made conservative against float32 rounding: each slab
 // bound is computed as one fma with a per-ray constant that already moves
 // the near bound down and the far bound up by more than the rounding of
@@ -139,8 +142,9 @@ __device__ __forceinline__ void test_triangle(const Ray& r, const float4* __rest
   }
 }
 
-template <bool kCount>
-__global__ void __launch_bounds__(kTraceThreads) k_trace(const TraceArgs a) {
+template <bool kCount, int kTileW, int kRaysPerLane>
+__global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) k_trace(const TraceArgs a) {
+  constexpr int kTileH = 32 * kRaysPerLane / kTileW;
   const int lane = threadIdx.x & 31;
   int32_t* __restrict__ status = a.status;
   int2 stack[kStackSize];
@@ -158,11 +162,17 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(const TraceArgs a) {
       if (lane == 0) atomicOr(a.status, kStatusBadIndex);
       continue;
     }
-    const int32_t col = (t_in % a.tiles_x) * kTileW + (lane & (kTileW - 1));
-    const int32_t row = (t_in / a.tiles_x) * kTileH + (lane >> 3);
+    const int32_t tile_x0 = (t_in % a.tiles_x) * kTileW;
+    const int32_t tile_y0 = (t_in / a.tiles_x) * kTileH;
+
+    for (int rr = 0; rr < kRaysPerLane; ++rr) {
+    const int idx = rr * 32 + lane;
+    const int32_t col = tile_x0 + (idx % kTileW);
+    const int32_t row = tile_y0 + (idx / kTileW);
     if (col >= a.W || row >= a.H) continue;
 
-    // ---- a3: ray generation from the sensor pose (p, q)
+    // ---- a3: ray generation from the sensor pose (p, q); recomputed per ray
+    // (L1-resident) so that nothing of it stays live during the traversal
     const float* P = a.poses + 7 * (int64_t)slot;
     const float px = __ldg(P), py = __ldg(P + 1), pz = __ldg(P + 2);
     const float qx = __ldg(P + 3), qy = __ldg(P + 4), qz = __ldg(P + 5), qw = __ldg(P + 6);
@@ -350,6 +360,7 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(const TraceArgs a) {
     const int64_t o = ((int64_t)slot * a.H + row) * a.W + col;
     a.out_depth[o] = v;
     a.out_seg[o] = seg;
+    }  // rays of this lane in the tile
   }
   if (kCount) {
 #pragma unroll
@@ -370,14 +381,26 @@ __global__ void __launch_bounds__(kTraceThreads) k_trace(const TraceArgs a) {
 
 int trace_blocks_per_sm(bool count) {
   int n = 0;
-  cudaError_t e = count ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<true>, kTraceThreads, 0)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<false>, kTraceThreads, 0);
+  cudaError_t e = count ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<true, 8, 1>, kTraceThreads, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<false, 8, 1>, kTraceThreads, 0);
   return (e == cudaSuccess && n > 0) ? n : 1;
 }
 
+bool trace_shape_supported(int tile_w, int rays_per_lane) {
+  for (int k = 0; k < kTraceShapes; ++k)
+    if (kTraceShape[k][0] == tile_w && kTraceShape[k][1] == rays_per_lane) return true;
+  return false;
+}
+
 cudaError_t launch_trace(const TraceArgs& a, int blocks, bool count, cudaStream_t s) {
-  if (count) k_trace<true><<<blocks, kTraceThreads, 0, s>>>(a);
-  else k_trace<false><<<blocks, kTraceThreads, 0, s>>>(a);
+  const int w = 1 << a.log2_tile_w, r = a.rays_per_lane;
+  if (count) k_trace<true, 8, 1><<<blocks, kTraceThreads, 0, s>>>(a);
+  else if (w == 8 && r == 1) k_trace<false, 8, 1><<<blocks, kTraceThreads, 0, s>>>(a);
+  else if (w == 4 && r == 1) k_trace<false, 4, 1><<<blocks, kTraceThreads, 0, s>>>(a);
+  else if (w == 8 && r == 2) k_trace<false, 8, 2><<<blocks, kTraceThreads, 0, s>>>(a);
+  else if (w == 16 && r == 2) k_trace<false, 16, 2><<<blocks, kTraceThreads, 0, s>>>(a);
+  else if (w == 16 && r == 4) k_trace<false, 16, 4><<<blocks, kTraceThreads, 0, s>>>(a);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

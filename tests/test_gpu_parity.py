@@ -334,3 +334,32 @@ def test_reference_splitting_keeps_results_and_adds_references(ctx):
     finally:
         ags.ags_scene_destroy(off)
         ags.ags_scene_destroy(on)
+
+
+def test_launch_shapes_and_autotune_keep_results(ctx):
+    """Every launch shape (tile, rays per lane, grid) renders the same bits; the autotuner's pick is
+    remembered for the scene and sensor shape."""
+    batch, spec, poses = S.obstacle_rooms(5, steps=1, width=70, height=45)  # ragged for every tile shape
+    scene = ags.ags_scene_build(ctx, batch)
+    try:
+        ref = render(ctx, scene, spec, poses[0])
+        for w, rpl, b in [(8, 1, 0), (4, 1, 0), (8, 2, 1), (16, 2, 0), (16, 4, 2)]:
+            ags.ags_set_launch_config(ctx, scene, spec, w, rpl, b)
+            assert ags.ags_get_launch_config(ctx, scene, spec)["tile_w"] == w
+            out = render(ctx, scene, spec, poses[0])
+            assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1]), (w, rpl, b)
+        for bad in [(3, 1, 0), (8, 3, 0), (64, 1, 0), (32, 1, 0), (8, 1, 10_000)]:
+            with pytest.raises(ags.AgsError):
+                ags.ags_set_launch_config(ctx, scene, spec, *bad)
+        ags.ags_set_launch_config(ctx, scene, spec, None)
+        p = torch.as_tensor(poses[0]).cuda()
+        d = torch.empty((5, 45, 70), device="cuda")
+        s = torch.empty((5, 45, 70), dtype=torch.int32, device="cuda")
+        best = ags.ags_autotune(ctx, scene, spec, p, d, s, 1)
+        assert best.ms > 0
+        assert ags.ags_get_launch_config(ctx, scene, spec) == best.as_dict()
+        out = render(ctx, scene, spec, poses[0])
+        assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1])
+        check_all(batch, spec, poses[0], out[0], out[1], tag="launch shapes 70x45")
+    finally:
+        ags.ags_scene_destroy(scene)
