@@ -33,6 +33,7 @@ UNIT = "Mrays/s"
 WORKLOADS = {
     "rooms": {"envs": 1024, "metric": METRIC},
     "forest": {"envs": 256, "metric": "Mrays/s at 256 LiDAR forests x 64x512 range+seg"},
+    "serving": {"envs": 8192, "metric": "served Mrays/s, 8192 rooms of 1k-200k triangles, mixed sensors; p50/p99 ms"},
 }
 PAPER_MRAYS = 340.5  # Table II, 1024 envs x 270x480 (RTX 3090; context)
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
@@ -54,6 +55,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--build-flags", type=int, default=0, help="ags_scene_build flags")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
+    ap.add_argument("--no-serving", action="store_true", help="skip the served-latency measurement")
     args = ap.parse_args()
     if args.envs is None:
         args.envs = WORKLOADS[args.workload]["envs"]
@@ -185,6 +187,104 @@ def cpu_baseline(batch, spec, poses, budget_s=12.0):
     return {"value": n / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} random rays ({k} from each of envs {envs}) at step 0, FP64 brute force "
                       f"over every triangle of the env, {dt:.1f} s"}
+
+
+# ---------------------------------------------------------------- serving
+def serving_specs():
+    from paper_2503_01471_gb300 import scenes as S
+    return [S.pinhole(240, 135), S.pinhole(480, 270), S.lidar(512, 64)]
+
+
+def serving_measure(ags, ctx, scene, n_envs, poses_step, specs, loads=(0.5, 1.0), duration=0.5, seq_max=2000,
+                    burst=20000, seed=5):
+    """Continuous-batching server under a burst (capacity) and Poisson arrivals at fractions of it, and the
+    sequential one-request-at-a-time launch on the same traces (first seq_max requests)."""
+    rng = np.random.default_rng(seed)
+    rays = np.array([sp.width * sp.height for sp in specs])
+
+    def trace(n, rate):
+        env = rng.integers(0, n_envs, n)
+        sp = rng.integers(0, len(specs), n)
+        reqs = ags.make_requests(env, sp, poses_step[env])
+        arrival = np.cumsum(rng.exponential(1.0 / rate, n)) if rate else np.zeros(n)
+        return reqs, arrival
+
+    def pct(x, q):
+        return float(np.percentile(x, q)) if len(x) else None
+
+    server = ags.ags_server_create(ctx, scene, specs, max_slots=512, max_inflight=3, arena_bytes=4 << 30)
+    try:
+        reqs, arr = trace(burst, None)
+        out = ags.ags_server_replay(server, reqs, arr)
+        span = float(out["t_done"].max() - out["t_submit"].min())
+        cap = burst / span
+        res = {"capacity_req_per_s": cap, "capacity_mrays_per_s": float(rays[reqs["spec"]].sum()) / span / 1e6,
+               "sensors": [f"{'camera' if sp.type == 0 else 'lidar'} {sp.height}x{sp.width}" for sp in specs],
+               "max_slots": 512, "max_inflight": 3, "loads": []}
+        for f in loads:
+            rate = f * cap
+            n = max(100, int(rate * duration))
+            reqs, arr = trace(n, rate)
+            out = ags.ags_server_replay(server, reqs, arr)
+            lat = (out["t_done"] - out["t_submit"]) * 1e3
+            m = min(seq_max, n)
+            seq = ags.ags_replay_sequential(ctx, scene, specs, reqs[:m], arr[:m])
+            slat = (seq["t_done"] - seq["t_submit"]) * 1e3
+            res["loads"].append({"load": f, "req_per_s": rate, "requests": n, "p50_ms": pct(lat, 50),
+                                 "p99_ms": pct(lat, 99), "mrays_per_s": float(rays[reqs["spec"]].sum()) /
+                                 float(out["t_done"].max() - out["t_submit"].min()) / 1e6,
+                                 "sequential": {"requests": m, "p50_ms": pct(slat, 50), "p99_ms": pct(slat, 99)}})
+        # a load the sequential launch can sustain: half its own capacity, same trace for both
+        reqs, arr = trace(300, None)
+        seq = ags.ags_replay_sequential(ctx, scene, specs, reqs, arr)
+        seq_cap = 300 / float(seq["t_done"].max() - seq["t_submit"].min())
+        rate = 0.5 * seq_cap
+        n = max(200, min(2000, int(rate * 2 * duration)))
+        reqs, arr = trace(n, rate)
+        out = ags.ags_server_replay(server, reqs, arr)
+        seq = ags.ags_replay_sequential(ctx, scene, specs, reqs, arr)
+        lat = (out["t_done"] - out["t_submit"]) * 1e3
+        slat = (seq["t_done"] - seq["t_submit"]) * 1e3
+        res["sequential_capacity_req_per_s"] = seq_cap
+        res["at_half_sequential_capacity"] = {
+            "req_per_s": rate, "requests": n, "batched": {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99)},
+            "sequential": {"p50_ms": pct(slat, 50), "p99_ms": pct(slat, 99)}}
+        st = ags.ags_server_stats(server)
+        res["batches"] = st["batches"]
+    finally:
+        ags.ags_server_destroy(server)
+    return res
+
+
+def bench_serving(args, rank, world, local):
+    """Serving workload: rooms of 1k-200k triangles, mixed camera and LiDAR requests."""
+    import torch
+
+    import paper_2503_01471_gb300 as ags
+    from paper_2503_01471_gb300 import build as B
+    from paper_2503_01471_gb300 import scenes as S
+
+    B.build()
+    torch.cuda.set_device(local)
+    batch, poses = S.serving_rooms(args.envs)
+    ctx = ags.ags_context_create(local)
+    t0 = time.perf_counter()
+    scene = ags.ags_scene_build(ctx, batch, args.build_flags)
+    build_s = time.perf_counter() - t0
+    n_tris = int(batch.env_tri_counts().sum())
+    specs = serving_specs()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        res = serving_measure(ags, ctx, scene, batch.n_envs, poses[0], specs,
+                              loads=(0.5, 0.75, 1.0, 1.25, 1.5), duration=1.0)
+    line = {"metric": WORKLOADS["serving"]["metric"], "value": res["capacity_mrays_per_s"], "unit": UNIT,
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"serving: {batch.n_envs} rooms, triangles log-uniform 1k-200k "
+                                   f"({n_tris / 1e6:.1f} M resident), Poisson arrivals",
+                       "tris": n_tris, "bvh_bytes": ags.ags_scene_stats(scene)[2]},
+            "serving": res, "clocks": clk.summary(), "build_ms": build_s * 1e3}
+    print(json.dumps(line), flush=True)
+    ags.ags_scene_destroy(scene)
+    ags.ags_context_destroy(ctx)
 
 
 # ---------------------------------------------------------------- workload
@@ -374,6 +474,9 @@ def bench_ours(args, rank, world, local):
     }
     if plain is not None:
         line["plain"] = plain
+    if args.workload == "rooms" and not args.no_serving:
+        # served latency on the same resident scene, mixed camera and LiDAR requests
+        line["serving"] = serving_measure(ags, ctx, scene, E, poses[0], serving_specs())
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(batch, spec, poses)
     if rank == 0:
@@ -389,6 +492,10 @@ def main():
     rank, world, local = dist_info()
     if args.impl == "reference":
         bench_reference(args, rank, world)
+        return
+    if args.workload == "serving":
+        if rank == 0:
+            bench_serving(args, rank, world, local)
         return
     bench_ours(args, rank, world, local)
 

@@ -201,6 +201,71 @@ ags_status ags_set_launch_config(ags_context* ctx, const ags_scene* scene, const
 ags_status ags_get_launch_config(ags_context* ctx, const ags_scene* scene, const ags_sensor_spec* spec,
                                  ags_launch_config* config);
 
+/* ---------------------------------------------------------------- serving
+ * A server renders a stream of requests against one resident scene with
+ * continuous batching (the paper has no counterpart: there the renderer is
+ * called once per simulation step). A worker thread takes waiting requests in
+ * arrival order and admits each as soon as a slot of the next batch and room
+ * in the device output arena are free (admission by free device memory); it
+ * launches the batch (every request with its own environment, sensor shape
+ * and pose, in one persistent launch) on one of max_inflight streams, so
+ * batches overlap on the GPU while later requests queue. Results stay in the
+ * arena -- device memory, for a GPU consumer -- until released. */
+typedef struct ags_server ags_server;
+
+typedef struct {
+  int32_t max_slots;          /* requests per batch, 1..65536 */
+  int32_t max_inflight;       /* batches on the GPU at once (streams), 1..16 */
+  int64_t arena_bytes;        /* output arena (8 bytes per ray); 0 = a quarter of free device memory */
+  const ags_sensor_spec* specs;  /* sensor shapes requests may use (copied) */
+  int32_t n_specs;            /* 1..256 */
+  int32_t auto_release;       /* nonzero: free a request's outputs as soon as it completes */
+} ags_server_config;
+
+typedef struct {
+  int32_t env;                /* environment of the scene */
+  int32_t spec;               /* index into the server's specs */
+  float pose[7];              /* sensor pose (px, py, pz, qx, qy, qz, qw) */
+  uint64_t tag;               /* caller's value, returned in the completion */
+} ags_request;
+
+typedef struct {
+  uint64_t request_id;
+  uint64_t tag;
+  int32_t status;             /* ags_status of the request */
+  const float* depth_dev;     /* [H][W] depth / range in the arena (valid until released) */
+  const int32_t* seg_dev;     /* [H][W] segment IDs */
+  double t_submit, t_start, t_done;  /* host steady-clock seconds: submitted, launched, seen done */
+} ags_completion;
+
+/* Create a server on a resident scene (the context's device). Allocates the
+ * arena (limited to 90% of the device memory free at creation), per-stream
+ * slot tables and a worker thread. */
+ags_status ags_server_create(ags_context* ctx, const ags_scene* scene, const ags_server_config* config,
+                             ags_server** out);
+/* Stop the worker after the requests on the GPU finish; waiting requests are dropped. */
+void ags_server_destroy(ags_server* server);
+/* Queue a request (validated now; AGS_ERR_BUSY if 2^20 requests wait). Thread-safe. */
+ags_status ags_server_submit(ags_server* server, const ags_request* request, uint64_t* request_id);
+/* Up to `max` completed requests, oldest first; never blocks. Thread-safe. */
+ags_status ags_server_poll(ags_server* server, ags_completion* out, int32_t max, int32_t* n_out);
+/* Free a completed request's outputs in the arena. Thread-safe. */
+ags_status ags_server_release(ags_server* server, uint64_t request_id);
+/* Counters; any pointer may be NULL. */
+ags_status ags_server_stats(ags_server* server, int64_t* submitted, int64_t* completed, int64_t* batches,
+                            int64_t* arena_free_bytes);
+/* Load generator: submit reqs[i] at arrival_s[i] seconds after the call
+ * starts (non-decreasing), collect every completion into out[i] and release
+ * it; returns when all n are done. No other submissions may run meanwhile. */
+ags_status ags_server_replay(ags_server* server, const ags_request* reqs, const double* arrival_s, int32_t n,
+                             ags_completion* out);
+/* Baseline for the same trace: one request at a time on the context's stream
+ * (ags_render_envs of its environment, then synchronise), each started no
+ * earlier than its arrival; out[i] as above (its buffers are freed on return). */
+ags_status ags_replay_sequential(ags_context* ctx, const ags_scene* scene, const ags_sensor_spec* specs,
+                                 int32_t n_specs, const ags_request* reqs, const double* arrival_s, int32_t n,
+                                 ags_completion* out);
+
 /* Synchronise `cuda_stream`, then read and clear the context's device status
  * word: AGS_OK; AGS_ERR_INVALID_ARG if a device sensor pose was non-finite or
  * had a zero quaternion (those rays report NaN, segment -1);
@@ -244,6 +309,10 @@ ags_status ags_transform_vertices_noalloc(ags_context* ctx, const float* base_ve
                                           int32_t n_vertices, const int32_t* submesh_vertex_offsets_dev,
                                           int32_t n_submeshes, const float* poses_dev,
                                           float* world_vertices_dev, void* cuda_stream);
+
+/* Copy `bytes` from device memory to host memory (synchronous), e.g. a
+ * completion's outputs. */
+ags_status ags_memcpy_d2h(void* dst_host, const void* src_dev, int64_t bytes);
 
 /* Thread-local text of the last error ("" if none). */
 const char* ags_last_error(void);

@@ -49,7 +49,9 @@ EXPORTS = [
     "ags_render_envs", "ags_render_host", "ags_render_count", "ags_stream_status", "ags_last_error",
     "ags_scene_n_envs", "ags_scene_get_world_triangles", "ags_scene_stats", "ags_scene_node_bytes",
     "ags_context_set_traversal_cap", "ags_transform_vertices_noalloc", "ags_autotune",
-    "ags_set_launch_config", "ags_get_launch_config",
+    "ags_set_launch_config", "ags_get_launch_config", "ags_memcpy_d2h", "ags_server_create", "ags_server_destroy",
+    "ags_server_submit", "ags_server_poll", "ags_server_release", "ags_server_stats", "ags_server_replay",
+    "ags_replay_sequential",
 ]
 
 
@@ -75,6 +77,34 @@ class ags_launch_config(ctypes.Structure):
     def as_dict(self):
         return {"tile_w": self.tile_w, "tile_h": 32 * self.rays_per_lane // self.tile_w,
                 "rays_per_lane": self.rays_per_lane, "blocks_per_sm": self.blocks_per_sm, "ms": self.ms}
+
+
+class ags_server_config(ctypes.Structure):
+    _fields_ = [("max_slots", ctypes.c_int32), ("max_inflight", ctypes.c_int32), ("arena_bytes", ctypes.c_int64),
+                ("specs", ctypes.c_void_p), ("n_specs", ctypes.c_int32), ("auto_release", ctypes.c_int32)]
+
+
+class ags_request(ctypes.Structure):
+    _fields_ = [("env", ctypes.c_int32), ("spec", ctypes.c_int32), ("pose", ctypes.c_float * 7),
+                ("tag", ctypes.c_uint64)]
+
+
+class ags_completion(ctypes.Structure):
+    _fields_ = [("request_id", ctypes.c_uint64), ("tag", ctypes.c_uint64), ("status", ctypes.c_int32),
+                ("depth_dev", ctypes.c_void_p), ("seg_dev", ctypes.c_void_p), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+REQUEST_DTYPE = np.dtype({"names": ["env", "spec", "pose", "tag"], "formats": ["<i4", "<i4", ("<f4", 7), "<u8"],
+                          "offsets": [ags_request.env.offset, ags_request.spec.offset, ags_request.pose.offset,
+                                      ags_request.tag.offset], "itemsize": ctypes.sizeof(ags_request)})
+COMPLETION_DTYPE = np.dtype({"names": ["request_id", "tag", "status", "depth_dev", "seg_dev", "t_submit", "t_start",
+                                       "t_done"],
+                             "formats": ["<u8", "<u8", "<i4", "<u8", "<u8", "<f8", "<f8", "<f8"],
+                             "offsets": [getattr(ags_completion, f).offset for f in
+                                         ("request_id", "tag", "status", "depth_dev", "seg_dev", "t_submit",
+                                          "t_start", "t_done")],
+                             "itemsize": ctypes.sizeof(ags_completion)})
 
 
 class ags_sensor_spec(ctypes.Structure):
@@ -127,6 +157,16 @@ def lib() -> ctypes.CDLL:
                                ctypes.POINTER(ags_launch_config)]),
         "ags_set_launch_config": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), ctypes.POINTER(ags_launch_config)]),
         "ags_get_launch_config": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), ctypes.POINTER(ags_launch_config)]),
+        "ags_memcpy_d2h": (i32, [vp, vp, i64]),
+        "ags_server_create": (i32, [vp, vp, ctypes.POINTER(ags_server_config), ctypes.POINTER(vp)]),
+        "ags_server_destroy": (None, [vp]),
+        "ags_server_submit": (i32, [vp, ctypes.POINTER(ags_request), ctypes.POINTER(ctypes.c_uint64)]),
+        "ags_server_poll": (i32, [vp, vp, i32, ctypes.POINTER(i32)]),
+        "ags_server_release": (i32, [vp, ctypes.c_uint64]),
+        "ags_server_stats": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                   ctypes.POINTER(i64)]),
+        "ags_server_replay": (i32, [vp, vp, vp, i32, vp]),
+        "ags_replay_sequential": (i32, [vp, vp, vp, i32, vp, vp, i32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -333,3 +373,80 @@ def ags_stream_status(ctx: int, stream=None) -> int:
 def ags_last_error() -> str:
     m = lib().ags_last_error()
     return m.decode() if m else ""
+
+
+# ---------------------------------------------------------------- serving
+def ags_memcpy_d2h(dst_host: np.ndarray, src_dev: int) -> None:
+    _check(lib().ags_memcpy_d2h(dst_host.ctypes.data, int(src_dev), dst_host.nbytes), "ags_memcpy_d2h")
+
+
+def _spec_array(specs):
+    arr = (ags_sensor_spec * len(specs))(*[make_spec(x) for x in specs])
+    return arr
+
+
+def ags_server_create(ctx: int, scene: int, specs, max_slots: int = 256, max_inflight: int = 2,
+                      arena_bytes: int = 0, auto_release: bool = False) -> int:
+    arr = _spec_array(specs)
+    cfg = ags_server_config(int(max_slots), int(max_inflight), int(arena_bytes), ctypes.cast(arr, ctypes.c_void_p),
+                            len(specs), 1 if auto_release else 0)
+    h = ctypes.c_void_p()
+    _check(lib().ags_server_create(ctx, scene, ctypes.byref(cfg), ctypes.byref(h)), "ags_server_create")
+    return h.value
+
+
+def ags_server_destroy(server: int) -> None:
+    lib().ags_server_destroy(server)
+
+
+def ags_server_submit(server: int, env: int, spec: int, pose, tag: int = 0) -> int:
+    r = ags_request(int(env), int(spec), (ctypes.c_float * 7)(*[float(x) for x in pose]), int(tag))
+    rid = ctypes.c_uint64()
+    _check(lib().ags_server_submit(server, ctypes.byref(r), ctypes.byref(rid)), "ags_server_submit")
+    return rid.value
+
+
+def ags_server_poll(server: int, max_n: int = 1024) -> np.ndarray:
+    out = np.zeros(max_n, COMPLETION_DTYPE)
+    n = ctypes.c_int32()
+    _check(lib().ags_server_poll(server, out.ctypes.data, int(max_n), ctypes.byref(n)), "ags_server_poll")
+    return out[: n.value]
+
+
+def ags_server_release(server: int, request_id: int) -> None:
+    _check(lib().ags_server_release(server, int(request_id)), "ags_server_release")
+
+
+def ags_server_stats(server: int) -> dict:
+    v = [ctypes.c_int64() for _ in range(4)]
+    _check(lib().ags_server_stats(server, *[ctypes.byref(x) for x in v]), "ags_server_stats")
+    return dict(zip(("submitted", "completed", "batches", "arena_free_bytes"), (x.value for x in v)))
+
+
+def make_requests(env, spec, poses, tags=None) -> np.ndarray:
+    n = len(env)
+    r = np.zeros(n, REQUEST_DTYPE)
+    r["env"] = env
+    r["spec"] = spec
+    r["pose"] = np.asarray(poses, np.float32).reshape(n, 7)
+    r["tag"] = np.arange(n) if tags is None else tags
+    return r
+
+
+def ags_server_replay(server: int, requests: np.ndarray, arrival_s) -> np.ndarray:
+    arr = np.ascontiguousarray(arrival_s, np.float64)
+    out = np.zeros(len(requests), COMPLETION_DTYPE)
+    req = np.ascontiguousarray(requests)
+    _check(lib().ags_server_replay(server, req.ctypes.data, arr.ctypes.data, len(req), out.ctypes.data),
+           "ags_server_replay")
+    return out
+
+
+def ags_replay_sequential(ctx: int, scene: int, specs, requests: np.ndarray, arrival_s) -> np.ndarray:
+    arr = np.ascontiguousarray(arrival_s, np.float64)
+    out = np.zeros(len(requests), COMPLETION_DTYPE)
+    req = np.ascontiguousarray(requests)
+    sa = _spec_array(specs)
+    _check(lib().ags_replay_sequential(ctx, scene, ctypes.cast(sa, ctypes.c_void_p), len(specs), req.ctypes.data,
+                                       arr.ctypes.data, len(req), out.ctypes.data), "ags_replay_sequential")
+    return out

@@ -11,6 +11,24 @@
 
 namespace ags {
 
+SensorParams sensor_params(const ags_sensor_spec* spec, int tile_w, int tile_h) {
+  SensorParams p;
+  p.W = spec->width;
+  p.H = spec->height;
+  p.type = spec->type;
+  p.near_mode = spec->near_mode;
+  p.inv_f = (float)(std::tan(0.5 * (double)spec->hfov_rad) / (0.5 * (double)spec->width));
+  p.hfov = spec->hfov_rad;
+  p.vmax = spec->vfov_max_rad;
+  p.dv = spec->height > 1 ? (float)(((double)spec->vfov_max_rad - (double)spec->vfov_min_rad) / (spec->height - 1))
+                          : 0.0f;
+  p.min_range = spec->min_range;
+  p.max_range = spec->max_range;
+  p.tiles_x = (spec->width + tile_w - 1) / tile_w;
+  p.tiles_per_env = p.tiles_x * ((spec->height + tile_h - 1) / tile_h);
+  return p;
+}
+
 namespace {
 thread_local std::string g_last_error;
 
@@ -96,27 +114,14 @@ ags_status fill_trace_args(ags_context* ctx, const ags_scene* sc, const ags_sens
   a.out_depth = depth;
   a.out_seg = seg;
   a.n = n;
-  a.W = spec->width;
-  a.H = spec->height;
-  a.type = spec->type;
-  a.near_mode = spec->near_mode;
-  a.inv_f = (float)(std::tan(0.5 * (double)spec->hfov_rad) / (0.5 * (double)spec->width));
-  a.hfov = spec->hfov_rad;
-  a.vmax = spec->vfov_max_rad;
-  a.dv = spec->height > 1 ? (float)(((double)spec->vfov_max_rad - (double)spec->vfov_min_rad) / (spec->height - 1)) : 0.0f;
-  a.min_range = spec->min_range;
-  a.max_range = spec->max_range;
   int lw = 0;
   while ((1 << lw) < cfg.tile_w) ++lw;
   a.log2_tile_w = lw;
   a.rays_per_lane = cfg.rays_per_lane;
   a.tile_h = 32 * cfg.rays_per_lane / cfg.tile_w;
-  a.tiles_x = (spec->width + cfg.tile_w - 1) / cfg.tile_w;
-  int64_t tiles_y = (spec->height + a.tile_h - 1) / a.tile_h;
-  int64_t per_env = (int64_t)a.tiles_x * tiles_y;
-  int64_t total = per_env * n;
+  a.sensor = sensor_params(spec, cfg.tile_w, a.tile_h);
+  int64_t total = (int64_t)a.sensor.tiles_per_env * n;
   if (total >= (1ll << 31)) return invalid("too many rays in one render call (tiles >= 2^31)");
-  a.tiles_per_env = (int32_t)per_env;
   a.total_tiles = total;
   a.status = ctx->d_status;
   a.counts = ctx->d_counts;
@@ -498,6 +503,13 @@ ags_status ags_scene_stats(const ags_scene* sc, int32_t env, int64_t* n_tris, in
   if (bytes) *bytes = nd * (int64_t)sizeof(WideNode) + refs * kTriFloat4 * (int64_t)sizeof(float4);
   return AGS_OK;
   AGS_API_END
+}
+
+ags_status ags_memcpy_d2h(void* dst, const void* src, int64_t bytes) {
+  if (bytes < 0 || (bytes > 0 && (!dst || !src))) return invalid("bad ags_memcpy_d2h arguments");
+  if (bytes == 0) return AGS_OK;
+  cudaError_t e = cudaMemcpy(dst, src, (size_t)bytes, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? AGS_OK : cuda_fail(e, "cudaMemcpy");
 }
 
 ags_status ags_set_launch_config(ags_context* ctx, const ags_scene* sc, const ags_sensor_spec* spec,

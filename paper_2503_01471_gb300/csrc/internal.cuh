@@ -121,6 +121,30 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
                        const float* poses_h, const int32_t* sub_env_h);
 
 // trace.cu
+// Ray pattern of one sensor shape (derived from ags_sensor_spec on the host).
+struct SensorParams {
+  int32_t W, H;
+  int32_t type;
+  int32_t near_mode;
+  float inv_f;               // camera: 1/f
+  float hfov, vmax, dv;      // LiDAR: azimuth span, top elevation, elevation step
+  float min_range, max_range;
+  int32_t tiles_x;           // warp tiles across a row for the launch shape
+  int32_t tiles_per_env;     // warp tiles per environment
+};
+
+// One request of a serving batch (slot mode of the render kernel).
+struct SlotEntry {
+  int32_t env;
+  int32_t spec;              // index into the batch's SensorParams table
+  int32_t tile_begin;        // first global tile of this slot
+  int32_t pad0;
+  int64_t out_offset;        // element offset of this slot's [H][W] outputs
+  float pose[7];
+  float pad1;
+};
+static_assert(sizeof(SlotEntry) == 56, "SlotEntry layout");
+
 struct TraceArgs {
   const WideNode* nodes;
   const float4* tris;
@@ -130,17 +154,15 @@ struct TraceArgs {
   int32_t n_scene_envs;
   const int32_t* env_ids;    // nullable
   const float* poses;        // [n][7]
-  float* out_depth;          // [n][H][W]
+  float* out_depth;          // [n][H][W] (slot mode: output arena)
   int32_t* out_seg;
   int32_t n;                 // environments rendered
-  int32_t W, H;
-  int32_t type;
-  int32_t near_mode;
-  float inv_f;               // camera: 1/f
-  float hfov, vmax, dv;      // LiDAR: azimuth span, top elevation, elevation step
-  float min_range, max_range;
+  SensorParams sensor;       // uniform mode
+  const SensorParams* specs; // slot mode: table of sensor shapes
+  int32_t n_specs;
+  const SlotEntry* slots;    // slot mode when non-null
+  int32_t n_slots;
   int32_t log2_tile_w, tile_h, rays_per_lane;  // a warp's tile: (1 << log2_tile_w) x tile_h pixels
-  int32_t tiles_x, tiles_per_env;
   int64_t total_tiles;
   int32_t max_visits;
   unsigned int* tile_counter;
@@ -152,6 +174,8 @@ cudaError_t launch_trace(const TraceArgs& a, int blocks, bool count, cudaStream_
 constexpr int kTraceShapes = 5;
 constexpr int kTraceShape[kTraceShapes][2] = {{8, 1}, {4, 1}, {8, 2}, {16, 2}, {16, 4}};
 bool trace_shape_supported(int tile_w, int rays_per_lane);
+// host: ray pattern of a validated spec for tiles of tile_w x tile_h
+SensorParams sensor_params(const ags_sensor_spec* spec, int tile_w, int tile_h);
 int trace_blocks_per_sm(bool count);
 
 }  // namespace ags

@@ -142,11 +142,234 @@ __device__ __forceinline__ void test_triangle(const Ray& r, const float4* __rest
   }
 }
 
-template <bool kCount, int kTileW, int kRaysPerLane>
-__global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) k_trace(const TraceArgs a) {
+// The rays of one warp tile: sensor shape `sen`, environment `env`, tile
+// index t_in within it; `slot` locates the pose and the outputs (the
+// environment's index in the launch, or the request's slot in the table).
+template <bool kSlots>
+__device__ __forceinline__ const float* slot_pose(const TraceArgs& a, int32_t slot) {
+  if constexpr (kSlots) return a.slots[slot].pose;
+  else return a.poses + 7 * (int64_t)slot;
+}
+template <bool kSlots>
+__device__ __forceinline__ int64_t slot_out(const TraceArgs& a, const SensorParams& sen, int32_t slot) {
+  if constexpr (kSlots) return __ldg(&a.slots[slot].out_offset);
+  else return (int64_t)slot * sen.H * sen.W;
+}
+
+template <bool kCount, int kTileW, int kRaysPerLane, bool kSlots>
+__device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParams& sen, int32_t env, int32_t t_in,
+                                           int32_t slot, int lane, int2* stack, unsigned long long& n_nodes,
+                                           unsigned long long& n_tris, unsigned long long& n_rays) {
   constexpr int kTileH = 32 * kRaysPerLane / kTileW;
-  const int lane = threadIdx.x & 31;
   int32_t* __restrict__ status = a.status;
+  const int32_t tile_x0 = (t_in % sen.tiles_x) * kTileW;
+  const int32_t tile_y0 = (t_in / sen.tiles_x) * kTileH;
+
+  for (int rr = 0; rr < kRaysPerLane; ++rr) {
+  const int idx = rr * 32 + lane;
+  const int32_t col = tile_x0 + (idx % kTileW);
+  const int32_t row = tile_y0 + (idx / kTileW);
+  const int32_t W = sen.W, H = sen.H;
+  if (col >= W || row >= H) continue;
+
+  // ---- a3: ray generation from the sensor pose (p, q); recomputed per ray
+  // (L1-resident) so that nothing of it stays live during the traversal
+  const float* P = slot_pose<kSlots>(a, slot);
+  const float px = __ldg(P), py = __ldg(P + 1), pz = __ldg(P + 2);
+  const float qx = __ldg(P + 3), qy = __ldg(P + 4), qz = __ldg(P + 5), qw = __ldg(P + 6);
+  const float n2 = qx * qx + qy * qy + qz * qz + qw * qw;
+  if (!(n2 >= 1e-30f) || !isfinite(n2) || !isfinite(px + py + pz)) {
+    // a pose the method cannot use: flag it and report NaN for this ray
+    atomicOr(status, kStatusBadPose);
+    if (!kCount) {
+      const int64_t o = slot_out<kSlots>(a, sen, slot) + (int64_t)row * W + col;
+      a.out_depth[o] = __int_as_float(0x7fc00000);
+      a.out_seg[o] = -1;
+    }
+    continue;
+  }
+  const float s = 2.0f / n2;
+  const float R00 = 1.0f - s * (qy * qy + qz * qz), R01 = s * (qx * qy - qz * qw), R02 = s * (qx * qz + qy * qw);
+  const float R10 = s * (qx * qy + qz * qw), R11 = 1.0f - s * (qx * qx + qz * qz), R12 = s * (qy * qz - qx * qw);
+  const float R20 = s * (qx * qz - qy * qw), R21 = s * (qy * qz + qx * qw), R22 = 1.0f - s * (qx * qx + qy * qy);
+  float lx, ly, lz;
+  if (sen.type == AGS_PINHOLE) {
+    // unnormalised (1, a, b): the distance along it is the depth itself
+    lx = 1.0f;
+    ly = (0.5f * (float)W - ((float)col + 0.5f)) * sen.inv_f;
+    lz = (0.5f * (float)H - ((float)row + 0.5f)) * sen.inv_f;
+  } else {
+    float sin_el, cos_el, sin_az, cos_az;
+    sincosf(sen.vmax - (float)row * sen.dv, &sin_el, &cos_el);
+    sincosf(sen.hfov * ((float)col / (float)W), &sin_az, &cos_az);
+    lx = cos_el * cos_az;
+    ly = cos_el * sin_az;
+    lz = sin_el;
+  }
+  Ray r;
+  r.ox = px;
+  r.oy = py;
+  r.oz = pz;
+  setup_ray(r, R00 * lx + R01 * ly + R02 * lz, R10 * lx + R11 * ly + R12 * lz, R20 * lx + R21 * ly + R22 * lz);
+
+  // ---- a4-a6: traversal, triangle tests, nearest hit
+  float t_best = sen.max_range;  // camera: depth limit; LiDAR: range limit (unit direction)
+  int32_t best_id = 0x7fffffff, best_seg = -1;
+  int32_t node = __ldg(a.env_root + env);
+  int sp = 0, visits = 0;
+  bool failed = false;
+  while (node >= 0) {
+    if (++visits > a.max_visits) {
+      atomicOr(status, kStatusIterationCap);
+      failed = true;
+      break;
+    }
+    if (node >= a.n_nodes) {
+      atomicOr(status, kStatusBadIndex);
+      failed = true;
+      break;
+    }
+    if (kCount) ++n_nodes;
+    const float4* np = reinterpret_cast<const float4*>(a.nodes + node);
+    const float4 h = __ldg(np);
+    const int32_t child_base = __float_as_int(h.x), tri_base = __float_as_int(h.y);
+    const uint32_t meta_lo = __float_as_uint(h.z), meta_hi = __float_as_uint(h.w);
+    const float t_cull = t_best * kCullSlack;
+    const uint32_t b0 = meta_lo & 0xFFu;
+    const int ni = (b0 & 0x80u) ? (int)min(b0 & 0xFu, 8u) : 0;
+    float tmins[8];
+    uint32_t hit_mask = 0;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const float4 nx4 = __ldg(np + r.onx + half), fx4 = __ldg(np + (4 - r.onx) + half);
+      const float4 ny4 = __ldg(np + r.ony + half), fy4 = __ldg(np + (12 - r.ony) + half);
+      const float4 nz4 = __ldg(np + r.onz + half), fz4 = __ldg(np + (20 - r.onz) + half);
+      const float nxs[4] = {nx4.x, nx4.y, nx4.z, nx4.w}, fxs[4] = {fx4.x, fx4.y, fx4.z, fx4.w};
+      const float nys[4] = {ny4.x, ny4.y, ny4.z, ny4.w}, fys[4] = {fy4.x, fy4.y, fy4.z, fy4.w};
+      const float nzs[4] = {nz4.x, nz4.y, nz4.z, nz4.w}, fzs[4] = {fz4.x, fz4.y, fz4.z, fz4.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = 4 * half + q;
+        const float tnx = __fmaf_rn(nxs[q], r.ix, r.cnx), tfx = __fmaf_rn(fxs[q], r.ix, r.cfx);
+        const float tny = __fmaf_rn(nys[q], r.iy, r.cny), tfy = __fmaf_rn(fys[q], r.iy, r.cfy);
+        const float tnz = __fmaf_rn(nzs[q], r.iz, r.cnz), tfz = __fmaf_rn(fzs[q], r.iz, r.cfz);
+        const float tmin = max3f(tnx, tny, fmaxf(tnz, 0.0f));
+        const float tmax = min3f(tfx, tfy, tfz) * kSlabSlack;
+        tmins[k] = tmin;
+        if (tmin <= fminf(tmax, t_cull)) hit_mask |= 1u << k;
+      }
+    }
+    const uint32_t inner_bits = (1u << ni) - 1u;
+    uint32_t leaf_mask = hit_mask & ~inner_bits;
+    const uint32_t inner_hits = hit_mask & inner_bits;
+    // leaves of this node first: they tighten t_best before descending
+    while (leaf_mask) {
+      const int k = __ffs(leaf_mask) - 1;
+      leaf_mask &= leaf_mask - 1;
+      const uint32_t m = ((k < 4 ? meta_lo : meta_hi) >> (8 * (k & 3))) & 0xFFu;
+      if (m == kMetaEmpty) continue;
+      const int32_t start = tri_base + (int32_t)(m >> 2);
+      const int32_t cnt = (int32_t)(m & 3u) + 1;
+      if (start < 0 || start + cnt > a.n_tris) {
+        atomicOr(status, kStatusBadIndex);
+        failed = true;
+        break;
+      }
+      for (int32_t x = 0; x < cnt; ++x) test_triangle(r, a.tris, start + x, t_best, best_id, best_seg);
+      if (kCount) n_tris += cnt;
+    }
+    if (failed) break;
+    const int n_inner = __popc(inner_hits);
+    if (n_inner == 1) {  // the common case: no ordering needed
+      node = child_base + (__ffs(inner_hits) - 1);
+      continue;
+    }
+    if (n_inner > 1) {
+      // nearest first (sorting network on keys: tmin bits with the slot in the low 3 bits)
+      uint32_t keys[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        keys[k] = ((inner_hits >> k) & 1u) ? ((__float_as_uint(tmins[k]) & ~7u) | (uint32_t)k) : 0xFFFFFFFFu;
+#define AGS_CSWAP(i, j)                         \
+  {                                             \
+  const uint32_t lo_ = min(keys[i], keys[j]); \
+  const uint32_t hi_ = max(keys[i], keys[j]); \
+  keys[i] = lo_;                              \
+  keys[j] = hi_;                              \
+  }
+      AGS_CSWAP(0, 1) AGS_CSWAP(2, 3) AGS_CSWAP(4, 5) AGS_CSWAP(6, 7)
+      AGS_CSWAP(0, 2) AGS_CSWAP(1, 3) AGS_CSWAP(4, 6) AGS_CSWAP(5, 7)
+      AGS_CSWAP(1, 2) AGS_CSWAP(5, 6) AGS_CSWAP(0, 4) AGS_CSWAP(3, 7)
+      AGS_CSWAP(1, 5) AGS_CSWAP(2, 6)
+      AGS_CSWAP(1, 4) AGS_CSWAP(3, 6)
+      AGS_CSWAP(2, 4) AGS_CSWAP(3, 5)
+      AGS_CSWAP(3, 4)
+#undef AGS_CSWAP
+      const uint32_t key_cull = __float_as_uint(t_best * kCullSlack);
+#pragma unroll
+      for (int k = 7; k >= 1; --k) {
+        if (keys[k] != 0xFFFFFFFFu && (keys[k] & ~7u) <= key_cull) {
+          if (sp >= kStackSize) {
+            atomicOr(status, kStatusStackOverflow);
+            failed = true;
+          } else {
+            stack[sp++] = make_int2(child_base + (int32_t)(keys[k] & 7u), (int32_t)(keys[k] & ~7u));
+          }
+        }
+      }
+      if (failed) break;
+      if ((keys[0] & ~7u) <= key_cull) {
+        node = child_base + (int32_t)(keys[0] & 7u);
+        continue;
+      }
+    }
+    node = -1;
+    const float t_pop = t_best * kCullSlack;
+    while (sp > 0) {
+      const int2 e = stack[--sp];
+      if (__int_as_float(e.y) <= t_pop) {
+        node = e.x;
+        break;
+      }
+    }
+  }
+
+  if (kCount) {
+    ++n_rays;
+    continue;
+  }
+  float v;
+  int32_t seg;
+  if (failed) {
+    v = __int_as_float(0x7fc00000);
+    seg = -1;
+  } else if (best_id != 0x7fffffff) {
+    v = t_best;
+    seg = best_seg;
+    if (v < sen.min_range) {
+      if (sen.near_mode == AGS_NEAR_CLAMP) {
+        v = sen.min_range;
+      } else {
+        v = sen.max_range;
+        seg = -1;
+      }
+    }
+  } else {
+    v = sen.max_range;
+    seg = -1;
+  }
+  const int64_t o = slot_out<kSlots>(a, sen, slot) + (int64_t)row * W + col;
+  a.out_depth[o] = v;
+  a.out_seg[o] = seg;
+  }  // rays of this lane in the tile
+}
+
+// kSlots: each tile belongs to one slot of a table (serving: every request has
+// its own environment, sensor shape, pose and output offset); otherwise all
+// environments of the launch share one sensor shape.
+template <bool kCount, int kTileW, int kRaysPerLane, bool kSlots>
+__global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) k_trace(const TraceArgs a) {
+  const int lane = threadIdx.x & 31;
   int2 stack[kStackSize];
   unsigned long long n_nodes = 0, n_tris = 0, n_rays = 0;
 
@@ -155,212 +378,38 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) k_trace(const 
     if (lane == 0) tile = atomicAdd(a.tile_counter, 1u);
     tile = __shfl_sync(0xffffffffu, tile, 0);
     if ((int64_t)tile >= a.total_tiles) break;
-    const int32_t slot = (int32_t)(tile / (unsigned)a.tiles_per_env);
-    const int32_t t_in = (int32_t)(tile - (unsigned)slot * (unsigned)a.tiles_per_env);
-    const int32_t env = a.env_ids ? __ldg(a.env_ids + slot) : slot;
+    int32_t env, t_in, slot, slot_spec = 0;
+    if constexpr (kSlots) {
+      // the slot holding this tile: last slot whose first tile is <= tile
+      int32_t lo = 0, hi = a.n_slots - 1;
+      while (lo < hi) {
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if ((unsigned)__ldg(&a.slots[mid].tile_begin) <= tile) lo = mid; else hi = mid - 1;
+      }
+      slot = lo;
+      env = __ldg(&a.slots[lo].env);
+      slot_spec = __ldg(&a.slots[lo].spec);
+      if ((unsigned)slot_spec >= (unsigned)a.n_specs) {
+        if (lane == 0) atomicOr(a.status, kStatusBadIndex);
+        continue;
+      }
+      t_in = (int32_t)(tile - (unsigned)__ldg(&a.slots[lo].tile_begin));
+    } else {
+      slot = (int32_t)(tile / (unsigned)a.sensor.tiles_per_env);
+      t_in = (int32_t)(tile - (unsigned)slot * (unsigned)a.sensor.tiles_per_env);
+      env = a.env_ids ? __ldg(a.env_ids + slot) : slot;
+    }
     if ((unsigned)env >= (unsigned)a.n_scene_envs) {
       if (lane == 0) atomicOr(a.status, kStatusBadIndex);
       continue;
     }
-    const int32_t tile_x0 = (t_in % a.tiles_x) * kTileW;
-    const int32_t tile_y0 = (t_in / a.tiles_x) * kTileH;
-
-    for (int rr = 0; rr < kRaysPerLane; ++rr) {
-    const int idx = rr * 32 + lane;
-    const int32_t col = tile_x0 + (idx % kTileW);
-    const int32_t row = tile_y0 + (idx / kTileW);
-    if (col >= a.W || row >= a.H) continue;
-
-    // ---- a3: ray generation from the sensor pose (p, q); recomputed per ray
-    // (L1-resident) so that nothing of it stays live during the traversal
-    const float* P = a.poses + 7 * (int64_t)slot;
-    const float px = __ldg(P), py = __ldg(P + 1), pz = __ldg(P + 2);
-    const float qx = __ldg(P + 3), qy = __ldg(P + 4), qz = __ldg(P + 5), qw = __ldg(P + 6);
-    const float n2 = qx * qx + qy * qy + qz * qz + qw * qw;
-    if (!(n2 >= 1e-30f) || !isfinite(n2) || !isfinite(px + py + pz)) {
-      // a pose the method cannot use: flag it and report NaN for this ray
-      atomicOr(status, kStatusBadPose);
-      if (!kCount) {
-        const int64_t o = ((int64_t)slot * a.H + row) * a.W + col;
-        a.out_depth[o] = __int_as_float(0x7fc00000);
-        a.out_seg[o] = -1;
-      }
-      continue;
-    }
-    const float s = 2.0f / n2;
-    const float R00 = 1.0f - s * (qy * qy + qz * qz), R01 = s * (qx * qy - qz * qw), R02 = s * (qx * qz + qy * qw);
-    const float R10 = s * (qx * qy + qz * qw), R11 = 1.0f - s * (qx * qx + qz * qz), R12 = s * (qy * qz - qx * qw);
-    const float R20 = s * (qx * qz - qy * qw), R21 = s * (qy * qz + qx * qw), R22 = 1.0f - s * (qx * qx + qy * qy);
-    float lx, ly, lz;
-    if (a.type == AGS_PINHOLE) {
-      // unnormalised (1, a, b): the distance along it is the depth itself
-      lx = 1.0f;
-      ly = (0.5f * (float)a.W - ((float)col + 0.5f)) * a.inv_f;
-      lz = (0.5f * (float)a.H - ((float)row + 0.5f)) * a.inv_f;
+    if constexpr (kSlots) {
+      trace_tile<kCount, kTileW, kRaysPerLane, true>(a, a.specs[slot_spec], env, t_in, slot, lane, stack, n_nodes,
+                                                     n_tris, n_rays);
     } else {
-      float sin_el, cos_el, sin_az, cos_az;
-      sincosf(a.vmax - (float)row * a.dv, &sin_el, &cos_el);
-      sincosf(a.hfov * ((float)col / (float)a.W), &sin_az, &cos_az);
-      lx = cos_el * cos_az;
-      ly = cos_el * sin_az;
-      lz = sin_el;
+      trace_tile<kCount, kTileW, kRaysPerLane, false>(a, a.sensor, env, t_in, slot, lane, stack, n_nodes, n_tris,
+                                                      n_rays);
     }
-    Ray r;
-    r.ox = px;
-    r.oy = py;
-    r.oz = pz;
-    setup_ray(r, R00 * lx + R01 * ly + R02 * lz, R10 * lx + R11 * ly + R12 * lz, R20 * lx + R21 * ly + R22 * lz);
-
-    // ---- a4-a6: traversal, triangle tests, nearest hit
-    float t_best = a.max_range;  // camera: depth limit; LiDAR: range limit (unit direction)
-    int32_t best_id = 0x7fffffff, best_seg = -1;
-    int32_t node = __ldg(a.env_root + env);
-    int sp = 0, visits = 0;
-    bool failed = false;
-    while (node >= 0) {
-      if (++visits > a.max_visits) {
-        atomicOr(status, kStatusIterationCap);
-        failed = true;
-        break;
-      }
-      if (node >= a.n_nodes) {
-        atomicOr(status, kStatusBadIndex);
-        failed = true;
-        break;
-      }
-      if (kCount) ++n_nodes;
-      const float4* np = reinterpret_cast<const float4*>(a.nodes + node);
-      const float4 h = __ldg(np);
-      const int32_t child_base = __float_as_int(h.x), tri_base = __float_as_int(h.y);
-      const uint32_t meta_lo = __float_as_uint(h.z), meta_hi = __float_as_uint(h.w);
-      const float t_cull = t_best * kCullSlack;
-      const uint32_t b0 = meta_lo & 0xFFu;
-      const int ni = (b0 & 0x80u) ? (int)min(b0 & 0xFu, 8u) : 0;
-      float tmins[8];
-      uint32_t hit_mask = 0;
-#pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        const float4 nx4 = __ldg(np + r.onx + half), fx4 = __ldg(np + (4 - r.onx) + half);
-        const float4 ny4 = __ldg(np + r.ony + half), fy4 = __ldg(np + (12 - r.ony) + half);
-        const float4 nz4 = __ldg(np + r.onz + half), fz4 = __ldg(np + (20 - r.onz) + half);
-        const float nxs[4] = {nx4.x, nx4.y, nx4.z, nx4.w}, fxs[4] = {fx4.x, fx4.y, fx4.z, fx4.w};
-        const float nys[4] = {ny4.x, ny4.y, ny4.z, ny4.w}, fys[4] = {fy4.x, fy4.y, fy4.z, fy4.w};
-        const float nzs[4] = {nz4.x, nz4.y, nz4.z, nz4.w}, fzs[4] = {fz4.x, fz4.y, fz4.z, fz4.w};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int k = 4 * half + q;
-          const float tnx = __fmaf_rn(nxs[q], r.ix, r.cnx), tfx = __fmaf_rn(fxs[q], r.ix, r.cfx);
-          const float tny = __fmaf_rn(nys[q], r.iy, r.cny), tfy = __fmaf_rn(fys[q], r.iy, r.cfy);
-          const float tnz = __fmaf_rn(nzs[q], r.iz, r.cnz), tfz = __fmaf_rn(fzs[q], r.iz, r.cfz);
-          const float tmin = max3f(tnx, tny, fmaxf(tnz, 0.0f));
-          const float tmax = min3f(tfx, tfy, tfz) * kSlabSlack;
-          tmins[k] = tmin;
-          if (tmin <= fminf(tmax, t_cull)) hit_mask |= 1u << k;
-        }
-      }
-      const uint32_t inner_bits = (1u << ni) - 1u;
-      uint32_t leaf_mask = hit_mask & ~inner_bits;
-      const uint32_t inner_hits = hit_mask & inner_bits;
-      // leaves of this node first: they tighten t_best before descending
-      while (leaf_mask) {
-        const int k = __ffs(leaf_mask) - 1;
-        leaf_mask &= leaf_mask - 1;
-        const uint32_t m = ((k < 4 ? meta_lo : meta_hi) >> (8 * (k & 3))) & 0xFFu;
-        if (m == kMetaEmpty) continue;
-        const int32_t start = tri_base + (int32_t)(m >> 2);
-        const int32_t cnt = (int32_t)(m & 3u) + 1;
-        if (start < 0 || start + cnt > a.n_tris) {
-          atomicOr(status, kStatusBadIndex);
-          failed = true;
-          break;
-        }
-        for (int32_t x = 0; x < cnt; ++x) test_triangle(r, a.tris, start + x, t_best, best_id, best_seg);
-        if (kCount) n_tris += cnt;
-      }
-      if (failed) break;
-      const int n_inner = __popc(inner_hits);
-      if (n_inner == 1) {  // the common case: no ordering needed
-        node = child_base + (__ffs(inner_hits) - 1);
-        continue;
-      }
-      if (n_inner > 1) {
-        // nearest first (sorting network on keys: tmin bits with the slot in the low 3 bits)
-        uint32_t keys[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          keys[k] = ((inner_hits >> k) & 1u) ? ((__float_as_uint(tmins[k]) & ~7u) | (uint32_t)k) : 0xFFFFFFFFu;
-#define AGS_CSWAP(i, j)                         \
-  {                                             \
-    const uint32_t lo_ = min(keys[i], keys[j]); \
-    const uint32_t hi_ = max(keys[i], keys[j]); \
-    keys[i] = lo_;                              \
-    keys[j] = hi_;                              \
-  }
-        AGS_CSWAP(0, 1) AGS_CSWAP(2, 3) AGS_CSWAP(4, 5) AGS_CSWAP(6, 7)
-        AGS_CSWAP(0, 2) AGS_CSWAP(1, 3) AGS_CSWAP(4, 6) AGS_CSWAP(5, 7)
-        AGS_CSWAP(1, 2) AGS_CSWAP(5, 6) AGS_CSWAP(0, 4) AGS_CSWAP(3, 7)
-        AGS_CSWAP(1, 5) AGS_CSWAP(2, 6)
-        AGS_CSWAP(1, 4) AGS_CSWAP(3, 6)
-        AGS_CSWAP(2, 4) AGS_CSWAP(3, 5)
-        AGS_CSWAP(3, 4)
-#undef AGS_CSWAP
-        const uint32_t key_cull = __float_as_uint(t_best * kCullSlack);
-#pragma unroll
-        for (int k = 7; k >= 1; --k) {
-          if (keys[k] != 0xFFFFFFFFu && (keys[k] & ~7u) <= key_cull) {
-            if (sp >= kStackSize) {
-              atomicOr(status, kStatusStackOverflow);
-              failed = true;
-            } else {
-              stack[sp++] = make_int2(child_base + (int32_t)(keys[k] & 7u), (int32_t)(keys[k] & ~7u));
-            }
-          }
-        }
-        if (failed) break;
-        if ((keys[0] & ~7u) <= key_cull) {
-          node = child_base + (int32_t)(keys[0] & 7u);
-          continue;
-        }
-      }
-      node = -1;
-      const float t_pop = t_best * kCullSlack;
-      while (sp > 0) {
-        const int2 e = stack[--sp];
-        if (__int_as_float(e.y) <= t_pop) {
-          node = e.x;
-          break;
-        }
-      }
-    }
-
-    if (kCount) {
-      ++n_rays;
-      continue;
-    }
-    float v;
-    int32_t seg;
-    if (failed) {
-      v = __int_as_float(0x7fc00000);
-      seg = -1;
-    } else if (best_id != 0x7fffffff) {
-      v = t_best;
-      seg = best_seg;
-      if (v < a.min_range) {
-        if (a.near_mode == AGS_NEAR_CLAMP) {
-          v = a.min_range;
-        } else {
-          v = a.max_range;
-          seg = -1;
-        }
-      }
-    } else {
-      v = a.max_range;
-      seg = -1;
-    }
-    const int64_t o = ((int64_t)slot * a.H + row) * a.W + col;
-    a.out_depth[o] = v;
-    a.out_seg[o] = seg;
-    }  // rays of this lane in the tile
   }
   if (kCount) {
 #pragma unroll
@@ -381,8 +430,8 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) k_trace(const 
 
 int trace_blocks_per_sm(bool count) {
   int n = 0;
-  cudaError_t e = count ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<true, 8, 1>, kTraceThreads, 0)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<false, 8, 1>, kTraceThreads, 0);
+  cudaError_t e = count ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<true, 8, 1, false>, kTraceThreads, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<false, 8, 1, false>, kTraceThreads, 0);
   return (e == cudaSuccess && n > 0) ? n : 1;
 }
 
@@ -394,13 +443,24 @@ bool trace_shape_supported(int tile_w, int rays_per_lane) {
 
 cudaError_t launch_trace(const TraceArgs& a, int blocks, bool count, cudaStream_t s) {
   const int w = 1 << a.log2_tile_w, r = a.rays_per_lane;
-  if (count) k_trace<true, 8, 1><<<blocks, kTraceThreads, 0, s>>>(a);
-  else if (w == 8 && r == 1) k_trace<false, 8, 1><<<blocks, kTraceThreads, 0, s>>>(a);
-  else if (w == 4 && r == 1) k_trace<false, 4, 1><<<blocks, kTraceThreads, 0, s>>>(a);
-  else if (w == 8 && r == 2) k_trace<false, 8, 2><<<blocks, kTraceThreads, 0, s>>>(a);
-  else if (w == 16 && r == 2) k_trace<false, 16, 2><<<blocks, kTraceThreads, 0, s>>>(a);
-  else if (w == 16 && r == 4) k_trace<false, 16, 4><<<blocks, kTraceThreads, 0, s>>>(a);
-  else return cudaErrorInvalidValue;
+  if (a.slots) {
+    if (w == 8 && r == 1) k_trace<false, 8, 1, true><<<blocks, kTraceThreads, 0, s>>>(a);
+    else return cudaErrorInvalidValue;
+  } else if (count) {
+    k_trace<true, 8, 1, false><<<blocks, kTraceThreads, 0, s>>>(a);
+  } else if (w == 8 && r == 1) {
+    k_trace<false, 8, 1, false><<<blocks, kTraceThreads, 0, s>>>(a);
+  } else if (w == 4 && r == 1) {
+    k_trace<false, 4, 1, false><<<blocks, kTraceThreads, 0, s>>>(a);
+  } else if (w == 8 && r == 2) {
+    k_trace<false, 8, 2, false><<<blocks, kTraceThreads, 0, s>>>(a);
+  } else if (w == 16 && r == 2) {
+    k_trace<false, 16, 2, false><<<blocks, kTraceThreads, 0, s>>>(a);
+  } else if (w == 16 && r == 4) {
+    k_trace<false, 16, 4, false><<<blocks, kTraceThreads, 0, s>>>(a);
+  } else {
+    return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

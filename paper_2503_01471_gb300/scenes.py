@@ -411,3 +411,41 @@ def lidar_forests(n_envs=256, steps=10, workload=3, envs=None, trees=(50, 200), 
     scene = scene_from_lists(lists)
     poses = np.ascontiguousarray(np.stack(walks, 1), np.float32)
     return scene, lidar(), poses
+
+
+def _primitive_pool(rng, n_each=16):
+    """Object-frame meshes reused across serving environments (each env still gets its own copy)."""
+    pool = []
+    for _ in range(n_each):
+        pool.append(box(*rng.uniform(0.5, 2.0, 3)))
+        pool.append(icosphere(rng.uniform(0.2, 1.0), 2))
+        pool.append(cylinder(rng.uniform(0.2, 0.6), rng.uniform(0.5, 3.0), 32))
+        pool.append(panel(rng.uniform(1.0, 3.0), rng, 32, 0.1))
+    return pool
+
+
+def serving_rooms(n_envs=8192, tri_lo=1000, tri_hi=200000, workload=5, steps=1):
+    """Rooms whose triangle counts are log-uniform in [tri_lo, tri_hi]: obstacles drawn from a pool of
+    primitive meshes until the count is reached, uniform poses. Returns (scene, sensor poses [steps, E, 7])."""
+    pool_rng = rng_for(workload, 10**6)
+    pool = _primitive_pool(pool_rng)
+    rv, rf = room()
+    lists, walks = [], []
+    lo = np.array([-ROOM_HALF_XY + WALL_MARGIN, -ROOM_HALF_XY + WALL_MARGIN, WALL_MARGIN])
+    hi = np.array([ROOM_HALF_XY - WALL_MARGIN, ROOM_HALF_XY - WALL_MARGIN, ROOM_HEIGHT - WALL_MARGIN])
+    for e in range(n_envs):
+        rng = rng_for(workload, e)
+        target = int(np.exp(rng.uniform(np.log(tri_lo), np.log(tri_hi))))
+        objs = [(rv, rf, IDENTITY_POSE, 0)]
+        total, k = rf.shape[0], 0
+        while total < target:
+            v, f = pool[int(rng.integers(0, len(pool)))]
+            p = np.array([rng.uniform(-ROOM_HALF_XY, ROOM_HALF_XY), rng.uniform(-ROOM_HALF_XY, ROOM_HALF_XY),
+                          rng.uniform(0, ROOM_HEIGHT)])
+            objs.append((v, f, np.concatenate([p, random_unit_quat(rng)]).astype(np.float32), k + 1))
+            total += f.shape[0]
+            k += 1
+        lists.append(objs)
+        p0, eul = room_camera_pose(rng)
+        walks.append(random_walk(p0[:3], eul, steps, rng, lo, hi))
+    return scene_from_lists(lists), np.ascontiguousarray(np.stack(walks, 1), np.float32)
