@@ -34,6 +34,7 @@ WORKLOADS = {
     "rooms": {"envs": 1024, "metric": METRIC},
     "forest": {"envs": 256, "metric": "Mrays/s at 256 LiDAR forests x 64x512 range+seg"},
     "serving": {"envs": 8192, "metric": "served Mrays/s, 8192 rooms of 1k-200k triangles, mixed sensors; p50/p99 ms"},
+    "precision": {"envs": 4096, "metric": "Mrays/s at 4096 rooms x 135x240 per BVH node format; depth error vs FP64"},
 }
 PAPER_MRAYS = 340.5  # Table II, 1024 envs x 270x480 (RTX 3090; context)
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
@@ -287,6 +288,93 @@ def bench_serving(args, rank, world, local):
     ags.ags_context_destroy(ctx)
 
 
+# ---------------------------------------------------------------- precision
+def bench_precision(args, rank, world, local):
+    """Node formats (float32, float16, 8-bit child bounds) on the same scenes: rays/s, bytes per ray,
+    bit-exactness of the outputs across formats, and depth error against the FP64 oracle."""
+    import torch
+
+    import oracle as O
+    import paper_2503_01471_gb300 as ags
+    from paper_2503_01471_gb300 import build as B
+    from paper_2503_01471_gb300 import scenes as S
+
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    batch, spec, poses = S.obstacle_rooms(args.envs, steps=args.walk, width=240, height=135)
+    E = batch.n_envs
+    ctx = ags.ags_context_create(local)
+    poses_d = torch.as_tensor(poses).to(dev)
+    depth = torch.empty((E, spec.height, spec.width), dtype=torch.float32, device=dev)
+    seg = torch.empty((E, spec.height, spec.width), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    rays = E * spec.width * spec.height
+    formats = {"fp32": ags.AGS_BVH_FP32, "fp16": ags.AGS_BVH_FP16, "q8": ags.AGS_BVH_Q8}
+    res, ref = {}, None
+    for name, flag in formats.items():
+        scene = ags.ags_scene_build(ctx, batch, flag | args.build_flags)
+        cfg = ags.ags_autotune(ctx, scene, spec, poses_d[0], depth, seg, 2).as_dict()
+        for i in range(args.warmup):
+            ags.ags_render(ctx, scene, spec, poses_d[i % poses_d.shape[0]], depth, seg, stream)
+        st, en = torch.cuda.Event(True), torch.cuda.Event(True)
+        torch.cuda.synchronize(dev)
+        st.record(stream)
+        for i in range(args.steps):
+            ags.ags_render(ctx, scene, spec, poses_d[(args.warmup + i) % poses_d.shape[0]], depth, seg, stream)
+        en.record(stream)
+        torch.cuda.synchronize(dev)
+        ags.ags_stream_status(ctx, stream)
+        ms = st.elapsed_time(en) / args.steps
+        r_c, n_c, t_c = ags.ags_render_count(ctx, scene, spec, poses_d[0])
+        nb = ags.ags_scene_node_bytes(scene)
+        b_ray = (n_c * nb + t_c * 48) / r_c + 8.0
+        ags.ags_render(ctx, scene, spec, poses_d[0], depth, seg, stream)
+        ags.ags_stream_status(ctx, stream)
+        out = (depth.cpu().numpy(), seg.cpu().numpy())
+        if ref is None:
+            ref = out
+        res[name] = {"mrays_per_s": rays / ms / 1e3, "ms_per_step": ms, "node_bytes": nb,
+                     "bvh_bytes": ags.ags_scene_stats(scene)[2], "bytes_per_ray": b_ray,
+                     "nodes_per_ray": n_c / r_c, "tris_per_ray": t_c / r_c, "launch_config": cfg,
+                     "bit_identical_to_fp32": bool(np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1]))}
+        ags.ags_scene_destroy(scene)
+    # depth error against the FP64 oracle (outputs are the same for every format)
+    rng = np.random.default_rng(11)
+    s_or = O.Sensor(type=0, width=spec.width, height=spec.height, hfov=float(np.float32(spec.hfov)),
+                    min_range=float(np.float32(spec.min_range)), max_range=float(np.float32(spec.max_range)))
+    abs_e, rel_e, counted, n_s, loose = [], [], 0, 0, 0
+    for e in rng.choice(E, min(E, 96), replace=False):
+        vs, ix, ps, sg = batch.env_submeshes(int(e))
+        tris, tseg = O.world_triangles(vs, ix, ps, sg)
+        rr = np.sort(rng.choice(spec.width * spec.height, 256, replace=False)).astype(np.int64)
+        resu = O.render(tris, tseg, s_or, poses[0][e].astype(np.float64), rr)
+        d = ref[0][e].reshape(-1)[rr].astype(np.float64)
+        g = ref[1][e].reshape(-1)[rr]
+        ok, cnt, strict = O.check(resu, d, g, s_or.max_range, with_strict=True)
+        if not ok.all():
+            raise RuntimeError(f"precision bench: env {e}: {int((~ok).sum())} rays outside the oracle's outcomes")
+        hit = (~cnt) & (resu["seg"] >= 0)
+        abs_e.append(np.abs(d - resu["v"])[hit])
+        rel_e.append((np.abs(d - resu["v"]) / resu["v"])[hit])
+        counted += int(cnt.sum())
+        loose += int((~cnt & ~strict).sum())
+        n_s += rr.shape[0]
+    a = np.concatenate(abs_e)
+    r = np.concatenate(rel_e)
+    err = {"sampled_rays": n_s, "single_outcome_hits": int(a.shape[0]), "counted": counted,
+           "beyond_tolerance": loose, "max_abs_m": float(a.max()), "p999_abs_m": float(np.percentile(a, 99.9)),
+           "max_rel": float(r.max()), "p999_rel": float(np.percentile(r, 99.9)),
+           "tolerance": "1e-5*d + 1e-6 m"}
+    line = {"metric": WORKLOADS["precision"]["metric"], "value": res["q8"]["mrays_per_s"], "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": f"obstacle rooms, {E} envs x 135x240 camera",
+                                            "tris": int(batch.env_tri_counts().sum())},
+            "formats": res, "depth_error_vs_fp64": err}
+    print(json.dumps(line), flush=True)
+    ags.ags_context_destroy(ctx)
+
+
 # ---------------------------------------------------------------- workload
 def make_workload(args, rank, world=1):
     from paper_2503_01471_gb300 import scenes as S
@@ -496,6 +584,10 @@ def main():
     if args.workload == "serving":
         if rank == 0:
             bench_serving(args, rank, world, local)
+        return
+    if args.workload == "precision":
+        if rank == 0:
+            bench_precision(args, rank, world, local)
         return
     bench_ours(args, rank, world, local)
 

@@ -93,14 +93,19 @@ typedef struct {
   uint32_t flags;        /* reserved, must be 0 */
 } ags_sensor_spec;
 
-/* Build flags: node format of the wide BVH (bits 0-7); the largest number of
+/* Build flags: node format of the wide BVH (bits 0-7; every format stores
+ * child boxes that contain the exact float32 ones, so results are
+ * bit-identical and only the memory per node and the decode work differ);
+ * the largest number of
  * triangles in one BVH leaf (bits 8-11: 1..4; 0 selects 2); and the splitting
  * of large triangles into several BVH references (bits 12-19): 0 selects 16
  * cells across an environment's largest extent, 1 turns splitting off, n >= 2
  * uses n cells. A triangle larger than a cell is referenced from up to 8
  * cells per axis (64 in all), each boxed by the triangle clipped to the cell;
  * results are identical with or without splitting. */
-#define AGS_BVH_FP32 0u
+#define AGS_BVH_FP32 0u  /* 208-byte nodes, float32 child boxes */
+#define AGS_BVH_FP16 1u  /* 128-byte nodes, float16 offsets from the node's origin, rounded outward */
+#define AGS_BVH_Q8 2u    /* 80-byte nodes, 8-bit steps of a power-of-two scale per axis, rounded outward */
 #define AGS_LEAF_SIZE(n) (((uint32_t)(n) & 0xFu) << 8)
 #define AGS_SPLIT_CELLS(n) (((uint32_t)(n) & 0xFFu) << 12)
 

@@ -34,6 +34,8 @@ AGS_LIDAR = 1
 AGS_NEAR_CLAMP = 0
 AGS_NEAR_INVALID = 1
 AGS_BVH_FP32 = 0
+AGS_BVH_FP16 = 1
+AGS_BVH_Q8 = 2
 
 
 def AGS_LEAF_SIZE(n: int) -> int:

@@ -7,6 +7,8 @@
 #include <cmath>
 #include <cstring>
 
+#include <cuda_fp16.h>
+
 #include "internal.cuh"
 
 namespace ags {
@@ -682,6 +684,99 @@ __global__ void k_gather_tris(const float4* __restrict__ packed, const int32_t* 
   out[3 * (int64_t)k + 2] = packed[3 * t + 2];
 }
 
+// ---------------------------------------------------------------- compressed nodes
+// Child bounds relative to the node's own box: float16 offsets rounded
+// outward, or 8-bit steps of a power-of-two scale per axis rounded outward,
+// so every stored box contains the exact float32 child box (culling stays
+// conservative and ray results stay bit-identical to the float32 nodes).
+struct __align__(16) NodeF16 {
+  int32_t child_base, tri_base;
+  uint32_t meta_lo, meta_hi;
+  float ox, oy, oz, pad;
+  __half lo_x[8], hi_x[8], lo_y[8], hi_y[8], lo_z[8], hi_z[8];
+};
+static_assert(sizeof(NodeF16) == 128, "NodeF16 layout");
+
+struct __align__(16) NodeQ8 {
+  float ox, oy, oz;
+  uint32_t exps;  // biased exponents of the x, y, z scales in bits 0-7, 8-15, 16-23
+  int32_t child_base, tri_base;
+  uint32_t meta_lo, meta_hi;
+  uint8_t lo_x[8], hi_x[8], lo_y[8], hi_y[8], lo_z[8], hi_z[8];
+};
+static_assert(sizeof(NodeQ8) == 80, "NodeQ8 layout");
+
+__device__ __forceinline__ bool slot_empty(const WideNode& n, int k) {
+  return ((((k < 4) ? n.meta_lo : n.meta_hi) >> (8 * (k & 3))) & 0xFFu) == kMetaEmpty;
+}
+
+template <int kFmt>
+__global__ void k_compress_nodes(const WideNode* __restrict__ in, int64_t n, void* __restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const WideNode w = in[i];
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int k = 0; k < 8; ++k) {
+    if (slot_empty(w, k)) continue;
+    lo[0] = fminf(lo[0], w.lox[k]); lo[1] = fminf(lo[1], w.loy[k]); lo[2] = fminf(lo[2], w.loz[k]);
+    hi[0] = fmaxf(hi[0], w.hix[k]); hi[1] = fmaxf(hi[1], w.hiy[k]); hi[2] = fmaxf(hi[2], w.hiz[k]);
+  }
+  for (int a = 0; a < 3; ++a)
+    if (!(lo[a] <= hi[a])) lo[a] = hi[a] = 0.0f;  // no valid child (cannot happen)
+  if constexpr (kFmt == kNodeFp16) {
+    NodeF16 o;
+    o.child_base = w.child_base; o.tri_base = w.tri_base; o.meta_lo = w.meta_lo; o.meta_hi = w.meta_hi;
+    o.ox = lo[0]; o.oy = lo[1]; o.oz = lo[2]; o.pad = 0.0f;
+    const __half inf = __ushort_as_half((unsigned short)0x7C00);
+    for (int k = 0; k < 8; ++k) {
+      if (slot_empty(w, k)) {
+        o.lo_x[k] = o.hi_x[k] = o.lo_y[k] = o.hi_y[k] = o.lo_z[k] = o.hi_z[k] = inf;
+        continue;
+      }
+      o.lo_x[k] = __float2half_rd(__fsub_rd(w.lox[k], lo[0])); o.hi_x[k] = __float2half_ru(__fsub_ru(w.hix[k], lo[0]));
+      o.lo_y[k] = __float2half_rd(__fsub_rd(w.loy[k], lo[1])); o.hi_y[k] = __float2half_ru(__fsub_ru(w.hiy[k], lo[1]));
+      o.lo_z[k] = __float2half_rd(__fsub_rd(w.loz[k], lo[2])); o.hi_z[k] = __float2half_ru(__fsub_ru(w.hiz[k], lo[2]));
+    }
+    reinterpret_cast<NodeF16*>(out)[i] = o;
+  } else {
+    NodeQ8 o;
+    o.child_base = w.child_base; o.tri_base = w.tri_base; o.meta_lo = w.meta_lo; o.meta_hi = w.meta_hi;
+    o.ox = lo[0]; o.oy = lo[1]; o.oz = lo[2];
+    float inv_s[3];
+    uint32_t exps = 0;
+    for (int a = 0; a < 3; ++a) {
+      // scale 2^e with 255 * 2^e >= extent (rounded up)
+      const float ext = __fsub_ru(hi[a], lo[a]);
+      const float v = __fdiv_ru(ext, 255.0f);
+      int e = -126;
+      if (v > 0.0f) {
+        frexpf(v, &e);
+        e = max(-126, min(e, 126));
+      }
+      exps |= (uint32_t)(e + 127) << (8 * a);
+      inv_s[a] = __uint_as_float((uint32_t)(127 - e) << 23);
+    }
+    o.exps = exps;
+    const float* clo[3] = {w.lox, w.loy, w.loz};
+    const float* chi[3] = {w.hix, w.hiy, w.hiz};
+    uint8_t* qlo[3] = {o.lo_x, o.lo_y, o.lo_z};
+    uint8_t* qhi[3] = {o.hi_x, o.hi_y, o.hi_z};
+    for (int k = 0; k < 8; ++k)
+      for (int a = 0; a < 3; ++a) {
+        if (slot_empty(w, k)) {
+          qlo[a][k] = 255;
+          qhi[a][k] = 0;
+          continue;
+        }
+        const float l = floorf(__fsub_rd(clo[a][k], lo[a]) * inv_s[a]);
+        const float h = ceilf(__fsub_ru(chi[a][k], lo[a]) * inv_s[a]);
+        qlo[a][k] = (uint8_t)fminf(fmaxf(l, 0.0f), 255.0f);
+        qhi[a][k] = (uint8_t)fminf(fmaxf(h, 0.0f), 255.0f);
+      }
+    reinterpret_cast<NodeQ8*>(out)[i] = o;
+  }
+}
+
 unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 // device allocations released on scope exit
@@ -756,6 +851,7 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
     std::vector<int32_t> env_root(E, -1);
     AGS_CHECK(cudaMemcpyAsync(sc->d.env_root, env_root.data(), (size_t)std::max(E, 1) * sizeof(int32_t),
                               cudaMemcpyHostToDevice, s));
+    sc->node_format = (int)(sc->flags & 0xFFu);
     AGS_CHECK(cudaMalloc(&sc->d.nodes, sizeof(WideNode)));
     sc->n_nodes = 0;
     sc->n_refs = 0;
@@ -945,9 +1041,18 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
     return AGS_ERR_CUDA;
   }
   sc->n_nodes = level_base;
-  AGS_CHECK(cudaMalloc(&sc->d.nodes, std::max<int64_t>(sc->n_nodes, 1) * sizeof(WideNode)));
-  AGS_CHECK(cudaMemcpyAsync(sc->d.nodes, d_nodes_tmp, (size_t)sc->n_nodes * sizeof(WideNode),
-                            cudaMemcpyDeviceToDevice, s));
+  sc->node_format = (int)(sc->flags & 0xFFu);
+  AGS_CHECK(cudaMalloc(&sc->d.nodes, std::max<int64_t>(sc->n_nodes, 1) * node_bytes_of(sc->node_format)));
+  if (sc->node_format == kNodeFp32) {
+    AGS_CHECK(cudaMemcpyAsync(sc->d.nodes, d_nodes_tmp, (size_t)sc->n_nodes * sizeof(WideNode),
+                              cudaMemcpyDeviceToDevice, s));
+  } else if (sc->n_nodes > 0) {
+    if (sc->node_format == kNodeFp16)
+      k_compress_nodes<kNodeFp16><<<blocks_for(sc->n_nodes, 128), 128, 0, s>>>(d_nodes_tmp, sc->n_nodes, sc->d.nodes);
+    else
+      k_compress_nodes<kNodeQ8><<<blocks_for(sc->n_nodes, 128), 128, 0, s>>>(d_nodes_tmp, sc->n_nodes, sc->d.nodes);
+    AGS_CHECK(cudaGetLastError());
+  }
   AGS_CHECK(cudaMalloc(&sc->d.tris, std::max<int64_t>(3 * (int64_t)R, 1) * sizeof(float4)));
   k_gather_tris<<<blocks_for(R, 256), 256, 0, s>>>(d_packed, d_ref_tri, d_vals, d_perm, R, sc->d.tris);
   AGS_CHECK(cudaGetLastError());

@@ -104,6 +104,7 @@ ags_status fill_trace_args(ags_context* ctx, const ags_scene* sc, const ags_sens
                            const int32_t* env_ids, const float* poses, float* depth, int32_t* seg, TraceArgs& a,
                            const ags_launch_config& cfg) {
   a.nodes = sc->d.nodes;
+  a.node_format = sc->node_format;
   a.tris = sc->d.tris;
   a.env_root = sc->d.env_root;
   a.n_nodes = (int32_t)sc->n_nodes;
@@ -229,7 +230,7 @@ ags_status ags_scene_build(ags_context* ctx, const ags_env_mesh* envs, int32_t n
   if (!ctx) return invalid("ctx is NULL");
   if (!envs) return invalid("envs is NULL");
   if (n_envs < 1 || n_envs > 65536) return invalid("n_envs must be in [1, 65536]");
-  if ((build_flags & 0xFFu) != AGS_BVH_FP32) return invalid("unsupported BVH node format in build_flags");
+  if ((build_flags & 0xFFu) > AGS_BVH_Q8) return invalid("unsupported BVH node format in build_flags");
   if ((build_flags & ~0xFFFFFu) != 0) return invalid("unknown bits in build_flags");
   if (((build_flags >> 8) & 0xFu) > (uint32_t)kMaxLeafTris) return invalid("leaf size must be 1..4");
   // sizes
@@ -322,7 +323,7 @@ void ags_scene_destroy(ags_scene* sc) {
 
 int32_t ags_scene_n_envs(const ags_scene* sc) { return sc ? sc->n_envs : -1; }
 
-int32_t ags_scene_node_bytes(const ags_scene* sc) { return sc ? (int32_t)sizeof(WideNode) : -1; }
+int32_t ags_scene_node_bytes(const ags_scene* sc) { return sc ? node_bytes_of(sc->node_format) : -1; }
 
 ags_status ags_render(ags_context* ctx, const ags_scene* sc, const ags_sensor_spec* spec, const float* poses,
                       float* depth, int32_t* seg, void* stream) {
@@ -500,7 +501,7 @@ ags_status ags_scene_stats(const ags_scene* sc, int32_t env, int64_t* n_tris, in
   }
   if (n_tris) *n_tris = t;
   if (n_nodes) *n_nodes = nd;
-  if (bytes) *bytes = nd * (int64_t)sizeof(WideNode) + refs * kTriFloat4 * (int64_t)sizeof(float4);
+  if (bytes) *bytes = nd * (int64_t)node_bytes_of(sc->node_format) + refs * kTriFloat4 * (int64_t)sizeof(float4);
   return AGS_OK;
   AGS_API_END
 }

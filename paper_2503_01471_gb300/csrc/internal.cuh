@@ -30,6 +30,12 @@ struct __align__(16) WideNode {
 };
 static_assert(sizeof(WideNode) == 208, "WideNode layout");
 
+// node formats of the traversal (ags_scene_build flags, bits 0-7)
+constexpr int kNodeFp32 = 0;  // WideNode, 208 B
+constexpr int kNodeFp16 = 1;  // 128 B: child bounds as float16 offsets from the node's origin
+constexpr int kNodeQ8 = 2;    // 80 B: child bounds as 8-bit steps of a power-of-two scale per axis
+inline int node_bytes_of(int fmt) { return fmt == kNodeFp16 ? 128 : (fmt == kNodeQ8 ? 80 : 208); }
+
 constexpr int kMaxLeafTris = 4;      // largest wide-BVH leaf (2-bit count field)
 constexpr int kDefaultLeafTris = 2;  // default leaf size (fewest instructions per ray on room scenes)
 constexpr uint8_t kMetaEmpty = 0xFF;
@@ -50,7 +56,7 @@ constexpr int kStatusBadPose = 8;
 struct SceneDevice {
   float4* world_verts = nullptr;   // [V] xyz world, w 0
   int32_t* tri_vidx = nullptr;     // [3F] global vertex indices (input order)
-  WideNode* nodes = nullptr;       // [n_nodes]
+  void* nodes = nullptr;           // [n_nodes] in the scene's node format
   float4* tris = nullptr;          // [3R] packed, one per BVH reference, leaf order
   int32_t* env_root = nullptr;     // [E] root node index, -1 if empty
 };
@@ -88,6 +94,7 @@ struct ags_scene {
   int32_t n_envs = 0;
   int64_t n_tris = 0, n_verts = 0, n_subs = 0, n_nodes = 0;
   int64_t n_refs = 0;                  // BVH references (triangles, some split into several)
+  int node_format = 0;                 // kNodeFp32 / kNodeFp16 / kNodeQ8
   uint32_t flags = 0;
   ags::SceneDevice d;
   std::vector<int64_t> env_tri_off;    // [E+1]
@@ -146,7 +153,8 @@ struct SlotEntry {
 static_assert(sizeof(SlotEntry) == 56, "SlotEntry layout");
 
 struct TraceArgs {
-  const WideNode* nodes;
+  const void* nodes;         // node_format layout
+  int32_t node_format;
   const float4* tris;
   const int32_t* env_root;
   int32_t n_nodes;           // bounds for the node and triangle indices read

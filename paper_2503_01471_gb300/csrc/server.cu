@@ -185,6 +185,7 @@ bool launch_batch(ags_server* sv) {
   cudaMemcpyAsync(sv->d_slots[lane], hs, n * sizeof(SlotEntry), cudaMemcpyHostToDevice, s);
   TraceArgs a{};
   a.nodes = sv->scene->d.nodes;
+  a.node_format = sv->scene->node_format;
   a.tris = sv->scene->d.tris;
   a.env_root = sv->scene->d.env_root;
   a.n_nodes = (int32_t)sv->scene->n_nodes;

@@ -5,6 +5,8 @@
 // in L2 while all SMs work on it), generates the rays in registers, walks the
 // environment's 8-wide BVH with a per-thread stack, tests leaf triangles with
 // a watertight float32 test and writes depth/range and segment ID.
+#include <cuda_fp16.h>
+
 #include "internal.cuh"
 
 namespace ags {
@@ -145,6 +147,126 @@ __device__ __forceinline__ void test_triangle(const Ray& r, const float4* __rest
 // The rays of one warp tile: sensor shape `sen`, environment `env`, tile
 // index t_in within it; `slot` locates the pose and the outputs (the
 // environment's index in the launch, or the request's slot in the table).
+// ---- one wide node: header, and per child the entry distance and whether
+// the ray's slab interval meets [0, t_cull]. Every bound t = b * ix + c is a
+// single fma whose constant is already lowered (near) or raised (far) by more
+// than the rounding of c, as for the float32 node.
+__device__ __forceinline__ void child_test(int k, float tnx, float tfx, float tny, float tfy, float tnz, float tfz,
+                                           float t_cull, float* tmins, uint32_t& hit_mask) {
+  const float tmin = max3f(tnx, tny, fmaxf(tnz, 0.0f));
+  const float tmax = min3f(tfx, tfy, tfz) * kSlabSlack;
+  tmins[k] = tmin;
+  if (tmin <= fminf(tmax, t_cull)) hit_mask |= 1u << k;
+}
+
+// near / far constants of one axis for a node whose bounds are origin + b:
+// c = (origin - o) / d, computed as one fma from the ray's lowered / raised
+// constants, then moved away again by the rounding of that fma
+__device__ __forceinline__ void node_axis(float origin, float inv, float cn_ray, float cf_ray, float& cn, float& cf) {
+  const float n = __fmaf_rn(origin, inv, cn_ray), f = __fmaf_rn(origin, inv, cf_ray);
+  cn = n - kSlabEps * fabsf(n);
+  cf = f + kSlabEps * fabsf(f);
+}
+
+template <int kFmt>
+__device__ __forceinline__ void test_node(const void* __restrict__ nodes, int32_t node, const Ray& r, float t_cull,
+                                          int32_t& child_base, int32_t& tri_base, uint32_t& meta_lo,
+                                          uint32_t& meta_hi, float* tmins, uint32_t& hit_mask) {
+  hit_mask = 0;
+  if constexpr (kFmt == kNodeFp32) {
+    const float4* np = reinterpret_cast<const float4*>(nodes) + (int64_t)node * 13;
+    const float4 h = __ldg(np);
+    child_base = __float_as_int(h.x);
+    tri_base = __float_as_int(h.y);
+    meta_lo = __float_as_uint(h.z);
+    meta_hi = __float_as_uint(h.w);
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const float4 nx4 = __ldg(np + r.onx + half), fx4 = __ldg(np + (4 - r.onx) + half);
+      const float4 ny4 = __ldg(np + r.ony + half), fy4 = __ldg(np + (12 - r.ony) + half);
+      const float4 nz4 = __ldg(np + r.onz + half), fz4 = __ldg(np + (20 - r.onz) + half);
+      const float nxs[4] = {nx4.x, nx4.y, nx4.z, nx4.w}, fxs[4] = {fx4.x, fx4.y, fx4.z, fx4.w};
+      const float nys[4] = {ny4.x, ny4.y, ny4.z, ny4.w}, fys[4] = {fy4.x, fy4.y, fy4.z, fy4.w};
+      const float nzs[4] = {nz4.x, nz4.y, nz4.z, nz4.w}, fzs[4] = {fz4.x, fz4.y, fz4.z, fz4.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        child_test(4 * half + q, __fmaf_rn(nxs[q], r.ix, r.cnx), __fmaf_rn(fxs[q], r.ix, r.cfx),
+                   __fmaf_rn(nys[q], r.iy, r.cny), __fmaf_rn(fys[q], r.iy, r.cfy), __fmaf_rn(nzs[q], r.iz, r.cnz),
+                   __fmaf_rn(fzs[q], r.iz, r.cfz), t_cull, tmins, hit_mask);
+    }
+  } else if constexpr (kFmt == kNodeFp16) {
+    // 128 B: header, origin, then lo_x, hi_x, lo_y, hi_y, lo_z, hi_z as 8 halves each
+    const float4* np = reinterpret_cast<const float4*>(nodes) + (int64_t)node * 8;
+    const float4 h = __ldg(np), org = __ldg(np + 1);
+    child_base = __float_as_int(h.x);
+    tri_base = __float_as_int(h.y);
+    meta_lo = __float_as_uint(h.z);
+    meta_hi = __float_as_uint(h.w);
+    float cnx, cfx, cny, cfy, cnz, cfz;
+    node_axis(org.x, r.ix, r.cnx, r.cfx, cnx, cfx);
+    node_axis(org.y, r.iy, r.cny, r.cfy, cny, cfy);
+    node_axis(org.z, r.iz, r.cnz, r.cfz, cnz, cfz);
+    const int sx = (r.onx >> 1) & 1, sy = (r.ony >> 1) & 1, sz = (r.onz >> 1) & 1;  // 1: negative direction
+    const float4 nx = __ldg(np + 2 + sx), fx = __ldg(np + 3 - sx);
+    const float4 ny = __ldg(np + 4 + sy), fy = __ldg(np + 5 - sy);
+    const float4 nz = __ldg(np + 6 + sz), fz = __ldg(np + 7 - sz);
+    const float nxw[4] = {nx.x, nx.y, nx.z, nx.w}, fxw[4] = {fx.x, fx.y, fx.z, fx.w};
+    const float nyw[4] = {ny.x, ny.y, ny.z, ny.w}, fyw[4] = {fy.x, fy.y, fy.z, fy.w};
+    const float nzw[4] = {nz.x, nz.y, nz.z, nz.w}, fzw[4] = {fz.x, fz.y, fz.z, fz.w};
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const float2 bnx = __half22float2(*reinterpret_cast<const __half2*>(&nxw[w]));
+      const float2 bfx = __half22float2(*reinterpret_cast<const __half2*>(&fxw[w]));
+      const float2 bny = __half22float2(*reinterpret_cast<const __half2*>(&nyw[w]));
+      const float2 bfy = __half22float2(*reinterpret_cast<const __half2*>(&fyw[w]));
+      const float2 bnz = __half22float2(*reinterpret_cast<const __half2*>(&nzw[w]));
+      const float2 bfz = __half22float2(*reinterpret_cast<const __half2*>(&fzw[w]));
+      child_test(2 * w, __fmaf_rn(bnx.x, r.ix, cnx), __fmaf_rn(bfx.x, r.ix, cfx), __fmaf_rn(bny.x, r.iy, cny),
+                 __fmaf_rn(bfy.x, r.iy, cfy), __fmaf_rn(bnz.x, r.iz, cnz), __fmaf_rn(bfz.x, r.iz, cfz), t_cull, tmins,
+                 hit_mask);
+      child_test(2 * w + 1, __fmaf_rn(bnx.y, r.ix, cnx), __fmaf_rn(bfx.y, r.ix, cfx), __fmaf_rn(bny.y, r.iy, cny),
+                 __fmaf_rn(bfy.y, r.iy, cfy), __fmaf_rn(bnz.y, r.iz, cnz), __fmaf_rn(bfz.y, r.iz, cfz), t_cull, tmins,
+                 hit_mask);
+    }
+  } else {
+    // 80 B: origin + per-axis power-of-two scale exponents, header, then per
+    // axis 8 low and 8 high 8-bit bounds: bound = origin + q * 2^(e - 127)
+    const float4* np = reinterpret_cast<const float4*>(nodes) + (int64_t)node * 5;
+    const float4 org = __ldg(np), h = __ldg(np + 1);
+    child_base = __float_as_int(h.x);
+    tri_base = __float_as_int(h.y);
+    meta_lo = __float_as_uint(h.z);
+    meta_hi = __float_as_uint(h.w);
+    const uint32_t ex = __float_as_uint(org.w);
+    const float scx = __uint_as_float((ex & 0xFFu) << 23), scy = __uint_as_float(((ex >> 8) & 0xFFu) << 23),
+                scz = __uint_as_float(((ex >> 16) & 0xFFu) << 23);
+    float cnx, cfx, cny, cfy, cnz, cfz;
+    node_axis(org.x, r.ix, r.cnx, r.cfx, cnx, cfx);
+    node_axis(org.y, r.iy, r.cny, r.cfy, cny, cfy);
+    node_axis(org.z, r.iz, r.cnz, r.cfz, cnz, cfz);
+    const float ax = scx * r.ix, ay = scy * r.iy, az = scz * r.iz;  // exact: powers of two
+    const int sx = (r.onx >> 1) & 1, sy = (r.ony >> 1) & 1, sz = (r.onz >> 1) & 1;
+    const uint4 qx = __ldg(reinterpret_cast<const uint4*>(np + 2));
+    const uint4 qy = __ldg(reinterpret_cast<const uint4*>(np + 3));
+    const uint4 qz = __ldg(reinterpret_cast<const uint4*>(np + 4));
+    // near words: lo (x, y) for a positive direction, hi (z, w) for a negative one
+    const uint32_t nx0 = sx ? qx.z : qx.x, nx1 = sx ? qx.w : qx.y, fx0 = sx ? qx.x : qx.z, fx1 = sx ? qx.y : qx.w;
+    const uint32_t ny0 = sy ? qy.z : qy.x, ny1 = sy ? qy.w : qy.y, fy0 = sy ? qy.x : qy.z, fy1 = sy ? qy.y : qy.w;
+    const uint32_t nz0 = sz ? qz.z : qz.x, nz1 = sz ? qz.w : qz.y, fz0 = sz ? qz.x : qz.z, fz1 = sz ? qz.y : qz.w;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      // byte k of the word as the exact float q: bits 0x4B000000 | q = 2^23 + q
+      const uint32_t sel = 0x7440u | (uint32_t)(k & 3);
+      auto qf = [&](uint32_t w0, uint32_t w1) {
+        return __uint_as_float(__byte_perm(k < 4 ? w0 : w1, 0x4B000000u, sel)) - 8388608.0f;
+      };
+      child_test(k, __fmaf_rn(qf(nx0, nx1), ax, cnx), __fmaf_rn(qf(fx0, fx1), ax, cfx),
+                 __fmaf_rn(qf(ny0, ny1), ay, cny), __fmaf_rn(qf(fy0, fy1), ay, cfy),
+                 __fmaf_rn(qf(nz0, nz1), az, cnz), __fmaf_rn(qf(fz0, fz1), az, cfz), t_cull, tmins, hit_mask);
+    }
+  }
+}
+
 template <bool kSlots>
 __device__ __forceinline__ const float* slot_pose(const TraceArgs& a, int32_t slot) {
   if constexpr (kSlots) return a.slots[slot].pose;
@@ -156,7 +278,7 @@ __device__ __forceinline__ int64_t slot_out(const TraceArgs& a, const SensorPara
   else return (int64_t)slot * sen.H * sen.W;
 }
 
-template <bool kCount, int kTileW, int kRaysPerLane, bool kSlots>
+template <bool kCount, int kTileW, int kRaysPerLane, bool kSlots, int kFmt>
 __device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParams& sen, int32_t env, int32_t t_in,
                                            int32_t slot, int lane, int2* stack, unsigned long long& n_nodes,
                                            unsigned long long& n_tris, unsigned long long& n_rays) {
@@ -230,35 +352,14 @@ __device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParam
       break;
     }
     if (kCount) ++n_nodes;
-    const float4* np = reinterpret_cast<const float4*>(a.nodes + node);
-    const float4 h = __ldg(np);
-    const int32_t child_base = __float_as_int(h.x), tri_base = __float_as_int(h.y);
-    const uint32_t meta_lo = __float_as_uint(h.z), meta_hi = __float_as_uint(h.w);
     const float t_cull = t_best * kCullSlack;
+    int32_t child_base, tri_base;
+    uint32_t meta_lo, meta_hi;
+    float tmins[8];
+    uint32_t hit_mask;
+    test_node<kFmt>(a.nodes, node, r, t_cull, child_base, tri_base, meta_lo, meta_hi, tmins, hit_mask);
     const uint32_t b0 = meta_lo & 0xFFu;
     const int ni = (b0 & 0x80u) ? (int)min(b0 & 0xFu, 8u) : 0;
-    float tmins[8];
-    uint32_t hit_mask = 0;
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const float4 nx4 = __ldg(np + r.onx + half), fx4 = __ldg(np + (4 - r.onx) + half);
-      const float4 ny4 = __ldg(np + r.ony + half), fy4 = __ldg(np + (12 - r.ony) + half);
-      const float4 nz4 = __ldg(np + r.onz + half), fz4 = __ldg(np + (20 - r.onz) + half);
-      const float nxs[4] = {nx4.x, nx4.y, nx4.z, nx4.w}, fxs[4] = {fx4.x, fx4.y, fx4.z, fx4.w};
-      const float nys[4] = {ny4.x, ny4.y, ny4.z, ny4.w}, fys[4] = {fy4.x, fy4.y, fy4.z, fy4.w};
-      const float nzs[4] = {nz4.x, nz4.y, nz4.z, nz4.w}, fzs[4] = {fz4.x, fz4.y, fz4.z, fz4.w};
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int k = 4 * half + q;
-        const float tnx = __fmaf_rn(nxs[q], r.ix, r.cnx), tfx = __fmaf_rn(fxs[q], r.ix, r.cfx);
-        const float tny = __fmaf_rn(nys[q], r.iy, r.cny), tfy = __fmaf_rn(fys[q], r.iy, r.cfy);
-        const float tnz = __fmaf_rn(nzs[q], r.iz, r.cnz), tfz = __fmaf_rn(fzs[q], r.iz, r.cfz);
-        const float tmin = max3f(tnx, tny, fmaxf(tnz, 0.0f));
-        const float tmax = min3f(tfx, tfy, tfz) * kSlabSlack;
-        tmins[k] = tmin;
-        if (tmin <= fminf(tmax, t_cull)) hit_mask |= 1u << k;
-      }
-    }
     const uint32_t inner_bits = (1u << ni) - 1u;
     uint32_t leaf_mask = hit_mask & ~inner_bits;
     const uint32_t inner_hits = hit_mask & inner_bits;
@@ -367,7 +468,7 @@ __device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParam
 // kSlots: each tile belongs to one slot of a table (serving: every request has
 // its own environment, sensor shape, pose and output offset); otherwise all
 // environments of the launch share one sensor shape.
-template <bool kCount, int kTileW, int kRaysPerLane, bool kSlots>
+template <bool kCount, int kTileW, int kRaysPerLane, bool kSlots, int kFmt>
 __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) k_trace(const TraceArgs a) {
   const int lane = threadIdx.x & 31;
   int2 stack[kStackSize];
@@ -404,10 +505,10 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) k_trace(const 
       continue;
     }
     if constexpr (kSlots) {
-      trace_tile<kCount, kTileW, kRaysPerLane, true>(a, a.specs[slot_spec], env, t_in, slot, lane, stack, n_nodes,
+      trace_tile<kCount, kTileW, kRaysPerLane, true, kFmt>(a, a.specs[slot_spec], env, t_in, slot, lane, stack, n_nodes,
                                                      n_tris, n_rays);
     } else {
-      trace_tile<kCount, kTileW, kRaysPerLane, false>(a, a.sensor, env, t_in, slot, lane, stack, n_nodes, n_tris,
+      trace_tile<kCount, kTileW, kRaysPerLane, false, kFmt>(a, a.sensor, env, t_in, slot, lane, stack, n_nodes, n_tris,
                                                       n_rays);
     }
   }
@@ -430,8 +531,9 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) k_trace(const 
 
 int trace_blocks_per_sm(bool count) {
   int n = 0;
-  cudaError_t e = count ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<true, 8, 1, false>, kTraceThreads, 0)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<false, 8, 1, false>, kTraceThreads, 0);
+  cudaError_t e =
+      count ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<true, 8, 1, false, kNodeFp32>, kTraceThreads, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_trace<false, 8, 1, false, kNodeFp32>, kTraceThreads, 0);
   return (e == cudaSuccess && n > 0) ? n : 1;
 }
 
@@ -441,27 +543,39 @@ bool trace_shape_supported(int tile_w, int rays_per_lane) {
   return false;
 }
 
-cudaError_t launch_trace(const TraceArgs& a, int blocks, bool count, cudaStream_t s) {
+namespace {
+template <int kFmt>
+cudaError_t launch_fmt(const TraceArgs& a, int blocks, bool count, cudaStream_t s) {
   const int w = 1 << a.log2_tile_w, r = a.rays_per_lane;
   if (a.slots) {
-    if (w == 8 && r == 1) k_trace<false, 8, 1, true><<<blocks, kTraceThreads, 0, s>>>(a);
+    if (w == 8 && r == 1) k_trace<false, 8, 1, true, kFmt><<<blocks, kTraceThreads, 0, s>>>(a);
     else return cudaErrorInvalidValue;
   } else if (count) {
-    k_trace<true, 8, 1, false><<<blocks, kTraceThreads, 0, s>>>(a);
+    k_trace<true, 8, 1, false, kFmt><<<blocks, kTraceThreads, 0, s>>>(a);
   } else if (w == 8 && r == 1) {
-    k_trace<false, 8, 1, false><<<blocks, kTraceThreads, 0, s>>>(a);
+    k_trace<false, 8, 1, false, kFmt><<<blocks, kTraceThreads, 0, s>>>(a);
   } else if (w == 4 && r == 1) {
-    k_trace<false, 4, 1, false><<<blocks, kTraceThreads, 0, s>>>(a);
+    k_trace<false, 4, 1, false, kFmt><<<blocks, kTraceThreads, 0, s>>>(a);
   } else if (w == 8 && r == 2) {
-    k_trace<false, 8, 2, false><<<blocks, kTraceThreads, 0, s>>>(a);
+    k_trace<false, 8, 2, false, kFmt><<<blocks, kTraceThreads, 0, s>>>(a);
   } else if (w == 16 && r == 2) {
-    k_trace<false, 16, 2, false><<<blocks, kTraceThreads, 0, s>>>(a);
+    k_trace<false, 16, 2, false, kFmt><<<blocks, kTraceThreads, 0, s>>>(a);
   } else if (w == 16 && r == 4) {
-    k_trace<false, 16, 4, false><<<blocks, kTraceThreads, 0, s>>>(a);
+    k_trace<false, 16, 4, false, kFmt><<<blocks, kTraceThreads, 0, s>>>(a);
   } else {
     return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_trace(const TraceArgs& a, int blocks, bool count, cudaStream_t s) {
+  switch (a.node_format) {
+    case kNodeFp32: return launch_fmt<kNodeFp32>(a, blocks, count, s);
+    case kNodeFp16: return launch_fmt<kNodeFp16>(a, blocks, count, s);
+    case kNodeQ8: return launch_fmt<kNodeQ8>(a, blocks, count, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace ags

@@ -303,6 +303,8 @@ def test_bit_exact_across_bvh_variants(ctx):
     outs = []
     variants = [ags.AGS_LEAF_SIZE(n) for n in (1, 2, 3, 4)]
     variants += [ags.AGS_SPLIT_CELLS(1), ags.AGS_SPLIT_CELLS(64) | ags.AGS_LEAF_SIZE(2), ags.AGS_SPLIT_CELLS(4)]
+    variants += [ags.AGS_BVH_FP16, ags.AGS_BVH_Q8, ags.AGS_BVH_Q8 | ags.AGS_LEAF_SIZE(4) | ags.AGS_SPLIT_CELLS(1),
+                 ags.AGS_BVH_FP16 | ags.AGS_LEAF_SIZE(1)]
     for flags in variants:
         scene = ags.ags_scene_build(ctx, batch, flags)
         try:
@@ -363,3 +365,25 @@ def test_launch_shapes_and_autotune_keep_results(ctx):
         check_all(batch, spec, poses[0], out[0], out[1], tag="launch shapes 70x45")
     finally:
         ags.ags_scene_destroy(scene)
+
+
+@pytest.mark.parametrize("fmt", ["fp16", "q8"])
+def test_compressed_nodes_bit_exact_on_lidar_forest_and_launch_shapes(ctx, fmt):
+    """Compressed child bounds are rounded outward: the LiDAR forest (large ground triangles, long rays)
+    renders the same bits as with float32 nodes, under every launch shape, and matches the oracle."""
+    flag = ags.AGS_BVH_FP16 if fmt == "fp16" else ags.AGS_BVH_Q8
+    batch, spec, poses = S.lidar_forests(2, steps=1, trees=(6, 10), tris=(2000, 3000))
+    spec.width = 128
+    ref_scene = ags.ags_scene_build(ctx, batch)
+    scene = ags.ags_scene_build(ctx, batch, flag)
+    try:
+        assert ags.ags_scene_node_bytes(scene) == (128 if fmt == "fp16" else 80)
+        ref = render(ctx, ref_scene, spec, poses[0])
+        for w, rpl in [(8, 1), (4, 1), (8, 2), (16, 2), (16, 4)]:
+            ags.ags_set_launch_config(ctx, scene, spec, w, rpl, 0)
+            out = render(ctx, scene, spec, poses[0])
+            assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1]), (w, rpl)
+        check_all(batch, spec, poses[0], ref[0], ref[1], tag=f"LiDAR forest 64x128 ({fmt} nodes)")
+    finally:
+        ags.ags_scene_destroy(scene)
+        ags.ags_scene_destroy(ref_scene)
