@@ -141,6 +141,21 @@ ags_status ags_scene_build(ags_context* ctx, const ags_env_mesh* envs, int32_t n
 void ags_scene_destroy(ags_scene* scene);
 
 /*
+ * ags_scene_update_poses -- move every object of a resident scene to new
+ * poses (host float32 [sum n_submeshes][7], the order of ags_scene_build):
+ * Sec. III-D.1 updates M_{i,t} from the transforms T_{j,t} ("create, maintain
+ * and update"), there by rebuilding the BVH. AGS_UPDATE_REFIT transforms the
+ * vertices, rewrites the packed triangles and refits the node boxes bottom-up
+ * in the existing topology (float32 nodes only; fast, but the tree degrades
+ * as objects move far); AGS_UPDATE_REBUILD builds the whole scene again with
+ * the new poses. Both give exactly the images a freshly built scene gives.
+ * Synchronous; the scene must not be in use on any stream meanwhile.
+ */
+#define AGS_UPDATE_REFIT 0
+#define AGS_UPDATE_REBUILD 1
+ags_status ags_scene_update_poses(ags_context* ctx, ags_scene* scene, const float* obstacle_poses, int32_t mode);
+
+/*
  * ags_render -- Sec. III-D.1: cast one ray per pixel / beam of `spec` from
  * each environment's sensor pose and report the nearest hit.
  * sensor_poses_dev: device float32 [n_envs][7]. out_depth_dev: device float32

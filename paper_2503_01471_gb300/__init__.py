@@ -53,7 +53,7 @@ EXPORTS = [
     "ags_context_set_traversal_cap", "ags_transform_vertices_noalloc", "ags_autotune",
     "ags_set_launch_config", "ags_get_launch_config", "ags_memcpy_d2h", "ags_server_create", "ags_server_destroy",
     "ags_server_submit", "ags_server_poll", "ags_server_release", "ags_server_stats", "ags_server_replay",
-    "ags_replay_sequential",
+    "ags_replay_sequential", "ags_scene_update_poses",
 ]
 
 
@@ -169,6 +169,7 @@ def lib() -> ctypes.CDLL:
                                    ctypes.POINTER(i64)]),
         "ags_server_replay": (i32, [vp, vp, vp, i32, vp]),
         "ags_replay_sequential": (i32, [vp, vp, vp, i32, vp, vp, i32, vp]),
+        "ags_scene_update_poses": (i32, [vp, vp, vp, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -260,6 +261,17 @@ def ags_scene_build(ctx: int, batch, build_flags: int = AGS_BVH_FP32) -> int:
     _check(lib().ags_scene_build(ctx, envs.ctypes.data, E, poses.ctypes.data if J else None, int(build_flags),
                                  ctypes.byref(h)), "ags_scene_build")
     return h.value
+
+
+AGS_UPDATE_REFIT = 0
+AGS_UPDATE_REBUILD = 1
+
+
+def ags_scene_update_poses(ctx: int, scene: int, obstacle_poses, mode: int = AGS_UPDATE_REFIT) -> None:
+    """Move every object to new poses ([J,7] float32, build order): refit or rebuild the BVHs."""
+    p = np.ascontiguousarray(obstacle_poses, np.float32).reshape(-1, 7)
+    _check(lib().ags_scene_update_poses(ctx, scene, p.ctypes.data if p.size else None, int(mode)),
+           "ags_scene_update_poses")
 
 
 def ags_scene_destroy(scene: int) -> None:

@@ -675,10 +675,11 @@ __global__ void k_collapse_emit(const QueueItem* __restrict__ items, int32_t n_i
 
 __global__ void k_gather_tris(const float4* __restrict__ packed, const int32_t* __restrict__ ref_tri,
                               const uint32_t* __restrict__ vals, const int32_t* __restrict__ perm, int32_t R,
-                              float4* __restrict__ out) {
+                              float4* __restrict__ out, int32_t* __restrict__ leaf_tri) {
   int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= R) return;
   int64_t t = ref_tri[vals[perm[k]]];
+  leaf_tri[k] = (int32_t)t;
   out[3 * (int64_t)k] = packed[3 * t];
   out[3 * (int64_t)k + 1] = packed[3 * t + 1];
   out[3 * (int64_t)k + 2] = packed[3 * t + 2];
@@ -830,6 +831,12 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
   for (int32_t e = 0; e <= E; ++e) env_tri32[e] = (int32_t)sc->env_tri_off[e];
 
   AGS_CHECK(cudaMemcpyAsync(d_base, base_verts_h, 3 * (size_t)V * sizeof(float), cudaMemcpyHostToDevice, s));
+  // kept for ags_scene_update_poses: base vertices and sub-mesh vertex offsets on the device
+  AGS_CHECK(cudaMalloc(&sc->d.base_verts, std::max<int64_t>(3 * (int64_t)V, 1) * sizeof(float)));
+  AGS_CHECK(cudaMalloc(&sc->d.sub_vert_off, ((size_t)J + 1) * sizeof(int32_t)));
+  AGS_CHECK(cudaMemcpyAsync(sc->d.base_verts, base_verts_h, 3 * (size_t)V * sizeof(float), cudaMemcpyHostToDevice, s));
+  AGS_CHECK(cudaMemcpyAsync(sc->d.sub_vert_off, sub_vert_off_h, ((size_t)J + 1) * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, s));
   AGS_CHECK(cudaMemcpyAsync(d_poses, poses_h, 7 * (size_t)J * sizeof(float), cudaMemcpyHostToDevice, s));
   AGS_CHECK(cudaMemcpyAsync(d_sub_vert, sub_vert_off_h, ((size_t)J + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   AGS_CHECK(cudaMemcpyAsync(d_sub_tri, sub_tri32.data(), ((size_t)J + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
@@ -999,6 +1006,7 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
   int32_t n_items = (int32_t)q0.size();
   int32_t level_base = 0, tri_level_base = 0;
   int levels = 0;
+  sc->level_off.assign(1, 0);
   while (n_items > 0) {
     if (++levels > 4096) {
       set_error("BVH collapse did not terminate");
@@ -1033,6 +1041,7 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
     AGS_CHECK(cudaGetLastError());
     std::swap(d_q, d_q2);
     level_base = next_base;
+    sc->level_off.push_back(level_base);
     tri_level_base += tot[1];
     n_items = tot[0];
   }
@@ -1054,13 +1063,113 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
     AGS_CHECK(cudaGetLastError());
   }
   AGS_CHECK(cudaMalloc(&sc->d.tris, std::max<int64_t>(3 * (int64_t)R, 1) * sizeof(float4)));
-  k_gather_tris<<<blocks_for(R, 256), 256, 0, s>>>(d_packed, d_ref_tri, d_vals, d_perm, R, sc->d.tris);
+  AGS_CHECK(cudaMalloc(&sc->d.leaf_tri, std::max<int64_t>(R, 1) * sizeof(int32_t)));
+  k_gather_tris<<<blocks_for(R, 256), 256, 0, s>>>(d_packed, d_ref_tri, d_vals, d_perm, R, sc->d.tris,
+                                                   sc->d.leaf_tri);
   AGS_CHECK(cudaGetLastError());
   std::vector<unsigned long long> env_nodes(E);
   AGS_CHECK(cudaMemcpyAsync(env_nodes.data(), d_env_nodes, (size_t)E * sizeof(unsigned long long),
                             cudaMemcpyDeviceToHost, s));
   AGS_CHECK(cudaStreamSynchronize(s));
   for (int32_t e = 0; e < E; ++e) sc->env_nodes[e] = (int64_t)env_nodes[e];
+  return AGS_OK;
+}
+
+namespace {
+
+// new world xyz of every leaf-order triangle copy (the w words keep segment and index)
+__global__ void k_repack_tris(const int32_t* __restrict__ leaf_tri, const int32_t* __restrict__ vidx, int32_t R,
+                              const float4* __restrict__ world, float4* __restrict__ tris) {
+  int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= R) return;
+  const int64_t t = leaf_tri[k];
+  for (int c = 0; c < 3; ++c) {
+    const float4 v = world[vidx[3 * t + c]];
+    float4 o = tris[3 * (int64_t)k + c];
+    o.x = v.x;
+    o.y = v.y;
+    o.z = v.z;
+    tris[3 * (int64_t)k + c] = o;
+  }
+}
+
+// Refit one level of float32 wide nodes: each slot's box becomes the union of
+// its leaf triangles (whole-triangle boxes) or of its child node's slots
+// (already refitted: levels run from the deepest up).
+__global__ void k_refit_level(WideNode* __restrict__ nodes, int32_t begin, int32_t end, const float4* __restrict__ tris,
+                              int32_t n_nodes, int32_t n_tris, int* __restrict__ err) {
+  const int32_t i = begin + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= end) return;
+  WideNode& n = nodes[i];
+  const uint32_t b0 = n.meta_lo & 0xFFu;
+  const int ni = (b0 & 0x80u) ? (int)min(b0 & 0xFu, 8u) : 0;
+  for (int k = 0; k < 8; ++k) {
+    const uint32_t m = (((k < 4) ? n.meta_lo : n.meta_hi) >> (8 * (k & 3))) & 0xFFu;
+    if (m == kMetaEmpty) continue;
+    Box b = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    if (k < ni) {
+      const int32_t c = n.child_base + k;
+      if (c < 0 || c >= n_nodes) {
+        atomicOr(err, 1);
+        continue;
+      }
+      const WideNode& ch = nodes[c];
+      for (int q = 0; q < 8; ++q) {
+        const uint32_t mq = (((q < 4) ? ch.meta_lo : ch.meta_hi) >> (8 * (q & 3))) & 0xFFu;
+        if (mq == kMetaEmpty) continue;
+        b.lox = fminf(b.lox, ch.lox[q]); b.loy = fminf(b.loy, ch.loy[q]); b.loz = fminf(b.loz, ch.loz[q]);
+        b.hix = fmaxf(b.hix, ch.hix[q]); b.hiy = fmaxf(b.hiy, ch.hiy[q]); b.hiz = fmaxf(b.hiz, ch.hiz[q]);
+      }
+    } else {
+      const int32_t start = n.tri_base + (int32_t)(m >> 2), cnt = (int32_t)(m & 3u) + 1;
+      if (start < 0 || start + cnt > n_tris) {
+        atomicOr(err, 1);
+        continue;
+      }
+      for (int32_t x = 0; x < cnt; ++x) {
+        const Box tb = tri_box(tris, start + x);
+        b.lox = fminf(b.lox, tb.lox); b.loy = fminf(b.loy, tb.loy); b.loz = fminf(b.loz, tb.loz);
+        b.hix = fmaxf(b.hix, tb.hix); b.hiy = fmaxf(b.hiy, tb.hiy); b.hiz = fmaxf(b.hiz, tb.hiz);
+      }
+    }
+    n.lox[k] = b.lox; n.loy[k] = b.loy; n.loz[k] = b.loz;
+    n.hix[k] = b.hix; n.hiy[k] = b.hiy; n.hiz[k] = b.hiz;
+  }
+}
+
+}  // namespace
+
+ags_status refit_scene(ags_context* ctx, ags_scene* sc, const float* poses_h) {
+  cudaStream_t s = ctx->stream;
+  const int32_t V = (int32_t)sc->n_verts, J = (int32_t)sc->n_subs, R = (int32_t)sc->n_refs;
+  DevBufs tmp;
+  float *d_poses = nullptr, *d_rot = nullptr;
+  int* d_err = nullptr;
+  AGS_CHECK(tmp.alloc(&d_poses, 7 * (size_t)std::max(J, 1)));
+  AGS_CHECK(tmp.alloc(&d_rot, 18 * (size_t)std::max(J, 1)));
+  AGS_CHECK(tmp.alloc(&d_err, 1));
+  AGS_CHECK(cudaMemsetAsync(d_err, 0, sizeof(int), s));
+  if (J > 0) AGS_CHECK(cudaMemcpyAsync(d_poses, poses_h, 7 * (size_t)J * sizeof(float), cudaMemcpyHostToDevice, s));
+  if (J > 0) k_submesh_rotations<<<blocks_for(J, 128), 128, 0, s>>>(d_poses, J, d_rot);
+  if (V > 0)
+    k_transform_vertices<<<blocks_for(V, 256), 256, 0, s>>>(sc->d.base_verts, V, sc->d.sub_vert_off, J, d_rot, d_poses,
+                                                            sc->d.world_verts);
+  if (R > 0) k_repack_tris<<<blocks_for(R, 256), 256, 0, s>>>(sc->d.leaf_tri, sc->d.tri_vidx, R, sc->d.world_verts,
+                                                              sc->d.tris);
+  for (size_t l = sc->level_off.size(); l-- > 1;) {
+    const int32_t b = (int32_t)sc->level_off[l - 1], e = (int32_t)sc->level_off[l];
+    if (e > b)
+      k_refit_level<<<blocks_for(e - b, 128), 128, 0, s>>>(static_cast<WideNode*>(sc->d.nodes), b, e, sc->d.tris,
+                                                           (int32_t)sc->n_nodes, R, d_err);
+  }
+  AGS_CHECK(cudaGetLastError());
+  int err = 0;
+  AGS_CHECK(cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  AGS_CHECK(cudaStreamSynchronize(s));
+  if (err) {
+    set_error("refit met an out-of-range node or triangle index");
+    return AGS_ERR_CUDA;
+  }
   return AGS_OK;
 }
 

@@ -300,6 +300,12 @@ ags_status ags_scene_build(ags_context* ctx, const ags_env_mesh* envs, int32_t n
   DeviceGuard g(ctx->device);
   ags_status st = build_scene(ctx, sc.get(), base.data(), vidx.data(), sub_vert.data(), obstacle_poses,
                               sub_env.data());
+  if (st == AGS_OK) {
+    sc->h_base = std::move(base);
+    sc->h_vidx = std::move(vidx);
+    sc->h_sub_vert = std::move(sub_vert);
+    sc->h_sub_env = std::move(sub_env);
+  }
   if (st != AGS_OK) {
     cudaStreamSynchronize(ctx->stream);
     ags_scene_destroy(sc.release());
@@ -318,10 +324,62 @@ void ags_scene_destroy(ags_scene* sc) {
   cudaFree(sc->d.nodes);
   cudaFree(sc->d.tris);
   cudaFree(sc->d.env_root);
+  cudaFree(sc->d.leaf_tri);
+  cudaFree(sc->d.base_verts);
+  cudaFree(sc->d.sub_vert_off);
   delete sc;
 }
 
 int32_t ags_scene_n_envs(const ags_scene* sc) { return sc ? sc->n_envs : -1; }
+
+ags_status ags_scene_update_poses(ags_context* ctx, ags_scene* sc, const float* poses, int32_t mode) {
+  AGS_API_BEGIN
+  if (!ctx || !sc) return invalid("ctx or scene is NULL");
+  if (sc->ctx != ctx) return invalid("scene belongs to another context");
+  if (mode != AGS_UPDATE_REFIT && mode != AGS_UPDATE_REBUILD) return invalid("mode must be AGS_UPDATE_REFIT or AGS_UPDATE_REBUILD");
+  if (sc->n_subs > 0 && !poses) return invalid("poses is NULL");
+  for (int64_t j = 0; j < sc->n_subs; ++j) {
+    const float* p = poses + 7 * j;
+    for (int k = 0; k < 7; ++k)
+      if (!std::isfinite(p[k])) return invalid("non-finite pose");
+    double qn = (double)p[3] * p[3] + (double)p[4] * p[4] + (double)p[5] * p[5] + (double)p[6] * p[6];
+    if (!(qn > 1e-12)) return invalid("quaternion has zero length");
+  }
+  DeviceGuard g(ctx->device);
+  if (mode == AGS_UPDATE_REFIT) {
+    if (sc->node_format != kNodeFp32) return invalid("refit needs float32 nodes; use AGS_UPDATE_REBUILD");
+    return refit_scene(ctx, sc, poses);
+  }
+  // rebuild: a fresh scene from the kept inputs, then swap it in
+  std::unique_ptr<ags_scene> fresh(new ags_scene());
+  fresh->ctx = ctx;
+  fresh->n_envs = sc->n_envs;
+  fresh->n_tris = sc->n_tris;
+  fresh->n_verts = sc->n_verts;
+  fresh->n_subs = sc->n_subs;
+  fresh->flags = sc->flags;
+  fresh->env_tri_off = sc->env_tri_off;
+  fresh->env_vert_off = sc->env_vert_off;
+  fresh->env_sub_off = sc->env_sub_off;
+  fresh->sub_tri_off = sc->sub_tri_off;
+  fresh->sub_seg = sc->sub_seg;
+  ags_status st = build_scene(ctx, fresh.get(), sc->h_base.data(), sc->h_vidx.data(), sc->h_sub_vert.data(), poses,
+                              sc->h_sub_env.data());
+  if (st != AGS_OK) {
+    cudaStreamSynchronize(ctx->stream);
+    ags_scene_destroy(fresh.release());
+    return st;
+  }
+  fresh->h_base.swap(sc->h_base);
+  fresh->h_vidx.swap(sc->h_vidx);
+  fresh->h_sub_vert.swap(sc->h_sub_vert);
+  fresh->h_sub_env.swap(sc->h_sub_env);
+  fresh->launch = sc->launch;
+  std::swap(*sc, *fresh);
+  ags_scene_destroy(fresh.release());
+  return AGS_OK;
+  AGS_API_END
+}
 
 int32_t ags_scene_node_bytes(const ags_scene* sc) { return sc ? node_bytes_of(sc->node_format) : -1; }
 

@@ -59,6 +59,9 @@ struct SceneDevice {
   void* nodes = nullptr;           // [n_nodes] in the scene's node format
   float4* tris = nullptr;          // [3R] packed, one per BVH reference, leaf order
   int32_t* env_root = nullptr;     // [E] root node index, -1 if empty
+  int32_t* leaf_tri = nullptr;     // [R] input triangle of each leaf-order copy
+  float* base_verts = nullptr;     // [3V] object-frame vertices (for pose updates)
+  int32_t* sub_vert_off = nullptr; // [J+1]
 };
 
 struct Box {
@@ -104,6 +107,10 @@ struct ags_scene {
   std::vector<int32_t> sub_seg;        // [J]
   std::vector<int64_t> env_nodes;      // [E]
   std::vector<int64_t> env_ref_off;    // [E+1]
+  std::vector<int64_t> level_off;      // wide-node index where each collapse level starts (+ end)
+  // host copies of the inputs, for ags_scene_update_poses(..., AGS_UPDATE_REBUILD)
+  std::vector<float> h_base;
+  std::vector<int32_t> h_vidx, h_sub_vert, h_sub_env;
   mutable std::map<LaunchKey, ags_launch_config> launch;  // tuned or set launch shapes per sensor shape
 };
 
@@ -126,6 +133,8 @@ cudaError_t exclusive_scan(int32_t* data, int64_t n, int32_t* total_dev, void* t
 ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_h,
                        const int32_t* tri_vidx_h, const int32_t* sub_vert_off_h,
                        const float* poses_h, const int32_t* sub_env_h);
+
+ags_status refit_scene(ags_context* ctx, ags_scene* sc, const float* poses_h);
 
 // trace.cu
 // Ray pattern of one sensor shape (derived from ags_sensor_spec on the host).

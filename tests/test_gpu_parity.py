@@ -387,3 +387,45 @@ def test_compressed_nodes_bit_exact_on_lidar_forest_and_launch_shapes(ctx, fmt):
     finally:
         ags.ags_scene_destroy(scene)
         ags.ags_scene_destroy(ref_scene)
+
+
+def test_update_poses_refit_and_rebuild_match_a_fresh_build(ctx):
+    """Moving the obstacles by refit or by rebuild gives exactly the images of a scene built with the new
+    poses (the traversal is exact, so the tree shape cannot change a result), and they match the oracle."""
+    batch, spec, poses = S.obstacle_rooms(4, steps=1, width=64, height=48)
+    rng = np.random.default_rng(21)
+    new = batch.poses.copy()
+    movable = np.ones(new.shape[0], bool)
+    movable[batch.env_sub[:-1]] = False  # the rooms stay put
+    new[movable, :3] += rng.normal(0, 0.5, (movable.sum(), 3)).astype(np.float32)
+    q = rng.normal(size=(movable.sum(), 4))
+    new[movable, 3:] = (q / np.linalg.norm(q, axis=1, keepdims=True)).astype(np.float32)
+    moved = S.SceneBatch(batch.vertices, batch.indices, batch.sub_vert, batch.sub_tri, batch.sub_seg,
+                         batch.env_sub, new)
+    fresh = ags.ags_scene_build(ctx, moved)
+    refit = ags.ags_scene_build(ctx, batch)
+    rebuilt = ags.ags_scene_build(ctx, batch, ags.AGS_BVH_Q8)
+    try:
+        ref = render(ctx, fresh, spec, poses[0])
+        before = render(ctx, refit, spec, poses[0])
+        assert not np.array_equal(before[0], ref[0])
+        ags.ags_scene_update_poses(ctx, refit, new, ags.AGS_UPDATE_REFIT)
+        out = render(ctx, refit, spec, poses[0])
+        assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1])
+        with pytest.raises(ags.AgsError):
+            ags.ags_scene_update_poses(ctx, rebuilt, new, ags.AGS_UPDATE_REFIT)  # compressed nodes: rebuild only
+        ags.ags_scene_update_poses(ctx, rebuilt, new, ags.AGS_UPDATE_REBUILD)
+        out = render(ctx, rebuilt, spec, poses[0])
+        assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1])
+        for e in range(4):
+            a, _ = ags.ags_scene_get_world_triangles(refit, e)
+            b, _ = ags.ags_scene_get_world_triangles(fresh, e)
+            assert np.array_equal(a, b)
+        check_all(moved, spec, poses[0], ref[0], ref[1], tag="moved obstacles 64x48")
+        bad = new.copy()
+        bad[5, 3:] = 0.0
+        with pytest.raises(ags.AgsError):
+            ags.ags_scene_update_poses(ctx, refit, bad, ags.AGS_UPDATE_REFIT)
+    finally:
+        for sc in (fresh, refit, rebuilt):
+            ags.ags_scene_destroy(sc)
