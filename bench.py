@@ -35,6 +35,7 @@ WORKLOADS = {
     "forest": {"envs": 256, "metric": "Mrays/s at 256 LiDAR forests x 64x512 range+seg"},
     "serving": {"envs": 8192, "metric": "served Mrays/s, 8192 rooms of 1k-200k triangles, mixed sensors; p50/p99 ms"},
     "precision": {"envs": 4096, "metric": "Mrays/s at 4096 rooms x 135x240 per BVH node format; depth error vs FP64"},
+    "dynamic": {"envs": 1024, "metric": "ms per obstacle-pose update (refit vs rebuild), 1024 rooms; render Mrays/s"},
 }
 PAPER_MRAYS = 340.5  # Table II, 1024 envs x 270x480 (RTX 3090; context)
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
@@ -375,6 +376,74 @@ def bench_precision(args, rank, world, local):
     ags.ags_context_destroy(ctx)
 
 
+# ---------------------------------------------------------------- dynamic obstacles
+def bench_dynamic(args, rank, world, local):
+    """Obstacles moving every step: refit vs rebuild cost, and how the refitted tree's render speed drifts."""
+    import torch
+
+    import paper_2503_01471_gb300 as ags
+    from paper_2503_01471_gb300 import build as B
+    from paper_2503_01471_gb300 import scenes as S
+
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    batch, spec, poses = S.obstacle_rooms(args.envs, steps=args.walk, width=480, height=270)
+    E = batch.n_envs
+    ctx = ags.ags_context_create(local)
+    p = torch.as_tensor(poses[0]).to(dev)
+    depth = torch.empty((E, spec.height, spec.width), dtype=torch.float32, device=dev)
+    seg = torch.empty((E, spec.height, spec.width), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    rays = E * spec.width * spec.height
+
+    def render_ms(scene, reps=5):
+        ags.ags_render(ctx, scene, spec, p, depth, seg, stream)
+        st, en = torch.cuda.Event(True), torch.cuda.Event(True)
+        torch.cuda.synchronize(dev)
+        st.record(stream)
+        for _ in range(reps):
+            ags.ags_render(ctx, scene, spec, p, depth, seg, stream)
+        en.record(stream)
+        torch.cuda.synchronize(dev)
+        return st.elapsed_time(en) / reps
+
+    rng = np.random.default_rng(31)
+    movable = np.ones(batch.poses.shape[0], bool)
+    movable[batch.env_sub[:-1]] = False
+    refit = ags.ags_scene_build(ctx, batch)
+    rebuilt = ags.ags_scene_build(ctx, batch)
+    cur = batch.poses.copy()
+    rows = []
+    t_refit, t_rebuild = [], []
+    for step in range(args.steps + 1):
+        if step > 0:  # obstacles drift: 5 cm and 0.05 rad per step
+            cur[movable, :3] += rng.normal(0, 0.05, (movable.sum(), 3)).astype(np.float32)
+            dq = rng.normal(0, 0.025, (movable.sum(), 4)).astype(np.float32)
+            q = cur[movable, 3:] + dq
+            cur[movable, 3:] = q / np.linalg.norm(q, axis=1, keepdims=True)
+            t0 = time.perf_counter()
+            ags.ags_scene_update_poses(ctx, refit, cur, ags.AGS_UPDATE_REFIT)
+            t_refit.append((time.perf_counter() - t0) * 1e3)
+            t0 = time.perf_counter()
+            ags.ags_scene_update_poses(ctx, rebuilt, cur, ags.AGS_UPDATE_REBUILD)
+            t_rebuild.append((time.perf_counter() - t0) * 1e3)
+        if step in (0, 1, args.steps // 2, args.steps):
+            rows.append({"step": step, "refit_mrays_per_s": rays / render_ms(refit) / 1e3,
+                         "rebuild_mrays_per_s": rays / render_ms(rebuilt) / 1e3})
+    line = {"metric": WORKLOADS["dynamic"]["metric"], "value": float(np.median(t_refit)), "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"obstacle rooms, {E} envs, 270x480 camera; every obstacle moves each step",
+                       "tris": int(batch.env_tri_counts().sum())},
+            "refit_ms": {"median": float(np.median(t_refit)), "max": float(np.max(t_refit))},
+            "rebuild_ms": {"median": float(np.median(t_rebuild)), "max": float(np.max(t_rebuild))},
+            "render_after_updates": rows}
+    print(json.dumps(line), flush=True)
+    for sc in (refit, rebuilt):
+        ags.ags_scene_destroy(sc)
+    ags.ags_context_destroy(ctx)
+
+
 # ---------------------------------------------------------------- workload
 def make_workload(args, rank, world=1):
     from paper_2503_01471_gb300 import scenes as S
@@ -533,6 +602,27 @@ def bench_ours(args, rank, world, local):
                  "launches_per_step": E, "speedup_of_batched": (rays_per_step / (ms_step * 1e-3)) /
                  (rays_per_step / (pms * 1e-3))}
 
+    # the same step loop replayed from a captured CUDA graph (poses refreshed in a fixed buffer)
+    graph_pose = poses_d[0].clone()
+    g = ags.ags_render_graph_create(ctx, scene, spec, graph_pose, depth, seg)
+    try:
+        for i in range(args.warmup):
+            graph_pose.copy_(poses_d[i % walk])
+            ags.ags_render_graph_launch(g, stream)
+        torch.cuda.synchronize(dev)
+        start.record(stream)
+        for i in range(args.steps):
+            graph_pose.copy_(poses_d[(args.warmup + i) % walk])
+            ags.ags_render_graph_launch(g, stream)
+        stop.record(stream)
+        torch.cuda.synchronize(dev)
+        gms = start.elapsed_time(stop) / args.steps
+        ags.ags_stream_status(ctx, stream)
+    finally:
+        ags.ags_render_graph_destroy(g)
+    step_graph = {"value": rays_per_step * world / (gms * 1e-3) / 1e6, "unit": UNIT, "ms_per_step": gms,
+                  "api": "ags_render_graph_launch (tile-counter reset + k_trace captured once)"}
+
     hbm, peak_kind = peaks()
     achieved_gbs = b_ray * rays_per_step / (ms_step * 1e-3) / 1e9
     workload = workload_name(args, spec, E)
@@ -560,6 +650,7 @@ def bench_ours(args, rank, world, local):
         "build_ms": build_s * 1e3,
         "build_mtris_per_s": n_tris / build_s / 1e6,
     }
+    line["step_graph"] = step_graph
     if plain is not None:
         line["plain"] = plain
     if args.workload == "rooms" and not args.no_serving:
@@ -588,6 +679,10 @@ def main():
     if args.workload == "precision":
         if rank == 0:
             bench_precision(args, rank, world, local)
+        return
+    if args.workload == "dynamic":
+        if rank == 0:
+            bench_dynamic(args, rank, world, local)
         return
     bench_ours(args, rank, world, local)
 

@@ -286,6 +286,27 @@ ags_status ags_replay_sequential(ags_context* ctx, const ags_scene* scene, const
                                  int32_t n_specs, const ags_request* reqs, const double* arrival_s, int32_t n,
                                  ags_completion* out);
 
+/*
+ * Step graph: the render of one step (tile-counter reset + render kernel)
+ * captured once as a CUDA graph over fixed buffers, then replayed with one
+ * launch per step; the caller refreshes sensor_poses_dev between launches.
+ * One graph must not run on two streams at once (they share its counter).
+ * The graph holds the scene's device pointers: ags_scene_update_poses with
+ * AGS_UPDATE_REFIT keeps it valid, AGS_UPDATE_REBUILD and ags_scene_destroy
+ * invalidate it (destroy the graph first, then capture a new one). A launch
+ * config set after capture applies to new graphs only. Errors: NULL or
+ * mismatched handles and bad specs -> AGS_ERR_INVALID_ARG; capture or
+ * instantiate failures -> AGS_ERR_CUDA. Device-side limits are reported by
+ * ags_stream_status like any render. ags_render_graph_destroy synchronises
+ * the device before freeing.
+ */
+typedef struct ags_graph ags_graph;
+ags_status ags_render_graph_create(ags_context* ctx, const ags_scene* scene, const ags_sensor_spec* spec,
+                                   const float* sensor_poses_dev, float* out_depth_dev, int32_t* out_seg_dev,
+                                   ags_graph** out);
+ags_status ags_render_graph_launch(ags_graph* graph, void* cuda_stream);
+void ags_render_graph_destroy(ags_graph* graph);
+
 /* Synchronise `cuda_stream`, then read and clear the context's device status
  * word: AGS_OK; AGS_ERR_INVALID_ARG if a device sensor pose was non-finite or
  * had a zero quaternion (those rays report NaN, segment -1);

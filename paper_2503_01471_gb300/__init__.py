@@ -53,7 +53,8 @@ EXPORTS = [
     "ags_context_set_traversal_cap", "ags_transform_vertices_noalloc", "ags_autotune",
     "ags_set_launch_config", "ags_get_launch_config", "ags_memcpy_d2h", "ags_server_create", "ags_server_destroy",
     "ags_server_submit", "ags_server_poll", "ags_server_release", "ags_server_stats", "ags_server_replay",
-    "ags_replay_sequential", "ags_scene_update_poses",
+    "ags_replay_sequential", "ags_scene_update_poses", "ags_render_graph_create", "ags_render_graph_launch",
+    "ags_render_graph_destroy",
 ]
 
 
@@ -170,6 +171,9 @@ def lib() -> ctypes.CDLL:
         "ags_server_replay": (i32, [vp, vp, vp, i32, vp]),
         "ags_replay_sequential": (i32, [vp, vp, vp, i32, vp, vp, i32, vp]),
         "ags_scene_update_poses": (i32, [vp, vp, vp, i32]),
+        "ags_render_graph_create": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), vp, vp, vp, ctypes.POINTER(vp)]),
+        "ags_render_graph_launch": (i32, [vp, vp]),
+        "ags_render_graph_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -464,3 +468,20 @@ def ags_replay_sequential(ctx: int, scene: int, specs, requests: np.ndarray, arr
     _check(lib().ags_replay_sequential(ctx, scene, ctypes.cast(sa, ctypes.c_void_p), len(specs), req.ctypes.data,
                                        arr.ctypes.data, len(req), out.ctypes.data), "ags_replay_sequential")
     return out
+
+
+# ---------------------------------------------------------------- step graph
+def ags_render_graph_create(ctx: int, scene: int, spec, sensor_poses, out_depth, out_seg) -> int:
+    s = make_spec(spec)
+    h = ctypes.c_void_p()
+    _check(lib().ags_render_graph_create(ctx, scene, ctypes.byref(s), _ptr(sensor_poses), _ptr(out_depth),
+                                         _ptr(out_seg), ctypes.byref(h)), "ags_render_graph_create")
+    return h.value
+
+
+def ags_render_graph_launch(graph: int, stream=None) -> None:
+    _check(lib().ags_render_graph_launch(graph, _stream(stream)), "ags_render_graph_launch")
+
+
+def ags_render_graph_destroy(graph: int) -> None:
+    lib().ags_render_graph_destroy(graph)

@@ -564,6 +564,80 @@ ags_status ags_scene_stats(const ags_scene* sc, int32_t env, int64_t* n_tris, in
   AGS_API_END
 }
 
+}  // extern "C"
+
+struct ags_graph {
+  ags_context* ctx = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  unsigned int* counter = nullptr;
+};
+
+extern "C" {
+
+ags_status ags_render_graph_create(ags_context* ctx, const ags_scene* sc, const ags_sensor_spec* spec,
+                                   const float* poses, float* depth, int32_t* seg, ags_graph** out) {
+  AGS_API_BEGIN
+  if (!out) return invalid("out is NULL");
+  *out = nullptr;
+  if (!ctx || !sc) return invalid("ctx or scene is NULL");
+  if (sc->ctx != ctx) return invalid("scene belongs to another context");
+  ags_status st = check_spec(spec);
+  if (st != AGS_OK) return st;
+  if (!poses || !depth || !seg) return invalid("poses/depth/seg pointer is NULL");
+  DeviceGuard g(ctx->device);
+  std::unique_ptr<ags_graph> gr(new ags_graph());
+  gr->ctx = ctx;
+  cudaError_t e = cudaMalloc(&gr->counter, sizeof(unsigned int));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(graph counter)");
+  TraceArgs a{};
+  const ags_launch_config cfg = lookup_config(sc, spec);
+  if ((st = fill_trace_args(ctx, sc, spec, sc->n_envs, nullptr, poses, depth, seg, a, cfg)) != AGS_OK) {
+    cudaFree(gr->counter);
+    return st;
+  }
+  a.tile_counter = gr->counter;
+  cudaStream_t s = ctx->stream;
+  if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+    cudaFree(gr->counter);
+    return cuda_fail(e, "cudaStreamBeginCapture");
+  }
+  cudaMemsetAsync(gr->counter, 0, sizeof(unsigned int), s);
+  const int blocks = cfg.blocks_per_sm > 0 ? ctx->sm_count * cfg.blocks_per_sm : ctx->trace_blocks;
+  cudaError_t le = a.total_tiles > 0 ? launch_trace(a, blocks, false, s) : cudaSuccess;
+  e = cudaStreamEndCapture(s, &gr->graph);
+  if (le != cudaSuccess || e != cudaSuccess) {
+    if (gr->graph) cudaGraphDestroy(gr->graph);
+    cudaFree(gr->counter);
+    return cuda_fail(le != cudaSuccess ? le : e, "graph capture");
+  }
+  if ((e = cudaGraphInstantiate(&gr->exec, gr->graph, 0)) != cudaSuccess) {
+    cudaGraphDestroy(gr->graph);
+    cudaFree(gr->counter);
+    return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  *out = gr.release();
+  return AGS_OK;
+  AGS_API_END
+}
+
+ags_status ags_render_graph_launch(ags_graph* gr, void* stream) {
+  if (!gr) return invalid("graph is NULL");
+  DeviceGuard g(gr->ctx->device);
+  cudaError_t e = cudaGraphLaunch(gr->exec, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? AGS_OK : cuda_fail(e, "cudaGraphLaunch");
+}
+
+void ags_render_graph_destroy(ags_graph* gr) {
+  if (!gr) return;
+  DeviceGuard g(gr->ctx->device);
+  cudaDeviceSynchronize();
+  if (gr->exec) cudaGraphExecDestroy(gr->exec);
+  if (gr->graph) cudaGraphDestroy(gr->graph);
+  cudaFree(gr->counter);
+  delete gr;
+}
+
 ags_status ags_memcpy_d2h(void* dst, const void* src, int64_t bytes) {
   if (bytes < 0 || (bytes > 0 && (!dst || !src))) return invalid("bad ags_memcpy_d2h arguments");
   if (bytes == 0) return AGS_OK;

@@ -429,3 +429,22 @@ def test_update_poses_refit_and_rebuild_match_a_fresh_build(ctx):
     finally:
         for sc in (fresh, refit, rebuilt):
             ags.ags_scene_destroy(sc)
+
+
+def test_step_graph_replays_the_render(ctx):
+    batch, spec, poses = S.obstacle_rooms(3, steps=3, width=48, height=36)
+    scene = ags.ags_scene_build(ctx, batch)
+    p = torch.as_tensor(poses[0]).cuda()
+    d = torch.empty((3, 36, 48), device="cuda")
+    s = torch.empty((3, 36, 48), dtype=torch.int32, device="cuda")
+    g = ags.ags_render_graph_create(ctx, scene, spec, p, d, s)
+    try:
+        for step in range(3):
+            p.copy_(torch.as_tensor(poses[step]).cuda())
+            ags.ags_render_graph_launch(g)
+            ags.ags_stream_status(ctx)
+            ref = render(ctx, scene, spec, poses[step])
+            assert np.array_equal(d.cpu().numpy(), ref[0]) and np.array_equal(s.cpu().numpy(), ref[1])
+    finally:
+        ags.ags_render_graph_destroy(g)
+        ags.ags_scene_destroy(scene)
