@@ -28,6 +28,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 
 MAX_CAND = 4
+MAX_TRI = 8
 F_COUNTED = 1
 F_SILHOUETTE = 2
 F_NEAR_TIE = 4
@@ -36,6 +37,7 @@ F_GRAZING = 16
 F_OVERFLOW = 32
 F_MISS_OK = 64
 F_WIDE = 128
+F_TRI_OVERFLOW = 256
 
 PINHOLE = 0
 LIDAR = 1
@@ -83,17 +85,18 @@ class _Result(ctypes.Structure):
         ("v", ctypes.c_double), ("seg", ctypes.c_int32), ("tri", ctypes.c_int32),
         ("flags", ctypes.c_int32), ("n_cand", ctypes.c_int32),
         ("cand_seg", ctypes.c_int32 * MAX_CAND), ("cand_lo", ctypes.c_double * MAX_CAND),
-        ("cand_hi", ctypes.c_double * MAX_CAND),
+        ("cand_hi", ctypes.c_double * MAX_CAND), ("n_tri", ctypes.c_int32),
+        ("cand_tri", ctypes.c_int32 * MAX_TRI),
     ]
 
 
 RESULT_DTYPE = np.dtype({
-    "names": ["v", "seg", "tri", "flags", "n_cand", "cand_seg", "cand_lo", "cand_hi"],
+    "names": ["v", "seg", "tri", "flags", "n_cand", "cand_seg", "cand_lo", "cand_hi", "n_tri", "cand_tri"],
     "formats": ["<f8", "<i4", "<i4", "<i4", "<i4", ("<i4", MAX_CAND), ("<f8", MAX_CAND),
-                ("<f8", MAX_CAND)],
+                ("<f8", MAX_CAND), "<i4", ("<i4", MAX_TRI)],
     "offsets": [_Result.v.offset, _Result.seg.offset, _Result.tri.offset, _Result.flags.offset,
                 _Result.n_cand.offset, _Result.cand_seg.offset, _Result.cand_lo.offset,
-                _Result.cand_hi.offset],
+                _Result.cand_hi.offset, _Result.n_tri.offset, _Result.cand_tri.offset],
     "itemsize": ctypes.sizeof(_Result),
 })
 
@@ -121,6 +124,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                    ctypes.POINTER(_Sensor), dp, ctypes.POINTER(ctypes.c_int64),
                                    ctypes.c_int64, ctypes.c_void_p]
         lib.orc_render.restype = ctypes.c_int
+        lib.orc_hit_channels.argtypes = [dp, ctypes.c_int64, ctypes.POINTER(_Sensor), dp,
+                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32), dp,
+                                         ctypes.c_int64, dp, dp, dp]
+        lib.orc_hit_channels.restype = ctypes.c_int
         lib.orc_num_threads.argtypes = []
         lib.orc_num_threads.restype = ctypes.c_int
         _libs[key] = lib
@@ -223,6 +230,29 @@ def render(tris, seg, sensor: Sensor, pose, rays=None, lib=None) -> np.ndarray:
     if rc != 0:
         raise ValueError("orc_render: bad input")
     return out
+
+
+def hit_channels(tris, sensor: Sensor, pose, rays, face, v, lib=None):
+    """Barycentrics [n,2], world normals [n,3] and sensor-frame points [n,3] of rays (flat indices) that
+    hit triangle ``face`` (env-local; < 0 for a miss) and report value ``v``."""
+    lib = lib or load()
+    tris = np.ascontiguousarray(tris, dtype=np.float64).reshape(-1, 9)
+    pose = np.ascontiguousarray(pose, dtype=np.float64).reshape(7)
+    rays = np.ascontiguousarray(rays, dtype=np.int64).reshape(-1)
+    face = np.ascontiguousarray(face, dtype=np.int32).reshape(-1)
+    v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
+    n = rays.shape[0]
+    if face.shape[0] != n or v.shape[0] != n:
+        raise ValueError("rays, face and v disagree")
+    bary, normal, point = np.zeros((n, 2)), np.zeros((n, 3)), np.zeros((n, 3))
+    s = sensor._c()
+    rc = lib.orc_hit_channels(_dp(tris), tris.shape[0], ctypes.byref(s), _dp(pose),
+                              rays.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                              face.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), _dp(v), n, _dp(bary),
+                              _dp(normal), _dp(point))
+    if rc != 0:
+        raise ValueError("orc_hit_channels: bad input or degenerate face")
+    return bary, normal, point
 
 
 def num_threads(lib=None) -> int:

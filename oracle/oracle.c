@@ -117,6 +117,7 @@ int orc_ray(const orc_sensor* s, const double pose[7], int64_t row, int64_t col,
 typedef struct {
   double t_lo, t_hi; /* range of t a perturbed ray could report */
   int32_t seg;
+  int32_t tri;
   int32_t sure;      /* every ray within eps hits it inside the valid t range */
   int32_t edge;      /* possible but not geometrically sure */
   int32_t grazing;
@@ -284,6 +285,7 @@ static void render_one(const double* tris, const int32_t* seg, int64_t F, const 
     c->t_lo = ev.t_lo;
     c->t_hi = ev.t_hi;
     c->seg = seg[i];
+    c->tri = (int32_t)i;
     c->sure = ev.sure;
     c->edge = ev.edge;
     c->grazing = ev.grazing;
@@ -345,6 +347,10 @@ static void render_one(const double* tris, const int32_t* seg, int64_t F, const 
         vlo = fmax(vlo, s->min_range);
       }
     }
+    if (res->n_tri < ORC_MAX_TRI)
+      res->cand_tri[res->n_tri++] = c->tri;
+    else
+      flags |= ORC_F_TRI_OVERFLOW;
     int g;
     for (g = 0; g < res->n_cand; ++g)
       if (res->cand_seg[g] == c->seg) break;
@@ -383,6 +389,75 @@ int orc_render(const double* tris, const int32_t* seg, int64_t F, const orc_sens
     orc_cand list[ORC_LIST_CAP];
 #pragma omp for schedule(dynamic, 4)
     for (int64_t i = 0; i < n_rays; ++i) render_one(tris, seg, F, s, pose, rays[i], &out[i], list);
+  }
+  return 0;
+}
+
+/* ---- extra hit channels (Sec. III-D.1: "vertex (or mesh-face) indices
+ * alongside barycentric coordinates", "point clouds and surface normals") ----
+ * reading: the face index is the env-local triangle index; the barycentrics
+ * are those of the point where the ray meets the face's plane, weights of its
+ * second and third vertex; the normal is the face's geometric normal turned
+ * towards the sensor (meshes are two-sided); the point is the hit in the
+ * sensor frame, consistent with the reported value. */
+static void sensor_local(const orc_sensor* s, int64_t row, int64_t col, double local[3]) {
+  if (s->type == ORC_PINHOLE) {
+    /* the camera ray through the pixel centre, scaled to unit forward component */
+    double W = (double)s->width, H = (double)s->height;
+    double f = (W / 2.0) / tan(s->hfov / 2.0);
+    local[0] = 1.0;
+    local[1] = (W / 2.0 - ((double)col + 0.5)) / f;
+    local[2] = (H / 2.0 - ((double)row + 0.5)) / f;
+  } else {
+    double C = (double)s->height;
+    double phi = (s->height > 1) ? s->vfov_max - (double)row * (s->vfov_max - s->vfov_min) / (C - 1.0)
+                                 : s->vfov_max;
+    double psi = s->hfov * (double)col / (double)s->width;
+    local[0] = cos(phi) * cos(psi);
+    local[1] = cos(phi) * sin(psi);
+    local[2] = sin(phi);
+  }
+}
+
+int orc_hit_channels(const double* tris, int64_t F, const orc_sensor* s, const double pose[7],
+                     const int64_t* rays, const int32_t* face, const double* v, int64_t n,
+                     double* bary, double* normal, double* point) {
+  if (!s || !pose || n < 0 || (n > 0 && (!rays || !face || !v || !bary || !normal || !point))) return -1;
+  if (s->width <= 0 || s->height <= 0 || (s->type != ORC_PINHOLE && s->type != ORC_LIDAR)) return -1;
+  int64_t n_pix = (int64_t)s->width * s->height;
+  for (int64_t i = 0; i < n; ++i) {
+    if (rays[i] < 0 || rays[i] >= n_pix || face[i] >= F) return -1;
+    int64_t row = rays[i] / s->width, col = rays[i] % s->width;
+    double local[3];
+    sensor_local(s, row, col, local);
+    for (int k = 0; k < 3; ++k) point[3 * i + k] = v[i] * local[k];
+    for (int k = 0; k < 2; ++k) bary[2 * i + k] = 0.0;
+    for (int k = 0; k < 3; ++k) normal[3 * i + k] = 0.0;
+    if (face[i] < 0) continue;
+    double o[3], d[3], scale;
+    if (orc_ray(s, pose, row, col, o, d, &scale) != 0) return -1;
+    const double* tri = tris + 9 * (int64_t)face[i];
+    double e1[3], e2[3], nrm[3], q[3];
+    for (int k = 0; k < 3; ++k) {
+      e1[k] = tri[3 + k] - tri[k];
+      e2[k] = tri[6 + k] - tri[k];
+      q[k] = o[k] - tri[k];
+    }
+    cross3(e1, e2, nrm);
+    double nn = sqrt(dot3(nrm, nrm));
+    double nd = dot3(nrm, d);
+    if (nn == 0.0 || nd == 0.0) return -1;
+    /* the plane point o + t d with t = -(q.n)/(d.n), then its barycentrics
+     * from the areas of the sub-triangles it spans with the edges */
+    double t = -dot3(q, nrm) / nd;
+    double x[3], c1[3], c2[3];
+    for (int k = 0; k < 3; ++k) x[k] = q[k] + t * d[k]; /* hit point relative to v0 */
+    cross3(x, e2, c1);
+    cross3(e1, x, c2);
+    bary[2 * i] = dot3(c1, nrm) / (nn * nn);
+    bary[2 * i + 1] = dot3(c2, nrm) / (nn * nn);
+    double sgn = nd > 0.0 ? -1.0 : 1.0;
+    for (int k = 0; k < 3; ++k) normal[3 * i + k] = sgn * nrm[k] / nn;
   }
   return 0;
 }

@@ -33,6 +33,8 @@ extern "C" {
 
 /* maximum number of distinct-segment outcome groups reported per ray */
 #define ORC_MAX_CAND 4
+/* maximum number of candidate triangles listed per ray */
+#define ORC_MAX_TRI 8
 
 /* flag bits of orc_result.flags */
 #define ORC_F_COUNTED 1      /* more than one outcome (segment, or hit vs miss) is acceptable */
@@ -43,6 +45,7 @@ extern "C" {
 #define ORC_F_OVERFLOW 32    /* more than ORC_MAX_CAND segment groups (test must fail) */
 #define ORC_F_MISS_OK 64     /* "miss" (max_range, -1) is an acceptable outcome */
 #define ORC_F_WIDE 128       /* the error bands widen an outcome's value range beyond +-tol */
+#define ORC_F_TRI_OVERFLOW 256 /* more than ORC_MAX_TRI candidate triangles */
 
 typedef struct {
   int32_t type;        /* ORC_PINHOLE or ORC_LIDAR */
@@ -69,6 +72,8 @@ typedef struct {
   int32_t cand_seg[ORC_MAX_CAND];
   double cand_lo[ORC_MAX_CAND];   /* acceptable reported-value interval per segment */
   double cand_hi[ORC_MAX_CAND];
+  int32_t n_tri;       /* triangles a single-precision renderer may report (within the bands) */
+  int32_t cand_tri[ORC_MAX_TRI];
 } orc_result;
 
 /* Rotation matrix of the unit quaternion q/|q| (x, y, z, w order), row-major. */
@@ -89,6 +94,22 @@ int orc_ray(const orc_sensor* s, const double pose[7], int64_t row, int64_t col,
 int orc_render(const double* tris, const int32_t* seg, int64_t F,
                const orc_sensor* s, const double pose[7],
                const int64_t* rays, int64_t n_rays, orc_result* out);
+
+/* Extra hit channels of a ray (Sec. III-D.1: face indices with barycentric
+ * coordinates, surface normals, point clouds), for n rays (flat index
+ * row*width+col) that hit triangle face[i] of tris (or miss: face[i] < 0) and
+ * report value v[i]:
+ *   bary[2i..]   (u, v): weights of the triangle's second and third vertex at
+ *                the point where the ray meets the triangle's plane; 0 on a miss;
+ *   normal[3i..] unit geometric normal (v1 - v0) x (v2 - v0) in the world frame,
+ *                turned to face the sensor (n.d <= 0); 0 on a miss;
+ *   point[3i..]  the hit in the sensor frame, v[i] times the sensor-frame ray
+ *                direction scaled to unit reported value (camera: (1, a, b),
+ *                LiDAR: the unit direction).
+ * Returns 0, or -1 on bad input or a zero-area / parallel face. */
+int orc_hit_channels(const double* tris, int64_t F, const orc_sensor* s, const double pose[7],
+                     const int64_t* rays, const int32_t* face, const double* v, int64_t n,
+                     double* bary, double* normal, double* point);
 
 /* Number of OpenMP threads the oracle uses. */
 int orc_num_threads(void);

@@ -384,10 +384,119 @@ def pin_tie_break(lib):
         assert sorted(res["cand_seg"][0][:res["n_cand"][0]]) == [5, 8]
 
 
+# ---------------------------------------------------------------- extra hit channels
+def pin_channels_wall(lib):
+    """Wall at x = D in the sensor frame (either winding): the normal is minus the camera axis, and the
+    sensor-frame point, moved to the world, lies on the wall and on the pixel's ray."""
+    rng = np.random.default_rng(17)
+    for trial in range(6):
+        D = rng.uniform(0.5, 9.0)
+        q = rng.normal(size=4)
+        R = _rot_scipy(q)
+        p = rng.uniform(-3, 3, 3)
+        local = np.array([[D, -60, -60], [D, 60, -60], [D, 60, 60], [D, -60, 60]])
+        wv = local @ R.T + p
+        order = (0, 1, 2, 0, 2, 3) if trial % 2 == 0 else (0, 2, 1, 0, 3, 2)
+        tris = np.array([np.concatenate([wv[i] for i in order[:3]]), np.concatenate([wv[i] for i in order[3:]])])
+        seg = np.array([3, 3], np.int32)
+        pose = np.concatenate([p, q])
+        for s in (O.Sensor(O.PINHOLE, 24, 18, math.radians(87), 0.1, 10.0),
+                  O.Sensor(O.LIDAR, 16, 5, math.radians(80), 0.1, 1e5, -0.4, 0.4)):
+            n = s.width * s.height
+            rays = np.arange(n)
+            r = O.render(tris, seg, s, pose, lib=lib)
+            assert (r["seg"] == 3).all()
+            bary, normal, point = O.hit_channels(tris, s, pose, rays, r["tri"], r["v"], lib=lib)
+            assert np.allclose(normal, -R[:, 0], atol=1e-12)
+            Pw = point @ R.T + p
+            assert np.allclose((Pw - p) @ R[:, 0], D, rtol=0, atol=1e-9 * D)
+            for idx in range(n):
+                o, d, _ = O.ray(s, pose, idx // s.width, idx % s.width, lib)
+                assert np.linalg.norm(np.cross(Pw[idx] - o, d)) <= 1e-9 * np.linalg.norm(Pw[idx] - o)
+                assert (Pw[idx] - o) @ d > 0
+                w = tris[r["tri"][idx]].reshape(3, 3)
+                assert np.allclose(w[0] + bary[idx, 0] * (w[1] - w[0]) + bary[idx, 1] * (w[2] - w[0]), Pw[idx],
+                                   atol=1e-9)
+
+
+def pin_channels_linear_solve(lib):
+    """Barycentrics against numpy.linalg.solve of o + t d = v0 + u (v1 - v0) + w (v2 - v0), and the
+    normal against the null space of the edge vectors (SVD), on random triangles."""
+    rng = np.random.default_rng(18)
+    checked = 0
+    for trial in range(12):
+        F = int(rng.integers(1, 9))
+        tris = rng.uniform(-4, 4, (F, 9))
+        seg = rng.integers(0, 5, F).astype(np.int32)
+        s = O.Sensor(O.PINHOLE, 12, 9, math.radians(100), 0.05, 20.0)
+        pose = np.concatenate([rng.uniform(-1, 1, 3), rng.normal(size=4)])
+        res = O.render(tris, seg, s, pose, lib=lib)
+        hit = np.nonzero(res["tri"] >= 0)[0]
+        bary, normal, _ = O.hit_channels(tris, s, pose, hit, res["tri"][hit], res["v"][hit], lib=lib)
+        for k, idx in enumerate(hit):
+            if res["flags"][idx] & (O.F_SILHOUETTE | O.F_NEAR_TIE | O.F_RANGE_EDGE):
+                continue
+            o, d, _ = O.ray(s, pose, idx // 12, idx % 12, lib)
+            v0, v1, v2 = tris[res["tri"][idx]].reshape(3, 3)
+            t, u, w = np.linalg.solve(np.stack([d, v0 - v1, v0 - v2], 1), v0 - o)
+            assert abs(bary[k, 0] - u) < 1e-9 and abs(bary[k, 1] - w) < 1e-9, (trial, idx, bary[k], u, w)
+            nul = np.linalg.svd(np.stack([v1 - v0, v2 - v0]))[2][2]
+            assert abs(abs(float(normal[k] @ nul)) - 1.0) < 1e-12
+            assert float(normal[k] @ d) <= 0.0
+            checked += 1
+    assert checked > 300
+
+
+def pin_channels_icosphere(lib):
+    """Rays at an icosphere from outside: the face normal points out (within the facet angle), and the
+    reported face holds the hit point."""
+    from paper_2503_01471_gb300.scenes import icosphere_unit
+    v, f = icosphere_unit(2)
+    c = np.array([3.0, 0.2, -0.1])
+    tris = (v * 0.7 + c)[f].reshape(-1, 9)
+    seg = np.full(len(tris), 2, np.int32)
+    s = O.Sensor(O.PINHOLE, 32, 24, 0.6, 0.1, 20.0)
+    res = O.render(tris, seg, s, IDENT, lib=lib)
+    hit = np.nonzero(res["tri"] >= 0)[0]
+    assert hit.shape[0] > 100
+    bary, normal, point = O.hit_channels(tris, s, IDENT, hit, res["tri"][hit], res["v"][hit], lib=lib)
+    radial = point - c
+    radial /= np.linalg.norm(radial, axis=1, keepdims=True)
+    assert (np.sum(normal * radial, 1) > 0.95).all()
+    assert (bary >= -1e-12).all() and (bary.sum(1) <= 1 + 1e-12).all()
+
+
+def pin_channels_miss_and_lidar_norm(lib):
+    """A miss gives zero barycentrics and normal and the point at the reported value along the ray; a LiDAR
+    point's length is the range."""
+    s = O.Sensor(O.LIDAR, 32, 4, 2 * math.pi, 0.1, 30.0, -0.3, 0.3)
+    rays = np.arange(128)
+    v = np.linspace(1.0, 30.0, 128)
+    bary, normal, point = O.hit_channels(np.zeros((0, 9)), s, IDENT, rays, np.full(128, -1), v, lib=lib)
+    assert not bary.any() and not normal.any()
+    assert np.allclose(np.linalg.norm(point, axis=1), v, rtol=1e-14)
+    for idx in (0, 37, 127):
+        o, d, _ = O.ray(s, IDENT, idx // 32, idx % 32, lib)
+        assert np.allclose(point[idx], v[idx] * d, atol=1e-12)
+
+
+def pin_candidate_triangles(lib):
+    """A ray through the interior of one triangle lists only it; a ray along the shared edge of two
+    lists both."""
+    quad = [[3, -1, -1, 3, 1, -1, 3, 1, 1], [3, -1, -1, 3, 1, 1, 3, -1, 1]]  # diagonal through (3, 0, 0)
+    s = O.Sensor(O.PINHOLE, 1, 1, 1.0, 0.1, 10.0)
+    res = O.render(np.array(quad, float), np.array([4, 4], np.int32), s, IDENT, lib=lib)
+    assert sorted(res["cand_tri"][0][:res["n_tri"][0]]) == [0, 1]
+    off = np.array(quad, float) + np.array([0, 0.5, -0.3] * 3)
+    res = O.render(off, np.array([4, 4], np.int32), s, IDENT, lib=lib)
+    assert res["n_tri"][0] == 1 and res["cand_tri"][0][0] == res["tri"][0] == 1  # (y, z) = (-0.5, 0.3): y < z
+
+
 ALL_PINS = [
     pin_rotation_vs_scipy, pin_transform_vs_scipy, pin_transform_identity_exact,
     pin_camera_centre_and_corner, pin_camera_column_angles, pin_lidar_angles,
     pin_wall_depth_constant, pin_lidar_cylinder_facets, pin_icosphere_bounds, pin_hand_worked,
     pin_brute_force_linear_solve, pin_miss_exact, pin_translation_rotation_invariance,
-    pin_degenerate_never_hits, pin_tie_break,
+    pin_degenerate_never_hits, pin_tie_break, pin_channels_wall, pin_channels_linear_solve,
+    pin_channels_icosphere, pin_channels_miss_and_lidar_norm, pin_candidate_triangles,
 ]

@@ -43,6 +43,12 @@ MUTANTS = {
     "max_applies_to_range": ("double t_far = s->max_range / scale;", "double t_far = s->max_range;"),
     "hits_behind_sensor": ("    if (t >= 0.0 && t <= t_far) {", "    if (t <= t_far) {"),
     "degenerate_hits": ("  if (nn == 0.0) return; /* zero-area triangle: never hit */", "  if (nn < 0.0) return;"),
+    "bary_swapped": ("bary[2 * i] = dot3(c1, nrm) / (nn * nn);", "bary[2 * i] = dot3(c2, nrm) / (nn * nn);"),
+    "normal_not_turned": ("double sgn = nd > 0.0 ? -1.0 : 1.0;", "double sgn = 1.0;"),
+    "point_scaled_as_range": ("point[3 * i + k] = v[i] * local[k];",
+                              "point[3 * i + k] = v[i] * local[k] / sqrt(dot3(local, local));"),
+    "point_pixel_corner": ("local[1] = (W / 2.0 - ((double)col + 0.5)) / f;", "local[1] = (W / 2.0 - (double)col) / f;"),
+    "candidate_triangle_dropped": ("res->cand_tri[res->n_tri++] = c->tri;", "res->cand_tri[res->n_tri] = c->tri;"),
 }
 
 
