@@ -288,9 +288,10 @@ __device__ __forceinline__ float grid_bound(const SplitGrid& g, int a, int i) {
 }
 
 // Clip triangle (a, b, c) to the cell [lo, hi] (Sutherland-Hodgman against
-// its six planes); false if nothing is left, else the clipped polygon's box.
+// its six planes); false if nothing is left, else the clipped polygon's box
+// and the range of its vertices' barycentric weights (u of b, v of c).
 __device__ bool clip_to_cell(const float4& a, const float4& b, const float4& c, const float lo[3],
-                             const float hi[3], Box& out) {
+                             const float hi[3], Box& out, float bary[4]) {
   float P[9][3], Q[9][3];
   P[0][0] = a.x; P[0][1] = a.y; P[0][2] = a.z;
   P[1][0] = b.x; P[1][1] = b.y; P[1][2] = b.z;
@@ -329,7 +330,51 @@ __device__ bool clip_to_cell(const float4& a, const float4& b, const float4& c, 
     bx.loz = fminf(bx.loz, P[i][2]); bx.hiz = fmaxf(bx.hiz, P[i][2]);
   }
   out = bx;
+  // weights of b and c: u = ((x - a) x e2) . n / |n|^2, v = (e1 x (x - a)) . n / |n|^2
+  const float e1[3] = {b.x - a.x, b.y - a.y, b.z - a.z}, e2[3] = {c.x - a.x, c.y - a.y, c.z - a.z};
+  const float nx = e1[1] * e2[2] - e1[2] * e2[1], ny = e1[2] * e2[0] - e1[0] * e2[2], nz = e1[0] * e2[1] - e1[1] * e2[0];
+  const float inv = 1.0f / (nx * nx + ny * ny + nz * nz);
+  bary[0] = bary[1] = INFINITY;
+  bary[2] = bary[3] = -INFINITY;
+  for (int i = 0; i < n; ++i) {
+    const float x0 = P[i][0] - a.x, x1 = P[i][1] - a.y, x2 = P[i][2] - a.z;
+    const float u = ((x1 * e2[2] - x2 * e2[1]) * nx + (x2 * e2[0] - x0 * e2[2]) * ny + (x0 * e2[1] - x1 * e2[0]) * nz) * inv;
+    const float v = ((e1[1] * x2 - e1[2] * x1) * nx + (e1[2] * x0 - e1[0] * x2) * ny + (e1[0] * x1 - e1[1] * x0) * nz) * inv;
+    bary[0] = fminf(bary[0], u);
+    bary[1] = fminf(bary[1], v);
+    bary[2] = fmaxf(bary[2], u);
+    bary[3] = fmaxf(bary[3], v);
+  }
   return true;
+}
+
+// A reference's barycentric range [u0, u1] x [v0, v1] as four 16-bit steps
+// of 1/65535, rounded outward by a margin that covers the float32 rounding of
+// the clipping and of the weights (1/1024); a sliver (shortest altitude below
+// 1e-3 of the coordinates) or a non-finite range gets the whole triangle. The range
+// is fixed under any rigid motion of the triangle, so a refit can rebuild
+// the reference's box from it.
+constexpr uint32_t kBaryWholeLo = 0u, kBaryWholeHi = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint2 pack_bary(const float4& a, const float4& b, const float4& c, const float r[4]) {
+  const float e1x = b.x - a.x, e1y = b.y - a.y, e1z = b.z - a.z, e2x = c.x - a.x, e2y = c.y - a.y, e2z = c.z - a.z;
+  const float e3x = c.x - b.x, e3y = c.y - b.y, e3z = c.z - b.z;
+  const float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+  const float area2 = sqrtf(nx * nx + ny * ny + nz * nz);
+  const float lmax = sqrtf(fmaxf(fmaxf(e1x * e1x + e1y * e1y + e1z * e1z, e2x * e2x + e2y * e2y + e2z * e2z),
+                                 e3x * e3x + e3y * e3y + e3z * e3z));
+  const float cmax = fmaxf(fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(b.x))),
+                           fmaxf(fmaxf(fabsf(b.y), fabsf(b.z)), fmaxf(fmaxf(fabsf(c.x), fabsf(c.y)), fabsf(c.z))));
+  // shortest altitude = |n| / longest edge; at >= 1e-3 of the coordinates the
+  // weights' rounding stays well inside the margin
+  if (!(area2 > 0.0f) || !(area2 / lmax >= 1e-3f * fmaxf(cmax, 1.0f))) return make_uint2(kBaryWholeLo, kBaryWholeHi);
+  const float m = 1.0f / 1024.0f;
+  const float u0 = fmaxf(r[0] - m, 0.0f), v0 = fmaxf(r[1] - m, 0.0f), u1 = fminf(r[2] + m, 1.0f),
+              v1 = fminf(r[3] + m, 1.0f);
+  if (!(u0 <= u1) || !(v0 <= v1)) return make_uint2(kBaryWholeLo, kBaryWholeHi);
+  const uint32_t qu0 = (uint32_t)floorf(u0 * 65535.0f), qv0 = (uint32_t)floorf(v0 * 65535.0f);
+  const uint32_t qu1 = (uint32_t)ceilf(u1 * 65535.0f), qv1 = (uint32_t)ceilf(v1 * 65535.0f);
+  return make_uint2(qu0 | (qv0 << 16), min(qu1, 65535u) | (min(qv1, 65535u) << 16));
 }
 
 __device__ __forceinline__ float widen_dn(float x) { return x - 1.9073486328125e-6f * fmaxf(fabsf(x), 1.0f); }
@@ -341,7 +386,7 @@ __global__ void k_split(const float4* __restrict__ packed, const int32_t* __rest
                         const int32_t* __restrict__ bounds, float cells, int max_refs,
                         int32_t* __restrict__ counts,
                         const int32_t* __restrict__ ref_off, int32_t* __restrict__ ref_tri,
-                        Box* __restrict__ ref_box, int32_t* __restrict__ ref_env) {
+                        Box* __restrict__ ref_box, int32_t* __restrict__ ref_env, uint2* __restrict__ ref_bary) {
   int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= F) return;
   const int32_t e = tri_env[t];
@@ -361,6 +406,7 @@ __global__ void k_split(const float4* __restrict__ packed, const int32_t* __rest
       ref_tri[out] = t;
       ref_box[out] = tb;
       ref_env[out] = e;
+      ref_bary[out] = make_uint2(kBaryWholeLo, kBaryWholeHi);
     }
   } else {
     const float4 A = packed[3 * (int64_t)t], B = packed[3 * (int64_t)t + 1], C = packed[3 * (int64_t)t + 2];
@@ -374,13 +420,15 @@ __global__ void k_split(const float4* __restrict__ packed, const int32_t* __rest
           const float wlo[3] = {widen_dn(lo[0]), widen_dn(lo[1]), widen_dn(lo[2])};
           const float whi[3] = {widen_up(hi[0]), widen_up(hi[1]), widen_up(hi[2])};
           Box cb;
-          if (!clip_to_cell(A, B, C, wlo, whi, cb)) continue;
+          float br[4];
+          if (!clip_to_cell(A, B, C, wlo, whi, cb, br)) continue;
           if (kEmit) {
             Box r = {fmaxf(widen_dn(cb.lox), tb.lox), fmaxf(widen_dn(cb.loy), tb.loy), fmaxf(widen_dn(cb.loz), tb.loz),
                      fminf(widen_up(cb.hix), tb.hix), fminf(widen_up(cb.hiy), tb.hiy), fminf(widen_up(cb.hiz), tb.hiz)};
             ref_tri[out + count] = t;
             ref_box[out + count] = r;
             ref_env[out + count] = e;
+            ref_bary[out + count] = pack_bary(A, B, C, br);
           }
           ++count;
         }
@@ -390,6 +438,7 @@ __global__ void k_split(const float4* __restrict__ packed, const int32_t* __rest
         ref_tri[out] = t;
         ref_box[out] = tb;
         ref_env[out] = e;
+        ref_bary[out] = make_uint2(kBaryWholeLo, kBaryWholeHi);
       }
     }
   }
@@ -674,12 +723,15 @@ __global__ void k_collapse_emit(const QueueItem* __restrict__ items, int32_t n_i
 }
 
 __global__ void k_gather_tris(const float4* __restrict__ packed, const int32_t* __restrict__ ref_tri,
-                              const uint32_t* __restrict__ vals, const int32_t* __restrict__ perm, int32_t R,
-                              float4* __restrict__ out, int32_t* __restrict__ leaf_tri) {
+                              const uint2* __restrict__ ref_bary, const uint32_t* __restrict__ vals,
+                              const int32_t* __restrict__ perm, int32_t R, float4* __restrict__ out,
+                              int32_t* __restrict__ leaf_tri, uint2* __restrict__ leaf_bary) {
   int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= R) return;
-  int64_t t = ref_tri[vals[perm[k]]];
+  const int32_t ref = vals[perm[k]];
+  int64_t t = ref_tri[ref];
   leaf_tri[k] = (int32_t)t;
+  if (leaf_bary) leaf_bary[k] = ref_bary[ref];
   out[3 * (int64_t)k] = packed[3 * t];
   out[3 * (int64_t)k + 1] = packed[3 * t + 1];
   out[3 * (int64_t)k + 2] = packed[3 * t + 2];
@@ -895,7 +947,7 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
   // references per triangle are capped so that their total stays below 2^31
   const int max_refs = (int)std::max<int64_t>(1, std::min<int64_t>(kSplitMaxRefs, ((1ll << 31) - 2 - F) / F + 1));
   k_split<false><<<blocks_for(F, 128), 128, 0, s>>>(d_packed, d_tri_env, F, d_bounds, cells, max_refs, d_ref_count,
-                                                   nullptr, nullptr, nullptr, nullptr);
+                                                   nullptr, nullptr, nullptr, nullptr, nullptr);
   AGS_CHECK(cudaGetLastError());
   AGS_CHECK(exclusive_scan(d_ref_count, F, d_ref_tot, d_scan_f, s));
   k_env_ref_off<<<blocks_for((int64_t)E + 1, 128), 128, 0, s>>>(d_ref_count, d_env_tri, E, F, d_ref_tot, d_env_ref);
@@ -911,11 +963,13 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
   sc->n_refs = R;
   int32_t *d_ref_tri = nullptr, *d_ref_env = nullptr;
   Box* d_ref_box = nullptr;
+  uint2* d_ref_bary = nullptr;
   AGS_CHECK(tmp.alloc(&d_ref_tri, (size_t)R));
   AGS_CHECK(tmp.alloc(&d_ref_env, (size_t)R));
   AGS_CHECK(tmp.alloc(&d_ref_box, (size_t)R));
+  AGS_CHECK(tmp.alloc(&d_ref_bary, (size_t)R));
   k_split<true><<<blocks_for(F, 128), 128, 0, s>>>(d_packed, d_tri_env, F, d_bounds, cells, max_refs, nullptr,
-                                                  d_ref_count, d_ref_tri, d_ref_box, d_ref_env);
+                                                  d_ref_count, d_ref_tri, d_ref_box, d_ref_env, d_ref_bary);
   AGS_CHECK(cudaGetLastError());
 
   // roots and level-0 queue (environments with at least one reference)
@@ -1064,8 +1118,10 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
   }
   AGS_CHECK(cudaMalloc(&sc->d.tris, std::max<int64_t>(3 * (int64_t)R, 1) * sizeof(float4)));
   AGS_CHECK(cudaMalloc(&sc->d.leaf_tri, std::max<int64_t>(R, 1) * sizeof(int32_t)));
-  k_gather_tris<<<blocks_for(R, 256), 256, 0, s>>>(d_packed, d_ref_tri, d_vals, d_perm, R, sc->d.tris,
-                                                   sc->d.leaf_tri);
+  if (sc->node_format == kNodeFp32)  // refit (float32 nodes only) rebuilds split boxes from these
+    AGS_CHECK(cudaMalloc(&sc->d.leaf_bary, std::max<int64_t>(R, 1) * sizeof(uint2)));
+  k_gather_tris<<<blocks_for(R, 256), 256, 0, s>>>(d_packed, d_ref_tri, d_ref_bary, d_vals, d_perm, R, sc->d.tris,
+                                                   sc->d.leaf_tri, sc->d.leaf_bary);
   AGS_CHECK(cudaGetLastError());
   std::vector<unsigned long long> env_nodes(E);
   AGS_CHECK(cudaMemcpyAsync(env_nodes.data(), d_env_nodes, (size_t)E * sizeof(unsigned long long),
@@ -1093,11 +1149,37 @@ __global__ void k_repack_tris(const int32_t* __restrict__ leaf_tri, const int32_
   }
 }
 
+// Box of one leaf reference at the triangle's current position: the corners
+// of its barycentric range a + u e1 + v e2 (widened by the float32 rounding
+// of that sum), cut back to the triangle's own box. The range holds the
+// reference's piece of the triangle, and the pieces of a triangle's
+// references cover it, so culling stays conservative after any motion.
+__device__ Box ref_box_at(const float4* __restrict__ tris, int32_t k, uint2 q) {
+  const Box tb = tri_box(tris, k);
+  if (q.x == kBaryWholeLo && q.y == kBaryWholeHi) return tb;
+  const float4 a = tris[3 * (int64_t)k], b = tris[3 * (int64_t)k + 1], c = tris[3 * (int64_t)k + 2];
+  const float us[2] = {(float)(q.x & 0xFFFFu) / 65535.0f, (float)(q.y & 0xFFFFu) / 65535.0f};
+  const float vs[2] = {(float)(q.x >> 16) / 65535.0f, (float)(q.y >> 16) / 65535.0f};
+  Box r = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      const float x = a.x + us[i] * (b.x - a.x) + vs[j] * (c.x - a.x);
+      const float y = a.y + us[i] * (b.y - a.y) + vs[j] * (c.y - a.y);
+      const float z = a.z + us[i] * (b.z - a.z) + vs[j] * (c.z - a.z);
+      r.lox = fminf(r.lox, x); r.loy = fminf(r.loy, y); r.loz = fminf(r.loz, z);
+      r.hix = fmaxf(r.hix, x); r.hiy = fmaxf(r.hiy, y); r.hiz = fmaxf(r.hiz, z);
+    }
+  r.lox = fmaxf(widen_dn(r.lox), tb.lox); r.loy = fmaxf(widen_dn(r.loy), tb.loy); r.loz = fmaxf(widen_dn(r.loz), tb.loz);
+  r.hix = fminf(widen_up(r.hix), tb.hix); r.hiy = fminf(widen_up(r.hiy), tb.hiy); r.hiz = fminf(widen_up(r.hiz), tb.hiz);
+  return r;
+}
+
 // Refit one level of float32 wide nodes: each slot's box becomes the union of
-// its leaf triangles (whole-triangle boxes) or of its child node's slots
-// (already refitted: levels run from the deepest up).
+// its leaf references' boxes or of its child node's slots (already refitted:
+// levels run from the deepest up).
 __global__ void k_refit_level(WideNode* __restrict__ nodes, int32_t begin, int32_t end, const float4* __restrict__ tris,
-                              int32_t n_nodes, int32_t n_tris, int* __restrict__ err) {
+                              const uint2* __restrict__ leaf_bary, int32_t n_nodes, int32_t n_tris,
+                              int* __restrict__ err) {
   const int32_t i = begin + blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= end) return;
   WideNode& n = nodes[i];
@@ -1127,7 +1209,7 @@ __global__ void k_refit_level(WideNode* __restrict__ nodes, int32_t begin, int32
         continue;
       }
       for (int32_t x = 0; x < cnt; ++x) {
-        const Box tb = tri_box(tris, start + x);
+        const Box tb = ref_box_at(tris, start + x, leaf_bary[start + x]);
         b.lox = fminf(b.lox, tb.lox); b.loy = fminf(b.loy, tb.loy); b.loz = fminf(b.loz, tb.loz);
         b.hix = fmaxf(b.hix, tb.hix); b.hiy = fmaxf(b.hiy, tb.hiy); b.hiz = fmaxf(b.hiz, tb.hiz);
       }
@@ -1160,7 +1242,7 @@ ags_status refit_scene(ags_context* ctx, ags_scene* sc, const float* poses_h) {
     const int32_t b = (int32_t)sc->level_off[l - 1], e = (int32_t)sc->level_off[l];
     if (e > b)
       k_refit_level<<<blocks_for(e - b, 128), 128, 0, s>>>(static_cast<WideNode*>(sc->d.nodes), b, e, sc->d.tris,
-                                                           (int32_t)sc->n_nodes, R, d_err);
+                                                           sc->d.leaf_bary, (int32_t)sc->n_nodes, R, d_err);
   }
   AGS_CHECK(cudaGetLastError());
   int err = 0;

@@ -325,6 +325,7 @@ void ags_scene_destroy(ags_scene* sc) {
   cudaFree(sc->d.tris);
   cudaFree(sc->d.env_root);
   cudaFree(sc->d.leaf_tri);
+  cudaFree(sc->d.leaf_bary);
   cudaFree(sc->d.base_verts);
   cudaFree(sc->d.sub_vert_off);
   delete sc;

@@ -60,6 +60,7 @@ struct SceneDevice {
   float4* tris = nullptr;          // [3R] packed, one per BVH reference, leaf order
   int32_t* env_root = nullptr;     // [E] root node index, -1 if empty
   int32_t* leaf_tri = nullptr;     // [R] input triangle of each leaf-order copy
+  uint2* leaf_bary = nullptr;      // [R] barycentric range of each copy's piece (float32 nodes only)
   float* base_verts = nullptr;     // [3V] object-frame vertices (for pose updates)
   int32_t* sub_vert_off = nullptr; // [J+1]
 };
