@@ -170,6 +170,42 @@ ags_status ags_render(ags_context* ctx, const ags_scene* scene, const ags_sensor
                       void* cuda_stream);
 
 /*
+ * Extra hit channels (Sec. III-D.1: face indices with barycentric
+ * coordinates, surface normals, point clouds). Device buffers owned by the
+ * caller, one entry per ray in the layout of the depth output; each pointer
+ * may be NULL (that channel is not written); 4-byte aligned.
+ *   face    int32 [n_envs][H][W]: env-local index of the triangle hit
+ *           (sub-meshes concatenated in build order), -1 on a miss or on a
+ *           near hit reported as invalid;
+ *   bary    float [n_envs][H][W][2]: (u, v), the weights of that triangle's
+ *           second and third vertex at the hit (hit = (1-u-v) v0 + u v1 + v v2);
+ *           0 where face is -1;
+ *   normal  float [n_envs][H][W][3]: unit geometric normal (v1-v0) x (v2-v0)
+ *           in the world frame, turned to face the sensor; 0 where face is -1;
+ *   point   float [n_envs][H][W][3]: the hit in the sensor frame, the reported
+ *           value times the sensor-frame direction with unit reported
+ *           component (camera: depth * (1, a, b), so x = depth; LiDAR:
+ *           range * unit direction); misses sit at max_range along the ray.
+ * A ray that hits the traversal limits reports NaN weights, normal and point.
+ */
+typedef struct {
+  int32_t* face;
+  float* bary;
+  float* normal;
+  float* point;
+} ags_hit_channels;
+
+/*
+ * ags_render_channels -- ags_render (bit-identical depth/range and segment
+ * IDs) that also writes the extra hit channels listed in `channels` (NULL:
+ * none). Uses the 8x4 warp tile whatever launch shape is configured. Errors
+ * as ags_render; a misaligned channel pointer -> AGS_ERR_INVALID_ARG.
+ */
+ags_status ags_render_channels(ags_context* ctx, const ags_scene* scene, const ags_sensor_spec* spec,
+                               const float* sensor_poses_dev, float* out_depth_dev, int32_t* out_seg_dev,
+                               const ags_hit_channels* channels, void* cuda_stream);
+
+/*
  * ags_render_envs -- as ags_render for the n environments listed in
  * env_ids_dev (device int32 [n], each in [0, n_envs)); sensor_poses_dev is
  * [n][7] and the outputs are [n][height][width], in list order.

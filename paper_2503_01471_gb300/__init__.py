@@ -54,7 +54,7 @@ EXPORTS = [
     "ags_set_launch_config", "ags_get_launch_config", "ags_memcpy_d2h", "ags_server_create", "ags_server_destroy",
     "ags_server_submit", "ags_server_poll", "ags_server_release", "ags_server_stats", "ags_server_replay",
     "ags_replay_sequential", "ags_scene_update_poses", "ags_render_graph_create", "ags_render_graph_launch",
-    "ags_render_graph_destroy",
+    "ags_render_graph_destroy", "ags_render_channels",
 ]
 
 
@@ -71,6 +71,11 @@ class ags_submesh(ctypes.Structure):
 
 class ags_env_mesh(ctypes.Structure):
     _fields_ = [("submeshes", ctypes.c_void_p), ("n_submeshes", ctypes.c_int32)]
+
+
+class ags_hit_channels(ctypes.Structure):
+    _fields_ = [("face", ctypes.c_void_p), ("bary", ctypes.c_void_p), ("normal", ctypes.c_void_p),
+                ("point", ctypes.c_void_p)]
 
 
 class ags_launch_config(ctypes.Structure):
@@ -174,6 +179,8 @@ def lib() -> ctypes.CDLL:
         "ags_render_graph_create": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), vp, vp, vp, ctypes.POINTER(vp)]),
         "ags_render_graph_launch": (i32, [vp, vp]),
         "ags_render_graph_destroy": (None, [vp]),
+        "ags_render_channels": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), vp, vp, vp,
+                                      ctypes.POINTER(ags_hit_channels), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -485,3 +492,13 @@ def ags_render_graph_launch(graph: int, stream=None) -> None:
 
 def ags_render_graph_destroy(graph: int) -> None:
     lib().ags_render_graph_destroy(graph)
+
+
+# ---------------------------------------------------------------- extra hit channels
+def ags_render_channels(ctx: int, scene: int, spec, sensor_poses, out_depth, out_seg, face=None, bary=None,
+                        normal=None, point=None, stream=None) -> None:
+    """ags_render plus the extra hit channels given (device tensors; None = not written)."""
+    s = make_spec(spec)
+    ch = ags_hit_channels(_ptr(face) or None, _ptr(bary) or None, _ptr(normal) or None, _ptr(point) or None)
+    _check(lib().ags_render_channels(ctx, scene, ctypes.byref(s), _ptr(sensor_poses), _ptr(out_depth),
+                                     _ptr(out_seg), ctypes.byref(ch), _stream(stream)), "ags_render_channels")

@@ -889,6 +889,11 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
   AGS_CHECK(cudaMemcpyAsync(sc->d.base_verts, base_verts_h, 3 * (size_t)V * sizeof(float), cudaMemcpyHostToDevice, s));
   AGS_CHECK(cudaMemcpyAsync(sc->d.sub_vert_off, sub_vert_off_h, ((size_t)J + 1) * sizeof(int32_t),
                             cudaMemcpyHostToDevice, s));
+  AGS_CHECK(cudaMalloc(&sc->d.sub_tri_off, ((size_t)J + 1) * sizeof(int32_t)));
+  AGS_CHECK(cudaMalloc(&sc->d.sub_poses, std::max<int64_t>(7 * (int64_t)J, 1) * sizeof(float)));
+  AGS_CHECK(cudaMemcpyAsync(sc->d.sub_tri_off, sub_tri32.data(), ((size_t)J + 1) * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, s));
+  AGS_CHECK(cudaMemcpyAsync(sc->d.sub_poses, poses_h, 7 * (size_t)J * sizeof(float), cudaMemcpyHostToDevice, s));
   AGS_CHECK(cudaMemcpyAsync(d_poses, poses_h, 7 * (size_t)J * sizeof(float), cudaMemcpyHostToDevice, s));
   AGS_CHECK(cudaMemcpyAsync(d_sub_vert, sub_vert_off_h, ((size_t)J + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   AGS_CHECK(cudaMemcpyAsync(d_sub_tri, sub_tri32.data(), ((size_t)J + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s));
@@ -1174,12 +1179,74 @@ __device__ Box ref_box_at(const float4* __restrict__ tris, int32_t k, uint2 q) {
   return r;
 }
 
+// Rigid motion of each sub-mesh from its build pose to the new one: x -> R_rel (x - p_old) + p_new with R_rel =
+// R(q_new) R(q_old)^T, stored as 16 floats: R_rel row-major, p_old, p_new,
+// and 1 when the pose is bit-for-bit unchanged (the vertices do not move).
+__device__ __forceinline__ void quat_matrix(const float* q, float R[9]) {
+  const float x = q[0], y = q[1], z = q[2], w = q[3];
+  const float s = 2.0f / (x * x + y * y + z * z + w * w);
+  R[0] = 1.0f - s * (y * y + z * z); R[1] = s * (x * y - z * w);        R[2] = s * (x * z + y * w);
+  R[3] = s * (x * y + z * w);        R[4] = 1.0f - s * (x * x + z * z); R[5] = s * (y * z - x * w);
+  R[6] = s * (x * z - y * w);        R[7] = s * (y * z + x * w);        R[8] = 1.0f - s * (x * x + y * y);
+}
+
+__global__ void k_relative_motion(const float* __restrict__ old_poses, const float* __restrict__ new_poses, int32_t J,
+                                  float* __restrict__ motion) {
+  const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= J) return;
+  const float* po = old_poses + 7 * (int64_t)j;
+  const float* pn = new_poses + 7 * (int64_t)j;
+  float* m = motion + 16 * (int64_t)j;
+  bool same = true;
+  for (int k = 0; k < 7; ++k) same &= __float_as_uint(po[k]) == __float_as_uint(pn[k]);
+  float Ro[9], Rn[9];
+  quat_matrix(po + 3, Ro);
+  quat_matrix(pn + 3, Rn);
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) m[3 * r + c] = Rn[3 * r] * Ro[3 * c] + Rn[3 * r + 1] * Ro[3 * c + 1] + Rn[3 * r + 2] * Ro[3 * c + 2];
+  m[9] = po[0]; m[10] = po[1]; m[11] = po[2];
+  m[12] = pn[0]; m[13] = pn[1]; m[14] = pn[2];
+  m[15] = same ? 1.0f : 0.0f;
+}
+
+// The box b moved by a sub-mesh's motion: the box around its eight moved
+// corners, widened by 256 u (|corner| + |p_old| + |p_new|) per axis, which
+// bounds the float32 rounding of R_rel against the exact relative rotation
+// and of the world vertices at both poses.
+__device__ Box moved_box(const Box& b, const float* __restrict__ m) {
+  Box r = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+  const float pm = fmaxf(fmaxf(fabsf(m[9]), fabsf(m[10])), fabsf(m[11])) +
+                   fmaxf(fmaxf(fabsf(m[12]), fabsf(m[13])), fabsf(m[14]));
+  float cm = 0.0f;
+  for (int i = 0; i < 8; ++i) {
+    const float cx = (i & 1) ? b.hix : b.lox, cy = (i & 2) ? b.hiy : b.loy, cz = (i & 4) ? b.hiz : b.loz;
+    cm = fmaxf(cm, fmaxf(fmaxf(fabsf(cx), fabsf(cy)), fabsf(cz)));
+    const float dx = cx - m[9], dy = cy - m[10], dz = cz - m[11];
+    const float x = m[0] * dx + m[1] * dy + m[2] * dz + m[12];
+    const float y = m[3] * dx + m[4] * dy + m[5] * dz + m[13];
+    const float z = m[6] * dx + m[7] * dy + m[8] * dz + m[14];
+    r.lox = fminf(r.lox, x); r.loy = fminf(r.loy, y); r.loz = fminf(r.loz, z);
+    r.hix = fmaxf(r.hix, x); r.hiy = fmaxf(r.hiy, y); r.hiz = fmaxf(r.hiz, z);
+  }
+  const float w = 256.0f * 5.96046448e-8f * (cm + pm);
+  r.lox -= w; r.loy -= w; r.loz -= w;
+  r.hix += w; r.hiy += w; r.hiz += w;
+  return r;
+}
+
 // Refit one level of float32 wide nodes: each slot's box becomes the union of
-// its leaf references' boxes or of its child node's slots (already refitted:
-// levels run from the deepest up).
-__global__ void k_refit_level(WideNode* __restrict__ nodes, int32_t begin, int32_t end, const float4* __restrict__ tris,
-                              const uint2* __restrict__ leaf_bary, int32_t n_nodes, int32_t n_tris,
-                              int* __restrict__ err) {
+// its child node's slots (already refitted: levels run from the deepest up)
+// or, for a leaf slot, of its references' boxes. A reference's piece of its
+// triangle lies in its barycentric-range box and in the slot's box as built,
+// moved with the reference's sub-mesh from its build pose, so it lies in
+// their intersection; a sub-mesh back at its build pose keeps the built box.
+// Moving from the build pose (not from the last refit) keeps the rotation's
+// widening of the boxes from adding up over many updates.
+__global__ void k_refit_level(WideNode* __restrict__ nodes, const WideNode* __restrict__ built, int32_t begin,
+                              int32_t end, const float4* __restrict__ tris,
+                              const uint2* __restrict__ leaf_bary, const int32_t* __restrict__ leaf_tri,
+                              const int32_t* __restrict__ sub_tri_off, int32_t J, const float* __restrict__ motion,
+                              int32_t n_nodes, int32_t n_tris, int* __restrict__ err) {
   const int32_t i = begin + blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= end) return;
   WideNode& n = nodes[i];
@@ -1208,8 +1275,18 @@ __global__ void k_refit_level(WideNode* __restrict__ nodes, int32_t begin, int32
         atomicOr(err, 1);
         continue;
       }
+      const WideNode& nb = built[i];
+      const Box prev = {nb.lox[k], nb.loy[k], nb.loz[k], nb.hix[k], nb.hiy[k], nb.hiz[k]};
       for (int32_t x = 0; x < cnt; ++x) {
-        const Box tb = ref_box_at(tris, start + x, leaf_bary[start + x]);
+        Box tb = ref_box_at(tris, start + x, leaf_bary[start + x]);
+        const int32_t j = upper_bound_i32(sub_tri_off + 1, J, leaf_tri[start + x]);
+        if (j < J) {
+          const float* m = motion + 16 * (int64_t)j;
+          const Box mb = m[15] != 0.0f ? prev : moved_box(prev, m);
+          const Box ib = {fmaxf(tb.lox, mb.lox), fmaxf(tb.loy, mb.loy), fmaxf(tb.loz, mb.loz),
+                          fminf(tb.hix, mb.hix), fminf(tb.hiy, mb.hiy), fminf(tb.hiz, mb.hiz)};
+          if (ib.lox <= ib.hix && ib.loy <= ib.hiy && ib.loz <= ib.hiz) tb = ib;
+        }
         b.lox = fminf(b.lox, tb.lox); b.loy = fminf(b.loy, tb.loy); b.loz = fminf(b.loz, tb.loz);
         b.hix = fmaxf(b.hix, tb.hix); b.hiy = fmaxf(b.hiy, tb.hiy); b.hiz = fmaxf(b.hiz, tb.hiz);
       }
@@ -1223,16 +1300,23 @@ __global__ void k_refit_level(WideNode* __restrict__ nodes, int32_t begin, int32
 
 ags_status refit_scene(ags_context* ctx, ags_scene* sc, const float* poses_h) {
   cudaStream_t s = ctx->stream;
+  if (!sc->d.nodes_build && sc->n_nodes > 0) {
+    AGS_CHECK(cudaMalloc(&sc->d.nodes_build, (size_t)sc->n_nodes * sizeof(WideNode)));
+    AGS_CHECK(cudaMemcpyAsync(sc->d.nodes_build, sc->d.nodes, (size_t)sc->n_nodes * sizeof(WideNode),
+                              cudaMemcpyDeviceToDevice, s));
+  }
   const int32_t V = (int32_t)sc->n_verts, J = (int32_t)sc->n_subs, R = (int32_t)sc->n_refs;
   DevBufs tmp;
-  float *d_poses = nullptr, *d_rot = nullptr;
+  float *d_poses = nullptr, *d_rot = nullptr, *d_motion = nullptr;
   int* d_err = nullptr;
   AGS_CHECK(tmp.alloc(&d_poses, 7 * (size_t)std::max(J, 1)));
   AGS_CHECK(tmp.alloc(&d_rot, 18 * (size_t)std::max(J, 1)));
+  AGS_CHECK(tmp.alloc(&d_motion, 16 * (size_t)std::max(J, 1)));
   AGS_CHECK(tmp.alloc(&d_err, 1));
   AGS_CHECK(cudaMemsetAsync(d_err, 0, sizeof(int), s));
   if (J > 0) AGS_CHECK(cudaMemcpyAsync(d_poses, poses_h, 7 * (size_t)J * sizeof(float), cudaMemcpyHostToDevice, s));
   if (J > 0) k_submesh_rotations<<<blocks_for(J, 128), 128, 0, s>>>(d_poses, J, d_rot);
+  if (J > 0) k_relative_motion<<<blocks_for(J, 128), 128, 0, s>>>(sc->d.sub_poses, d_poses, J, d_motion);
   if (V > 0)
     k_transform_vertices<<<blocks_for(V, 256), 256, 0, s>>>(sc->d.base_verts, V, sc->d.sub_vert_off, J, d_rot, d_poses,
                                                             sc->d.world_verts);
@@ -1241,9 +1325,12 @@ ags_status refit_scene(ags_context* ctx, ags_scene* sc, const float* poses_h) {
   for (size_t l = sc->level_off.size(); l-- > 1;) {
     const int32_t b = (int32_t)sc->level_off[l - 1], e = (int32_t)sc->level_off[l];
     if (e > b)
-      k_refit_level<<<blocks_for(e - b, 128), 128, 0, s>>>(static_cast<WideNode*>(sc->d.nodes), b, e, sc->d.tris,
-                                                           sc->d.leaf_bary, (int32_t)sc->n_nodes, R, d_err);
+      k_refit_level<<<blocks_for(e - b, 128), 128, 0, s>>>(static_cast<WideNode*>(sc->d.nodes), sc->d.nodes_build, b,
+                                                           e, sc->d.tris,
+                                                           sc->d.leaf_bary, sc->d.leaf_tri, sc->d.sub_tri_off, J,
+                                                           d_motion, (int32_t)sc->n_nodes, R, d_err);
   }
+
   AGS_CHECK(cudaGetLastError());
   int err = 0;
   AGS_CHECK(cudaMemcpyAsync(&err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s));

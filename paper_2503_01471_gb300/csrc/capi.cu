@@ -326,6 +326,9 @@ void ags_scene_destroy(ags_scene* sc) {
   cudaFree(sc->d.env_root);
   cudaFree(sc->d.leaf_tri);
   cudaFree(sc->d.leaf_bary);
+  cudaFree(sc->d.sub_tri_off);
+  cudaFree(sc->d.sub_poses);
+  cudaFree(sc->d.nodes_build);
   cudaFree(sc->d.base_verts);
   cudaFree(sc->d.sub_vert_off);
   delete sc;
@@ -396,6 +399,36 @@ ags_status ags_render(ags_context* ctx, const ags_scene* sc, const ags_sensor_sp
   TraceArgs a{};
   const ags_launch_config cfg = lookup_config(sc, spec);
   if ((st = fill_trace_args(ctx, sc, spec, sc->n_envs, nullptr, poses, depth, seg, a, cfg)) != AGS_OK) return st;
+  return launch(ctx, a, static_cast<cudaStream_t>(stream), false, cfg.blocks_per_sm);
+  AGS_API_END
+}
+
+ags_status ags_render_channels(ags_context* ctx, const ags_scene* sc, const ags_sensor_spec* spec, const float* poses,
+                               float* depth, int32_t* seg, const ags_hit_channels* ch, void* stream) {
+  AGS_API_BEGIN
+  if (!ctx || !sc) return invalid("ctx or scene is NULL");
+  if (sc->ctx != ctx) return invalid("scene belongs to another context");
+  ags_status st = check_spec(spec);
+  if (st != AGS_OK) return st;
+  if (!poses || !depth || !seg) return invalid("poses/depth/seg pointer is NULL");
+  if (ch) {
+    const void* ps[4] = {ch->face, ch->bary, ch->normal, ch->point};
+    for (const void* p : ps)
+      if (reinterpret_cast<uintptr_t>(p) % 4 != 0) return invalid("channel pointer not 4-byte aligned");
+  }
+  DeviceGuard g(ctx->device);
+  TraceArgs a{};
+  ags_launch_config cfg = lookup_config(sc, spec);
+  cfg.tile_w = 8;
+  cfg.rays_per_lane = 1;
+  if ((st = fill_trace_args(ctx, sc, spec, sc->n_envs, nullptr, poses, depth, seg, a, cfg)) != AGS_OK) return st;
+  if (ch) {
+    a.out_face = ch->face;
+    a.out_bary = ch->bary;
+    a.out_normal = ch->normal;
+    a.out_point = ch->point;
+    a.channels = 1;
+  }
   return launch(ctx, a, static_cast<cudaStream_t>(stream), false, cfg.blocks_per_sm);
   AGS_API_END
 }

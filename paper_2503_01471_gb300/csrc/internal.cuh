@@ -63,6 +63,9 @@ struct SceneDevice {
   uint2* leaf_bary = nullptr;      // [R] barycentric range of each copy's piece (float32 nodes only)
   float* base_verts = nullptr;     // [3V] object-frame vertices (for pose updates)
   int32_t* sub_vert_off = nullptr; // [J+1]
+  int32_t* sub_tri_off = nullptr;  // [J+1] (refit: sub-mesh of a triangle)
+  float* sub_poses = nullptr;      // [J][7] poses the BVH was built with
+  WideNode* nodes_build = nullptr; // refit: copy of the nodes as built, taken at the first refit
 };
 
 struct Box {
@@ -174,6 +177,14 @@ struct TraceArgs {
   const float* poses;        // [n][7]
   float* out_depth;          // [n][H][W] (slot mode: output arena)
   int32_t* out_seg;
+  // extra hit channels (channel kernel only; each nullable): face index
+  // [n][H][W], barycentrics [n][H][W][2], world normal and sensor-frame
+  // point [n][H][W][3]
+  int32_t* out_face;
+  float* out_bary;
+  float* out_normal;
+  float* out_point;
+  int32_t channels;          // nonzero: launch the channel kernel
   int32_t n;                 // environments rendered
   SensorParams sensor;       // uniform mode
   const SensorParams* specs; // slot mode: table of sensor shapes

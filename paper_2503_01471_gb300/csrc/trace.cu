@@ -113,8 +113,9 @@ __device__ __forceinline__ void shear(const Ray& r, const float4 v, float& X, fl
   Z = __fmaf_rn(r.m2x, ax, __fmaf_rn(r.m2y, ay, __fmul_rn(r.m2z, az)));
 }
 
+template <bool kChannels>
 __device__ __forceinline__ void test_triangle(const Ray& r, const float4* __restrict__ tris, int32_t k,
-                                              float& t_best, int32_t& best_id, int32_t& best_seg) {
+                                              float& t_best, int32_t& best_id, int32_t& best_seg, int32_t& best_k) {
   const float4 a = __ldg(tris + 3 * (int64_t)k);
   const float4 b = __ldg(tris + 3 * (int64_t)k + 1);
   const float4 c = __ldg(tris + 3 * (int64_t)k + 2);
@@ -141,7 +142,47 @@ __device__ __forceinline__ void test_triangle(const Ray& r, const float4* __rest
     t_best = t;
     best_id = id;
     best_seg = __float_as_int(a.w);
+    if constexpr (kChannels) best_k = k;
   }
+}
+
+// Barycentric weights (of the second and third vertex) of the ray's hit on
+// packed triangle k: the edge functions of the watertight test, recomputed
+// with the same operations, over their sum.
+__device__ __forceinline__ void hit_barycentrics(const Ray& r, const float4* __restrict__ tris, int32_t k, float& u,
+                                                 float& v) {
+  const float4 a = __ldg(tris + 3 * (int64_t)k);
+  const float4 b = __ldg(tris + 3 * (int64_t)k + 1);
+  const float4 c = __ldg(tris + 3 * (int64_t)k + 2);
+  float Ax, Ay, Az, Bx, By, Bz, Cx, Cy, Cz;
+  shear(r, a, Ax, Ay, Az);
+  shear(r, b, Bx, By, Bz);
+  shear(r, c, Cx, Cy, Cz);
+  const float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+  const float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+  const float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+  const float det = U + V + W;
+  u = __fdiv_rn(V, det);
+  v = __fdiv_rn(W, det);
+}
+
+// Unit geometric normal (b - a) x (c - a) of packed triangle k, turned to
+// face the ray (direction d).
+__device__ __forceinline__ void hit_normal(const float4* __restrict__ tris, int32_t k, float dx, float dy, float dz,
+                                           float& nx, float& ny, float& nz) {
+  const float4 a = __ldg(tris + 3 * (int64_t)k);
+  const float4 b = __ldg(tris + 3 * (int64_t)k + 1);
+  const float4 c = __ldg(tris + 3 * (int64_t)k + 2);
+  const float e1x = b.x - a.x, e1y = b.y - a.y, e1z = b.z - a.z;
+  const float e2x = c.x - a.x, e2y = c.y - a.y, e2z = c.z - a.z;
+  nx = e1y * e2z - e1z * e2y;
+  ny = e1z * e2x - e1x * e2z;
+  nz = e1x * e2y - e1y * e2x;
+  float s = rsqrtf(nx * nx + ny * ny + nz * nz);
+  if (nx * dx + ny * dy + nz * dz > 0.0f) s = -s;
+  nx *= s;
+  ny *= s;
+  nz *= s;
 }
 
 // The rays of one warp tile: sensor shape `sen`, environment `env`, tile
@@ -267,6 +308,25 @@ __device__ __forceinline__ void test_node(const void* __restrict__ nodes, int32_
   }
 }
 
+// a3: the sensor-frame direction of pixel / beam (row, col). Camera: the
+// unnormalised (1, a, b) through the pixel centre, so the distance along it
+// is the depth itself; LiDAR: the unit beam direction (distance = range).
+__device__ __forceinline__ void sensor_dir(const SensorParams& sen, int32_t row, int32_t col, float& lx, float& ly,
+                                           float& lz) {
+  if (sen.type == AGS_PINHOLE) {
+    lx = 1.0f;
+    ly = (0.5f * (float)sen.W - ((float)col + 0.5f)) * sen.inv_f;
+    lz = (0.5f * (float)sen.H - ((float)row + 0.5f)) * sen.inv_f;
+  } else {
+    float sin_el, cos_el, sin_az, cos_az;
+    sincosf(sen.vmax - (float)row * sen.dv, &sin_el, &cos_el);
+    sincosf(sen.hfov * ((float)col / (float)sen.W), &sin_az, &cos_az);
+    lx = cos_el * cos_az;
+    ly = cos_el * sin_az;
+    lz = sin_el;
+  }
+}
+
 template <bool kSlots>
 __device__ __forceinline__ const float* slot_pose(const TraceArgs& a, int32_t slot) {
   if constexpr (kSlots) return a.slots[slot].pose;
@@ -278,7 +338,7 @@ __device__ __forceinline__ int64_t slot_out(const TraceArgs& a, const SensorPara
   else return (int64_t)slot * sen.H * sen.W;
 }
 
-template <bool kCount, int kTileW, int kRaysPerLane, bool kSlots, int kFmt>
+template <bool kCount, int kTileW, int kRaysPerLane, bool kSlots, int kFmt, bool kChannels>
 __device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParams& sen, int32_t env, int32_t t_in,
                                            int32_t slot, int lane, int2* stack, unsigned long long& n_nodes,
                                            unsigned long long& n_tris, unsigned long long& n_rays) {
@@ -315,19 +375,7 @@ __device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParam
   const float R10 = s * (qx * qy + qz * qw), R11 = 1.0f - s * (qx * qx + qz * qz), R12 = s * (qy * qz - qx * qw);
   const float R20 = s * (qx * qz - qy * qw), R21 = s * (qy * qz + qx * qw), R22 = 1.0f - s * (qx * qx + qy * qy);
   float lx, ly, lz;
-  if (sen.type == AGS_PINHOLE) {
-    // unnormalised (1, a, b): the distance along it is the depth itself
-    lx = 1.0f;
-    ly = (0.5f * (float)W - ((float)col + 0.5f)) * sen.inv_f;
-    lz = (0.5f * (float)H - ((float)row + 0.5f)) * sen.inv_f;
-  } else {
-    float sin_el, cos_el, sin_az, cos_az;
-    sincosf(sen.vmax - (float)row * sen.dv, &sin_el, &cos_el);
-    sincosf(sen.hfov * ((float)col / (float)W), &sin_az, &cos_az);
-    lx = cos_el * cos_az;
-    ly = cos_el * sin_az;
-    lz = sin_el;
-  }
+  sensor_dir(sen, row, col, lx, ly, lz);
   Ray r;
   r.ox = px;
   r.oy = py;
@@ -336,7 +384,7 @@ __device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParam
 
   // ---- a4-a6: traversal, triangle tests, nearest hit
   float t_best = sen.max_range;  // camera: depth limit; LiDAR: range limit (unit direction)
-  int32_t best_id = 0x7fffffff, best_seg = -1;
+  int32_t best_id = 0x7fffffff, best_seg = -1, best_k = -1;
   int32_t node = __ldg(a.env_root + env);
   int sp = 0, visits = 0;
   bool failed = false;
@@ -376,7 +424,8 @@ __device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParam
         failed = true;
         break;
       }
-      for (int32_t x = 0; x < cnt; ++x) test_triangle(r, a.tris, start + x, t_best, best_id, best_seg);
+      for (int32_t x = 0; x < cnt; ++x)
+        test_triangle<kChannels>(r, a.tris, start + x, t_best, best_id, best_seg, best_k);
       if (kCount) n_tris += cnt;
     }
     if (failed) break;
@@ -462,13 +511,41 @@ __device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParam
   const int64_t o = slot_out<kSlots>(a, sen, slot) + (int64_t)row * W + col;
   a.out_depth[o] = v;
   a.out_seg[o] = seg;
+  if constexpr (kChannels) {
+    // extra hit channels of the reported hit (a miss or a near hit reported
+    // as invalid: face -1, zero weights and normal)
+    const float nan = __int_as_float(0x7fc00000);
+    int32_t face = failed ? -1 : (seg >= 0 ? best_id : -1);
+    float bu = failed ? nan : 0.0f, bv = bu, nx = bu, ny = bu, nz = bu;
+    if (face >= 0 && best_k >= 0) {
+      hit_barycentrics(r, a.tris, best_k, bu, bv);
+      hit_normal(a.tris, best_k, __frcp_rn(r.ix), __frcp_rn(r.iy), __frcp_rn(r.iz), nx, ny, nz);
+    }
+    if (a.out_face) a.out_face[o] = face;
+    if (a.out_bary) {
+      a.out_bary[2 * o] = bu;
+      a.out_bary[2 * o + 1] = bv;
+    }
+    if (a.out_normal) {
+      a.out_normal[3 * o] = nx;
+      a.out_normal[3 * o + 1] = ny;
+      a.out_normal[3 * o + 2] = nz;
+    }
+    if (a.out_point) {
+      // the hit in the sensor frame: reported value along the sensor-frame direction
+      sensor_dir(sen, row, col, lx, ly, lz);
+      a.out_point[3 * o] = v * lx;
+      a.out_point[3 * o + 1] = v * ly;
+      a.out_point[3 * o + 2] = v * lz;
+    }
+  }
   }  // rays of this lane in the tile
 }
 
 // kSlots: each tile belongs to one slot of a table (serving: every request has
 // its own environment, sensor shape, pose and output offset); otherwise all
 // environments of the launch share one sensor shape.
-template <bool kCount, int kTileW, int kRaysPerLane, bool kSlots, int kFmt>
+template <bool kCount, int kTileW, int kRaysPerLane, bool kSlots, int kFmt, bool kChannels = false>
 __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) k_trace(const TraceArgs a) {
   const int lane = threadIdx.x & 31;
   int2 stack[kStackSize];
@@ -505,11 +582,11 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) k_trace(const 
       continue;
     }
     if constexpr (kSlots) {
-      trace_tile<kCount, kTileW, kRaysPerLane, true, kFmt>(a, a.specs[slot_spec], env, t_in, slot, lane, stack, n_nodes,
-                                                     n_tris, n_rays);
+      trace_tile<kCount, kTileW, kRaysPerLane, true, kFmt, kChannels>(a, a.specs[slot_spec], env, t_in, slot, lane,
+                                                                   stack, n_nodes, n_tris, n_rays);
     } else {
-      trace_tile<kCount, kTileW, kRaysPerLane, false, kFmt>(a, a.sensor, env, t_in, slot, lane, stack, n_nodes, n_tris,
-                                                      n_rays);
+      trace_tile<kCount, kTileW, kRaysPerLane, false, kFmt, kChannels>(a, a.sensor, env, t_in, slot, lane, stack,
+                                                                    n_nodes, n_tris, n_rays);
     }
   }
   if (kCount) {
@@ -549,6 +626,9 @@ cudaError_t launch_fmt(const TraceArgs& a, int blocks, bool count, cudaStream_t 
   const int w = 1 << a.log2_tile_w, r = a.rays_per_lane;
   if (a.slots) {
     if (w == 8 && r == 1) k_trace<false, 8, 1, true, kFmt><<<blocks, kTraceThreads, 0, s>>>(a);
+    else return cudaErrorInvalidValue;
+  } else if (a.channels) {
+    if (w == 8 && r == 1 && !count) k_trace<false, 8, 1, false, kFmt, true><<<blocks, kTraceThreads, 0, s>>>(a);
     else return cudaErrorInvalidValue;
   } else if (count) {
     k_trace<true, 8, 1, false, kFmt><<<blocks, kTraceThreads, 0, s>>>(a);

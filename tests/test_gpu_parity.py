@@ -15,7 +15,7 @@ import paper_2503_01471_gb300 as ags
 from paper_2503_01471_gb300 import build as B
 from paper_2503_01471_gb300 import scenes as S
 
-from helpers import compare_env, describe_failures, oracle_env
+from helpers import check_channels, compare_env, describe_channel_failures, describe_failures, oracle_env, oracle_sensor
 
 pytestmark = pytest.mark.gpu
 
@@ -431,6 +431,33 @@ def test_update_poses_refit_and_rebuild_match_a_fresh_build(ctx):
             ags.ags_scene_destroy(sc)
 
 
+def test_refit_after_moving_every_object_including_split_walls(ctx):
+    """The rooms themselves (large split wall triangles) turn and move too: refit boxes built from each
+    reference's barycentric range still cover every triangle, so the images equal a fresh build's."""
+    batch, spec, poses = S.obstacle_rooms(3, steps=1, width=48, height=36)
+    rng = np.random.default_rng(22)
+    refit = ags.ags_scene_build(ctx, batch)
+    try:
+        cur = batch.poses.copy()
+        for step in range(3):
+            cur[:, :3] += rng.normal(0, 0.3, (cur.shape[0], 3)).astype(np.float32)
+            q = cur[:, 3:] + rng.normal(0, 0.2, (cur.shape[0], 4)).astype(np.float32)
+            cur[:, 3:] = q / np.linalg.norm(q, axis=1, keepdims=True)
+            ags.ags_scene_update_poses(ctx, refit, cur, ags.AGS_UPDATE_REFIT)
+            moved = S.SceneBatch(batch.vertices, batch.indices, batch.sub_vert, batch.sub_tri, batch.sub_seg,
+                                 batch.env_sub, cur.copy())
+            fresh = ags.ags_scene_build(ctx, moved)
+            try:
+                a = render(ctx, refit, spec, poses[0])
+                b = render(ctx, fresh, spec, poses[0])
+                assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), step
+            finally:
+                ags.ags_scene_destroy(fresh)
+        check_all(moved, spec, poses[0], a[0], a[1], tag="refit, every object moved 48x36")
+    finally:
+        ags.ags_scene_destroy(refit)
+
+
 def test_step_graph_replays_the_render(ctx):
     batch, spec, poses = S.obstacle_rooms(3, steps=3, width=48, height=36)
     scene = ags.ags_scene_build(ctx, batch)
@@ -448,3 +475,75 @@ def test_step_graph_replays_the_render(ctx):
     finally:
         ags.ags_render_graph_destroy(g)
         ags.ags_scene_destroy(scene)
+
+
+# ---------------------------------------------------------------- extra hit channels
+def render_channels(ctx, scene, spec, poses, which=("face", "bary", "normal", "point")):
+    E = poses.shape[0]
+    H, W = spec.height, spec.width
+    p = torch.as_tensor(np.ascontiguousarray(poses, np.float32)).cuda()
+    depth = torch.empty((E, H, W), device="cuda")
+    seg = torch.empty((E, H, W), dtype=torch.int32, device="cuda")
+    shapes = {"face": ((E, H, W), torch.int32), "bary": ((E, H, W, 2), torch.float32),
+              "normal": ((E, H, W, 3), torch.float32), "point": ((E, H, W, 3), torch.float32)}
+    ch = {k: torch.full(shapes[k][0], 7, dtype=shapes[k][1], device="cuda") for k in which}
+    ags.ags_render_channels(ctx, scene, spec, p, depth, seg, **ch)
+    ags.ags_stream_status(ctx)
+    return depth.cpu().numpy(), seg.cpu().numpy(), {k: v.cpu().numpy() for k, v in ch.items()}
+
+
+@pytest.mark.parametrize("sensor", ["camera", "lidar", "camera_near_invalid"])
+def test_hit_channels_match_oracle(ctx, sensor):
+    """Face index, barycentrics, normal and sensor-frame point against the FP64 oracle on every ray;
+    depth and segment IDs bit-identical to the plain render."""
+    batch, spec, poses = S.obstacle_rooms(3, steps=1, width=40, height=30)
+    if sensor == "lidar":
+        spec = S.lidar(128, 24, (-30.0, 30.0), 0.2, 12.0)
+    elif sensor == "camera_near_invalid":
+        spec.near_mode, spec.min_range = ags.AGS_NEAR_INVALID, 1.2
+    scene = ags.ags_scene_build(ctx, batch)
+    try:
+        d0, s0 = render(ctx, scene, spec, poses[0])
+        d, s, ch = render_channels(ctx, scene, spec, poses[0])
+        assert np.array_equal(d, d0) and np.array_equal(s, s0)
+        n = spec.width * spec.height
+        rays = np.arange(n, dtype=np.int64)
+        total = 0
+        for e in range(3):
+            ok, counted, res = compare_env(batch, e, spec, poses[0][e], d[e], s[e])
+            assert ok.all(), describe_failures(ok, res, d[e].reshape(-1), s[e].reshape(-1), rays)
+            det = {}
+            okc = check_channels(batch, e, spec, poses[0][e], res, s[e], d[e], ch["face"][e], ch["bary"][e],
+                                 ch["normal"][e], ch["point"][e], rays, det)
+            assert okc.all(), f"env {e}: {int((~okc).sum())} rays\n" + describe_channel_failures(
+                okc, det, res, ch["face"][e].reshape(-1), ch["bary"][e].reshape(-1, 2), ch["normal"][e].reshape(-1, 3))
+            total += int((s[e] >= 0).sum())
+        print(f"[parity] hit channels {sensor} {spec.height}x{spec.width}: {3 * n} rays, {total} hits, all within "
+              f"the channel tolerances")
+    finally:
+        ags.ags_scene_destroy(scene)
+
+
+def test_hit_channels_subsets_and_formats_are_bit_identical(ctx):
+    """Any subset of channels gives the same bits, and so do compressed nodes and another leaf size."""
+    batch, spec, poses = S.obstacle_rooms(2, steps=1, width=33, height=17)
+    scenes = [ags.ags_scene_build(ctx, batch, f) for f in (ags.AGS_BVH_FP32, ags.AGS_BVH_FP16, ags.AGS_BVH_Q8)]
+    try:
+        _, _, ref = render_channels(ctx, scenes[0], spec, poses[0])
+        for sc in scenes[1:]:
+            _, _, got = render_channels(ctx, sc, spec, poses[0])
+            for k in ref:
+                assert np.array_equal(ref[k], got[k]), k
+        for which in (("point",), ("face", "normal"), ("bary",)):
+            _, _, got = render_channels(ctx, scenes[0], spec, poses[0], which)
+            for k in which:
+                assert np.array_equal(ref[k], got[k]), k
+        p = torch.as_tensor(poses[0]).cuda()
+        d = torch.empty((2, 17, 33), device="cuda")
+        sg = torch.empty((2, 17, 33), dtype=torch.int32, device="cuda")
+        buf = torch.empty(2 * 17 * 33 * 3 + 1, device="cuda")
+        with pytest.raises(ags.AgsError):  # misaligned channel pointer
+            ags.ags_render_channels(ctx, scenes[0], spec, p, d, sg, point=buf.data_ptr() + 2)
+    finally:
+        for sc in scenes:
+            ags.ags_scene_destroy(sc)
