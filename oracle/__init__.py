@@ -86,17 +86,18 @@ class _Result(ctypes.Structure):
         ("flags", ctypes.c_int32), ("n_cand", ctypes.c_int32),
         ("cand_seg", ctypes.c_int32 * MAX_CAND), ("cand_lo", ctypes.c_double * MAX_CAND),
         ("cand_hi", ctypes.c_double * MAX_CAND), ("n_tri", ctypes.c_int32),
-        ("cand_tri", ctypes.c_int32 * MAX_TRI),
+        ("cand_tri", ctypes.c_int32 * MAX_TRI), ("t_hit", ctypes.c_double),
     ]
 
 
 RESULT_DTYPE = np.dtype({
-    "names": ["v", "seg", "tri", "flags", "n_cand", "cand_seg", "cand_lo", "cand_hi", "n_tri", "cand_tri"],
+    "names": ["v", "seg", "tri", "flags", "n_cand", "cand_seg", "cand_lo", "cand_hi", "n_tri", "cand_tri",
+              "t_hit"],
     "formats": ["<f8", "<i4", "<i4", "<i4", "<i4", ("<i4", MAX_CAND), ("<f8", MAX_CAND),
-                ("<f8", MAX_CAND), "<i4", ("<i4", MAX_TRI)],
+                ("<f8", MAX_CAND), "<i4", ("<i4", MAX_TRI), "<f8"],
     "offsets": [_Result.v.offset, _Result.seg.offset, _Result.tri.offset, _Result.flags.offset,
                 _Result.n_cand.offset, _Result.cand_seg.offset, _Result.cand_lo.offset,
-                _Result.cand_hi.offset, _Result.n_tri.offset, _Result.cand_tri.offset],
+                _Result.cand_hi.offset, _Result.n_tri.offset, _Result.cand_tri.offset, _Result.t_hit.offset],
     "itemsize": ctypes.sizeof(_Result),
 })
 
@@ -128,6 +129,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32), dp,
                                          ctypes.c_int64, dp, dp, dp]
         lib.orc_hit_channels.restype = ctypes.c_int
+        lib.orc_shadow.argtypes = [dp, ctypes.c_int64, ctypes.POINTER(_Sensor), dp, dp, ctypes.c_double,
+                                   ctypes.POINTER(ctypes.c_int64), ctypes.c_void_p, ctypes.c_int64,
+                                   ctypes.POINTER(ctypes.c_int32)]
+        lib.orc_shadow.restype = ctypes.c_int
         lib.orc_num_threads.argtypes = []
         lib.orc_num_threads.restype = ctypes.c_int
         _libs[key] = lib
@@ -253,6 +258,26 @@ def hit_channels(tris, sensor: Sensor, pose, rays, face, v, lib=None):
     if rc != 0:
         raise ValueError("orc_hit_channels: bad input or degenerate face")
     return bary, normal, point
+
+
+def shadow(tris, sensor: Sensor, pose, baseline, eps, rays, res, lib=None) -> np.ndarray:
+    """Stereo shadow verdicts (0 free, 1 shadowed, 2 either) of rays whose oracle results are ``res``."""
+    lib = lib or load()
+    tris = np.ascontiguousarray(tris, dtype=np.float64).reshape(-1, 9)
+    pose = np.ascontiguousarray(pose, dtype=np.float64).reshape(7)
+    baseline = np.ascontiguousarray(baseline, dtype=np.float64).reshape(3)
+    rays = np.ascontiguousarray(rays, dtype=np.int64).reshape(-1)
+    res = np.ascontiguousarray(res)
+    if res.dtype != RESULT_DTYPE or res.shape[0] != rays.shape[0]:
+        raise ValueError("res must be the oracle results of the listed rays")
+    out = np.zeros(rays.shape[0], np.int32)
+    s = sensor._c()
+    rc = lib.orc_shadow(_dp(tris), tris.shape[0], ctypes.byref(s), _dp(pose), _dp(baseline), float(eps),
+                        rays.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), res.ctypes.data, rays.shape[0],
+                        out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    if rc != 0:
+        raise ValueError("orc_shadow: bad input")
+    return out
 
 
 def num_threads(lib=None) -> int:

@@ -132,7 +132,7 @@ typedef struct {
 
 static void eval_triangle(const double* tri, const double o[3], const double d[3],
                           const double u[3], const double w[3], double t_far, double et0,
-                          double et_far, const orc_sensor* bands, orc_tri_eval* r) {
+                          double et_far, const orc_sensor* bands, double vert_extra, orc_tri_eval* r) {
   memset(r, 0, sizeof(*r));
   double a[3], b[3], c[3];
   for (int k = 0; k < 3; ++k) {
@@ -181,7 +181,7 @@ static void eval_triangle(const double* tri, const double o[3], const double d[3
     if (fabs(tri[6 + k]) > cmax) cmax = fabs(tri[6 + k]);
   }
   rmax = fmax(sqrt(dot3(a, a)), fmax(sqrt(dot3(b, b)), sqrt(dot3(c, c))));
-  double vert = sqrt(3.0) * bands->vert_rel * cmax;
+  double vert = sqrt(3.0) * bands->vert_rel * cmax + vert_extra;
   double eps = vert + (bands->dir_rel + bands->arith_rel) * rmax;
   double len0 = hypot(pc[0] - pb[0], pc[1] - pb[1]);
   double len1 = hypot(pa[0] - pc[0], pa[1] - pc[1]);
@@ -261,7 +261,7 @@ static void render_one(const double* tris, const int32_t* seg, int64_t F, const 
 
   orc_tri_eval ev;
   for (int64_t i = 0; i < F; ++i) {
-    eval_triangle(tris + 9 * i, o, d, u, w, t_far, et0, et_far, s, &ev);
+    eval_triangle(tris + 9 * i, o, d, u, w, t_far, et0, et_far, s, 0.0, &ev);
     if (ev.exact_hit && (ev.t_exact < best_t || (ev.t_exact == best_t && i < best_i))) {
       best_t = ev.t_exact;
       best_i = i;
@@ -292,6 +292,7 @@ static void render_one(const double* tris, const int32_t* seg, int64_t F, const 
   }
 
   /* exact answer (a6): value, clamp, miss */
+  res->t_hit = best_i >= 0 ? best_t : INFINITY;
   if (best_i >= 0) {
     double v = best_t * scale;
     if (v > s->max_range) v = s->max_range;
@@ -458,6 +459,81 @@ int orc_hit_channels(const double* tris, int64_t F, const orc_sensor* s, const d
     bary[2 * i + 1] = dot3(c2, nrm) / (nn * nn);
     double sgn = nd > 0.0 ? -1.0 : 1.0;
     for (int k = 0; k < 3; ++k) normal[3 * i + k] = sgn * nrm[k] / nn;
+  }
+  return 0;
+}
+
+/* ---- stereo shadows (Sec. III-D.1: rays projected back from the points of
+ * intersection towards the second sensor; pixels whose ray meets the
+ * environment are invalid) ----
+ * reading: the second sensor sits at o2 = p + R(q) b (b in the sensor frame);
+ * the pixel is shadowed when a triangle meets the segment P + s (o2 - P) at
+ * some s in [eps, 1], where P is the exact hit; eps keeps the surface at P
+ * itself out. The verdict is banded like a render: the renderer's P may sit
+ * up to e_P from the exact one, so every triangle is judged with that much
+ * extra vertex displacement; a triangle possibly but not surely on the
+ * segment makes the verdict "either". */
+static void orthobasis(const double d[3], double u[3], double w[3]) {
+  double h[3] = {0, 0, 0};
+  int kmin = 0;
+  for (int k = 1; k < 3; ++k)
+    if (fabs(d[k]) < fabs(d[kmin])) kmin = k;
+  h[kmin] = 1.0;
+  cross3(d, h, u);
+  double un = sqrt(dot3(u, u));
+  for (int k = 0; k < 3; ++k) u[k] /= un;
+  cross3(d, u, w);
+}
+
+int orc_shadow(const double* tris, int64_t F, const orc_sensor* s, const double pose[7],
+               const double baseline[3], double eps, const int64_t* rays, const orc_result* res,
+               int64_t n, int32_t* out) {
+  if (!s || !pose || !baseline || n < 0 || (n > 0 && (!rays || !res || !out)) || (F > 0 && !tris)) return -1;
+  if (s->width <= 0 || s->height <= 0 || (s->type != ORC_PINHOLE && s->type != ORC_LIDAR)) return -1;
+  if (!(eps >= 0.0 && eps < 1.0)) return -1;
+  int64_t n_pix = (int64_t)s->width * s->height;
+  for (int64_t i = 0; i < n; ++i)
+    if (rays[i] < 0 || rays[i] >= n_pix) return -1;
+  double R[9];
+  orc_rotation(pose + 3, R);
+  double o2[3];
+  matvec(R, baseline, o2);
+  for (int k = 0; k < 3; ++k) o2[k] += pose[k];
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t i = 0; i < n; ++i) {
+    out[i] = 0;
+    if (res[i].seg < 0 || !(res[i].t_hit < INFINITY)) continue;
+    int64_t row = rays[i] / s->width, col = rays[i] % s->width;
+    double o[3], d[3], scale;
+    orc_ray(s, pose, row, col, o, d, &scale);
+    double P[3], seg[3];
+    for (int k = 0; k < 3; ++k) {
+      P[k] = o[k] + res[i].t_hit * d[k];
+      seg[k] = o2[k] - P[k];
+    }
+    double L = sqrt(dot3(seg, seg));
+    if (L == 0.0) continue;
+    double dir[3], start[3], u[3], w[3];
+    for (int k = 0; k < 3; ++k) {
+      dir[k] = seg[k] / L;
+      start[k] = P[k] + eps * L * dir[k];
+    }
+    orthobasis(dir, u, w);
+    /* how far the renderer's P may sit from the exact one: the value
+     * tolerance along the ray, the direction and arithmetic bands across it,
+     * and float32 rounding of the segment's ends */
+    double pmax = 1.0;
+    for (int k = 0; k < 3; ++k) pmax = fmax(pmax, fmax(fabs(P[k]), fabs(o2[k])));
+    double e_p = tolv(res[i].t_hit * scale) / scale + 4.0 * (s->dir_rel + s->arith_rel) * res[i].t_hit +
+                 8.0 * 5.9604644775390625e-8 * pmax;
+    double t_far = (1.0 - eps) * L;
+    int verdict = 0;
+    orc_tri_eval ev;
+    for (int64_t f = 0; f < F && verdict != 1; ++f) {
+      eval_triangle(tris + 9 * f, start, dir, u, w, t_far, e_p, e_p, s, e_p, &ev);
+      if (ev.possible) verdict = (ev.sure && !ev.grazing) ? 1 : 2;
+    }
+    out[i] = verdict;
   }
   return 0;
 }

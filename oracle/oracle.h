@@ -74,6 +74,7 @@ typedef struct {
   double cand_hi[ORC_MAX_CAND];
   int32_t n_tri;       /* triangles a single-precision renderer may report (within the bands) */
   int32_t cand_tri[ORC_MAX_TRI];
+  double t_hit;        /* exact distance to the nearest hit along the unit ray (INFINITY: none) */
 } orc_result;
 
 /* Rotation matrix of the unit quaternion q/|q| (x, y, z, w order), row-major. */
@@ -110,6 +111,16 @@ int orc_render(const double* tris, const int32_t* seg, int64_t F,
 int orc_hit_channels(const double* tris, int64_t F, const orc_sensor* s, const double pose[7],
                      const int64_t* rays, const int32_t* face, const double* v, int64_t n,
                      double* bary, double* normal, double* point);
+
+/* Stereo shadow verdict of each listed ray (Sec. III-D.1): with the second
+ * sensor at o2 = p + R(q) baseline and P the exact hit of ray i (from
+ * res[i], an orc_render result for the same ray), out[i] = 1 if a triangle
+ * surely meets the segment P + s (o2 - P) for s in [eps, 1], 0 if none can,
+ * 2 if one lies within the error bands (either verdict is acceptable);
+ * rays without a reported hit get 0. Returns 0, or -1 on bad input. */
+int orc_shadow(const double* tris, int64_t F, const orc_sensor* s, const double pose[7],
+               const double baseline[3], double eps, const int64_t* rays, const orc_result* res,
+               int64_t n, int32_t* out);
 
 /* Number of OpenMP threads the oracle uses. */
 int orc_num_threads(void);

@@ -492,6 +492,98 @@ def pin_candidate_triangles(lib):
     assert res["n_tri"][0] == 1 and res["cand_tri"][0][0] == res["tri"][0] == 1  # (y, z) = (-0.5, 0.3): y < z
 
 
+# ---------------------------------------------------------------- stereo shadows
+def _rect(x, y0, y1, z0, z1):
+    return [[x, y0, z0, x, y1, z0, x, y1, z1], [x, y0, z0, x, y1, z1, x, y0, z1]]
+
+
+def pin_shadow_plate_closed_form(lib):
+    """Wall at x = D behind a plate at x = D/2, second sensor at baseline (0, b, 0): a wall pixel is
+    shadowed iff the segment from its wall point to the second sensor crosses the plate, which happens
+    where it meets x = D/2, at the midpoint; plate pixels are never shadowed."""
+    rng = np.random.default_rng(19)
+    n_sh = 0
+    for _ in range(5):
+        D = rng.uniform(2.0, 8.0)
+        y0, z0 = rng.uniform(-1.5, 0.5), rng.uniform(-1.0, 0.3)
+        y1, z1 = y0 + rng.uniform(0.3, 1.2), z0 + rng.uniform(0.3, 1.0)
+        b = rng.uniform(0.4, 1.0) * rng.choice([-1.0, 1.0])
+        tris = np.array(_rect(D, -80, 80, -80, 80) + _rect(D / 2, y0, y1, z0, z1), float)
+        seg = np.array([0, 0, 1, 1], np.int32)
+        s = O.Sensor(O.PINHOLE, 48, 36, math.radians(90), 0.1, 50.0)
+        r = O.render(tris, seg, s, IDENT, lib=lib)
+        rays = np.arange(48 * 36)
+        sh = O.shadow(tris, s, IDENT, [0, b, 0], 1e-4, rays, r, lib=lib)
+        for i in rays:
+            _, d, _ = O.ray(s, IDENT, i // 48, i % 48, lib)
+            P = d * (D / d[0])
+            cy, cz = (P[1] + b) / 2, P[2] / 2  # midpoint of P and (0, b, 0)
+            m = 1e-6 + 1e-4 * D
+            inside = y0 + m < cy < y1 - m and z0 + m < cz < z1 - m
+            outside = cy < y0 - m or cy > y1 + m or cz < z0 - m or cz > z1 + m
+            if r["seg"][i] == 1:
+                assert sh[i] == 0
+            elif inside:
+                assert sh[i] in (1, 2)
+                n_sh += sh[i] == 1
+            elif outside:
+                assert sh[i] == 0, (i, cy, cz)
+    assert n_sh > 20
+
+
+def pin_shadow_zero_baseline_and_open_scene(lib):
+    """A second sensor at the first one's position sees every hit (the segment is the primary ray
+    reversed, and the hit is the nearest); with no geometry between, nothing is shadowed."""
+    vs, ix, ps, sg, _, _ = _room_scene()
+    sc_tris, sc_seg = O.world_triangles(vs, ix, ps, sg)
+    s = O.Sensor(O.PINHOLE, 24, 18, math.radians(87), 0.2, 10.0)
+    rng = np.random.default_rng(20)
+    for _ in range(3):
+        pose = np.concatenate([rng.uniform(-3, 3, 2), [rng.uniform(0.5, 3.5)], rng.normal(size=4)])
+        r = O.render(sc_tris, sc_seg, s, pose, lib=lib)
+        rays = np.arange(24 * 18)
+        sh = O.shadow(sc_tris, s, pose, [0, 0, 0], 1e-4, rays, r, lib=lib)
+        assert (sh != 1).all() and (sh == 2).mean() < 0.05
+    wall = np.array(_rect(5.0, -50, 50, -50, 50), float)
+    r = O.render(wall, np.array([0, 0], np.int32), s, IDENT, lib=lib)
+    sh = O.shadow(wall, s, IDENT, [0, -0.3, 0.1], 1e-4, np.arange(24 * 18), r, lib=lib)
+    assert (sh == 0).all()
+
+
+def pin_shadow_linear_solve(lib):
+    """Shadow verdicts against numpy.linalg.solve of P + s (o2 - P) = v0 + u e1 + w e2 on random scenes."""
+    rng = np.random.default_rng(21)
+    checked = 0
+    for trial in range(10):
+        F = int(rng.integers(2, 10))
+        tris = rng.uniform(-4, 4, (F, 9))
+        seg = np.arange(F, dtype=np.int32)
+        s = O.Sensor(O.PINHOLE, 12, 9, math.radians(100), 0.05, 20.0)
+        pose = np.concatenate([rng.uniform(-1, 1, 3), rng.normal(size=4)])
+        base = rng.uniform(-2, 2, 3)
+        r = O.render(tris, seg, s, pose, lib=lib)
+        rays = np.arange(12 * 9)
+        sh = O.shadow(tris, s, pose, base, 1e-4, rays, r, lib=lib)
+        R = _rot_scipy(pose[3:])
+        o2 = pose[:3] + R @ base
+        for i in rays:
+            if r["seg"][i] < 0 or sh[i] == 2:
+                continue
+            o, d, _ = O.ray(s, pose, i // 12, i % 12, lib)
+            P = o + r["t_hit"][i] * d
+            hit = False
+            for tri in tris:
+                v0, v1, v2 = tri[:3], tri[3:6], tri[6:]
+                M = np.stack([o2 - P, v0 - v1, v0 - v2], 1)
+                if abs(np.linalg.det(M)) < 1e-12:
+                    continue
+                t, u, w = np.linalg.solve(M, v0 - P)
+                hit |= bool(u >= 0 and w >= 0 and u + w <= 1 and 1e-4 <= t <= 1)
+            assert sh[i] == int(hit), (trial, i)
+            checked += 1
+    assert checked > 200
+
+
 ALL_PINS = [
     pin_rotation_vs_scipy, pin_transform_vs_scipy, pin_transform_identity_exact,
     pin_camera_centre_and_corner, pin_camera_column_angles, pin_lidar_angles,
@@ -499,4 +591,5 @@ ALL_PINS = [
     pin_brute_force_linear_solve, pin_miss_exact, pin_translation_rotation_invariance,
     pin_degenerate_never_hits, pin_tie_break, pin_channels_wall, pin_channels_linear_solve,
     pin_channels_icosphere, pin_channels_miss_and_lidar_norm, pin_candidate_triangles,
+    pin_shadow_plate_closed_form, pin_shadow_zero_baseline_and_open_scene, pin_shadow_linear_solve,
 ]

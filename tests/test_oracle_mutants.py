@@ -49,6 +49,10 @@ MUTANTS = {
                               "point[3 * i + k] = v[i] * local[k] / sqrt(dot3(local, local));"),
     "point_pixel_corner": ("local[1] = (W / 2.0 - ((double)col + 0.5)) / f;", "local[1] = (W / 2.0 - (double)col) / f;"),
     "candidate_triangle_dropped": ("res->cand_tri[res->n_tri++] = c->tri;", "res->cand_tri[res->n_tri] = c->tri;"),
+    "baseline_in_world_frame": ("  matvec(R, baseline, o2);\n", "  for (int k = 0; k < 3; ++k) o2[k] = baseline[k];\n"),
+    "shadow_from_sensor_origin": ("      P[k] = o[k] + res[i].t_hit * d[k];", "      P[k] = o[k];"),
+    "shadow_without_eps": ("      start[k] = P[k] + eps * L * dir[k];", "      start[k] = P[k];"),
+    "shadow_segment_too_long": ("    double t_far = (1.0 - eps) * L;", "    double t_far = 2.0 * L;"),
 }
 
 
