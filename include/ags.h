@@ -206,6 +206,31 @@ ags_status ags_render_channels(ags_context* ctx, const ags_scene* scene, const a
                                const ags_hit_channels* channels, void* cuda_stream);
 
 /*
+ * Stereo shadows (Sec. III-D.1: rays projected back from the points of
+ * intersection towards the second sensor; pixels whose ray meets the
+ * environment are invalid). The second sensor sits at baseline (metres, in
+ * the sensor frame: +x forward, +y left, +z up) from the rendered one. A hit
+ * P is shadowed when a triangle meets the segment P + s (o2 - P) for s in
+ * [eps, 1]; eps (0 -> 1e-4) keeps the surface at P itself out. A shadowed
+ * pixel is reported as invalid: max_range, segment -1, face -1.
+ */
+typedef struct {
+  float baseline[3];
+  float eps;
+} ags_stereo;
+
+/*
+ * ags_render_ex -- ags_render with optional extra hit channels (NULL: none)
+ * and optional stereo shadow invalidation (NULL: none). Depth and segment IDs
+ * are bit-identical to ags_render where no pixel is shadowed. Uses the 8x4
+ * warp tile. Errors as ags_render; a misaligned channel pointer, a
+ * non-finite baseline or eps outside (0, 1) -> AGS_ERR_INVALID_ARG.
+ */
+ags_status ags_render_ex(ags_context* ctx, const ags_scene* scene, const ags_sensor_spec* spec,
+                         const float* sensor_poses_dev, float* out_depth_dev, int32_t* out_seg_dev,
+                         const ags_hit_channels* channels, const ags_stereo* stereo, void* cuda_stream);
+
+/*
  * ags_render_envs -- as ags_render for the n environments listed in
  * env_ids_dev (device int32 [n], each in [0, n_envs)); sensor_poses_dev is
  * [n][7] and the outputs are [n][height][width], in list order.

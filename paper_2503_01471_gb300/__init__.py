@@ -54,7 +54,7 @@ EXPORTS = [
     "ags_set_launch_config", "ags_get_launch_config", "ags_memcpy_d2h", "ags_server_create", "ags_server_destroy",
     "ags_server_submit", "ags_server_poll", "ags_server_release", "ags_server_stats", "ags_server_replay",
     "ags_replay_sequential", "ags_scene_update_poses", "ags_render_graph_create", "ags_render_graph_launch",
-    "ags_render_graph_destroy", "ags_render_channels",
+    "ags_render_graph_destroy", "ags_render_channels", "ags_render_ex",
 ]
 
 
@@ -76,6 +76,10 @@ class ags_env_mesh(ctypes.Structure):
 class ags_hit_channels(ctypes.Structure):
     _fields_ = [("face", ctypes.c_void_p), ("bary", ctypes.c_void_p), ("normal", ctypes.c_void_p),
                 ("point", ctypes.c_void_p)]
+
+
+class ags_stereo(ctypes.Structure):
+    _fields_ = [("baseline", ctypes.c_float * 3), ("eps", ctypes.c_float)]
 
 
 class ags_launch_config(ctypes.Structure):
@@ -181,6 +185,8 @@ def lib() -> ctypes.CDLL:
         "ags_render_graph_destroy": (None, [vp]),
         "ags_render_channels": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), vp, vp, vp,
                                       ctypes.POINTER(ags_hit_channels), vp]),
+        "ags_render_ex": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), vp, vp, vp, ctypes.POINTER(ags_hit_channels),
+                                ctypes.POINTER(ags_stereo), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -502,3 +508,22 @@ def ags_render_channels(ctx: int, scene: int, spec, sensor_poses, out_depth, out
     ch = ags_hit_channels(_ptr(face) or None, _ptr(bary) or None, _ptr(normal) or None, _ptr(point) or None)
     _check(lib().ags_render_channels(ctx, scene, ctypes.byref(s), _ptr(sensor_poses), _ptr(out_depth),
                                      _ptr(out_seg), ctypes.byref(ch), _stream(stream)), "ags_render_channels")
+
+
+def ags_render_ex(ctx: int, scene: int, spec, sensor_poses, out_depth, out_seg, face=None, bary=None, normal=None,
+                  point=None, baseline=None, eps=0.0, stream=None) -> None:
+    """ags_render with optional hit channels (device tensors) and, when ``baseline`` (3 floats, sensor frame)
+    is given, stereo shadow invalidation towards a second sensor there."""
+    s = make_spec(spec)
+    chans = (face, bary, normal, point)
+    ch = None
+    if any(c is not None for c in chans):
+        ch = ctypes.byref(ags_hit_channels(*(_ptr(c) or None for c in chans)))
+    st = None
+    if baseline is not None:
+        b = [float(x) for x in baseline]
+        if len(b) != 3:
+            raise ValueError("baseline needs 3 values")
+        st = ctypes.byref(ags_stereo((ctypes.c_float * 3)(*b), float(eps)))
+    _check(lib().ags_render_ex(ctx, scene, ctypes.byref(s), _ptr(sensor_poses), _ptr(out_depth), _ptr(out_seg), ch,
+                               st, _stream(stream)), "ags_render_ex")

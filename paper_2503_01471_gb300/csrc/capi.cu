@@ -405,6 +405,12 @@ ags_status ags_render(ags_context* ctx, const ags_scene* sc, const ags_sensor_sp
 
 ags_status ags_render_channels(ags_context* ctx, const ags_scene* sc, const ags_sensor_spec* spec, const float* poses,
                                float* depth, int32_t* seg, const ags_hit_channels* ch, void* stream) {
+  return ags_render_ex(ctx, sc, spec, poses, depth, seg, ch, nullptr, stream);
+}
+
+ags_status ags_render_ex(ags_context* ctx, const ags_scene* sc, const ags_sensor_spec* spec, const float* poses,
+                         float* depth, int32_t* seg, const ags_hit_channels* ch, const ags_stereo* stereo,
+                         void* stream) {
   AGS_API_BEGIN
   if (!ctx || !sc) return invalid("ctx or scene is NULL");
   if (sc->ctx != ctx) return invalid("scene belongs to another context");
@@ -427,7 +433,17 @@ ags_status ags_render_channels(ags_context* ctx, const ags_scene* sc, const ags_
     a.out_bary = ch->bary;
     a.out_normal = ch->normal;
     a.out_point = ch->point;
-    a.channels = 1;
+    a.extra |= 1;
+  }
+  if (stereo) {
+    for (int k = 0; k < 3; ++k) {
+      if (!std::isfinite(stereo->baseline[k])) return invalid("stereo baseline is not finite");
+      a.baseline[k] = stereo->baseline[k];
+    }
+    const float eps = stereo->eps == 0.0f ? 1e-4f : stereo->eps;
+    if (!(eps > 0.0f && eps < 1.0f)) return invalid("stereo eps must lie in (0, 1)");
+    a.shadow_eps = eps;
+    a.extra |= 2;
   }
   return launch(ctx, a, static_cast<cudaStream_t>(stream), false, cfg.blocks_per_sm);
   AGS_API_END

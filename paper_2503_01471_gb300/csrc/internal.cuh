@@ -184,7 +184,9 @@ struct TraceArgs {
   float* out_bary;
   float* out_normal;
   float* out_point;
-  int32_t channels;          // nonzero: launch the channel kernel
+  int32_t extra;             // bit 0: hit channels; bit 1: stereo shadow test
+  float baseline[3];         // stereo: second sensor's origin in the sensor frame
+  float shadow_eps;          // stereo: the shadow segment starts at this fraction
   int32_t n;                 // environments rendered
   SensorParams sensor;       // uniform mode
   const SensorParams* specs; // slot mode: table of sensor shapes

@@ -14,6 +14,9 @@ namespace ags {
 namespace {
 
 constexpr int kTraceThreads = 128;
+// optional work of the render kernel (template bits)
+constexpr int kExtraChannels = 1;  // face index, barycentrics, normal, sensor-frame point
+constexpr int kExtraShadow = 2;    // stereo shadow test towards a second sensor
 #ifndef AGS_TRACE_MIN_BLOCKS
 #define AGS_TRACE_MIN_BLOCKS 7
 #endif
@@ -308,6 +311,100 @@ __device__ __forceinline__ void test_node(const void* __restrict__ nodes, int32_
   }
 }
 
+// Any-hit test of packed triangle k against the segment o + t d, t in
+// [t0, 1] (the same watertight arithmetic as test_triangle).
+__device__ __forceinline__ bool segment_hits(const Ray& r, const float4* __restrict__ tris, int32_t k, float t0) {
+  const float4 a = __ldg(tris + 3 * (int64_t)k);
+  const float4 b = __ldg(tris + 3 * (int64_t)k + 1);
+  const float4 c = __ldg(tris + 3 * (int64_t)k + 2);
+  float Ax, Ay, Az, Bx, By, Bz, Cx, Cy, Cz;
+  shear(r, a, Ax, Ay, Az);
+  shear(r, b, Bx, By, Bz);
+  shear(r, c, Cx, Cy, Cz);
+  const float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+  const float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+  const float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+  const bool neg = (U < 0.0f) || (V < 0.0f) || (W < 0.0f);
+  const bool pos = (U > 0.0f) || (V > 0.0f) || (W > 0.0f);
+  if (neg && pos) return false;
+  const float det = U + V + W;
+  if (det == 0.0f) return false;
+  const float T = __fmaf_rn(U, Az, __fmaf_rn(V, Bz, __fmul_rn(W, Cz)));
+  if (T != 0.0f && ((__float_as_uint(T) ^ __float_as_uint(det)) >> 31)) return false;
+  const float t = __fdiv_rn(fabsf(T), fabsf(det));
+  return t >= t0 && t <= 1.0f;
+}
+
+// Stereo shadow (Sec. III-D.1): does any triangle of environment env meet
+// the segment from P to the second sensor, o = P, d = o2 - P, t in [t0, 1]?
+// The traversal stops at the first such triangle; children are visited in
+// slot order. Limits set the status word and `failed`.
+template <int kFmt>
+__device__ bool occluded(const TraceArgs& a, int32_t env, float px, float py, float pz, float dx, float dy, float dz,
+                         float t0, int2* stack, bool& failed) {
+  Ray r;
+  r.ox = px;
+  r.oy = py;
+  r.oz = pz;
+  setup_ray(r, dx, dy, dz);
+  int32_t node = __ldg(a.env_root + env);
+  int sp = 0, visits = 0;
+  const float t_cull = kCullSlack;
+  while (node >= 0) {
+    if (++visits > a.max_visits) {
+      atomicOr(a.status, kStatusIterationCap);
+      failed = true;
+      return false;
+    }
+    if (node >= a.n_nodes) {
+      atomicOr(a.status, kStatusBadIndex);
+      failed = true;
+      return false;
+    }
+    int32_t child_base, tri_base;
+    uint32_t meta_lo, meta_hi, hit_mask;
+    float tmins[8];
+    test_node<kFmt>(a.nodes, node, r, t_cull, child_base, tri_base, meta_lo, meta_hi, tmins, hit_mask);
+    const uint32_t b0 = meta_lo & 0xFFu;
+    const int ni = (b0 & 0x80u) ? (int)min(b0 & 0xFu, 8u) : 0;
+    const uint32_t inner_bits = (1u << ni) - 1u;
+    uint32_t leaf_mask = hit_mask & ~inner_bits;
+    uint32_t inner_hits = hit_mask & inner_bits;
+    while (leaf_mask) {
+      const int k = __ffs(leaf_mask) - 1;
+      leaf_mask &= leaf_mask - 1;
+      const uint32_t m = ((k < 4 ? meta_lo : meta_hi) >> (8 * (k & 3))) & 0xFFu;
+      if (m == kMetaEmpty) continue;
+      const int32_t start = tri_base + (int32_t)(m >> 2);
+      const int32_t cnt = (int32_t)(m & 3u) + 1;
+      if (start < 0 || start + cnt > a.n_tris) {
+        atomicOr(a.status, kStatusBadIndex);
+        failed = true;
+        return false;
+      }
+      for (int32_t x = 0; x < cnt; ++x)
+        if (segment_hits(r, a.tris, start + x, t0)) return true;
+    }
+    node = -1;
+    if (inner_hits) {
+      node = child_base + (__ffs(inner_hits) - 1);
+      inner_hits &= inner_hits - 1;
+      while (inner_hits) {
+        if (sp >= kStackSize) {
+          atomicOr(a.status, kStatusStackOverflow);
+          failed = true;
+          return false;
+        }
+        stack[sp++] = make_int2(child_base + (__ffs(inner_hits) - 1), 0);
+        inner_hits &= inner_hits - 1;
+      }
+    } else if (sp > 0) {
+      node = stack[--sp].x;
+    }
+  }
+  return false;
+}
+
 // a3: the sensor-frame direction of pixel / beam (row, col). Camera: the
 // unnormalised (1, a, b) through the pixel centre, so the distance along it
 // is the depth itself; LiDAR: the unit beam direction (distance = range).
@@ -338,7 +435,7 @@ __device__ __forceinline__ int64_t slot_out(const TraceArgs& a, const SensorPara
   else return (int64_t)slot * sen.H * sen.W;
 }
 
-template <bool kCount, int kTileW, int kRaysPerLane, bool kSlots, int kFmt, bool kChannels>
+template <bool kCount, int kTileW, int kRaysPerLane, bool kSlots, int kFmt, int kExtra>
 __device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParams& sen, int32_t env, int32_t t_in,
                                            int32_t slot, int lane, int2* stack, unsigned long long& n_nodes,
                                            unsigned long long& n_tris, unsigned long long& n_rays) {
@@ -425,7 +522,7 @@ __device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParam
         break;
       }
       for (int32_t x = 0; x < cnt; ++x)
-        test_triangle<kChannels>(r, a.tris, start + x, t_best, best_id, best_seg, best_k);
+        test_triangle<(kExtra & kExtraChannels) != 0>(r, a.tris, start + x, t_best, best_id, best_seg, best_k);
       if (kCount) n_tris += cnt;
     }
     if (failed) break;
@@ -508,10 +605,34 @@ __device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParam
     v = sen.max_range;
     seg = -1;
   }
+  if constexpr ((kExtra & kExtraShadow) != 0) {
+    if (!failed && seg >= 0) {
+      // the hit point P and the second sensor o2 = p + R b, both in the world
+      float sx, sy, sz;
+      sensor_dir(sen, row, col, sx, sy, sz);
+      const float dwx = R00 * sx + R01 * sy + R02 * sz, dwy = R10 * sx + R11 * sy + R12 * sz,
+                  dwz = R20 * sx + R21 * sy + R22 * sz;
+      const float Px = px + t_best * dwx, Py = py + t_best * dwy, Pz = pz + t_best * dwz;
+      const float bx = a.baseline[0], by = a.baseline[1], bz = a.baseline[2];
+      const float o2x = px + (R00 * bx + R01 * by + R02 * bz), o2y = py + (R10 * bx + R11 * by + R12 * bz),
+                  o2z = pz + (R20 * bx + R21 * by + R22 * bz);
+      bool sfail = false;
+      const bool shadowed =
+          occluded<kFmt>(a, env, Px, Py, Pz, o2x - Px, o2y - Py, o2z - Pz, a.shadow_eps, stack, sfail);
+      if (sfail) {
+        failed = true;
+        v = __int_as_float(0x7fc00000);
+        seg = -1;
+      } else if (shadowed) {
+        v = sen.max_range;
+        seg = -1;
+      }
+    }
+  }
   const int64_t o = slot_out<kSlots>(a, sen, slot) + (int64_t)row * W + col;
   a.out_depth[o] = v;
   a.out_seg[o] = seg;
-  if constexpr (kChannels) {
+  if constexpr ((kExtra & kExtraChannels) != 0) {
     // extra hit channels of the reported hit (a miss or a near hit reported
     // as invalid: face -1, zero weights and normal)
     const float nan = __int_as_float(0x7fc00000);
@@ -545,7 +666,7 @@ __device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParam
 // kSlots: each tile belongs to one slot of a table (serving: every request has
 // its own environment, sensor shape, pose and output offset); otherwise all
 // environments of the launch share one sensor shape.
-template <bool kCount, int kTileW, int kRaysPerLane, bool kSlots, int kFmt, bool kChannels = false>
+template <bool kCount, int kTileW, int kRaysPerLane, bool kSlots, int kFmt, int kExtra = 0>
 __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) k_trace(const TraceArgs a) {
   const int lane = threadIdx.x & 31;
   int2 stack[kStackSize];
@@ -582,10 +703,10 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) k_trace(const 
       continue;
     }
     if constexpr (kSlots) {
-      trace_tile<kCount, kTileW, kRaysPerLane, true, kFmt, kChannels>(a, a.specs[slot_spec], env, t_in, slot, lane,
+      trace_tile<kCount, kTileW, kRaysPerLane, true, kFmt, kExtra>(a, a.specs[slot_spec], env, t_in, slot, lane,
                                                                    stack, n_nodes, n_tris, n_rays);
     } else {
-      trace_tile<kCount, kTileW, kRaysPerLane, false, kFmt, kChannels>(a, a.sensor, env, t_in, slot, lane, stack,
+      trace_tile<kCount, kTileW, kRaysPerLane, false, kFmt, kExtra>(a, a.sensor, env, t_in, slot, lane, stack,
                                                                     n_nodes, n_tris, n_rays);
     }
   }
@@ -627,8 +748,12 @@ cudaError_t launch_fmt(const TraceArgs& a, int blocks, bool count, cudaStream_t 
   if (a.slots) {
     if (w == 8 && r == 1) k_trace<false, 8, 1, true, kFmt><<<blocks, kTraceThreads, 0, s>>>(a);
     else return cudaErrorInvalidValue;
-  } else if (a.channels) {
-    if (w == 8 && r == 1 && !count) k_trace<false, 8, 1, false, kFmt, true><<<blocks, kTraceThreads, 0, s>>>(a);
+  } else if (a.extra) {
+    if (w != 8 || r != 1 || count) return cudaErrorInvalidValue;
+    if (a.extra == kExtraChannels) k_trace<false, 8, 1, false, kFmt, kExtraChannels><<<blocks, kTraceThreads, 0, s>>>(a);
+    else if (a.extra == kExtraShadow) k_trace<false, 8, 1, false, kFmt, kExtraShadow><<<blocks, kTraceThreads, 0, s>>>(a);
+    else if (a.extra == (kExtraChannels | kExtraShadow))
+      k_trace<false, 8, 1, false, kFmt, kExtraChannels | kExtraShadow><<<blocks, kTraceThreads, 0, s>>>(a);
     else return cudaErrorInvalidValue;
   } else if (count) {
     k_trace<true, 8, 1, false, kFmt><<<blocks, kTraceThreads, 0, s>>>(a);

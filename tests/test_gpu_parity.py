@@ -547,3 +547,72 @@ def test_hit_channels_subsets_and_formats_are_bit_identical(ctx):
     finally:
         for sc in scenes:
             ags.ags_scene_destroy(sc)
+
+
+# ---------------------------------------------------------------- stereo shadows
+@pytest.mark.parametrize("baseline", [(0.0, -0.095, 0.0), (0.0, -0.6, 0.2)])
+def test_stereo_shadows_match_oracle(ctx, baseline):
+    """A pixel is invalidated exactly when the oracle's segment from the hit to the second sensor surely
+    meets a triangle, kept (bit-identical) when it surely does not; either where the oracle's bands allow."""
+    batch, spec, poses = S.obstacle_rooms(3, steps=1, width=40, height=30)
+    scene = ags.ags_scene_build(ctx, batch)
+    E, H, W = 3, 30, 40
+    try:
+        d0, s0 = render(ctx, scene, spec, poses[0])
+        p = torch.as_tensor(poses[0]).cuda()
+        d = torch.empty((E, H, W), device="cuda")
+        sg = torch.empty((E, H, W), dtype=torch.int32, device="cuda")
+        face = torch.empty((E, H, W), dtype=torch.int32, device="cuda")
+        ags.ags_render_ex(ctx, scene, spec, p, d, sg, face=face, baseline=baseline)
+        ags.ags_stream_status(ctx)
+        d, sg, face = d.cpu().numpy(), sg.cpu().numpy(), face.cpu().numpy()
+        _, _, ch = render_channels(ctx, scene, spec, poses[0], ("face",))
+        miss_v = np.float32(spec.max_range)
+        n_sh = n_either = 0
+        rays = np.arange(H * W, dtype=np.int64)
+        for e in range(E):
+            tris, tseg = oracle_env(batch, e)
+            s = oracle_sensor(spec)
+            pose64 = np.asarray(poses[0][e], np.float32).astype(np.float64)
+            res = O.render(tris, tseg, s, pose64, rays)
+            verdict = O.shadow(tris, s, pose64, np.asarray(baseline, np.float32).astype(np.float64),
+                               np.float32(1e-4), rays, res)
+            a0, b0 = d0[e].reshape(-1), s0[e].reshape(-1)
+            a, b = d[e].reshape(-1), sg[e].reshape(-1)
+            kept = (a == a0) & (b == b0)
+            invalid = (a == miss_v) & (b == -1)
+            loose = (res["flags"] & (O.F_COUNTED | O.F_WIDE)) != 0
+            free = b0 == -1
+            ok = np.where(free, kept, np.where(loose | (verdict == 2), kept | invalid,
+                                               np.where(verdict == 1, invalid, kept)))
+            bad = np.nonzero(~ok)[0][:5]
+            assert ok.all(), [(int(i), float(a0[i]), int(b0[i]), float(a[i]), int(b[i]), int(verdict[i]),
+                               int(res["flags"][i])) for i in bad]
+            # the face channel follows the verdict: -1 where invalidated, as without stereo elsewhere
+            f, f0 = face[e].reshape(-1), ch["face"][e].reshape(-1)
+            assert np.array_equal(f[b == -1], np.full(int((b == -1).sum()), -1))
+            assert np.array_equal(f[b >= 0], f0[b >= 0])
+            n_sh += int(((b == -1) & (b0 >= 0)).sum())
+            n_either += int((verdict == 2).sum())
+        print(f"[parity] stereo baseline {baseline}: {E * H * W} rays, {n_sh} shadowed, {n_either} either")
+        assert n_sh > 0
+    finally:
+        ags.ags_scene_destroy(scene)
+
+
+def test_stereo_zero_baseline_shadows_nothing_and_bad_args(ctx):
+    batch, spec, poses = S.obstacle_rooms(2, steps=1, width=24, height=16)
+    scene = ags.ags_scene_build(ctx, batch)
+    try:
+        d0, s0 = render(ctx, scene, spec, poses[0])
+        p = torch.as_tensor(poses[0]).cuda()
+        d = torch.empty((2, 16, 24), device="cuda")
+        sg = torch.empty((2, 16, 24), dtype=torch.int32, device="cuda")
+        ags.ags_render_ex(ctx, scene, spec, p, d, sg, baseline=(0.0, 0.0, 0.0))
+        ags.ags_stream_status(ctx)
+        assert np.array_equal(d.cpu().numpy(), d0) and np.array_equal(sg.cpu().numpy(), s0)
+        for bad in (dict(baseline=(float("nan"), 0, 0)), dict(baseline=(0, 0.1, 0), eps=1.5)):
+            with pytest.raises(ags.AgsError):
+                ags.ags_render_ex(ctx, scene, spec, p, d, sg, **bad)
+    finally:
+        ags.ags_scene_destroy(scene)
