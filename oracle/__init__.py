@@ -41,6 +41,7 @@ F_TRI_OVERFLOW = 256
 
 PINHOLE = 0
 LIDAR = 1
+RAY_TABLE = 2
 NEAR_CLAMP = 0
 NEAR_INVALID = 1
 
@@ -76,7 +77,7 @@ class _Sensor(ctypes.Structure):
         ("near_mode", ctypes.c_int32), ("hfov", ctypes.c_double), ("vfov_min", ctypes.c_double),
         ("vfov_max", ctypes.c_double), ("min_range", ctypes.c_double),
         ("max_range", ctypes.c_double), ("vert_rel", ctypes.c_double),
-        ("dir_rel", ctypes.c_double), ("arith_rel", ctypes.c_double),
+        ("dir_rel", ctypes.c_double), ("arith_rel", ctypes.c_double), ("dirs", ctypes.c_void_p),
     ]
 
 
@@ -158,11 +159,16 @@ class Sensor:
     vert_rel: float = VERT_REL
     dir_rel: float = DIR_REL
     arith_rel: float = ARITH_REL
+    dirs: np.ndarray | None = None  # RAY_TABLE: [height, width, 3] sensor-frame directions
 
     def _c(self) -> _Sensor:
+        ptr = None
+        if self.dirs is not None:
+            self._dirs64 = np.ascontiguousarray(self.dirs, np.float64).reshape(self.height, self.width, 3)
+            ptr = self._dirs64.ctypes.data
         return _Sensor(self.type, self.width, self.height, self.near_mode, self.hfov,
                        self.vfov_min, self.vfov_max, self.min_range, self.max_range,
-                       self.vert_rel, self.dir_rel, self.arith_rel)
+                       self.vert_rel, self.dir_rel, self.arith_rel, ptr)
 
 
 def rotation(q, lib=None) -> np.ndarray:

@@ -99,6 +99,16 @@ int orc_ray(const orc_sensor* s, const double pose[7], int64_t row, int64_t col,
     local[2] = sin(phi);
     matvec(R, local, d);
     *scale = 1.0; /* range = distance between sensor and hit */
+  } else if (s->type == ORC_RAY_TABLE && s->dirs) {
+    /* Sec. III-D.1 (user-defined sensors with their own projection model):
+     * the pixel's direction is given; the value is the distance along it in
+     * units of its length, so (1, a, b) rows give depth and unit rows range */
+    const double* g = s->dirs + 3 * (row * (int64_t)s->width + col);
+    double n = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    if (!(n > 0.0) || !isfinite(n)) return -1;
+    for (int k = 0; k < 3; ++k) local[k] = g[k] / n;
+    matvec(R, local, d);
+    *scale = 1.0 / n;
   } else {
     return -1;
   }
@@ -377,14 +387,25 @@ static void render_one(const double* tris, const int32_t* seg, int64_t F, const 
   res->flags = flags;
 }
 
+/* a sensor the oracle can cast every listed ray of */
+static int sensor_ok(const orc_sensor* s, const int64_t* rays, int64_t n_rays) {
+  if (s->width <= 0 || s->height <= 0) return 0;
+  if (s->type != ORC_PINHOLE && s->type != ORC_LIDAR && !(s->type == ORC_RAY_TABLE && s->dirs)) return 0;
+  int64_t n_pix = (int64_t)s->width * s->height;
+  double o[3], d[3], scale, pose[7] = {0, 0, 0, 0, 0, 0, 1};
+  for (int64_t i = 0; i < n_rays; ++i) {
+    if (rays[i] < 0 || rays[i] >= n_pix) return 0;
+    if (s->type == ORC_RAY_TABLE && orc_ray(s, pose, rays[i] / s->width, rays[i] % s->width, o, d, &scale) != 0)
+      return 0;
+  }
+  return 1;
+}
+
 int orc_render(const double* tris, const int32_t* seg, int64_t F, const orc_sensor* s,
                const double pose[7], const int64_t* rays, int64_t n_rays, orc_result* out) {
   if (!s || !pose || !out || (F > 0 && (!tris || !seg)) || F < 0 || n_rays < 0) return -1;
-  if (s->width <= 0 || s->height <= 0) return -1;
-  if (s->type != ORC_PINHOLE && s->type != ORC_LIDAR) return -1;
-  int64_t n_pix = (int64_t)s->width * s->height;
-  for (int64_t i = 0; i < n_rays; ++i)
-    if (rays[i] < 0 || rays[i] >= n_pix) return -1;
+  if (n_rays > 0 && !rays) return -1;
+  if (!sensor_ok(s, rays, n_rays)) return -1;
 #pragma omp parallel
   {
     orc_cand list[ORC_LIST_CAP];
@@ -402,7 +423,10 @@ int orc_render(const double* tris, const int32_t* seg, int64_t F, const orc_sens
  * towards the sensor (meshes are two-sided); the point is the hit in the
  * sensor frame, consistent with the reported value. */
 static void sensor_local(const orc_sensor* s, int64_t row, int64_t col, double local[3]) {
-  if (s->type == ORC_PINHOLE) {
+  if (s->type == ORC_RAY_TABLE) {
+    /* the given direction: distance along it is the reported value */
+    for (int k = 0; k < 3; ++k) local[k] = s->dirs[3 * (row * (int64_t)s->width + col) + k];
+  } else if (s->type == ORC_PINHOLE) {
     /* the camera ray through the pixel centre, scaled to unit forward component */
     double W = (double)s->width, H = (double)s->height;
     double f = (W / 2.0) / tan(s->hfov / 2.0);
@@ -424,10 +448,9 @@ int orc_hit_channels(const double* tris, int64_t F, const orc_sensor* s, const d
                      const int64_t* rays, const int32_t* face, const double* v, int64_t n,
                      double* bary, double* normal, double* point) {
   if (!s || !pose || n < 0 || (n > 0 && (!rays || !face || !v || !bary || !normal || !point))) return -1;
-  if (s->width <= 0 || s->height <= 0 || (s->type != ORC_PINHOLE && s->type != ORC_LIDAR)) return -1;
-  int64_t n_pix = (int64_t)s->width * s->height;
+  if (!sensor_ok(s, rays, n)) return -1;
   for (int64_t i = 0; i < n; ++i) {
-    if (rays[i] < 0 || rays[i] >= n_pix || face[i] >= F) return -1;
+    if (face[i] >= F) return -1;
     int64_t row = rays[i] / s->width, col = rays[i] % s->width;
     double local[3];
     sensor_local(s, row, col, local);
@@ -489,11 +512,8 @@ int orc_shadow(const double* tris, int64_t F, const orc_sensor* s, const double 
                const double baseline[3], double eps, const int64_t* rays, const orc_result* res,
                int64_t n, int32_t* out) {
   if (!s || !pose || !baseline || n < 0 || (n > 0 && (!rays || !res || !out)) || (F > 0 && !tris)) return -1;
-  if (s->width <= 0 || s->height <= 0 || (s->type != ORC_PINHOLE && s->type != ORC_LIDAR)) return -1;
+  if (!sensor_ok(s, rays, n)) return -1;
   if (!(eps >= 0.0 && eps < 1.0)) return -1;
-  int64_t n_pix = (int64_t)s->width * s->height;
-  for (int64_t i = 0; i < n; ++i)
-    if (rays[i] < 0 || rays[i] >= n_pix) return -1;
   double R[9];
   orc_rotation(pose + 3, R);
   double o2[3];

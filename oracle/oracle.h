@@ -28,6 +28,7 @@ extern "C" {
 
 #define ORC_PINHOLE 0
 #define ORC_LIDAR 1
+#define ORC_RAY_TABLE 2 /* user projection model: one sensor-frame direction per pixel */
 #define ORC_NEAR_CLAMP 0
 #define ORC_NEAR_INVALID 1
 
@@ -61,6 +62,8 @@ typedef struct {
   double vert_rel;     /* world vertex coordinate error, relative to max(|coord|, 1) */
   double dir_rel;      /* ray direction error, relative */
   double arith_rel;    /* intersection arithmetic error, relative to the vertex distance */
+  const double* dirs;  /* ORC_RAY_TABLE: [height][width][3] sensor-frame directions; the reported
+                          value is the distance along each in units of its length */
 } orc_sensor;
 
 typedef struct {

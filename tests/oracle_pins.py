@@ -584,6 +584,44 @@ def pin_shadow_linear_solve(lib):
     assert checked > 200
 
 
+# ---------------------------------------------------------------- user projection model (ray table)
+def pin_ray_table_reproduces_builtin_models(lib):
+    """A table holding the camera's (1, a, b) rows renders exactly like the camera (depth), and one
+    holding the LiDAR's unit beams exactly like the LiDAR (range)."""
+    vs, ix, ps, sg, _, _ = _room_scene()
+    tris, seg = O.world_triangles(vs, ix, ps, sg)
+    rng = np.random.default_rng(22)
+    pose = np.concatenate([[0.5, -0.3, 1.7], rng.normal(size=4)])
+    cam = O.Sensor(O.PINHOLE, 20, 14, math.radians(87), 0.2, 10.0)
+    f = 10.0 / math.tan(math.radians(87) / 2)
+    cols, rows = np.meshgrid(np.arange(20) + 0.5, np.arange(14) + 0.5)
+    table = np.stack([np.ones_like(cols), (10.0 - cols) / f, (7.0 - rows) / f], -1)
+    tab = O.Sensor(O.RAY_TABLE, 20, 14, 0.0, 0.2, 10.0, dirs=table)
+    a, b = O.render(tris, seg, cam, pose, lib=lib), O.render(tris, seg, tab, pose, lib=lib)
+    assert np.allclose(a["v"], b["v"], rtol=1e-12, atol=1e-12) and np.array_equal(a["seg"], b["seg"])
+    lid = O.Sensor(O.LIDAR, 32, 8, 2 * math.pi, 0.2, 10.0, -0.4, 0.4)
+    R = _rot_scipy(pose[3:])
+    beams = np.array([R.T @ O.ray(lid, pose, k, j, lib)[1] for k in range(8) for j in range(32)]).reshape(8, 32, 3)
+    tab = O.Sensor(O.RAY_TABLE, 32, 8, 0.0, 0.2, 10.0, dirs=beams)
+    a, b = O.render(tris, seg, lid, pose, lib=lib), O.render(tris, seg, tab, pose, lib=lib)
+    assert np.allclose(a["v"], b["v"], rtol=1e-12, atol=1e-12) and np.array_equal(a["seg"], b["seg"])
+
+
+def pin_ray_table_wall_units(lib):
+    """Wall at x = D: a row g with g_x > 0 reports D / g_x (distance in units of |g|), whatever |g|."""
+    rng = np.random.default_rng(23)
+    D = 3.5
+    wall = np.array(_rect(D, -80, 80, -80, 80), float)
+    g = rng.normal(size=(6, 9, 3))
+    g[..., 0] = np.abs(g[..., 0]) + 0.3
+    g *= rng.uniform(0.2, 5.0, (6, 9, 1))
+    tab = O.Sensor(O.RAY_TABLE, 9, 6, 0.0, 0.01, 1e4, dirs=g)
+    r = O.render(wall, np.array([0, 0], np.int32), tab, IDENT, lib=lib)
+    assert np.allclose(r["v"], (D / g[..., 0]).reshape(-1), rtol=1e-12)
+    _, _, point = O.hit_channels(wall, tab, IDENT, np.arange(54), r["tri"], r["v"], lib=lib)
+    assert np.allclose(point[:, 0], D, rtol=1e-12)
+
+
 ALL_PINS = [
     pin_rotation_vs_scipy, pin_transform_vs_scipy, pin_transform_identity_exact,
     pin_camera_centre_and_corner, pin_camera_column_angles, pin_lidar_angles,
@@ -592,4 +630,5 @@ ALL_PINS = [
     pin_degenerate_never_hits, pin_tie_break, pin_channels_wall, pin_channels_linear_solve,
     pin_channels_icosphere, pin_channels_miss_and_lidar_norm, pin_candidate_triangles,
     pin_shadow_plate_closed_form, pin_shadow_zero_baseline_and_open_scene, pin_shadow_linear_solve,
+    pin_ray_table_reproduces_builtin_models, pin_ray_table_wall_units,
 ]

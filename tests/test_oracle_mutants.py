@@ -53,6 +53,8 @@ MUTANTS = {
     "shadow_from_sensor_origin": ("      P[k] = o[k] + res[i].t_hit * d[k];", "      P[k] = o[k];"),
     "shadow_without_eps": ("      start[k] = P[k] + eps * L * dir[k];", "      start[k] = P[k];"),
     "shadow_segment_too_long": ("    double t_far = (1.0 - eps) * L;", "    double t_far = 2.0 * L;"),
+    "ray_table_scale_inverted": ("    *scale = 1.0 / n;", "    *scale = n;"),
+    "ray_table_not_normalised": ("    for (int k = 0; k < 3; ++k) local[k] = g[k] / n;", "    for (int k = 0; k < 3; ++k) local[k] = g[k];"),
 }
 
 
