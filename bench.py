@@ -85,7 +85,7 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("trace.cu", "internal.cuh"):
+    for f in ("trace.cu", "trace_kernel.cuh", "internal.cuh"):
         with open(os.path.join(ROOT, "paper_2503_01471_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

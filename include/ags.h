@@ -77,7 +77,7 @@ typedef struct {
   int32_t n_submeshes;
 } ags_env_mesh;
 
-typedef enum { AGS_PINHOLE = 0, AGS_LIDAR = 1 } ags_sensor_type;
+typedef enum { AGS_PINHOLE = 0, AGS_LIDAR = 1, AGS_RAY_TABLE = 2 } ags_sensor_type;
 typedef enum { AGS_NEAR_CLAMP = 0, AGS_NEAR_INVALID = 1 } ags_near_mode;
 
 typedef struct {
@@ -220,15 +220,34 @@ typedef struct {
 } ags_stereo;
 
 /*
- * ags_render_ex -- ags_render with optional extra hit channels (NULL: none)
- * and optional stereo shadow invalidation (NULL: none). Depth and segment IDs
- * are bit-identical to ags_render where no pixel is shadowed. Uses the 8x4
- * warp tile. Errors as ags_render; a misaligned channel pointer, a
- * non-finite baseline or eps outside (0, 1) -> AGS_ERR_INVALID_ARG.
+ * Options of ags_render_ex; every member may be NULL.
+ *   channels   extra hit channels to write;
+ *   stereo     stereo shadow invalidation towards a second sensor;
+ *   ray_table  device float [height][width][3], the sensor-frame direction
+ *              of each pixel of an AGS_RAY_TABLE sensor (a user projection
+ *              model, Sec. III-D.1: e.g. a dome LiDAR or a fisheye). The
+ *              reported value is the distance along each row in units of its
+ *              length: (1, a, b) rows give depth, unit rows give range. Such a
+ *              sensor ignores hfov and the elevations; a zero or non-finite
+ *              row reports NaN and sets the status as a bad pose does. The
+ *              table stays owned by the caller and must outlive the render.
+ */
+typedef struct {
+  const ags_hit_channels* channels;
+  const ags_stereo* stereo;
+  const float* ray_table;
+} ags_render_options;
+
+/*
+ * ags_render_ex -- ags_render with the options above (NULL: none). Depth and
+ * segment IDs are bit-identical to ags_render where no pixel is shadowed.
+ * Uses the 8x4 warp tile. Errors as ags_render; a misaligned channel pointer,
+ * a non-finite baseline, eps outside (0, 1), or an AGS_RAY_TABLE sensor
+ * without a table (or a table for another sensor type) -> AGS_ERR_INVALID_ARG.
  */
 ags_status ags_render_ex(ags_context* ctx, const ags_scene* scene, const ags_sensor_spec* spec,
                          const float* sensor_poses_dev, float* out_depth_dev, int32_t* out_seg_dev,
-                         const ags_hit_channels* channels, const ags_stereo* stereo, void* cuda_stream);
+                         const ags_render_options* options, void* cuda_stream);
 
 /*
  * ags_render_envs -- as ags_render for the n environments listed in

@@ -31,6 +31,7 @@ STATUS_NAMES = {0: "AGS_OK", 1: "AGS_ERR_INVALID_ARG", 2: "AGS_ERR_OUT_OF_MEMORY
 
 AGS_PINHOLE = 0
 AGS_LIDAR = 1
+AGS_RAY_TABLE = 2
 AGS_NEAR_CLAMP = 0
 AGS_NEAR_INVALID = 1
 AGS_BVH_FP32 = 0
@@ -80,6 +81,11 @@ class ags_hit_channels(ctypes.Structure):
 
 class ags_stereo(ctypes.Structure):
     _fields_ = [("baseline", ctypes.c_float * 3), ("eps", ctypes.c_float)]
+
+
+class ags_render_options(ctypes.Structure):
+    _fields_ = [("channels", ctypes.POINTER(ags_hit_channels)), ("stereo", ctypes.POINTER(ags_stereo)),
+                ("ray_table", ctypes.c_void_p)]
 
 
 class ags_launch_config(ctypes.Structure):
@@ -185,8 +191,8 @@ def lib() -> ctypes.CDLL:
         "ags_render_graph_destroy": (None, [vp]),
         "ags_render_channels": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), vp, vp, vp,
                                       ctypes.POINTER(ags_hit_channels), vp]),
-        "ags_render_ex": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), vp, vp, vp, ctypes.POINTER(ags_hit_channels),
-                                ctypes.POINTER(ags_stereo), vp]),
+        "ags_render_ex": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), vp, vp, vp,
+                                ctypes.POINTER(ags_render_options), vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -511,19 +517,21 @@ def ags_render_channels(ctx: int, scene: int, spec, sensor_poses, out_depth, out
 
 
 def ags_render_ex(ctx: int, scene: int, spec, sensor_poses, out_depth, out_seg, face=None, bary=None, normal=None,
-                  point=None, baseline=None, eps=0.0, stream=None) -> None:
-    """ags_render with optional hit channels (device tensors) and, when ``baseline`` (3 floats, sensor frame)
-    is given, stereo shadow invalidation towards a second sensor there."""
+                  point=None, baseline=None, eps=0.0, ray_table=None, stream=None) -> None:
+    """ags_render with optional hit channels (device tensors), stereo shadow invalidation towards a second
+    sensor at ``baseline`` (3 floats, sensor frame), and, for an AGS_RAY_TABLE spec, its device direction
+    table ``ray_table`` [height, width, 3]."""
     s = make_spec(spec)
     chans = (face, bary, normal, point)
     ch = None
     if any(c is not None for c in chans):
-        ch = ctypes.byref(ags_hit_channels(*(_ptr(c) or None for c in chans)))
+        ch = ctypes.pointer(ags_hit_channels(*(_ptr(c) or None for c in chans)))
     st = None
     if baseline is not None:
         b = [float(x) for x in baseline]
         if len(b) != 3:
             raise ValueError("baseline needs 3 values")
-        st = ctypes.byref(ags_stereo((ctypes.c_float * 3)(*b), float(eps)))
-    _check(lib().ags_render_ex(ctx, scene, ctypes.byref(s), _ptr(sensor_poses), _ptr(out_depth), _ptr(out_seg), ch,
-                               st, _stream(stream)), "ags_render_ex")
+        st = ctypes.pointer(ags_stereo((ctypes.c_float * 3)(*b), float(eps)))
+    opt = ags_render_options(ch, st, _ptr(ray_table) or None)
+    _check(lib().ags_render_ex(ctx, scene, ctypes.byref(s), _ptr(sensor_poses), _ptr(out_depth), _ptr(out_seg),
+                               ctypes.byref(opt), _stream(stream)), "ags_render_ex")

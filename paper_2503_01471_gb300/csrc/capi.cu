@@ -26,6 +26,7 @@ SensorParams sensor_params(const ags_sensor_spec* spec, int tile_w, int tile_h) 
   p.max_range = spec->max_range;
   p.tiles_x = (spec->width + tile_w - 1) / tile_w;
   p.tiles_per_env = p.tiles_x * ((spec->height + tile_h - 1) / tile_h);
+  p.dirs = nullptr;
   return p;
 }
 
@@ -50,9 +51,12 @@ ags_status invalid(const std::string& msg) {
 
 bool finite3(const float* v) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
 
-ags_status check_spec(const ags_sensor_spec* s) {
+ags_status check_spec(const ags_sensor_spec* s, bool with_table) {
   if (!s) return invalid("spec is NULL");
-  if (s->type != AGS_PINHOLE && s->type != AGS_LIDAR) return invalid("spec.type must be AGS_PINHOLE or AGS_LIDAR");
+  if (s->type == AGS_RAY_TABLE && !with_table) return invalid("AGS_RAY_TABLE sensors render through ags_render_ex");
+  if (s->type != AGS_RAY_TABLE && with_table) return invalid("a ray table needs an AGS_RAY_TABLE sensor");
+  if (s->type != AGS_PINHOLE && s->type != AGS_LIDAR && s->type != AGS_RAY_TABLE)
+    return invalid("spec.type must be AGS_PINHOLE, AGS_LIDAR or AGS_RAY_TABLE");
   if (s->width < 1 || s->width > 16384 || s->height < 1 || s->height > 16384)
     return invalid("spec.width/height must be in [1, 16384]");
   if (!std::isfinite(s->min_range) || !std::isfinite(s->max_range) || s->min_range < 0.0f ||
@@ -63,7 +67,7 @@ ags_status check_spec(const ags_sensor_spec* s) {
   const double pi = 3.14159265358979323846;
   if (s->type == AGS_PINHOLE) {
     if (!(s->hfov_rad > 0.0f) || !(s->hfov_rad < (float)pi)) return invalid("camera hfov must be in (0, pi)");
-  } else {
+  } else if (s->type == AGS_LIDAR) {
     if (!(s->hfov_rad > 0.0f) || !(s->hfov_rad <= (float)(2.0 * pi) + 1e-6f))
       return invalid("LiDAR azimuth span must be in (0, 2 pi]");
     if (!std::isfinite(s->vfov_min_rad) || !std::isfinite(s->vfov_max_rad) || s->vfov_min_rad < -(float)(pi / 2) - 1e-6f ||
@@ -392,7 +396,7 @@ ags_status ags_render(ags_context* ctx, const ags_scene* sc, const ags_sensor_sp
   AGS_API_BEGIN
   if (!ctx || !sc) return invalid("ctx or scene is NULL");
   if (sc->ctx != ctx) return invalid("scene belongs to another context");
-  ags_status st = check_spec(spec);
+  ags_status st = check_spec(spec, false);
   if (st != AGS_OK) return st;
   if (!poses || !depth || !seg) return invalid("poses/depth/seg pointer is NULL");
   DeviceGuard g(ctx->device);
@@ -405,16 +409,20 @@ ags_status ags_render(ags_context* ctx, const ags_scene* sc, const ags_sensor_sp
 
 ags_status ags_render_channels(ags_context* ctx, const ags_scene* sc, const ags_sensor_spec* spec, const float* poses,
                                float* depth, int32_t* seg, const ags_hit_channels* ch, void* stream) {
-  return ags_render_ex(ctx, sc, spec, poses, depth, seg, ch, nullptr, stream);
+  ags_render_options opt{ch, nullptr, nullptr};
+  return ags_render_ex(ctx, sc, spec, poses, depth, seg, &opt, stream);
 }
 
 ags_status ags_render_ex(ags_context* ctx, const ags_scene* sc, const ags_sensor_spec* spec, const float* poses,
-                         float* depth, int32_t* seg, const ags_hit_channels* ch, const ags_stereo* stereo,
-                         void* stream) {
+                         float* depth, int32_t* seg, const ags_render_options* opt, void* stream) {
   AGS_API_BEGIN
+  const ags_hit_channels* ch = opt ? opt->channels : nullptr;
+  const ags_stereo* stereo = opt ? opt->stereo : nullptr;
+  const float* table = opt ? opt->ray_table : nullptr;
   if (!ctx || !sc) return invalid("ctx or scene is NULL");
   if (sc->ctx != ctx) return invalid("scene belongs to another context");
-  ags_status st = check_spec(spec);
+  if (table && reinterpret_cast<uintptr_t>(table) % 4 != 0) return invalid("ray table not 4-byte aligned");
+  ags_status st = check_spec(spec, table != nullptr);
   if (st != AGS_OK) return st;
   if (!poses || !depth || !seg) return invalid("poses/depth/seg pointer is NULL");
   if (ch) {
@@ -428,6 +436,8 @@ ags_status ags_render_ex(ags_context* ctx, const ags_scene* sc, const ags_sensor
   cfg.tile_w = 8;
   cfg.rays_per_lane = 1;
   if ((st = fill_trace_args(ctx, sc, spec, sc->n_envs, nullptr, poses, depth, seg, a, cfg)) != AGS_OK) return st;
+  a.sensor.dirs = table;
+  if (table) a.extra |= 4;
   if (ch) {
     a.out_face = ch->face;
     a.out_bary = ch->bary;
@@ -454,7 +464,7 @@ ags_status ags_render_envs(ags_context* ctx, const ags_scene* sc, const ags_sens
   AGS_API_BEGIN
   if (!ctx || !sc) return invalid("ctx or scene is NULL");
   if (sc->ctx != ctx) return invalid("scene belongs to another context");
-  ags_status st = check_spec(spec);
+  ags_status st = check_spec(spec, false);
   if (st != AGS_OK) return st;
   if (n < 0) return invalid("n < 0");
   if (n > 0 && (!env_ids || !poses || !depth || !seg)) return invalid("env_ids/poses/depth/seg pointer is NULL");
@@ -497,7 +507,7 @@ ags_status ags_render_host(ags_context* ctx, const ags_scene* sc, const ags_sens
   AGS_API_BEGIN
   if (!ctx || !sc) return invalid("ctx or scene is NULL");
   if (sc->ctx != ctx) return invalid("scene belongs to another context");
-  ags_status st = check_spec(spec);
+  ags_status st = check_spec(spec, false);
   if (st != AGS_OK) return st;
   if (!poses_h || !depth_h || !seg_h) return invalid("poses/depth/seg pointer is NULL");
   DeviceGuard g(ctx->device);
@@ -537,7 +547,7 @@ ags_status ags_render_count(ags_context* ctx, const ags_scene* sc, const ags_sen
   AGS_API_BEGIN
   if (!ctx || !sc) return invalid("ctx or scene is NULL");
   if (sc->ctx != ctx) return invalid("scene belongs to another context");
-  ags_status st = check_spec(spec);
+  ags_status st = check_spec(spec, false);
   if (st != AGS_OK) return st;
   if (!poses || !counts_host) return invalid("poses/counts pointer is NULL");
   DeviceGuard g(ctx->device);
@@ -632,7 +642,7 @@ ags_status ags_render_graph_create(ags_context* ctx, const ags_scene* sc, const 
   *out = nullptr;
   if (!ctx || !sc) return invalid("ctx or scene is NULL");
   if (sc->ctx != ctx) return invalid("scene belongs to another context");
-  ags_status st = check_spec(spec);
+  ags_status st = check_spec(spec, false);
   if (st != AGS_OK) return st;
   if (!poses || !depth || !seg) return invalid("poses/depth/seg pointer is NULL");
   DeviceGuard g(ctx->device);
@@ -700,7 +710,7 @@ ags_status ags_set_launch_config(ags_context* ctx, const ags_scene* sc, const ag
   AGS_API_BEGIN
   if (!ctx || !sc) return invalid("ctx or scene is NULL");
   if (sc->ctx != ctx) return invalid("scene belongs to another context");
-  ags_status st = check_spec(spec);
+  ags_status st = check_spec(spec, false);
   if (st != AGS_OK) return st;
   if (!config) {
     sc->launch.erase({spec->type, spec->width, spec->height});
@@ -716,7 +726,7 @@ ags_status ags_get_launch_config(ags_context* ctx, const ags_scene* sc, const ag
                                  ags_launch_config* config) {
   AGS_API_BEGIN
   if (!ctx || !sc || !config) return invalid("ctx, scene or config is NULL");
-  ags_status st = check_spec(spec);
+  ags_status st = check_spec(spec, false);
   if (st != AGS_OK) return st;
   *config = lookup_config(sc, spec);
   return AGS_OK;
@@ -728,7 +738,7 @@ ags_status ags_autotune(ags_context* ctx, const ags_scene* sc, const ags_sensor_
   AGS_API_BEGIN
   if (!ctx || !sc) return invalid("ctx or scene is NULL");
   if (sc->ctx != ctx) return invalid("scene belongs to another context");
-  ags_status st = check_spec(spec);
+  ags_status st = check_spec(spec, false);
   if (st != AGS_OK) return st;
   if (!poses || !depth || !seg || !best) return invalid("poses/depth/seg/best pointer is NULL");
   if (repeats < 1 || repeats > 1000) return invalid("repeats must be in [1, 1000]");

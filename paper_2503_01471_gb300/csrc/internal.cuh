@@ -151,6 +151,7 @@ struct SensorParams {
   float min_range, max_range;
   int32_t tiles_x;           // warp tiles across a row for the launch shape
   int32_t tiles_per_env;     // warp tiles per environment
+  const float* dirs;         // AGS_RAY_TABLE: [H][W][3] sensor-frame directions
 };
 
 // One request of a serving batch (slot mode of the render kernel).
@@ -184,7 +185,7 @@ struct TraceArgs {
   float* out_bary;
   float* out_normal;
   float* out_point;
-  int32_t extra;             // bit 0: hit channels; bit 1: stereo shadow test
+  int32_t extra;             // bit 0: hit channels; bit 1: stereo shadow test; bit 2: ray table
   float baseline[3];         // stereo: second sensor's origin in the sensor frame
   float shadow_eps;          // stereo: the shadow segment starts at this fraction
   int32_t n;                 // environments rendered
@@ -201,6 +202,7 @@ struct TraceArgs {
   unsigned long long* counts;
 };
 cudaError_t launch_trace(const TraceArgs& a, int blocks, bool count, cudaStream_t s);
+cudaError_t launch_trace_extra(const TraceArgs& a, int blocks, cudaStream_t s);  // a.extra != 0
 // compiled launch shapes of the render kernel: {tile width, rays per lane}
 constexpr int kTraceShapes = 5;
 constexpr int kTraceShape[kTraceShapes][2] = {{8, 1}, {4, 1}, {8, 2}, {16, 2}, {16, 4}};

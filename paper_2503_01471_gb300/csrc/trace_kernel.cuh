@@ -1,0 +1,755 @@
+// The render kernel, shared by the translation units that instantiate it.
+// Batched ray casting (Sec. III-D.1: "individual rays are cast outwards
+// per-pixel to evaluate intersection with M_{i,t}"; range vs depth): one
+// persistent launch over every environment's rays. Each warp repeatedly takes
+// an 8x4 tile of pixels (env-major order, so one environment's BVH stays hot
+// in L2 while all SMs work on it), generates the rays in registers, walks the
+// environment's 8-wide BVH with a per-thread stack, tests leaf triangles with
+// a watertight float32 test and writes depth/range and segment ID.
+#pragma once
+#include <cuda_fp16.h>
+
+#include "internal.cuh"
+
+namespace ags {
+
+namespace {
+
+constexpr int kTraceThreads = 128;
+// optional work of the render kernel (template bits)
+constexpr int kExtraChannels = 1;  // face index, barycentrics, normal, sensor-frame point
+constexpr int kExtraShadow = 2;    // stereo shadow test towards a second sensor
+constexpr int kExtraTable = 4;     // sensor-frame directions from a caller's table
+#ifndef AGS_TRACE_MIN_BLOCKS
+#define AGS_TRACE_MIN_BLOCKS 7
+#endif
+constexpr int kTraceMinBlocks = AGS_TRACE_MIN_BLOCKS;  // resident blocks per SM the register budget targets
+constexpr int kStackSize = 64;
+// Box culling is made conservative against float32 rounding: each slab
+// bound is computed as one fma with a per-ray constant that already moves
+// the near bound down and the far bound up by more than the rounding of
+// -o/d, the slab exit is scaled up by (1 + 4u) and the current nearest hit by
+// (1 + 2^-12), so a box holding the eventual nearest triangle is never skipped.
+constexpr float kSlabSlack = 1.0f + 4.0f * 5.96046448e-8f;
+constexpr float kCullSlack = 1.0f + 2.44140625e-4f;
+constexpr float kSlabEps = 4.0f * 5.96046448e-8f;
+
+struct Ray {
+  float ox, oy, oz;
+  float ix, iy, iz;          // 1 / direction
+  float cnx, cny, cnz;       // near-bound constants: -o/d, lowered
+  float cfx, cfy, cfz;       // far-bound constants: -o/d, raised
+  int onx, ony, onz;         // float4 offsets of the near-bound arrays in a node (octant)
+  // watertight test: rows of the shear that maps (v - o) to the ray's frame
+  float m0x, m0y, m0z, m1x, m1y, m1z, m2x, m2y, m2z;
+};
+
+__device__ __forceinline__ float nonzero(float d) {
+  // an exactly-zero direction component is replaced by a tiny one of the same
+  // sign for both the box and the triangle test, keeping them consistent
+  return fabsf(d) < 1e-30f ? copysignf(1e-30f, d) : d;
+}
+
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+__device__ __forceinline__ void setup_ray(Ray& r, float dx, float dy, float dz) {
+  dx = nonzero(dx);
+  dy = nonzero(dy);
+  dz = nonzero(dz);
+  r.ix = 1.0f / dx;
+  r.iy = 1.0f / dy;
+  r.iz = 1.0f / dz;
+  const float px = -r.ox * r.ix, py = -r.oy * r.iy, pz = -r.oz * r.iz;
+  const float ex = kSlabEps * fabsf(px), ey = kSlabEps * fabsf(py), ez = kSlabEps * fabsf(pz);
+  r.cnx = px - ex;
+  r.cfx = px + ex;
+  r.cny = py - ey;
+  r.cfy = py + ey;
+  r.cnz = pz - ez;
+  r.cfz = pz + ez;
+  // node layout (float4 units): header, lox[2], hix[2], loy[2], hiy[2], loz[2], hiz[2]
+  r.onx = r.ix >= 0.0f ? 1 : 3;
+  r.ony = r.iy >= 0.0f ? 5 : 7;
+  r.onz = r.iz >= 0.0f ? 9 : 11;
+  // watertight shear: z axis = largest |d| component, x/y the next two in
+  // cyclic order (swapped when d_z < 0 to keep the winding)
+  const float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
+  const int kz = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
+  int kx = kz == 2 ? 0 : kz + 1;
+  int ky = kx == 2 ? 0 : kx + 1;
+  const float dkz = kz == 0 ? dx : (kz == 1 ? dy : dz);
+  if (dkz < 0.0f) {
+    const int t = kx;
+    kx = ky;
+    ky = t;
+  }
+  const float dkx = kx == 0 ? dx : (kx == 1 ? dy : dz);
+  const float dky = ky == 0 ? dx : (ky == 1 ? dy : dz);
+  const float Sx = dkx / dkz, Sy = dky / dkz, Sz = 1.0f / dkz;
+  r.m0x = (kx == 0 ? 1.0f : 0.0f) - (kz == 0 ? Sx : 0.0f);
+  r.m0y = (kx == 1 ? 1.0f : 0.0f) - (kz == 1 ? Sx : 0.0f);
+  r.m0z = (kx == 2 ? 1.0f : 0.0f) - (kz == 2 ? Sx : 0.0f);
+  r.m1x = (ky == 0 ? 1.0f : 0.0f) - (kz == 0 ? Sy : 0.0f);
+  r.m1y = (ky == 1 ? 1.0f : 0.0f) - (kz == 1 ? Sy : 0.0f);
+  r.m1z = (ky == 2 ? 1.0f : 0.0f) - (kz == 2 ? Sy : 0.0f);
+  r.m2x = kz == 0 ? Sz : 0.0f;
+  r.m2y = kz == 1 ? Sz : 0.0f;
+  r.m2z = kz == 2 ? Sz : 0.0f;
+}
+
+// Watertight ray/triangle test (Woop, Benthin, Wald 2013), two-sided with
+// closed edges. Each vertex is sheared by the same per-ray rows (so a vertex
+// shared by two triangles gets the same coordinates in both), and each edge
+// function is an explicitly rounded difference of two rounded products, so a
+// shared edge gives exactly opposite values in its two triangles and no ray
+// slips between them.
+__device__ __forceinline__ void shear(const Ray& r, const float4 v, float& X, float& Y, float& Z) {
+  const float ax = __fsub_rn(v.x, r.ox), ay = __fsub_rn(v.y, r.oy), az = __fsub_rn(v.z, r.oz);
+  X = __fmaf_rn(r.m0x, ax, __fmaf_rn(r.m0y, ay, __fmul_rn(r.m0z, az)));
+  Y = __fmaf_rn(r.m1x, ax, __fmaf_rn(r.m1y, ay, __fmul_rn(r.m1z, az)));
+  Z = __fmaf_rn(r.m2x, ax, __fmaf_rn(r.m2y, ay, __fmul_rn(r.m2z, az)));
+}
+
+template <bool kChannels>
+__device__ __forceinline__ void test_triangle(const Ray& r, const float4* __restrict__ tris, int32_t k,
+                                              float& t_best, int32_t& best_id, int32_t& best_seg, int32_t& best_k) {
+  const float4 a = __ldg(tris + 3 * (int64_t)k);
+  const float4 b = __ldg(tris + 3 * (int64_t)k + 1);
+  const float4 c = __ldg(tris + 3 * (int64_t)k + 2);
+  float Ax, Ay, Az, Bx, By, Bz, Cx, Cy, Cz;
+  shear(r, a, Ax, Ay, Az);
+  shear(r, b, Bx, By, Bz);
+  shear(r, c, Cx, Cy, Cz);
+  const float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+  const float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+  const float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+  const bool neg = (U < 0.0f) || (V < 0.0f) || (W < 0.0f);
+  const bool pos = (U > 0.0f) || (V > 0.0f) || (W > 0.0f);
+  if (neg && pos) return;
+  const float det = U + V + W;
+  if (det == 0.0f) return;
+  const float T = __fmaf_rn(U, Az, __fmaf_rn(V, Bz, __fmul_rn(W, Cz)));
+  // reject t < 0, and |t| beyond the current best (with slack) before dividing
+  if (T != 0.0f && ((__float_as_uint(T) ^ __float_as_uint(det)) >> 31)) return;
+  const float aT = fabsf(T), adet = fabsf(det);
+  if (aT > t_best * adet * kCullSlack) return;
+  const float t = __fdiv_rn(aT, adet);
+  const int32_t id = __float_as_int(b.w);
+  if (t < t_best || (t == t_best && id < best_id)) {
+    t_best = t;
+    best_id = id;
+    best_seg = __float_as_int(a.w);
+    if constexpr (kChannels) best_k = k;
+  }
+}
+
+// Barycentric weights (of the second and third vertex) of the ray's hit on
+// packed triangle k: the edge functions of the watertight test, recomputed
+// with the same operations, over their sum.
+__device__ __forceinline__ void hit_barycentrics(const Ray& r, const float4* __restrict__ tris, int32_t k, float& u,
+                                                 float& v) {
+  const float4 a = __ldg(tris + 3 * (int64_t)k);
+  const float4 b = __ldg(tris + 3 * (int64_t)k + 1);
+  const float4 c = __ldg(tris + 3 * (int64_t)k + 2);
+  float Ax, Ay, Az, Bx, By, Bz, Cx, Cy, Cz;
+  shear(r, a, Ax, Ay, Az);
+  shear(r, b, Bx, By, Bz);
+  shear(r, c, Cx, Cy, Cz);
+  const float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+  const float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+  const float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+  const float det = U + V + W;
+  u = __fdiv_rn(V, det);
+  v = __fdiv_rn(W, det);
+}
+
+// Unit geometric normal (b - a) x (c - a) of packed triangle k, turned to
+// face the ray (direction d).
+__device__ __forceinline__ void hit_normal(const float4* __restrict__ tris, int32_t k, float dx, float dy, float dz,
+                                           float& nx, float& ny, float& nz) {
+  const float4 a = __ldg(tris + 3 * (int64_t)k);
+  const float4 b = __ldg(tris + 3 * (int64_t)k + 1);
+  const float4 c = __ldg(tris + 3 * (int64_t)k + 2);
+  const float e1x = b.x - a.x, e1y = b.y - a.y, e1z = b.z - a.z;
+  const float e2x = c.x - a.x, e2y = c.y - a.y, e2z = c.z - a.z;
+  nx = e1y * e2z - e1z * e2y;
+  ny = e1z * e2x - e1x * e2z;
+  nz = e1x * e2y - e1y * e2x;
+  float s = rsqrtf(nx * nx + ny * ny + nz * nz);
+  if (nx * dx + ny * dy + nz * dz > 0.0f) s = -s;
+  nx *= s;
+  ny *= s;
+  nz *= s;
+}
+
+// The rays of one warp tile: sensor shape `sen`, environment `env`, tile
+// index t_in within it; `slot` locates the pose and the outputs (the
+// environment's index in the launch, or the request's slot in the table).
+// ---- one wide node: header, and per child the entry distance and whether
+// the ray's slab interval meets [0, t_cull]. Every bound t = b * ix + c is a
+// single fma whose constant is already lowered (near) or raised (far) by more
+// than the rounding of c, as for the float32 node.
+__device__ __forceinline__ void child_test(int k, float tnx, float tfx, float tny, float tfy, float tnz, float tfz,
+                                           float t_cull, float* tmins, uint32_t& hit_mask) {
+  const float tmin = max3f(tnx, tny, fmaxf(tnz, 0.0f));
+  const float tmax = min3f(tfx, tfy, tfz) * kSlabSlack;
+  tmins[k] = tmin;
+  if (tmin <= fminf(tmax, t_cull)) hit_mask |= 1u << k;
+}
+
+// near / far constants of one axis for a node whose bounds are origin + b:
+// c = (origin - o) / d, computed as one fma from the ray's lowered / raised
+// constants, then moved away again by the rounding of that fma
+__device__ __forceinline__ void node_axis(float origin, float inv, float cn_ray, float cf_ray, float& cn, float& cf) {
+  const float n = __fmaf_rn(origin, inv, cn_ray), f = __fmaf_rn(origin, inv, cf_ray);
+  cn = n - kSlabEps * fabsf(n);
+  cf = f + kSlabEps * fabsf(f);
+}
+
+template <int kFmt>
+__device__ __forceinline__ void test_node(const void* __restrict__ nodes, int32_t node, const Ray& r, float t_cull,
+                                          int32_t& child_base, int32_t& tri_base, uint32_t& meta_lo,
+                                          uint32_t& meta_hi, float* tmins, uint32_t& hit_mask) {
+  hit_mask = 0;
+  if constexpr (kFmt == kNodeFp32) {
+    const float4* np = reinterpret_cast<const float4*>(nodes) + (int64_t)node * 13;
+    const float4 h = __ldg(np);
+    child_base = __float_as_int(h.x);
+    tri_base = __float_as_int(h.y);
+    meta_lo = __float_as_uint(h.z);
+    meta_hi = __float_as_uint(h.w);
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const float4 nx4 = __ldg(np + r.onx + half), fx4 = __ldg(np + (4 - r.onx) + half);
+      const float4 ny4 = __ldg(np + r.ony + half), fy4 = __ldg(np + (12 - r.ony) + half);
+      const float4 nz4 = __ldg(np + r.onz + half), fz4 = __ldg(np + (20 - r.onz) + half);
+      const float nxs[4] = {nx4.x, nx4.y, nx4.z, nx4.w}, fxs[4] = {fx4.x, fx4.y, fx4.z, fx4.w};
+      const float nys[4] = {ny4.x, ny4.y, ny4.z, ny4.w}, fys[4] = {fy4.x, fy4.y, fy4.z, fy4.w};
+      const float nzs[4] = {nz4.x, nz4.y, nz4.z, nz4.w}, fzs[4] = {fz4.x, fz4.y, fz4.z, fz4.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        child_test(4 * half + q, __fmaf_rn(nxs[q], r.ix, r.cnx), __fmaf_rn(fxs[q], r.ix, r.cfx),
+                   __fmaf_rn(nys[q], r.iy, r.cny), __fmaf_rn(fys[q], r.iy, r.cfy), __fmaf_rn(nzs[q], r.iz, r.cnz),
+                   __fmaf_rn(fzs[q], r.iz, r.cfz), t_cull, tmins, hit_mask);
+    }
+  } else if constexpr (kFmt == kNodeFp16) {
+    // 128 B: header, origin, then lo_x, hi_x, lo_y, hi_y, lo_z, hi_z as 8 halves each
+    const float4* np = reinterpret_cast<const float4*>(nodes) + (int64_t)node * 8;
+    const float4 h = __ldg(np), org = __ldg(np + 1);
+    child_base = __float_as_int(h.x);
+    tri_base = __float_as_int(h.y);
+    meta_lo = __float_as_uint(h.z);
+    meta_hi = __float_as_uint(h.w);
+    float cnx, cfx, cny, cfy, cnz, cfz;
+    node_axis(org.x, r.ix, r.cnx, r.cfx, cnx, cfx);
+    node_axis(org.y, r.iy, r.cny, r.cfy, cny, cfy);
+    node_axis(org.z, r.iz, r.cnz, r.cfz, cnz, cfz);
+    const int sx = (r.onx >> 1) & 1, sy = (r.ony >> 1) & 1, sz = (r.onz >> 1) & 1;  // 1: negative direction
+    const float4 nx = __ldg(np + 2 + sx), fx = __ldg(np + 3 - sx);
+    const float4 ny = __ldg(np + 4 + sy), fy = __ldg(np + 5 - sy);
+    const float4 nz = __ldg(np + 6 + sz), fz = __ldg(np + 7 - sz);
+    const float nxw[4] = {nx.x, nx.y, nx.z, nx.w}, fxw[4] = {fx.x, fx.y, fx.z, fx.w};
+    const float nyw[4] = {ny.x, ny.y, ny.z, ny.w}, fyw[4] = {fy.x, fy.y, fy.z, fy.w};
+    const float nzw[4] = {nz.x, nz.y, nz.z, nz.w}, fzw[4] = {fz.x, fz.y, fz.z, fz.w};
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const float2 bnx = __half22float2(*reinterpret_cast<const __half2*>(&nxw[w]));
+      const float2 bfx = __half22float2(*reinterpret_cast<const __half2*>(&fxw[w]));
+      const float2 bny = __half22float2(*reinterpret_cast<const __half2*>(&nyw[w]));
+      const float2 bfy = __half22float2(*reinterpret_cast<const __half2*>(&fyw[w]));
+      const float2 bnz = __half22float2(*reinterpret_cast<const __half2*>(&nzw[w]));
+      const float2 bfz = __half22float2(*reinterpret_cast<const __half2*>(&fzw[w]));
+      child_test(2 * w, __fmaf_rn(bnx.x, r.ix, cnx), __fmaf_rn(bfx.x, r.ix, cfx), __fmaf_rn(bny.x, r.iy, cny),
+                 __fmaf_rn(bfy.x, r.iy, cfy), __fmaf_rn(bnz.x, r.iz, cnz), __fmaf_rn(bfz.x, r.iz, cfz), t_cull, tmins,
+                 hit_mask);
+      child_test(2 * w + 1, __fmaf_rn(bnx.y, r.ix, cnx), __fmaf_rn(bfx.y, r.ix, cfx), __fmaf_rn(bny.y, r.iy, cny),
+                 __fmaf_rn(bfy.y, r.iy, cfy), __fmaf_rn(bnz.y, r.iz, cnz), __fmaf_rn(bfz.y, r.iz, cfz), t_cull, tmins,
+                 hit_mask);
+    }
+  } else {
+    // 80 B: origin + per-axis power-of-two scale exponents, header, then per
+    // axis 8 low and 8 high 8-bit bounds: bound = origin + q * 2^(e - 127)
+    const float4* np = reinterpret_cast<const float4*>(nodes) + (int64_t)node * 5;
+    const float4 org = __ldg(np), h = __ldg(np + 1);
+    child_base = __float_as_int(h.x);
+    tri_base = __float_as_int(h.y);
+    meta_lo = __float_as_uint(h.z);
+    meta_hi = __float_as_uint(h.w);
+    const uint32_t ex = __float_as_uint(org.w);
+    const float scx = __uint_as_float((ex & 0xFFu) << 23), scy = __uint_as_float(((ex >> 8) & 0xFFu) << 23),
+                scz = __uint_as_float(((ex >> 16) & 0xFFu) << 23);
+    float cnx, cfx, cny, cfy, cnz, cfz;
+    node_axis(org.x, r.ix, r.cnx, r.cfx, cnx, cfx);
+    node_axis(org.y, r.iy, r.cny, r.cfy, cny, cfy);
+    node_axis(org.z, r.iz, r.cnz, r.cfz, cnz, cfz);
+    const float ax = scx * r.ix, ay = scy * r.iy, az = scz * r.iz;  // exact: powers of two
+    const int sx = (r.onx >> 1) & 1, sy = (r.ony >> 1) & 1, sz = (r.onz >> 1) & 1;
+    const uint4 qx = __ldg(reinterpret_cast<const uint4*>(np + 2));
+    const uint4 qy = __ldg(reinterpret_cast<const uint4*>(np + 3));
+    const uint4 qz = __ldg(reinterpret_cast<const uint4*>(np + 4));
+    // near words: lo (x, y) for a positive direction, hi (z, w) for a negative one
+    const uint32_t nx0 = sx ? qx.z : qx.x, nx1 = sx ? qx.w : qx.y, fx0 = sx ? qx.x : qx.z, fx1 = sx ? qx.y : qx.w;
+    const uint32_t ny0 = sy ? qy.z : qy.x, ny1 = sy ? qy.w : qy.y, fy0 = sy ? qy.x : qy.z, fy1 = sy ? qy.y : qy.w;
+    const uint32_t nz0 = sz ? qz.z : qz.x, nz1 = sz ? qz.w : qz.y, fz0 = sz ? qz.x : qz.z, fz1 = sz ? qz.y : qz.w;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      // byte k of the word as the exact float q: bits 0x4B000000 | q = 2^23 + q
+      const uint32_t sel = 0x7440u | (uint32_t)(k & 3);
+      auto qf = [&](uint32_t w0, uint32_t w1) {
+        return __uint_as_float(__byte_perm(k < 4 ? w0 : w1, 0x4B000000u, sel)) - 8388608.0f;
+      };
+      child_test(k, __fmaf_rn(qf(nx0, nx1), ax, cnx), __fmaf_rn(qf(fx0, fx1), ax, cfx),
+                 __fmaf_rn(qf(ny0, ny1), ay, cny), __fmaf_rn(qf(fy0, fy1), ay, cfy),
+                 __fmaf_rn(qf(nz0, nz1), az, cnz), __fmaf_rn(qf(fz0, fz1), az, cfz), t_cull, tmins, hit_mask);
+    }
+  }
+}
+
+// Any-hit test of packed triangle k against the segment o + t d, t in
+// [t0, 1] (the same watertight arithmetic as test_triangle).
+__device__ __forceinline__ bool segment_hits(const Ray& r, const float4* __restrict__ tris, int32_t k, float t0) {
+  const float4 a = __ldg(tris + 3 * (int64_t)k);
+  const float4 b = __ldg(tris + 3 * (int64_t)k + 1);
+  const float4 c = __ldg(tris + 3 * (int64_t)k + 2);
+  float Ax, Ay, Az, Bx, By, Bz, Cx, Cy, Cz;
+  shear(r, a, Ax, Ay, Az);
+  shear(r, b, Bx, By, Bz);
+  shear(r, c, Cx, Cy, Cz);
+  const float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+  const float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+  const float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+  const bool neg = (U < 0.0f) || (V < 0.0f) || (W < 0.0f);
+  const bool pos = (U > 0.0f) || (V > 0.0f) || (W > 0.0f);
+  if (neg && pos) return false;
+  const float det = U + V + W;
+  if (det == 0.0f) return false;
+  const float T = __fmaf_rn(U, Az, __fmaf_rn(V, Bz, __fmul_rn(W, Cz)));
+  if (T != 0.0f && ((__float_as_uint(T) ^ __float_as_uint(det)) >> 31)) return false;
+  const float t = __fdiv_rn(fabsf(T), fabsf(det));
+  return t >= t0 && t <= 1.0f;
+}
+
+// Stereo shadow (Sec. III-D.1): does any triangle of environment env meet
+// the segment from P to the second sensor, o = P, d = o2 - P, t in [t0, 1]?
+// The traversal stops at the first such triangle; children are visited in
+// slot order. Limits set the status word and `failed`.
+template <int kFmt>
+__device__ bool occluded(const TraceArgs& a, int32_t env, float px, float py, float pz, float dx, float dy, float dz,
+                         float t0, int2* stack, bool& failed) {
+  Ray r;
+  r.ox = px;
+  r.oy = py;
+  r.oz = pz;
+  setup_ray(r, dx, dy, dz);
+  int32_t node = __ldg(a.env_root + env);
+  int sp = 0, visits = 0;
+  const float t_cull = kCullSlack;
+  while (node >= 0) {
+    if (++visits > a.max_visits) {
+      atomicOr(a.status, kStatusIterationCap);
+      failed = true;
+      return false;
+    }
+    if (node >= a.n_nodes) {
+      atomicOr(a.status, kStatusBadIndex);
+      failed = true;
+      return false;
+    }
+    int32_t child_base, tri_base;
+    uint32_t meta_lo, meta_hi, hit_mask;
+    float tmins[8];
+    test_node<kFmt>(a.nodes, node, r, t_cull, child_base, tri_base, meta_lo, meta_hi, tmins, hit_mask);
+    const uint32_t b0 = meta_lo & 0xFFu;
+    const int ni = (b0 & 0x80u) ? (int)min(b0 & 0xFu, 8u) : 0;
+    const uint32_t inner_bits = (1u << ni) - 1u;
+    uint32_t leaf_mask = hit_mask & ~inner_bits;
+    uint32_t inner_hits = hit_mask & inner_bits;
+    while (leaf_mask) {
+      const int k = __ffs(leaf_mask) - 1;
+      leaf_mask &= leaf_mask - 1;
+      const uint32_t m = ((k < 4 ? meta_lo : meta_hi) >> (8 * (k & 3))) & 0xFFu;
+      if (m == kMetaEmpty) continue;
+      const int32_t start = tri_base + (int32_t)(m >> 2);
+      const int32_t cnt = (int32_t)(m & 3u) + 1;
+      if (start < 0 || start + cnt > a.n_tris) {
+        atomicOr(a.status, kStatusBadIndex);
+        failed = true;
+        return false;
+      }
+      for (int32_t x = 0; x < cnt; ++x)
+        if (segment_hits(r, a.tris, start + x, t0)) return true;
+    }
+    node = -1;
+    if (inner_hits) {
+      node = child_base + (__ffs(inner_hits) - 1);
+      inner_hits &= inner_hits - 1;
+      while (inner_hits) {
+        if (sp >= kStackSize) {
+          atomicOr(a.status, kStatusStackOverflow);
+          failed = true;
+          return false;
+        }
+        stack[sp++] = make_int2(child_base + (__ffs(inner_hits) - 1), 0);
+        inner_hits &= inner_hits - 1;
+      }
+    } else if (sp > 0) {
+      node = stack[--sp].x;
+    }
+  }
+  return false;
+}
+
+// a3: the sensor-frame direction of pixel / beam (row, col). Camera: the
+// unnormalised (1, a, b) through the pixel centre, so the distance along it
+// is the depth itself; LiDAR: the unit beam direction (distance = range);
+// ray table: the caller's row as given (distance in units of its length).
+template <bool kTable>
+__device__ __forceinline__ void sensor_dir(const SensorParams& sen, int32_t row, int32_t col, float& lx, float& ly,
+                                           float& lz) {
+  if constexpr (kTable) {
+    const float* g = sen.dirs + 3 * ((int64_t)row * sen.W + col);
+    lx = __ldg(g);
+    ly = __ldg(g + 1);
+    lz = __ldg(g + 2);
+  } else if (sen.type == AGS_PINHOLE) {
+    lx = 1.0f;
+    ly = __fmul_rn(0.5f * (float)sen.W - ((float)col + 0.5f), sen.inv_f);  // the difference is exact
+    lz = __fmul_rn(0.5f * (float)sen.H - ((float)row + 0.5f), sen.inv_f);
+  } else {
+    float sin_el, cos_el, sin_az, cos_az;
+    sincosf(sen.vmax - (float)row * sen.dv, &sin_el, &cos_el);
+    sincosf(sen.hfov * ((float)col / (float)sen.W), &sin_az, &cos_az);
+    lx = cos_el * cos_az;
+    ly = cos_el * sin_az;
+    lz = sin_el;
+  }
+}
+
+template <bool kSlots>
+__device__ __forceinline__ const float* slot_pose(const TraceArgs& a, int32_t slot) {
+  if constexpr (kSlots) return a.slots[slot].pose;
+  else return a.poses + 7 * (int64_t)slot;
+}
+template <bool kSlots>
+__device__ __forceinline__ int64_t slot_out(const TraceArgs& a, const SensorParams& sen, int32_t slot) {
+  if constexpr (kSlots) return __ldg(&a.slots[slot].out_offset);
+  else return (int64_t)slot * sen.H * sen.W;
+}
+
+template <bool kCount, int kTileW, int kRaysPerLane, bool kSlots, int kFmt, int kExtra>
+__device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParams& sen, int32_t env, int32_t t_in,
+                                           int32_t slot, int lane, int2* stack, unsigned long long& n_nodes,
+                                           unsigned long long& n_tris, unsigned long long& n_rays) {
+  constexpr int kTileH = 32 * kRaysPerLane / kTileW;
+  int32_t* __restrict__ status = a.status;
+  const int32_t tile_x0 = (t_in % sen.tiles_x) * kTileW;
+  const int32_t tile_y0 = (t_in / sen.tiles_x) * kTileH;
+
+  for (int rr = 0; rr < kRaysPerLane; ++rr) {
+  const int idx = rr * 32 + lane;
+  const int32_t col = tile_x0 + (idx % kTileW);
+  const int32_t row = tile_y0 + (idx / kTileW);
+  const int32_t W = sen.W, H = sen.H;
+  if (col >= W || row >= H) continue;
+
+  // ---- a3: ray generation from the sensor pose (p, q); recomputed per ray
+  // (L1-resident) so that nothing of it stays live during the traversal
+  const float* P = slot_pose<kSlots>(a, slot);
+  const float px = __ldg(P), py = __ldg(P + 1), pz = __ldg(P + 2);
+  const float qx = __ldg(P + 3), qy = __ldg(P + 4), qz = __ldg(P + 5), qw = __ldg(P + 6);
+  const float n2 = qx * qx + qy * qy + qz * qz + qw * qw;
+  if (!(n2 >= 1e-30f) || !isfinite(n2) || !isfinite(px + py + pz)) {
+    // a pose the method cannot use: flag it and report NaN for this ray
+    atomicOr(status, kStatusBadPose);
+    if (!kCount) {
+      const int64_t o = slot_out<kSlots>(a, sen, slot) + (int64_t)row * W + col;
+      a.out_depth[o] = __int_as_float(0x7fc00000);
+      a.out_seg[o] = -1;
+    }
+    continue;
+  }
+  const float s = 2.0f / n2;
+  const float R00 = 1.0f - s * (qy * qy + qz * qz), R01 = s * (qx * qy - qz * qw), R02 = s * (qx * qz + qy * qw);
+  const float R10 = s * (qx * qy + qz * qw), R11 = 1.0f - s * (qx * qx + qz * qz), R12 = s * (qy * qz - qx * qw);
+  const float R20 = s * (qx * qz - qy * qw), R21 = s * (qy * qz + qx * qw), R22 = 1.0f - s * (qx * qx + qy * qy);
+  float lx, ly, lz;
+  sensor_dir<(kExtra & kExtraTable) != 0>(sen, row, col, lx, ly, lz);
+  if ((kExtra & kExtraTable) != 0 && (!isfinite(lx + ly + lz) || (lx == 0.0f && ly == 0.0f && lz == 0.0f))) {
+    // a table row the method cannot cast: flagged like an unusable pose
+    atomicOr(status, kStatusBadPose);
+    if (!kCount) {
+      const int64_t o = slot_out<kSlots>(a, sen, slot) + (int64_t)row * W + col;
+      a.out_depth[o] = __int_as_float(0x7fc00000);
+      a.out_seg[o] = -1;
+    }
+    continue;
+  }
+  Ray r;
+  r.ox = px;
+  r.oy = py;
+  r.oz = pz;
+  // world direction R l with explicitly rounded operations: the same bits
+  // whether l comes from the camera model (lx = 1 folded) or from a table
+  setup_ray(r, __fmaf_rn(R02, lz, __fmaf_rn(R01, ly, __fmul_rn(R00, lx))),
+            __fmaf_rn(R12, lz, __fmaf_rn(R11, ly, __fmul_rn(R10, lx))),
+            __fmaf_rn(R22, lz, __fmaf_rn(R21, ly, __fmul_rn(R20, lx))));
+
+  // ---- a4-a6: traversal, triangle tests, nearest hit
+  float t_best = sen.max_range;  // camera: depth limit; LiDAR: range limit (unit direction)
+  int32_t best_id = 0x7fffffff, best_seg = -1, best_k = -1;
+  int32_t node = __ldg(a.env_root + env);
+  int sp = 0, visits = 0;
+  bool failed = false;
+  while (node >= 0) {
+    if (++visits > a.max_visits) {
+      atomicOr(status, kStatusIterationCap);
+      failed = true;
+      break;
+    }
+    if (node >= a.n_nodes) {
+      atomicOr(status, kStatusBadIndex);
+      failed = true;
+      break;
+    }
+    if (kCount) ++n_nodes;
+    const float t_cull = t_best * kCullSlack;
+    int32_t child_base, tri_base;
+    uint32_t meta_lo, meta_hi;
+    float tmins[8];
+    uint32_t hit_mask;
+    test_node<kFmt>(a.nodes, node, r, t_cull, child_base, tri_base, meta_lo, meta_hi, tmins, hit_mask);
+    const uint32_t b0 = meta_lo & 0xFFu;
+    const int ni = (b0 & 0x80u) ? (int)min(b0 & 0xFu, 8u) : 0;
+    const uint32_t inner_bits = (1u << ni) - 1u;
+    uint32_t leaf_mask = hit_mask & ~inner_bits;
+    const uint32_t inner_hits = hit_mask & inner_bits;
+    // leaves of this node first: they tighten t_best before descending
+    while (leaf_mask) {
+      const int k = __ffs(leaf_mask) - 1;
+      leaf_mask &= leaf_mask - 1;
+      const uint32_t m = ((k < 4 ? meta_lo : meta_hi) >> (8 * (k & 3))) & 0xFFu;
+      if (m == kMetaEmpty) continue;
+      const int32_t start = tri_base + (int32_t)(m >> 2);
+      const int32_t cnt = (int32_t)(m & 3u) + 1;
+      if (start < 0 || start + cnt > a.n_tris) {
+        atomicOr(status, kStatusBadIndex);
+        failed = true;
+        break;
+      }
+      for (int32_t x = 0; x < cnt; ++x)
+        test_triangle<(kExtra & kExtraChannels) != 0>(r, a.tris, start + x, t_best, best_id, best_seg, best_k);
+      if (kCount) n_tris += cnt;
+    }
+    if (failed) break;
+    const int n_inner = __popc(inner_hits);
+    if (n_inner == 1) {  // the common case: no ordering needed
+      node = child_base + (__ffs(inner_hits) - 1);
+      continue;
+    }
+    if (n_inner > 1) {
+      // nearest first (sorting network on keys: tmin bits with the slot in the low 3 bits)
+      uint32_t keys[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        keys[k] = ((inner_hits >> k) & 1u) ? ((__float_as_uint(tmins[k]) & ~7u) | (uint32_t)k) : 0xFFFFFFFFu;
+#define AGS_CSWAP(i, j)                         \
+  {                                             \
+  const uint32_t lo_ = min(keys[i], keys[j]); \
+  const uint32_t hi_ = max(keys[i], keys[j]); \
+  keys[i] = lo_;                              \
+  keys[j] = hi_;                              \
+  }
+      AGS_CSWAP(0, 1) AGS_CSWAP(2, 3) AGS_CSWAP(4, 5) AGS_CSWAP(6, 7)
+      AGS_CSWAP(0, 2) AGS_CSWAP(1, 3) AGS_CSWAP(4, 6) AGS_CSWAP(5, 7)
+      AGS_CSWAP(1, 2) AGS_CSWAP(5, 6) AGS_CSWAP(0, 4) AGS_CSWAP(3, 7)
+      AGS_CSWAP(1, 5) AGS_CSWAP(2, 6)
+      AGS_CSWAP(1, 4) AGS_CSWAP(3, 6)
+      AGS_CSWAP(2, 4) AGS_CSWAP(3, 5)
+      AGS_CSWAP(3, 4)
+#undef AGS_CSWAP
+      const uint32_t key_cull = __float_as_uint(t_best * kCullSlack);
+#pragma unroll
+      for (int k = 7; k >= 1; --k) {
+        if (keys[k] != 0xFFFFFFFFu && (keys[k] & ~7u) <= key_cull) {
+          if (sp >= kStackSize) {
+            atomicOr(status, kStatusStackOverflow);
+            failed = true;
+          } else {
+            stack[sp++] = make_int2(child_base + (int32_t)(keys[k] & 7u), (int32_t)(keys[k] & ~7u));
+          }
+        }
+      }
+      if (failed) break;
+      if ((keys[0] & ~7u) <= key_cull) {
+        node = child_base + (int32_t)(keys[0] & 7u);
+        continue;
+      }
+    }
+    node = -1;
+    const float t_pop = t_best * kCullSlack;
+    while (sp > 0) {
+      const int2 e = stack[--sp];
+      if (__int_as_float(e.y) <= t_pop) {
+        node = e.x;
+        break;
+      }
+    }
+  }
+
+  if (kCount) {
+    ++n_rays;
+    continue;
+  }
+  float v;
+  int32_t seg;
+  if (failed) {
+    v = __int_as_float(0x7fc00000);
+    seg = -1;
+  } else if (best_id != 0x7fffffff) {
+    v = t_best;
+    seg = best_seg;
+    if (v < sen.min_range) {
+      if (sen.near_mode == AGS_NEAR_CLAMP) {
+        v = sen.min_range;
+      } else {
+        v = sen.max_range;
+        seg = -1;
+      }
+    }
+  } else {
+    v = sen.max_range;
+    seg = -1;
+  }
+  if constexpr ((kExtra & kExtraShadow) != 0) {
+    if (!failed && seg >= 0) {
+      // the hit point P and the second sensor o2 = p + R b, both in the world
+      float sx, sy, sz;
+      sensor_dir<(kExtra & kExtraTable) != 0>(sen, row, col, sx, sy, sz);
+      const float dwx = __fmaf_rn(R02, sz, __fmaf_rn(R01, sy, __fmul_rn(R00, sx))),
+                  dwy = __fmaf_rn(R12, sz, __fmaf_rn(R11, sy, __fmul_rn(R10, sx))),
+                  dwz = __fmaf_rn(R22, sz, __fmaf_rn(R21, sy, __fmul_rn(R20, sx)));
+      const float Px = px + t_best * dwx, Py = py + t_best * dwy, Pz = pz + t_best * dwz;
+      const float bx = a.baseline[0], by = a.baseline[1], bz = a.baseline[2];
+      const float o2x = px + (R00 * bx + R01 * by + R02 * bz), o2y = py + (R10 * bx + R11 * by + R12 * bz),
+                  o2z = pz + (R20 * bx + R21 * by + R22 * bz);
+      bool sfail = false;
+      const bool shadowed =
+          occluded<kFmt>(a, env, Px, Py, Pz, o2x - Px, o2y - Py, o2z - Pz, a.shadow_eps, stack, sfail);
+      if (sfail) {
+        failed = true;
+        v = __int_as_float(0x7fc00000);
+        seg = -1;
+      } else if (shadowed) {
+        v = sen.max_range;
+        seg = -1;
+      }
+    }
+  }
+  const int64_t o = slot_out<kSlots>(a, sen, slot) + (int64_t)row * W + col;
+  a.out_depth[o] = v;
+  a.out_seg[o] = seg;
+  if constexpr ((kExtra & kExtraChannels) != 0) {
+    // extra hit channels of the reported hit (a miss or a near hit reported
+    // as invalid: face -1, zero weights and normal)
+    const float nan = __int_as_float(0x7fc00000);
+    int32_t face = failed ? -1 : (seg >= 0 ? best_id : -1);
+    float bu = failed ? nan : 0.0f, bv = bu, nx = bu, ny = bu, nz = bu;
+    if (face >= 0 && best_k >= 0) {
+      hit_barycentrics(r, a.tris, best_k, bu, bv);
+      hit_normal(a.tris, best_k, __frcp_rn(r.ix), __frcp_rn(r.iy), __frcp_rn(r.iz), nx, ny, nz);
+    }
+    if (a.out_face) a.out_face[o] = face;
+    if (a.out_bary) {
+      a.out_bary[2 * o] = bu;
+      a.out_bary[2 * o + 1] = bv;
+    }
+    if (a.out_normal) {
+      a.out_normal[3 * o] = nx;
+      a.out_normal[3 * o + 1] = ny;
+      a.out_normal[3 * o + 2] = nz;
+    }
+    if (a.out_point) {
+      // the hit in the sensor frame: reported value along the sensor-frame direction
+      sensor_dir<(kExtra & kExtraTable) != 0>(sen, row, col, lx, ly, lz);
+      a.out_point[3 * o] = v * lx;
+      a.out_point[3 * o + 1] = v * ly;
+      a.out_point[3 * o + 2] = v * lz;
+    }
+  }
+  }  // rays of this lane in the tile
+}
+
+// kSlots: each tile belongs to one slot of a table (serving: every request has
+// its own environment, sensor shape, pose and output offset); otherwise all
+// environments of the launch share one sensor shape.
+template <bool kCount, int kTileW, int kRaysPerLane, bool kSlots, int kFmt, int kExtra = 0>
+__global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) k_trace(const TraceArgs a) {
+  const int lane = threadIdx.x & 31;
+  int2 stack[kStackSize];
+  unsigned long long n_nodes = 0, n_tris = 0, n_rays = 0;
+
+  while (true) {
+    unsigned int tile = 0;
+    if (lane == 0) tile = atomicAdd(a.tile_counter, 1u);
+    tile = __shfl_sync(0xffffffffu, tile, 0);
+    if ((int64_t)tile >= a.total_tiles) break;
+    int32_t env, t_in, slot, slot_spec = 0;
+    if constexpr (kSlots) {
+      // the slot holding this tile: last slot whose first tile is <= tile
+      int32_t lo = 0, hi = a.n_slots - 1;
+      while (lo < hi) {
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if ((unsigned)__ldg(&a.slots[mid].tile_begin) <= tile) lo = mid; else hi = mid - 1;
+      }
+      slot = lo;
+      env = __ldg(&a.slots[lo].env);
+      slot_spec = __ldg(&a.slots[lo].spec);
+      if ((unsigned)slot_spec >= (unsigned)a.n_specs) {
+        if (lane == 0) atomicOr(a.status, kStatusBadIndex);
+        continue;
+      }
+      t_in = (int32_t)(tile - (unsigned)__ldg(&a.slots[lo].tile_begin));
+    } else {
+      slot = (int32_t)(tile / (unsigned)a.sensor.tiles_per_env);
+      t_in = (int32_t)(tile - (unsigned)slot * (unsigned)a.sensor.tiles_per_env);
+      env = a.env_ids ? __ldg(a.env_ids + slot) : slot;
+    }
+    if ((unsigned)env >= (unsigned)a.n_scene_envs) {
+      if (lane == 0) atomicOr(a.status, kStatusBadIndex);
+      continue;
+    }
+    if constexpr (kSlots) {
+      trace_tile<kCount, kTileW, kRaysPerLane, true, kFmt, kExtra>(a, a.specs[slot_spec], env, t_in, slot, lane,
+                                                                   stack, n_nodes, n_tris, n_rays);
+    } else {
+      trace_tile<kCount, kTileW, kRaysPerLane, false, kFmt, kExtra>(a, a.sensor, env, t_in, slot, lane, stack,
+                                                                    n_nodes, n_tris, n_rays);
+    }
+  }
+  if (kCount) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      n_nodes += __shfl_xor_sync(0xffffffffu, n_nodes, o);
+      n_tris += __shfl_xor_sync(0xffffffffu, n_tris, o);
+      n_rays += __shfl_xor_sync(0xffffffffu, n_rays, o);
+    }
+    if (lane == 0) {
+      atomicAdd(a.counts, n_rays);
+      atomicAdd(a.counts + 1, n_nodes);
+      atomicAdd(a.counts + 2, n_tris);
+    }
+  }
+}
+
+}  // namespace
+
+}  // namespace ags

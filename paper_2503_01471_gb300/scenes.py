@@ -138,6 +138,31 @@ def lidar(azimuth_bins=512, channels=64, vfov_deg=(-22.5, 22.5), min_range=0.3,
                       math.radians(vfov_deg[0]), math.radians(vfov_deg[1]), near_mode)
 
 
+def dome_lidar(azimuth_bins=512, channels=64, min_range=0.3, max_range=50.0):
+    """Hemispherical dome LiDAR: channels from the horizon (0 deg) to the zenith (90 deg) all around."""
+    return lidar(azimuth_bins, channels, (0.0, 90.0), min_range, max_range)
+
+
+def ray_table_spec(width, height, min_range=0.2, max_range=10.0, near_mode=0):
+    """Sensor spec of a user projection model; its directions come from a separate table."""
+    return SensorSpec(2, width, height, 0.0, min_range, max_range, near_mode=near_mode)
+
+
+def fisheye_table(width, height, fov_deg=180.0):
+    """Equidistant fisheye (image radius proportional to the angle off the +x optical axis), unit
+    sensor-frame rows [height, width, 3]; pixels beyond the image circle look along its rim."""
+    half = math.radians(fov_deg) / 2
+    cx, cy = width / 2.0, height / 2.0
+    rad = min(cx, cy)
+    cols, rows = np.meshgrid(np.arange(width) + 0.5, np.arange(height) + 0.5)
+    u, v = (cx - cols) / rad, (cy - rows) / rad  # +u left (+y), +v up (+z)
+    r = np.hypot(u, v)
+    theta = np.minimum(r, 1.0) * half
+    phi = np.arctan2(v, u)
+    out = np.stack([np.cos(theta), np.sin(theta) * np.cos(phi), np.sin(theta) * np.sin(phi)], -1)
+    return np.ascontiguousarray(out, np.float32)
+
+
 # ---------------------------------------------------------------- primitives
 IDENTITY_POSE = np.array([0, 0, 0, 0, 0, 0, 1], np.float32)
 

@@ -47,6 +47,12 @@ def describe_failures(ok, res, depth, seg, rays, limit=5):
 U32 = 2.0 ** -24  # unit roundoff of float32
 
 
+def check_channels_sensor(tris, s, pose64, res, seg, depth, ch, e, rays, detail=None):
+    """check_channels for an explicit oracle scene and sensor (channel arrays ``ch`` [E, ...], env e)."""
+    return _check_channels(tris, s, pose64, res, seg, depth, ch["face"][e], ch["bary"][e], ch["normal"][e],
+                           ch["point"][e], rays, detail)
+
+
 def check_channels(batch, e, spec, pose, res, seg, depth, face, bary, normal, point, rays, detail=None):
     """Element-wise acceptance of the extra hit channels of env e on the listed rays (flat [H*W] inputs);
     ``res`` is the oracle's result for the same rays. Returns a bool array.
@@ -65,8 +71,11 @@ def check_channels(batch, e, spec, pose, res, seg, depth, face, bary, normal, po
     ``detail`` (a dict) receives each check's pass mask and the errors, for failure reports.
     """
     tris, _ = oracle_env(batch, e)
-    s = oracle_sensor(spec)
-    pose64 = np.asarray(pose, np.float32).astype(np.float64)
+    return _check_channels(tris, oracle_sensor(spec), np.asarray(pose, np.float32).astype(np.float64), res, seg,
+                           depth, face, bary, normal, point, rays, detail)
+
+
+def _check_channels(tris, s, pose64, res, seg, depth, face, bary, normal, point, rays, detail):
     g = np.asarray(seg).reshape(-1)[rays]
     v = np.asarray(depth, np.float32).reshape(-1)[rays].astype(np.float64)
     f = np.asarray(face).reshape(-1)[rays]

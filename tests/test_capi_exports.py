@@ -43,6 +43,7 @@ def test_struct_layouts_match_the_header():
     assert ctypes.sizeof(ags.ags_sensor_spec) == 40
     assert ctypes.sizeof(ags.ags_hit_channels) == 32
     assert ctypes.sizeof(ags.ags_stereo) == 16
+    assert ctypes.sizeof(ags.ags_render_options) == 24
 
 
 def test_null_arguments_are_rejected_without_a_device(lib):

@@ -6,6 +6,8 @@ max_range with segment -1; segment IDs exact. Rays where several outcomes are
 correct within the float32 error bands (edges, near ties, range limits) must
 match one of the outcomes the oracle lists for them, and are counted.
 """
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -15,7 +17,8 @@ import paper_2503_01471_gb300 as ags
 from paper_2503_01471_gb300 import build as B
 from paper_2503_01471_gb300 import scenes as S
 
-from helpers import check_channels, compare_env, describe_channel_failures, describe_failures, oracle_env, oracle_sensor
+from helpers import (check_channels, check_channels_sensor, compare_env, describe_channel_failures, describe_failures,
+                     oracle_env, oracle_sensor)
 
 pytestmark = pytest.mark.gpu
 
@@ -614,5 +617,83 @@ def test_stereo_zero_baseline_shadows_nothing_and_bad_args(ctx):
         for bad in (dict(baseline=(float("nan"), 0, 0)), dict(baseline=(0, 0.1, 0), eps=1.5)):
             with pytest.raises(ags.AgsError):
                 ags.ags_render_ex(ctx, scene, spec, p, d, sg, **bad)
+    finally:
+        ags.ags_scene_destroy(scene)
+
+
+# ---------------------------------------------------------------- user projection models
+def test_ray_table_of_camera_rows_is_bit_identical_to_the_camera(ctx):
+    """A table holding the camera's own float32 (1, a, b) rows renders bit-identically to the camera."""
+    batch, spec, poses = S.obstacle_rooms(2, steps=1, width=37, height=23)
+    scene = ags.ags_scene_build(ctx, batch)
+    try:
+        d0, s0 = render(ctx, scene, spec, poses[0])
+        W, H = spec.width, spec.height
+        inv_f = np.float32(math.tan(0.5 * float(np.float32(spec.hfov))) / (0.5 * W))
+        col = np.arange(W, dtype=np.float32)[None, :]
+        row = np.arange(H, dtype=np.float32)[:, None]
+        ly = (np.float32(0.5) * np.float32(W) - (col + np.float32(0.5))) * inv_f
+        lz = (np.float32(0.5) * np.float32(H) - (row + np.float32(0.5))) * inv_f
+        table = np.stack(np.broadcast_arrays(np.ones((H, W), np.float32), ly, lz), -1).astype(np.float32)
+        tspec = S.ray_table_spec(W, H, spec.min_range, spec.max_range)
+        p = torch.as_tensor(poses[0]).cuda()
+        d = torch.empty((2, H, W), device="cuda")
+        sg = torch.empty((2, H, W), dtype=torch.int32, device="cuda")
+        ags.ags_render_ex(ctx, scene, tspec, p, d, sg, ray_table=torch.as_tensor(table).cuda())
+        ags.ags_stream_status(ctx)
+        assert np.array_equal(d.cpu().numpy(), d0) and np.array_equal(sg.cpu().numpy(), s0)
+        with pytest.raises(ags.AgsError):  # a ray-table spec without its table
+            ags.ags_render(ctx, scene, tspec, p, d, sg)
+        with pytest.raises(ags.AgsError):  # a table for a camera spec
+            ags.ags_render_ex(ctx, scene, spec, p, d, sg, ray_table=torch.as_tensor(table).cuda())
+    finally:
+        ags.ags_scene_destroy(scene)
+
+
+@pytest.mark.parametrize("model", ["fisheye", "dome", "random"])
+def test_user_projection_models_match_oracle(ctx, model):
+    """A 180-degree equidistant fisheye, a dome LiDAR and random scaled rows against the FP64 oracle on
+    every ray (with extra channels)."""
+    batch, _, poses = S.obstacle_rooms(2, steps=1, width=8, height=8)
+    W, H = 48, 32
+    if model == "fisheye":
+        table = S.fisheye_table(W, H, 180.0)
+        spec = S.ray_table_spec(W, H, 0.2, 10.0)
+    elif model == "random":
+        rng = np.random.default_rng(24)
+        table = (rng.normal(size=(H, W, 3)) * rng.uniform(0.3, 3.0, (H, W, 1))).astype(np.float32)
+        spec = S.ray_table_spec(W, H, 0.05, 8.0)
+    else:
+        table = None
+        spec = S.dome_lidar(W, H, 0.2, 12.0)
+    scene = ags.ags_scene_build(ctx, batch)
+    try:
+        p = torch.as_tensor(poses[0]).cuda()
+        d = torch.empty((2, H, W), device="cuda")
+        sg = torch.empty((2, H, W), dtype=torch.int32, device="cuda")
+        ch = {"face": torch.empty((2, H, W), dtype=torch.int32, device="cuda"),
+              "bary": torch.empty((2, H, W, 2), device="cuda"), "normal": torch.empty((2, H, W, 3), device="cuda"),
+              "point": torch.empty((2, H, W, 3), device="cuda")}
+        ags.ags_render_ex(ctx, scene, spec, p, d, sg, ray_table=None if table is None else torch.as_tensor(table).cuda(),
+                          **ch)
+        ags.ags_stream_status(ctx)
+        d, sg = d.cpu().numpy(), sg.cpu().numpy()
+        ch = {k: v.cpu().numpy() for k, v in ch.items()}
+        rays = np.arange(W * H, dtype=np.int64)
+        for e in range(2):
+            tris, tseg = oracle_env(batch, e)
+            s = oracle_sensor(spec)
+            if table is not None:
+                s.dirs = table.astype(np.float64)
+            pose64 = np.asarray(poses[0][e], np.float32).astype(np.float64)
+            res = O.render(tris, tseg, s, pose64, rays)
+            ok, counted, strict = O.check(res, d[e].reshape(-1), sg[e].reshape(-1), s.max_range, with_strict=True)
+            assert ok.all(), describe_failures(ok, res, d[e].reshape(-1), sg[e].reshape(-1), rays)
+            det = {}
+            okc = check_channels_sensor(tris, s, pose64, res, sg[e], d[e], ch, e, rays, det)
+            assert okc.all(), describe_channel_failures(okc, det, res, ch["face"][e].reshape(-1),
+                                                        ch["bary"][e].reshape(-1, 2), ch["normal"][e].reshape(-1, 3))
+            print(f"[parity] {model} {H}x{W}: {W * H} rays, {int(counted.sum())} counted, "
+                  f"{int((~strict & ~counted).sum())} beyond strict")
     finally:
         ags.ags_scene_destroy(scene)
