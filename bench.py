@@ -36,9 +36,10 @@ WORKLOADS = {
     "serving": {"envs": 8192, "metric": "served Mrays/s, 8192 rooms of 1k-200k triangles, mixed sensors; p50/p99 ms"},
     "precision": {"envs": 4096, "metric": "Mrays/s at 4096 rooms x 135x240 per BVH node format; depth error vs FP64"},
     "dynamic": {"envs": 1024, "metric": "ms per obstacle-pose update (refit vs rebuild), 1024 rooms; render Mrays/s"},
+    "features": {"envs": 1024, "metric": "Mrays/s at 1024 rooms per sensor feature (hit channels, stereo, projection models)"},
 }
 PAPER_MRAYS = 340.5  # Table II, 1024 envs x 270x480 (RTX 3090; context)
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "k_trace_rooms_1024x270x480_traffic.md")
 
 
 def parse():
@@ -91,15 +92,17 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload):
-    """DRAM bytes per launch of the trace kernel from a committed ncu summary, if it matches this source."""
+def profiled_traffic(workload, kernel):
+    """DRAM bytes per launch of the render kernel from the committed ncu summary, if its row matches this
+    workload, this kernel instance and the current kernel source; else None."""
     try:
         with open(PROFILE_TRAFFIC) as fh:
-            d = json.load(fh)
-        ent = d.get(workload)
-        if ent and ent.get("kernel_hash") == kernel_source_hash():
-            return float(ent["dram_bytes_per_launch"])
-    except Exception:
+            for line in fh:
+                cells = [c.strip() for c in line.strip().strip("|").split("|")]
+                if len(cells) == 7 and cells[0] == workload and cells[1] == kernel \
+                        and cells[2] == kernel_source_hash():
+                    return float(cells[5])
+    except (OSError, ValueError):
         pass
     return None
 
@@ -444,6 +447,92 @@ def bench_dynamic(args, rank, world, local):
     ags.ags_context_destroy(ctx)
 
 
+# ---------------------------------------------------------------- sensor features
+def bench_features(args, rank, world, local):
+    """Cost of the extra sensor features on the 1024-room scene: hit channels, stereo shadows, a fisheye
+    ray table, a dome LiDAR and the 848x480 navigation-task camera, each against the plain render."""
+    import torch
+
+    import paper_2503_01471_gb300 as ags
+    from paper_2503_01471_gb300 import build as B
+    from paper_2503_01471_gb300 import scenes as S
+
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    batch, spec, poses = S.obstacle_rooms(args.envs, steps=args.walk, width=480, height=270)
+    E = batch.n_envs
+    ctx = ags.ags_context_create(local)
+    scene = ags.ags_scene_build(ctx, batch)
+    poses_d = torch.as_tensor(poses).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, rays):
+        for i in range(args.warmup):
+            fn(i)
+        st, en = torch.cuda.Event(True), torch.cuda.Event(True)
+        torch.cuda.synchronize(dev)
+        st.record(stream)
+        for i in range(args.steps):
+            fn(args.warmup + i)
+        en.record(stream)
+        torch.cuda.synchronize(dev)
+        ags.ags_stream_status(ctx, stream)
+        ms = st.elapsed_time(en) / args.steps
+        return {"mrays_per_s": rays / ms / 1e3, "ms_per_step": ms}
+
+    def buffers(sp, chans=False):
+        H, W = sp.height, sp.width
+        b = {"d": torch.empty((E, H, W), device=dev), "s": torch.empty((E, H, W), dtype=torch.int32, device=dev)}
+        if chans:
+            b.update(face=torch.empty((E, H, W), dtype=torch.int32, device=dev),
+                     bary=torch.empty((E, H, W, 2), device=dev), normal=torch.empty((E, H, W, 3), device=dev),
+                     point=torch.empty((E, H, W, 3), device=dev))
+        return b
+
+    out = {}
+    walk = poses_d.shape[0]
+    rays = E * spec.width * spec.height
+    b = buffers(spec, True)
+    ch = {k: b[k] for k in ("face", "bary", "normal", "point")}
+    out["camera_270x480"] = timed(lambda i: ags.ags_render(ctx, scene, spec, poses_d[i % walk], b["d"], b["s"], stream),
+                                  rays)
+    out["camera_270x480_channels"] = timed(
+        lambda i: ags.ags_render_ex(ctx, scene, spec, poses_d[i % walk], b["d"], b["s"], stream=stream, **ch), rays)
+    out["camera_270x480_stereo"] = timed(
+        lambda i: ags.ags_render_ex(ctx, scene, spec, poses_d[i % walk], b["d"], b["s"], baseline=(0.0, -0.095, 0.0),
+                                    stream=stream), rays)
+    out["camera_270x480_channels_stereo"] = timed(
+        lambda i: ags.ags_render_ex(ctx, scene, spec, poses_d[i % walk], b["d"], b["s"], baseline=(0.0, -0.095, 0.0),
+                                    stream=stream, **ch), rays)
+    del b, ch
+    fs = S.ray_table_spec(480, 270, 0.2, 10.0)
+    table = torch.as_tensor(S.fisheye_table(480, 270, 180.0)).to(dev)
+    b = buffers(fs)
+    out["fisheye_180_270x480_table"] = timed(
+        lambda i: ags.ags_render_ex(ctx, scene, fs, poses_d[i % walk], b["d"], b["s"], ray_table=table, stream=stream),
+        rays)
+    del b
+    dome = S.dome_lidar(512, 64, 0.2, 12.0)
+    b = buffers(dome)
+    out["dome_lidar_64x512"] = timed(lambda i: ags.ags_render(ctx, scene, dome, poses_d[i % walk], b["d"], b["s"], stream),
+                                     E * 64 * 512)
+    del b
+    nav = S.pinhole(848, 480, 87.0, 0.2, 10.0)
+    b = buffers(nav)
+    out["camera_480x848"] = timed(lambda i: ags.ags_render(ctx, scene, nav, poses_d[i % walk], b["d"], b["s"], stream),
+                                  E * 848 * 480)
+    del b
+    line = {"metric": WORKLOADS["features"]["metric"], "value": out["camera_270x480"]["mrays_per_s"], "unit": UNIT,
+            "higher_is_better": True, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": f"obstacle rooms, {E} envs; each feature on the same scene",
+                                            "tris": int(batch.env_tri_counts().sum())},
+            "features": out}
+    print(json.dumps(line), flush=True)
+    ags.ags_scene_destroy(scene)
+    ags.ags_context_destroy(ctx)
+
+
 # ---------------------------------------------------------------- workload
 def make_workload(args, rank, world=1):
     from paper_2503_01471_gb300 import scenes as S
@@ -626,7 +715,10 @@ def bench_ours(args, rank, world, local):
     hbm, peak_kind = peaks()
     achieved_gbs = b_ray * rays_per_step / (ms_step * 1e-3) / 1e9
     workload = workload_name(args, spec, E)
-    traffic = profiled_traffic(f"{args.workload}:{E}x{spec.height}x{spec.width}")
+    lc = ags.ags_get_launch_config(ctx, scene, spec)
+    fmt = args.build_flags & 0xFF
+    traffic = profiled_traffic(f"{args.workload}:{E}x{spec.height}x{spec.width}",
+                               f"k_trace<0, {lc['tile_w']}, {lc['rays_per_lane']}, 0, {fmt}, 0>")
     line = {
         "metric": WORKLOADS[args.workload]["metric"], "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -683,6 +775,10 @@ def main():
     if args.workload == "dynamic":
         if rank == 0:
             bench_dynamic(args, rank, world, local)
+        return
+    if args.workload == "features":
+        if rank == 0:
+            bench_features(args, rank, world, local)
         return
     bench_ours(args, rank, world, local)
 
