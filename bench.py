@@ -663,7 +663,8 @@ def bench_ours(args, rank, world, local):
         e2e_s = float(t.item())
     e2e = {"value": rays_per_step * world / e2e_s / 1e6, "unit": UNIT,
            "h2d_bytes_per_step": E * 7 * 4, "d2h_bytes_per_step": 2 * E * spec.width * spec.height * 4,
-           "api": "ags_render_host (pinned host buffers, synchronous)"}
+           "api": "ags_render_host (page-locked host buffers: poses copied in, the kernel writes depth+seg in place "
+                  "over the host link; synchronous)"}
 
     # plain per-env launches (one ags_render_envs call per environment), same outputs
     plain = None

@@ -263,7 +263,11 @@ ags_status ags_render_envs(ags_context* ctx, const ags_scene* scene, const ags_s
  * [n_envs][7] to the device, renders into context-owned device buffers and
  * copies depth/range and segment IDs back into out_depth_host and
  * out_seg_host ([n_envs][height][width]). Synchronous; returns the device
- * status of this render as ags_stream_status would.
+ * status of this render as ags_stream_status would. When both output buffers
+ * are page-locked (cudaHostAlloc, cudaHostRegister, torch pin_memory), the
+ * render kernel writes them in place through their mapped device addresses
+ * (over the host link, no staging buffer and no copy-back); otherwise the
+ * outputs are rendered into context-owned device memory and copied back.
  */
 ags_status ags_render_host(ags_context* ctx, const ags_scene* scene, const ags_sensor_spec* spec,
                            const float* sensor_poses_host, float* out_depth_host,

@@ -502,6 +502,22 @@ ags_status ags_stream_status(ags_context* ctx, void* stream) {
   AGS_API_END
 }
 
+}  // extern "C"
+
+namespace {
+// The device address of page-locked host memory (cudaHostAlloc / cudaHostRegister), or null.
+void* mapped_host(const void* h) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, h) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+}  // namespace
+
+extern "C" {
+
 ags_status ags_render_host(ags_context* ctx, const ags_scene* sc, const ags_sensor_spec* spec, const float* poses_h,
                            float* depth_h, int32_t* seg_h) {
   AGS_API_BEGIN
@@ -514,7 +530,11 @@ ags_status ags_render_host(ags_context* ctx, const ags_scene* sc, const ags_sens
   const int64_t n = sc->n_envs, pix = (int64_t)spec->width * spec->height;
   const size_t pose_b = ((size_t)n * 7 * sizeof(float) + 255) & ~size_t(255);
   const size_t out_b = ((size_t)(n * pix) * sizeof(float) + 255) & ~size_t(255);
-  const size_t need = pose_b + 2 * out_b;
+  // page-locked outputs: the kernel writes them in place over the host link (no staging, no copy-back)
+  float* depth_m = static_cast<float*>(mapped_host(depth_h));
+  int32_t* seg_m = static_cast<int32_t*>(mapped_host(seg_h));
+  const bool direct = depth_m && seg_m;
+  const size_t need = pose_b + (direct ? 0 : 2 * out_b);
   cudaError_t e;
   if (ctx->stage_bytes < need) {
     cudaFree(ctx->stage);
@@ -532,6 +552,11 @@ ags_status ags_render_host(ags_context* ctx, const ags_scene* sc, const ags_sens
     return cuda_fail(e, "cudaMemcpyAsync(poses)");
   TraceArgs a{};
   const ags_launch_config cfg = lookup_config(sc, spec);
+  if (direct) {
+    if ((st = fill_trace_args(ctx, sc, spec, (int32_t)n, nullptr, d_pose, depth_m, seg_m, a, cfg)) != AGS_OK) return st;
+    if ((st = launch(ctx, a, s, false, cfg.blocks_per_sm)) != AGS_OK) return st;
+    return ags_stream_status(ctx, s);
+  }
   if ((st = fill_trace_args(ctx, sc, spec, (int32_t)n, nullptr, d_pose, d_depth, d_seg, a, cfg)) != AGS_OK) return st;
   if ((st = launch(ctx, a, s, false, cfg.blocks_per_sm)) != AGS_OK) return st;
   if ((e = cudaMemcpyAsync(depth_h, d_depth, (size_t)(n * pix) * sizeof(float), cudaMemcpyDeviceToHost, s)) !=

@@ -697,3 +697,22 @@ def test_user_projection_models_match_oracle(ctx, model):
                   f"{int((~strict & ~counted).sum())} beyond strict")
     finally:
         ags.ags_scene_destroy(scene)
+
+
+def test_host_path_with_page_locked_outputs_writes_in_place(ctx):
+    """ags_render_host into page-locked buffers (written by the kernel over the host link) equals the device
+    render and the pageable-buffer path bit for bit."""
+    batch, spec, poses = S.obstacle_rooms(3, steps=1, width=40, height=30)
+    scene = ags.ags_scene_build(ctx, batch)
+    try:
+        d0, s0 = render(ctx, scene, spec, poses[0])
+        pd = torch.full((3, 30, 40), 7.0).pin_memory()
+        ps = torch.full((3, 30, 40), 7, dtype=torch.int32).pin_memory()
+        pp = torch.as_tensor(np.ascontiguousarray(poses[0])).pin_memory()
+        for _ in range(2):
+            ags.ags_render_host(ctx, scene, spec, pp.numpy(), pd.numpy(), ps.numpy())
+            assert np.array_equal(pd.numpy(), d0) and np.array_equal(ps.numpy(), s0)
+        hd, hs = ags.ags_render_host(ctx, scene, spec, np.ascontiguousarray(poses[0]))
+        assert np.array_equal(hd, d0) and np.array_equal(hs, s0)
+    finally:
+        ags.ags_scene_destroy(scene)
