@@ -86,7 +86,8 @@ def peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("trace.cu", "trace_kernel.cuh", "internal.cuh"):
+    # the render kernel and everything that shapes what it traverses (BVH builders)
+    for f in ("trace.cu", "trace_kernel.cuh", "internal.cuh", "build.cu", "ploc.cu", "radix_sort.cu"):
         with open(os.path.join(ROOT, "paper_2503_01471_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -108,6 +108,11 @@ typedef struct {
 #define AGS_BVH_Q8 2u    /* 80-byte nodes, 8-bit steps of a power-of-two scale per axis, rounded outward */
 #define AGS_LEAF_SIZE(n) (((uint32_t)(n) & 0xFu) << 8)
 #define AGS_SPLIT_CELLS(n) (((uint32_t)(n) & 0xFFu) << 12)
+/* Binary tree under the wide nodes: by default locally-ordered clustering of
+ * the Morton-sorted references (lower surface-area cost, slower build); this
+ * bit selects the Morton radix tree instead (faster build). Results are
+ * identical either way. */
+#define AGS_BUILD_LBVH (1u << 20)
 
 /* Launch shape of the persistent render kernel for one (scene, sensor shape):
  * each warp repeatedly takes a tile of tile_w x (32 * rays_per_lane / tile_w)

@@ -37,6 +37,7 @@ AGS_NEAR_INVALID = 1
 AGS_BVH_FP32 = 0
 AGS_BVH_FP16 = 1
 AGS_BVH_Q8 = 2
+AGS_BUILD_LBVH = 1 << 20
 
 
 def AGS_LEAF_SIZE(n: int) -> int:

@@ -15,11 +15,6 @@ namespace ags {
 
 namespace {
 
-#define AGS_CHECK(call)                                     \
-  do {                                                      \
-    cudaError_t _e = (call);                                \
-    if (_e != cudaSuccess) return cuda_fail(_e, #call);     \
-  } while (0)
 
 // ---------------------------------------------------------------- float-float
 // Transform arithmetic in unevaluated float pairs (hi + lo) built from
@@ -833,23 +828,6 @@ __global__ void k_compress_nodes(const WideNode* __restrict__ in, int64_t n, voi
 unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 // device allocations released on scope exit
-struct DevBufs {
-  std::vector<void*> ptrs;
-  ~DevBufs() {
-    for (void* p : ptrs) cudaFree(p);
-  }
-  template <class T>
-  cudaError_t alloc(T** p, size_t count) {
-    void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
-    if (e == cudaSuccess) {
-      ptrs.push_back(q);
-      *p = static_cast<T*>(q);
-    }
-    return e;
-  }
-};
-
 }  // namespace
 
 ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_h, const int32_t* tri_vidx_h,
@@ -1024,14 +1002,31 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
   AGS_CHECK(tmp.alloc(&d_last, (size_t)R));
   AGS_CHECK(tmp.alloc(&d_visits, (size_t)R));
   AGS_CHECK(cudaMemsetAsync(d_visits, 0, (size_t)R * sizeof(int32_t), s));
-  k_karras<<<blocks_for(R, 256), 256, 0, s>>>(d_keys, R, key_shift, d_env_ref, d_left, d_right, d_pin, d_pleaf,
-                                              d_first, d_last);
   Box *d_leaf_box, *d_inner_box;
   AGS_CHECK(tmp.alloc(&d_leaf_box, (size_t)R));
   AGS_CHECK(tmp.alloc(&d_inner_box, (size_t)R));
-  k_refit<<<blocks_for(R, 256), 256, 0, s>>>(d_ref_box, d_vals, R, d_left, d_right, d_pin, d_pleaf, d_leaf_box,
-                                             d_inner_box, d_visits);
-  AGS_CHECK(cudaGetLastError());
+  if (sc->flags & AGS_BUILD_LBVH) {
+    // Morton radix tree (Karras 2012) and an atomic bottom-up refit
+    k_karras<<<blocks_for(R, 256), 256, 0, s>>>(d_keys, R, key_shift, d_env_ref, d_left, d_right, d_pin, d_pleaf,
+                                                d_first, d_last);
+    k_refit<<<blocks_for(R, 256), 256, 0, s>>>(d_ref_box, d_vals, R, d_left, d_right, d_pin, d_pleaf, d_leaf_box,
+                                               d_inner_box, d_visits);
+    AGS_CHECK(cudaGetLastError());
+  } else {
+    // locally-ordered clustering (default): lower surface-area cost
+    std::vector<int32_t> roots;
+    ags_status st = build_ploc(d_keys, d_vals, R, key_shift, d_env_ref, E, d_ref_box, d_leaf_box, d_left, d_right,
+                               d_first, d_last, d_inner_box, roots, s);
+    if (st != AGS_OK) return st;
+    for (QueueItem& q : q0) {
+      if (q.ref < 0) continue;  // a single reference: the leaf keeps its position
+      if (roots[q.env] < 0 || roots[q.env] >= R) {
+        set_error("clustering left an environment without a root");
+        return AGS_ERR_CUDA;
+      }
+      q.ref = roots[q.env];
+    }
+  }
 
   // collapse into 8-wide nodes, level by level
   // wide nodes: at most R/(L+1) + E without inner children (each covers more

@@ -133,6 +133,43 @@ cudaError_t sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* alt_keys, uint3
 size_t scan_temp_bytes(int64_t n);
 cudaError_t exclusive_scan(int32_t* data, int64_t n, int32_t* total_dev, void* temp, cudaStream_t s);
 
+// device scratch freed when the holder goes out of scope
+struct DevBufs {
+  std::vector<void*> ptrs;
+  DevBufs() = default;
+  DevBufs(const DevBufs&) = delete;
+  DevBufs& operator=(const DevBufs&) = delete;
+  ~DevBufs() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <class T>
+  cudaError_t alloc(T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, (count > 1 ? count : 1) * sizeof(T));
+    if (e == cudaSuccess) {
+      ptrs.push_back(q);
+      *p = static_cast<T*>(q);
+    }
+    return e;
+  }
+};
+
+#define AGS_CHECK(call)                                 \
+  do {                                                  \
+    cudaError_t _e = (call);                            \
+    if (_e != cudaSuccess) return cuda_fail(_e, #call); \
+  } while (0)
+
+// ploc.cu: binary BVH by locally-ordered clustering over the R references
+// sorted environment-major by Morton code (keys, vals). Writes inner nodes
+// 0..n_inner-1 (left/right: inner id, or ~position of a leaf), their boxes
+// and depth-first position ranges [first, last]; reorders vals and writes
+// leaf_box in that depth-first order; roots[e] = root of environment e
+// (inner id, ~position for a single reference, -1 when empty).
+ags_status build_ploc(const uint64_t* keys, uint32_t* vals, int32_t R, int key_shift, const int32_t* env_ref_off,
+                      int32_t E, const Box* ref_box, Box* leaf_box, int32_t* left, int32_t* right, int32_t* first,
+                      int32_t* last, Box* inner_box, std::vector<int32_t>& roots, cudaStream_t s);
+
 // build.cu
 ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_h,
                        const int32_t* tri_vidx_h, const int32_t* sub_vert_off_h,

@@ -308,6 +308,9 @@ def test_bit_exact_across_bvh_variants(ctx):
     variants += [ags.AGS_SPLIT_CELLS(1), ags.AGS_SPLIT_CELLS(64) | ags.AGS_LEAF_SIZE(2), ags.AGS_SPLIT_CELLS(4)]
     variants += [ags.AGS_BVH_FP16, ags.AGS_BVH_Q8, ags.AGS_BVH_Q8 | ags.AGS_LEAF_SIZE(4) | ags.AGS_SPLIT_CELLS(1),
                  ags.AGS_BVH_FP16 | ags.AGS_LEAF_SIZE(1)]
+    # the Morton radix tree instead of clustering, alone and with the other options
+    variants += [ags.AGS_BUILD_LBVH, ags.AGS_BUILD_LBVH | ags.AGS_LEAF_SIZE(4) | ags.AGS_SPLIT_CELLS(1),
+                 ags.AGS_BUILD_LBVH | ags.AGS_BVH_Q8]
     for flags in variants:
         scene = ags.ags_scene_build(ctx, batch, flags)
         try:
