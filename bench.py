@@ -93,19 +93,23 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload, kernel):
-    """DRAM bytes per launch of the render kernel from the committed ncu summary, if its row matches this
-    workload, this kernel instance and the current kernel source; else None."""
+def profiled_counters(workload, kernel):
+    """(DRAM bytes, warp instructions) per launch of the render kernel from the committed ncu summary, if its
+    row matches this workload, this kernel instance and the current kernel and builder sources; else None."""
     try:
         with open(PROFILE_TRAFFIC) as fh:
             for line in fh:
                 cells = [c.strip() for c in line.strip().strip("|").split("|")]
                 if len(cells) == 7 and cells[0] == workload and cells[1] == kernel \
                         and cells[2] == kernel_source_hash():
-                    return float(cells[5])
+                    return float(cells[5]), float(cells[6])
     except (OSError, ValueError):
         pass
     return None
+
+
+# instruction issue limit of one GB300: 152 SMs x 4 schedulers x 1 warp instruction per cycle x 2.07 GHz
+ISSUE_PEAK_G = 152 * 4 * 2.07
 
 
 class ClockSampler:
@@ -719,8 +723,9 @@ def bench_ours(args, rank, world, local):
     workload = workload_name(args, spec, E)
     lc = ags.ags_get_launch_config(ctx, scene, spec)
     fmt = args.build_flags & 0xFF
-    traffic = profiled_traffic(f"{args.workload}:{E}x{spec.height}x{spec.width}",
-                               f"k_trace<0, {lc['tile_w']}, {lc['rays_per_lane']}, 0, {fmt}, 0>")
+    counters = profiled_counters(f"{args.workload}:{E}x{spec.height}x{spec.width}",
+                                 f"k_trace<0, {lc['tile_w']}, {lc['rays_per_lane']}, 0, {fmt}, 0>")
+    traffic = counters[0] if counters else None
     line = {
         "metric": WORKLOADS[args.workload]["metric"], "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -737,6 +742,11 @@ def bench_ours(args, rank, world, local):
                      "peak_kind": peak_kind + " hbm_gbs (copy)",
                      "bytes_per_ray": b_ray, "nodes_per_ray": nodes_c / rays_c, "tris_per_ray": tris_c / rays_c,
                      "node_bytes": node_b, "kernel": "k_trace"},
+        "roofline_issue": None if counters is None else {
+            "bound": "alu", "achieved": counters[1] / (ms_step * 1e-3) / 1e9, "peak": ISSUE_PEAK_G,
+            "unit": "G warp instructions/s", "frac": counters[1] / (ms_step * 1e-3) / 1e9 / ISSUE_PEAK_G,
+            "instructions_per_launch": counters[1],
+            "peak_kind": "152 SMs x 4 schedulers x 1 warp instruction/cycle x 2.07 GHz (max SM clock)"},
         "clocks": clk.summary(),
         "e2e": e2e,
         "gpu_launches": args.steps,
