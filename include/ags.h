@@ -288,6 +288,22 @@ ags_status ags_render_count(ags_context* ctx, const ags_scene* scene, const ags_
                             const float* sensor_poses_dev, uint64_t counts_host[3]);
 
 /*
+ * ags_autotune_build -- build-time tuning of the reference splitting (the
+ * AGS_SPLIT_CELLS setting, 0 = the default 16 cells, 1 = off): the scene is
+ * rebuilt, from its kept inputs and current object poses, with each listed
+ * setting; `repeats` renders of `spec` (default launch shape, after one
+ * warm-up, into the caller's buffers) are timed per setting, and the fastest
+ * BVH is kept in `scene` (same handle; results are identical for every
+ * setting). *best_cells receives the kept setting. Settings that run out of
+ * device memory are skipped. Launch-shape choices of the scene are cleared
+ * when its BVH changes (run ags_autotune afterwards). Synchronous. Rebuilds
+ * invalidate captured graphs (as AGS_UPDATE_REBUILD does).
+ */
+ags_status ags_autotune_build(ags_context* ctx, ags_scene* scene, const ags_sensor_spec* spec,
+                              const float* sensor_poses_dev, float* out_depth_dev, int32_t* out_seg_dev,
+                              const uint32_t* split_cells, int32_t n_cells, int32_t repeats, uint32_t* best_cells);
+
+/*
  * ags_autotune -- time the render of `scene` with `spec` under each compiled
  * launch shape (tiles 8x4, 4x8, 8x8, 16x4, 16x8; full or reduced grid),
  * `repeats` timed renders each after one warm-up, on the context's

@@ -56,7 +56,7 @@ EXPORTS = [
     "ags_set_launch_config", "ags_get_launch_config", "ags_memcpy_d2h", "ags_server_create", "ags_server_destroy",
     "ags_server_submit", "ags_server_poll", "ags_server_release", "ags_server_stats", "ags_server_replay",
     "ags_replay_sequential", "ags_scene_update_poses", "ags_render_graph_create", "ags_render_graph_launch",
-    "ags_render_graph_destroy", "ags_render_channels", "ags_render_ex",
+    "ags_render_graph_destroy", "ags_render_channels", "ags_render_ex", "ags_autotune_build",
 ]
 
 
@@ -194,6 +194,8 @@ def lib() -> ctypes.CDLL:
                                       ctypes.POINTER(ags_hit_channels), vp]),
         "ags_render_ex": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), vp, vp, vp,
                                 ctypes.POINTER(ags_render_options), vp]),
+        "ags_autotune_build": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), vp, vp, vp,
+                                     ctypes.POINTER(ctypes.c_uint32), i32, i32, ctypes.POINTER(ctypes.c_uint32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -536,3 +538,14 @@ def ags_render_ex(ctx: int, scene: int, spec, sensor_poses, out_depth, out_seg, 
     opt = ags_render_options(ch, st, _ptr(ray_table) or None)
     _check(lib().ags_render_ex(ctx, scene, ctypes.byref(s), _ptr(sensor_poses), _ptr(out_depth), _ptr(out_seg),
                                ctypes.byref(opt), _stream(stream)), "ags_render_ex")
+
+
+def ags_autotune_build(ctx: int, scene: int, spec, sensor_poses, out_depth, out_seg, split_cells=(16, 32, 48, 64),
+                       repeats: int = 2) -> int:
+    """Rebuild the scene with each reference-splitting setting, keep the fastest; returns its cell count."""
+    s = make_spec(spec)
+    c = (ctypes.c_uint32 * len(split_cells))(*[int(x) for x in split_cells])
+    best = ctypes.c_uint32()
+    _check(lib().ags_autotune_build(ctx, scene, ctypes.byref(s), _ptr(sensor_poses), _ptr(out_depth), _ptr(out_seg),
+                                    c, len(split_cells), int(repeats), ctypes.byref(best)), "ags_autotune_build")
+    return int(best.value)

@@ -309,10 +309,12 @@ ags_status ags_scene_build(ags_context* ctx, const ags_env_mesh* envs, int32_t n
     sc->h_vidx = std::move(vidx);
     sc->h_sub_vert = std::move(sub_vert);
     sc->h_sub_env = std::move(sub_env);
+    if (J > 0) sc->h_poses.assign(obstacle_poses, obstacle_poses + 7 * J);
   }
   if (st != AGS_OK) {
     cudaStreamSynchronize(ctx->stream);
     ags_scene_destroy(sc.release());
+    cudaGetLastError();  // a failed allocation must not surface in a later call
     return st;
   }
   *out = sc.release();
@@ -340,6 +342,55 @@ void ags_scene_destroy(ags_scene* sc) {
 
 int32_t ags_scene_n_envs(const ags_scene* sc) { return sc ? sc->n_envs : -1; }
 
+}  // extern "C"
+
+namespace {
+struct SceneDeleter {
+  void operator()(ags_scene* s) const { ags_scene_destroy(s); }
+};
+using ScenePtr = std::unique_ptr<ags_scene, SceneDeleter>;
+
+// A fresh scene built from the kept inputs of sc with the given object poses and build flags.
+ags_status rebuild_like(ags_context* ctx, const ags_scene* sc, const float* poses, uint32_t flags, ScenePtr& out) {
+  ScenePtr fresh(new ags_scene());
+  fresh->ctx = ctx;
+  fresh->n_envs = sc->n_envs;
+  fresh->n_tris = sc->n_tris;
+  fresh->n_verts = sc->n_verts;
+  fresh->n_subs = sc->n_subs;
+  fresh->flags = flags;
+  fresh->env_tri_off = sc->env_tri_off;
+  fresh->env_vert_off = sc->env_vert_off;
+  fresh->env_sub_off = sc->env_sub_off;
+  fresh->sub_tri_off = sc->sub_tri_off;
+  fresh->sub_seg = sc->sub_seg;
+  ags_status st = build_scene(ctx, fresh.get(), sc->h_base.data(), sc->h_vidx.data(), sc->h_sub_vert.data(), poses,
+                              sc->h_sub_env.data());
+  if (st != AGS_OK) {
+    cudaStreamSynchronize(ctx->stream);
+    cudaGetLastError();  // a failed allocation must not surface in a later call
+    return st;
+  }
+  out = std::move(fresh);
+  return AGS_OK;
+}
+
+// sc takes over fresh's device structures (keeping its own handle, host copies and, if asked, its launch
+// choices); fresh leaves with sc's old device structures and is destroyed.
+void adopt(ags_scene* sc, ScenePtr& fresh, bool keep_launch) {
+  fresh->h_base.swap(sc->h_base);
+  fresh->h_vidx.swap(sc->h_vidx);
+  fresh->h_sub_vert.swap(sc->h_sub_vert);
+  fresh->h_sub_env.swap(sc->h_sub_env);
+  fresh->h_poses.swap(sc->h_poses);
+  if (keep_launch) fresh->launch = sc->launch;
+  std::swap(*sc, *fresh);
+  fresh.reset();
+}
+}  // namespace
+
+extern "C" {
+
 ags_status ags_scene_update_poses(ags_context* ctx, ags_scene* sc, const float* poses, int32_t mode) {
   AGS_API_BEGIN
   if (!ctx || !sc) return invalid("ctx or scene is NULL");
@@ -354,38 +405,17 @@ ags_status ags_scene_update_poses(ags_context* ctx, ags_scene* sc, const float* 
     if (!(qn > 1e-12)) return invalid("quaternion has zero length");
   }
   DeviceGuard g(ctx->device);
+  ags_status st;
   if (mode == AGS_UPDATE_REFIT) {
     if (sc->node_format != kNodeFp32) return invalid("refit needs float32 nodes; use AGS_UPDATE_REBUILD");
-    return refit_scene(ctx, sc, poses);
+    st = refit_scene(ctx, sc, poses);
+  } else {
+    // rebuild: a fresh scene from the kept inputs, then swap it in
+    ScenePtr fresh;
+    if ((st = rebuild_like(ctx, sc, poses, sc->flags, fresh)) == AGS_OK) adopt(sc, fresh, true);
   }
-  // rebuild: a fresh scene from the kept inputs, then swap it in
-  std::unique_ptr<ags_scene> fresh(new ags_scene());
-  fresh->ctx = ctx;
-  fresh->n_envs = sc->n_envs;
-  fresh->n_tris = sc->n_tris;
-  fresh->n_verts = sc->n_verts;
-  fresh->n_subs = sc->n_subs;
-  fresh->flags = sc->flags;
-  fresh->env_tri_off = sc->env_tri_off;
-  fresh->env_vert_off = sc->env_vert_off;
-  fresh->env_sub_off = sc->env_sub_off;
-  fresh->sub_tri_off = sc->sub_tri_off;
-  fresh->sub_seg = sc->sub_seg;
-  ags_status st = build_scene(ctx, fresh.get(), sc->h_base.data(), sc->h_vidx.data(), sc->h_sub_vert.data(), poses,
-                              sc->h_sub_env.data());
-  if (st != AGS_OK) {
-    cudaStreamSynchronize(ctx->stream);
-    ags_scene_destroy(fresh.release());
-    return st;
-  }
-  fresh->h_base.swap(sc->h_base);
-  fresh->h_vidx.swap(sc->h_vidx);
-  fresh->h_sub_vert.swap(sc->h_sub_vert);
-  fresh->h_sub_env.swap(sc->h_sub_env);
-  fresh->launch = sc->launch;
-  std::swap(*sc, *fresh);
-  ags_scene_destroy(fresh.release());
-  return AGS_OK;
+  if (st == AGS_OK && sc->n_subs > 0) sc->h_poses.assign(poses, poses + 7 * sc->n_subs);
+  return st;
   AGS_API_END
 }
 
@@ -810,6 +840,81 @@ ags_status ags_autotune(ags_context* ctx, const ags_scene* sc, const ags_sensor_
   if ((st = ags_stream_status(ctx, s)) != AGS_OK) return st;
   sc->launch[{spec->type, spec->width, spec->height}] = top;
   *best = top;
+  return AGS_OK;
+  AGS_API_END
+}
+
+}  // extern "C"
+
+namespace {
+// Mean time of `repeats` renders of every environment (default launch shape), after one warm-up.
+ags_status time_render(ags_context* ctx, const ags_scene* sc, const ags_sensor_spec* spec, const float* poses,
+                       float* depth, int32_t* seg, int repeats, float* ms) {
+  cudaStream_t s = ctx->stream;
+  TraceArgs a{};
+  const ags_launch_config c = default_config();
+  ags_status st = fill_trace_args(ctx, sc, spec, sc->n_envs, nullptr, poses, depth, seg, a, c);
+  if (st != AGS_OK) return st;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return cuda_fail(e, "cudaEventCreate");
+  }
+  st = launch(ctx, a, s, false, 0);
+  if (st == AGS_OK && (e = cudaEventRecord(e0, s)) != cudaSuccess) st = cuda_fail(e, "cudaEventRecord");
+  for (int r = 0; r < repeats && st == AGS_OK; ++r) st = launch(ctx, a, s, false, 0);
+  if (st == AGS_OK && ((e = cudaEventRecord(e1, s)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+                       (e = cudaEventElapsedTime(ms, e0, e1)) != cudaSuccess))
+    st = cuda_fail(e, "build tuning timing");
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != AGS_OK) return st;
+  *ms /= repeats;
+  return ags_stream_status(ctx, s);
+}
+}  // namespace
+
+extern "C" {
+
+ags_status ags_autotune_build(ags_context* ctx, ags_scene* sc, const ags_sensor_spec* spec, const float* poses,
+                              float* depth, int32_t* seg, const uint32_t* cells, int32_t n_cells, int32_t repeats,
+                              uint32_t* best_cells) {
+  AGS_API_BEGIN
+  if (!ctx || !sc) return invalid("ctx or scene is NULL");
+  if (sc->ctx != ctx) return invalid("scene belongs to another context");
+  ags_status st = check_spec(spec, false);
+  if (st != AGS_OK) return st;
+  if (!poses || !depth || !seg || !best_cells || (n_cells > 0 && !cells)) return invalid("NULL pointer argument");
+  if (n_cells < 0 || n_cells > 64) return invalid("n_cells must be in [0, 64]");
+  if (repeats < 1 || repeats > 1000) return invalid("repeats must be in [1, 1000]");
+  for (int32_t k = 0; k < n_cells; ++k)
+    if (cells[k] > 255u) return invalid("split cell counts must be in [0, 255]");
+  if (sc->n_subs > 0 && sc->h_poses.size() != 7 * (size_t)sc->n_subs) return invalid("scene has no kept poses");
+  DeviceGuard g(ctx->device);
+  const uint32_t split_mask = 0xFFu << 12;
+  const uint32_t current = (sc->flags >> 12) & 0xFFu;
+  float best_ms = 0.0f;
+  if ((st = time_render(ctx, sc, spec, poses, depth, seg, repeats, &best_ms)) != AGS_OK) return st;
+  uint32_t best = current;
+  ScenePtr best_scene;
+  const float* h_poses = sc->n_subs > 0 ? sc->h_poses.data() : nullptr;
+  for (int32_t k = 0; k < n_cells; ++k) {
+    if (cells[k] == current) continue;
+    ScenePtr cand;
+    st = rebuild_like(ctx, sc, h_poses, (sc->flags & ~split_mask) | (cells[k] << 12), cand);
+    if (st == AGS_ERR_OUT_OF_MEMORY) continue;  // this setting does not fit: skip it
+    if (st != AGS_OK) return st;
+    float ms = 0.0f;
+    if ((st = time_render(ctx, cand.get(), spec, poses, depth, seg, repeats, &ms)) != AGS_OK) return st;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = cells[k];
+      best_scene = std::move(cand);
+    }
+  }
+  if (best_scene) adopt(sc, best_scene, false);
+  *best_cells = best;
   return AGS_OK;
   AGS_API_END
 }

@@ -115,6 +115,7 @@ struct ags_scene {
   // host copies of the inputs, for ags_scene_update_poses(..., AGS_UPDATE_REBUILD)
   std::vector<float> h_base;
   std::vector<int32_t> h_vidx, h_sub_vert, h_sub_env;
+  std::vector<float> h_poses;  // the current object poses [J][7] (rebuilds start from these)
   mutable std::map<LaunchKey, ags_launch_config> launch;  // tuned or set launch shapes per sensor shape
 };
 

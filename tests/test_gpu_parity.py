@@ -719,3 +719,35 @@ def test_host_path_with_page_locked_outputs_writes_in_place(ctx):
         assert np.array_equal(hd, d0) and np.array_equal(hs, s0)
     finally:
         ags.ags_scene_destroy(scene)
+
+
+def test_build_tuning_keeps_results_and_updates(ctx):
+    """Rebuilding with each splitting setting and keeping the fastest changes no output bit; the tuned
+    scene still refits to exactly a fresh build's images."""
+    batch, spec, poses = S.obstacle_rooms(3, steps=1, width=40, height=30)
+    scene = ags.ags_scene_build(ctx, batch)
+    try:
+        d0, s0 = render(ctx, scene, spec, poses[0])
+        p = torch.as_tensor(poses[0]).cuda()
+        d = torch.empty((3, 30, 40), device="cuda")
+        sg = torch.empty((3, 30, 40), dtype=torch.int32, device="cuda")
+        best = ags.ags_autotune_build(ctx, scene, spec, p, d, sg, (1, 16, 48), 1)
+        assert best in (0, 1, 16, 48)
+        d1, s1 = render(ctx, scene, spec, poses[0])
+        assert np.array_equal(d1, d0) and np.array_equal(s1, s0)
+        with pytest.raises(ags.AgsError):
+            ags.ags_autotune_build(ctx, scene, spec, p, d, sg, (300,), 1)
+        rng = np.random.default_rng(23)
+        new = batch.poses.copy()
+        new[:, :3] += rng.normal(0, 0.2, (new.shape[0], 3)).astype(np.float32)
+        ags.ags_scene_update_poses(ctx, scene, new, ags.AGS_UPDATE_REFIT)
+        moved = S.SceneBatch(batch.vertices, batch.indices, batch.sub_vert, batch.sub_tri, batch.sub_seg,
+                             batch.env_sub, new)
+        fresh = ags.ags_scene_build(ctx, moved)
+        try:
+            a, b = render(ctx, scene, spec, poses[0]), render(ctx, fresh, spec, poses[0])
+            assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        finally:
+            ags.ags_scene_destroy(fresh)
+    finally:
+        ags.ags_scene_destroy(scene)
