@@ -64,3 +64,36 @@ def test_context_on_a_missing_device_fails_cleanly(lib):
     assert st in (ags.AGS_ERR_CUDA, ags.AGS_ERR_INVALID_ARG)
     assert h.value is None
     assert ags.ags_last_error() != ""
+
+
+def test_header_compiles_as_c_and_links(tmp_path, lib):
+    """include/ags.h is plain C: a C99 program that takes the address of every declared function compiles
+    with warnings as errors and links against the library; creating a context without a device fails with
+    a status, not a crash."""
+    names = declared_functions()
+    src = tmp_path / "use_ags.c"
+    body = "\n".join(f"  (void (*)(void))&{n}," for n in names)
+    src.write_text(f"""#include <stdio.h>
+#include "ags.h"
+static void (*const table[])(void) = {{
+{body}
+}};
+int main(void) {{
+  ags_context *ctx = 0;
+  ags_status st = ags_context_create(0, &ctx);
+  if (st == AGS_OK) ags_context_destroy(ctx);
+  printf("%d %d\\n", (int)(sizeof table / sizeof table[0]), (int)st);
+  return 0;
+}}
+""")
+    import subprocess
+    exe = tmp_path / "use_ags"
+    so = B.LIB if hasattr(B, "LIB") else None
+    libdir = os.path.dirname(so) if so else os.path.join(ROOT, "paper_2503_01471_gb300", "_build")
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-o", str(exe), "-L", libdir, "-lags", f"-Wl,-rpath,{libdir}"], check=True)
+    import torch
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    assert int(out[0]) == len(names)
+    if not torch.cuda.is_available():
+        assert int(out[1]) != 0  # no device here: an error status
