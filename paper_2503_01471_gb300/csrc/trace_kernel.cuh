@@ -315,8 +315,9 @@ __device__ __forceinline__ void test_node(const void* __restrict__ nodes, int32_
 }
 
 // Any-hit test of packed triangle k against the segment o + t d, t in
-// [t0, 1] (the same watertight arithmetic as test_triangle).
-__device__ __forceinline__ bool segment_hits(const Ray& r, const float4* __restrict__ tris, int32_t k, float t0) {
+// [t0, t1] (the same watertight arithmetic as test_triangle).
+__device__ __forceinline__ bool segment_hits(const Ray& r, const float4* __restrict__ tris, int32_t k, float t0,
+                                             float t1) {
   const float4 a = __ldg(tris + 3 * (int64_t)k);
   const float4 b = __ldg(tris + 3 * (int64_t)k + 1);
   const float4 c = __ldg(tris + 3 * (int64_t)k + 2);
@@ -335,16 +336,19 @@ __device__ __forceinline__ bool segment_hits(const Ray& r, const float4* __restr
   const float T = __fmaf_rn(U, Az, __fmaf_rn(V, Bz, __fmul_rn(W, Cz)));
   if (T != 0.0f && ((__float_as_uint(T) ^ __float_as_uint(det)) >> 31)) return false;
   const float t = __fdiv_rn(fabsf(T), fabsf(det));
-  return t >= t0 && t <= 1.0f;
+  return t >= t0 && t <= t1;
 }
 
 // Stereo shadow (Sec. III-D.1): does any triangle of environment env meet
-// the segment from P to the second sensor, o = P, d = o2 - P, t in [t0, 1]?
-// The traversal stops at the first such triangle; children are visited in
-// slot order. Limits set the status word and `failed`.
+// the segment o + t d, t in [t0, t1]? The caller casts it from the second
+// sensor towards the hit P (o = o2, d = P - o2, t in [0, 1 - eps]): the same
+// segment as from P back to the sensor, but every ray of a warp starts at
+// the same point, which keeps the warp's traversals alike. The traversal
+// stops at the first such triangle; children are visited in slot order.
+// Limits set the status word and `failed`.
 template <int kFmt>
 __device__ bool occluded(const TraceArgs& a, int32_t env, float px, float py, float pz, float dx, float dy, float dz,
-                         float t0, int2* stack, bool& failed) {
+                         float t0, float t1, int2* stack, bool& failed) {
   Ray r;
   r.ox = px;
   r.oy = py;
@@ -386,7 +390,7 @@ __device__ bool occluded(const TraceArgs& a, int32_t env, float px, float py, fl
         return false;
       }
       for (int32_t x = 0; x < cnt; ++x)
-        if (segment_hits(r, a.tris, start + x, t0)) return true;
+        if (segment_hits(r, a.tris, start + x, t0, t1)) return true;
     }
     node = -1;
     if (inner_hits) {
@@ -642,8 +646,8 @@ __device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParam
       const float o2x = px + (R00 * bx + R01 * by + R02 * bz), o2y = py + (R10 * bx + R11 * by + R12 * bz),
                   o2z = pz + (R20 * bx + R21 * by + R22 * bz);
       bool sfail = false;
-      const bool shadowed =
-          occluded<kFmt>(a, env, Px, Py, Pz, o2x - Px, o2y - Py, o2z - Pz, a.shadow_eps, stack, sfail);
+      const bool shadowed = occluded<kFmt>(a, env, o2x, o2y, o2z, Px - o2x, Py - o2y, Pz - o2z, 0.0f,
+                                           1.0f - a.shadow_eps, stack, sfail);
       if (sfail) {
         failed = true;
         v = __int_as_float(0x7fc00000);
