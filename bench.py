@@ -421,9 +421,10 @@ def bench_dynamic(args, rank, world, local):
     movable[batch.env_sub[:-1]] = False
     refit = ags.ags_scene_build(ctx, batch)
     rebuilt = ags.ags_scene_build(ctx, batch)
+    two = ags.ags_scene_build(ctx, batch, ags.AGS_BUILD_INSTANCED)
     cur = batch.poses.copy()
     rows = []
-    t_refit, t_rebuild = [], []
+    t_refit, t_rebuild, t_two = [], [], []
     for step in range(args.steps + 1):
         if step > 0:  # obstacles drift: 5 cm and 0.05 rad per step
             cur[movable, :3] += rng.normal(0, 0.05, (movable.sum(), 3)).astype(np.float32)
@@ -436,18 +437,23 @@ def bench_dynamic(args, rank, world, local):
             t0 = time.perf_counter()
             ags.ags_scene_update_poses(ctx, rebuilt, cur, ags.AGS_UPDATE_REBUILD)
             t_rebuild.append((time.perf_counter() - t0) * 1e3)
+            t0 = time.perf_counter()
+            ags.ags_scene_update_poses(ctx, two, cur, ags.AGS_UPDATE_REBUILD)
+            t_two.append((time.perf_counter() - t0) * 1e3)
         if step in (0, 1, args.steps // 2, args.steps):
             rows.append({"step": step, "refit_mrays_per_s": rays / render_ms(refit) / 1e3,
-                         "rebuild_mrays_per_s": rays / render_ms(rebuilt) / 1e3})
+                         "rebuild_mrays_per_s": rays / render_ms(rebuilt) / 1e3,
+                         "two_level_mrays_per_s": rays / render_ms(two) / 1e3})
     line = {"metric": WORKLOADS["dynamic"]["metric"], "value": float(np.median(t_refit)), "unit": "ms",
             "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"obstacle rooms, {E} envs, 270x480 camera; every obstacle moves each step",
                        "tris": int(batch.env_tri_counts().sum())},
             "refit_ms": {"median": float(np.median(t_refit)), "max": float(np.max(t_refit))},
             "rebuild_ms": {"median": float(np.median(t_rebuild)), "max": float(np.max(t_rebuild))},
+            "two_level_update_ms": {"median": float(np.median(t_two)), "max": float(np.max(t_two))},
             "render_after_updates": rows}
     print(json.dumps(line), flush=True)
-    for sc in (refit, rebuilt):
+    for sc in (refit, rebuilt, two):
         ags.ags_scene_destroy(sc)
     ags.ags_context_destroy(ctx)
 

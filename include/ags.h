@@ -113,6 +113,16 @@ typedef struct {
  * bit selects the Morton radix tree instead (faster build). Results are
  * identical either way. */
 #define AGS_BUILD_LBVH (1u << 20)
+/* Two-level scene: every object (sub-mesh) gets its own BVH, built once in its
+ * own frame, and each environment a small BVH over its objects' world boxes;
+ * rays are moved into an object's frame to walk its BVH. ags_scene_update_poses
+ * then only rebuilds the small top level (either mode). Float32 nodes only; at
+ * most 65536 objects; renders through ags_render / ags_render_envs /
+ * ags_render_host / step graphs with the 8x4 tile; not with extra channels,
+ * stereo, ray tables, counting, splitting tuning or serving (those return
+ * AGS_ERR_INVALID_ARG). Results agree with a single-level scene within float32
+ * rounding, not bit for bit. */
+#define AGS_BUILD_INSTANCED (1u << 21)
 
 /* Launch shape of the persistent render kernel for one (scene, sensor shape):
  * each warp repeatedly takes a tile of tile_w x (32 * rays_per_lane / tile_w)

@@ -38,6 +38,7 @@ AGS_BVH_FP32 = 0
 AGS_BVH_FP16 = 1
 AGS_BVH_Q8 = 2
 AGS_BUILD_LBVH = 1 << 20
+AGS_BUILD_INSTANCED = 1 << 21
 
 
 def AGS_LEAF_SIZE(n: int) -> int:

@@ -1293,6 +1293,20 @@ __global__ void k_refit_level(WideNode* __restrict__ nodes, const WideNode* __re
 
 }  // namespace
 
+ags_status transform_vertices(const float* base_dev, int32_t V, const int32_t* sub_vert_off_dev, int32_t J,
+                              const float* poses_dev, float4* world_dev, cudaStream_t s) {
+  DevBufs tmp;
+  float* d_rot = nullptr;
+  AGS_CHECK(tmp.alloc(&d_rot, 18 * (size_t)std::max(J, 1)));
+  if (J > 0) k_submesh_rotations<<<blocks_for(J, 128), 128, 0, s>>>(poses_dev, J, d_rot);
+  if (V > 0)
+    k_transform_vertices<<<blocks_for(V, 256), 256, 0, s>>>(base_dev, V, sub_vert_off_dev, J, d_rot, poses_dev,
+                                                            world_dev);
+  AGS_CHECK(cudaGetLastError());
+  AGS_CHECK(cudaStreamSynchronize(s));  // the scratch is freed on return
+  return AGS_OK;
+}
+
 ags_status refit_scene(ags_context* ctx, ags_scene* sc, const float* poses_h) {
   cudaStream_t s = ctx->stream;
   if (!sc->d.nodes_build && sc->n_nodes > 0) {

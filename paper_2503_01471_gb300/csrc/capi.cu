@@ -107,12 +107,31 @@ ags_status check_config(ags_context* ctx, const ags_launch_config* c) {
 ags_status fill_trace_args(ags_context* ctx, const ags_scene* sc, const ags_sensor_spec* spec, int32_t n,
                            const int32_t* env_ids, const float* poses, float* depth, int32_t* seg, TraceArgs& a,
                            const ags_launch_config& cfg) {
-  a.nodes = sc->d.nodes;
-  a.node_format = sc->node_format;
-  a.tris = sc->d.tris;
-  a.env_root = sc->d.env_root;
-  a.n_nodes = (int32_t)sc->n_nodes;
-  a.n_tris = (int32_t)sc->n_refs;
+  if (sc->objects) {
+    // two levels: the top level walks like a scene, the objects below it
+    if (cfg.tile_w != 8 || cfg.rays_per_lane != 1) return invalid("two-level scenes render with the 8x4 tile");
+    a.nodes = sc->top->d.nodes;
+    a.node_format = kNodeFp32;
+    a.tris = sc->top->d.tris;
+    a.env_root = sc->top->d.env_root;
+    a.n_nodes = (int32_t)sc->top->n_nodes;
+    a.n_tris = (int32_t)sc->top->n_refs;
+    a.instanced = 1;
+    a.inst = sc->d_inst;
+    a.n_inst = (int32_t)sc->n_subs;
+    a.env_sub = sc->d_env_sub;
+    a.obj_nodes = sc->objects->d.nodes;
+    a.obj_tris = sc->objects->d.tris;
+    a.obj_n_nodes = (int32_t)sc->objects->n_nodes;
+    a.obj_n_tris = (int32_t)sc->objects->n_refs;
+  } else {
+    a.nodes = sc->d.nodes;
+    a.node_format = sc->node_format;
+    a.tris = sc->d.tris;
+    a.env_root = sc->d.env_root;
+    a.n_nodes = (int32_t)sc->n_nodes;
+    a.n_tris = (int32_t)sc->n_refs;
+  }
   a.n_scene_envs = sc->n_envs;
   a.env_ids = env_ids;
   a.poses = poses;
@@ -235,7 +254,9 @@ ags_status ags_scene_build(ags_context* ctx, const ags_env_mesh* envs, int32_t n
   if (!envs) return invalid("envs is NULL");
   if (n_envs < 1 || n_envs > 65536) return invalid("n_envs must be in [1, 65536]");
   if ((build_flags & 0xFFu) > AGS_BVH_Q8) return invalid("unsupported BVH node format in build_flags");
-  if ((build_flags & ~(0xFFFFFu | AGS_BUILD_LBVH)) != 0) return invalid("unknown bits in build_flags");
+  if ((build_flags & ~(0xFFFFFu | AGS_BUILD_LBVH | AGS_BUILD_INSTANCED)) != 0) return invalid("unknown bits in build_flags");
+  if ((build_flags & AGS_BUILD_INSTANCED) && (build_flags & 0xFFu) != AGS_BVH_FP32)
+    return invalid("two-level scenes use float32 nodes");
   if (((build_flags >> 8) & 0xFu) > (uint32_t)kMaxLeafTris) return invalid("leaf size must be 1..4");
   // sizes
   int64_t J = 0, V = 0, F = 0;
@@ -302,8 +323,11 @@ ags_status ags_scene_build(ags_context* ctx, const ags_env_mesh* envs, int32_t n
     sc->env_sub_off[e + 1] = j_all;
   }
   DeviceGuard g(ctx->device);
-  ags_status st = build_scene(ctx, sc.get(), base.data(), vidx.data(), sub_vert.data(), obstacle_poses,
-                              sub_env.data());
+  ags_status st = (build_flags & AGS_BUILD_INSTANCED)
+                      ? build_instanced(ctx, sc.get(), base.data(), vidx.data(), sub_vert.data(), obstacle_poses,
+                                        sub_env.data())
+                      : build_scene(ctx, sc.get(), base.data(), vidx.data(), sub_vert.data(), obstacle_poses,
+                                    sub_env.data());
   if (st == AGS_OK) {
     sc->h_base = std::move(base);
     sc->h_vidx = std::move(vidx);
@@ -325,6 +349,7 @@ ags_status ags_scene_build(ags_context* ctx, const ags_env_mesh* envs, int32_t n
 void ags_scene_destroy(ags_scene* sc) {
   if (!sc) return;
   DeviceGuard g(sc->ctx->device);
+  destroy_instanced(sc);
   cudaFree(sc->d.world_verts);
   cudaFree(sc->d.tri_vidx);
   cudaFree(sc->d.nodes);
@@ -406,7 +431,9 @@ ags_status ags_scene_update_poses(ags_context* ctx, ags_scene* sc, const float* 
   }
   DeviceGuard g(ctx->device);
   ags_status st;
-  if (mode == AGS_UPDATE_REFIT) {
+  if (sc->objects) {
+    st = update_instanced(ctx, sc, poses);  // two levels: rewrite the object table, rebuild the top level
+  } else if (mode == AGS_UPDATE_REFIT) {
     if (sc->node_format != kNodeFp32) return invalid("refit needs float32 nodes; use AGS_UPDATE_REBUILD");
     st = refit_scene(ctx, sc, poses);
   } else {
@@ -452,6 +479,8 @@ ags_status ags_render_ex(ags_context* ctx, const ags_scene* sc, const ags_sensor
   if (!ctx || !sc) return invalid("ctx or scene is NULL");
   if (sc->ctx != ctx) return invalid("scene belongs to another context");
   if (table && reinterpret_cast<uintptr_t>(table) % 4 != 0) return invalid("ray table not 4-byte aligned");
+  if (sc->objects && (ch || stereo || table))
+    return invalid("two-level scenes render without channels, stereo or ray tables");
   ags_status st = check_spec(spec, table != nullptr);
   if (st != AGS_OK) return st;
   if (!poses || !depth || !seg) return invalid("poses/depth/seg pointer is NULL");
@@ -605,6 +634,7 @@ ags_status ags_render_count(ags_context* ctx, const ags_scene* sc, const ags_sen
   ags_status st = check_spec(spec, false);
   if (st != AGS_OK) return st;
   if (!poses || !counts_host) return invalid("poses/counts pointer is NULL");
+  if (sc->objects) return invalid("counting needs a single-level scene");
   DeviceGuard g(ctx->device);
   TraceArgs a{};
   if ((st = fill_trace_args(ctx, sc, spec, sc->n_envs, nullptr, poses, nullptr, nullptr, a, default_config())) !=
@@ -772,6 +802,8 @@ ags_status ags_set_launch_config(ags_context* ctx, const ags_scene* sc, const ag
     return AGS_OK;
   }
   if ((st = check_config(ctx, config)) != AGS_OK) return st;
+  if (sc->objects && (config->tile_w != 8 || config->rays_per_lane != 1))
+    return invalid("two-level scenes render with the 8x4 tile");
   sc->launch[{spec->type, spec->width, spec->height}] = *config;
   return AGS_OK;
   AGS_API_END
@@ -814,6 +846,7 @@ ags_status ags_autotune(ags_context* ctx, const ags_scene* sc, const ags_sensor_
   for (int gi = 0; gi < 2 && st == AGS_OK; ++gi) {
     if (gi == 1 && grids[1] == 0) break;
     for (int k = 0; k < kTraceShapes && st == AGS_OK; ++k) {
+      if (sc->objects && (kTraceShape[k][0] != 8 || kTraceShape[k][1] != 1)) continue;  // two levels: 8x4 only
       ags_launch_config c = {kTraceShape[k][0], kTraceShape[k][1], grids[gi], 0.0f};
       TraceArgs a{};
       if ((st = fill_trace_args(ctx, sc, spec, sc->n_envs, nullptr, poses, depth, seg, a, c)) != AGS_OK) break;
@@ -883,6 +916,7 @@ ags_status ags_autotune_build(ags_context* ctx, ags_scene* sc, const ags_sensor_
   AGS_API_BEGIN
   if (!ctx || !sc) return invalid("ctx or scene is NULL");
   if (sc->ctx != ctx) return invalid("scene belongs to another context");
+  if (sc->objects) return invalid("splitting tuning needs a single-level scene");
   ags_status st = check_spec(spec, false);
   if (st != AGS_OK) return st;
   if (!poses || !depth || !seg || !best_cells || (n_cells > 0 && !cells)) return invalid("NULL pointer argument");

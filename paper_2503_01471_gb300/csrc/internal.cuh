@@ -72,6 +72,18 @@ struct Box {
   float lox, loy, loz, hix, hiy, hiz;
 };
 
+// One object of a two-level scene: the rotation that takes world vectors to
+// the object's frame, its position, the root of its own BVH and its first
+// triangle within its environment.
+struct InstanceDev {
+  float rt[9];          // R(q)^T, row-major
+  float p[3];
+  int32_t root;         // wide node in the object-level pool, -1 for an empty object
+  int32_t tri_base;     // environment-local index of the object's first triangle
+  int32_t pad[2];
+};
+static_assert(sizeof(InstanceDev) == 64, "InstanceDev layout");
+
 }  // namespace ags
 
 struct ags_context {
@@ -117,6 +129,13 @@ struct ags_scene {
   std::vector<int32_t> h_vidx, h_sub_vert, h_sub_env;
   std::vector<float> h_poses;  // the current object poses [J][7] (rebuilds start from these)
   mutable std::map<LaunchKey, ags_launch_config> launch;  // tuned or set launch shapes per sensor shape
+  // two-level scenes (AGS_BUILD_INSTANCED): a BVH per object in its own frame (`objects`, one
+  // environment per object) and per environment a BVH over its objects' world boxes (`top`)
+  ags_scene* objects = nullptr;
+  ags_scene* top = nullptr;
+  ags::InstanceDev* d_inst = nullptr;  // [J]
+  int32_t* d_env_sub = nullptr;        // [E+1]
+  std::vector<double> h_obj_box;       // [J][6] object-frame bounds of each object's vertices
 };
 
 namespace ags {
@@ -171,6 +190,17 @@ ags_status build_ploc(const uint64_t* keys, uint32_t* vals, int32_t R, int key_s
                       int32_t E, const Box* ref_box, Box* leaf_box, int32_t* left, int32_t* right, int32_t* first,
                       int32_t* last, Box* inner_box, std::vector<int32_t>& roots, cudaStream_t s);
 
+// build.cu: world vertices v' = R(q) v + p of every sub-mesh (float-float, as the scene build)
+ags_status transform_vertices(const float* base_dev, int32_t V, const int32_t* sub_vert_off_dev, int32_t J,
+                              const float* poses_dev, float4* world_dev, cudaStream_t s);
+
+// instanced.cu: two-level scenes. build_instanced fills sc (its sizes and offsets already set) from the
+// host inputs; update_instanced moves the objects; destroy_instanced frees what the two levels hold.
+ags_status build_instanced(ags_context* ctx, ags_scene* sc, const float* base_verts_h, const int32_t* tri_vidx_h,
+                           const int32_t* sub_vert_off_h, const float* poses_h, const int32_t* sub_env_h);
+ags_status update_instanced(ags_context* ctx, ags_scene* sc, const float* poses_h);
+void destroy_instanced(ags_scene* sc);
+
 // build.cu
 ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_h,
                        const int32_t* tri_vidx_h, const int32_t* sub_vert_off_h,
@@ -224,6 +254,14 @@ struct TraceArgs {
   float* out_normal;
   float* out_point;
   int32_t extra;             // bit 0: hit channels; bit 1: stereo shadow test; bit 2: ray table
+  // two-level scenes: nodes / tris / env_root above are the top level over objects
+  int32_t instanced;
+  const InstanceDev* inst;
+  int32_t n_inst;
+  const int32_t* env_sub;    // [E+1] first object of each environment
+  const void* obj_nodes;     // object-level pool (float32 nodes)
+  const float4* obj_tris;
+  int32_t obj_n_nodes, obj_n_tris;
   float baseline[3];         // stereo: second sensor's origin in the sensor frame
   float shadow_eps;          // stereo: the shadow segment starts at this fraction
   int32_t n;                 // environments rendered
@@ -241,6 +279,7 @@ struct TraceArgs {
 };
 cudaError_t launch_trace(const TraceArgs& a, int blocks, bool count, cudaStream_t s);
 cudaError_t launch_trace_extra(const TraceArgs& a, int blocks, cudaStream_t s);  // a.extra != 0
+cudaError_t launch_trace_inst(const TraceArgs& a, int blocks, cudaStream_t s);   // a.instanced != 0
 // compiled launch shapes of the render kernel: {tile width, rays per lane}
 constexpr int kTraceShapes = 5;
 constexpr int kTraceShape[kTraceShapes][2] = {{8, 1}, {4, 1}, {8, 2}, {16, 2}, {16, 4}};

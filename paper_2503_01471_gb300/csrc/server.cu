@@ -252,6 +252,7 @@ ags_status ags_server_create(ags_context* ctx, const ags_scene* scene, const ags
     *out = nullptr;
     if (!ctx || !scene || !cfg) return invalid_arg("ctx, scene or config is NULL");
     if (scene->ctx != ctx) return invalid_arg("scene belongs to another context");
+    if (scene->objects) return invalid_arg("serving needs a single-level scene");
     if (cfg->max_slots < 1 || cfg->max_slots > 65536) return invalid_arg("max_slots must be in [1, 65536]");
     if (cfg->max_inflight < 1 || cfg->max_inflight > 16) return invalid_arg("max_inflight must be in [1, 16]");
     if (cfg->n_specs < 1 || cfg->n_specs > 256 || !cfg->specs) return invalid_arg("need 1..256 sensor specs");

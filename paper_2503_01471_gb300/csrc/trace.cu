@@ -51,6 +51,7 @@ cudaError_t launch_fmt(const TraceArgs& a, int blocks, bool count, cudaStream_t 
 }  // namespace
 
 cudaError_t launch_trace(const TraceArgs& a, int blocks, bool count, cudaStream_t s) {
+  if (a.instanced) return count ? cudaErrorInvalidValue : launch_trace_inst(a, blocks, s);
   switch (a.node_format) {
     case kNodeFp32: return launch_fmt<kNodeFp32>(a, blocks, count, s);
     case kNodeFp16: return launch_fmt<kNodeFp16>(a, blocks, count, s);

@@ -751,3 +751,90 @@ def test_build_tuning_keeps_results_and_updates(ctx):
             ags.ags_scene_destroy(fresh)
     finally:
         ags.ags_scene_destroy(scene)
+
+
+# ---------------------------------------------------------------- two-level scenes
+@pytest.mark.parametrize("sensor", ["camera", "lidar"])
+def test_two_level_scene_matches_oracle(ctx, sensor):
+    """Objects with their own BVHs under a per-environment BVH over their boxes: every ray against the
+    oracle, and against a single-level scene of the same objects within the tolerance."""
+    batch, spec, poses = S.obstacle_rooms(3, steps=1, width=64, height=48)
+    if sensor == "lidar":
+        spec = S.lidar(128, 24, (-30.0, 30.0), 0.2, 12.0)
+    two = ags.ags_scene_build(ctx, batch, ags.AGS_BUILD_INSTANCED)
+    one = ags.ags_scene_build(ctx, batch)
+    try:
+        d2, s2 = render(ctx, two, spec, poses[0])
+        d1, s1 = render(ctx, one, spec, poses[0])
+        check_all(batch, spec, poses[0], d2, s2, tag=f"two-level {sensor} {spec.height}x{spec.width}")
+        same_seg = (s1 == s2).mean()
+        assert same_seg > 0.99
+        both = (s1 >= 0) & (s2 >= 0) & (s1 == s2)
+        assert np.all(np.abs(d1[both] - d2[both]) <= 1e-5 * d1[both] + 1e-6)
+        for e in range(3):
+            a, sa = ags.ags_scene_get_world_triangles(two, e)
+            b, sb = ags.ags_scene_get_world_triangles(one, e)
+            assert np.array_equal(a, b) and np.array_equal(sa, sb)
+    finally:
+        ags.ags_scene_destroy(two)
+        ags.ags_scene_destroy(one)
+
+
+def test_two_level_scene_updates_and_limits(ctx):
+    """Moving every object rewrites the object table and rebuilds only the top level; the images then
+    match the oracle of the moved scene. Unsupported options are refused."""
+    batch, spec, poses = S.obstacle_rooms(3, steps=1, width=48, height=36)
+    two = ags.ags_scene_build(ctx, batch, ags.AGS_BUILD_INSTANCED)
+    try:
+        rng = np.random.default_rng(25)
+        cur = batch.poses.copy()
+        for step in range(2):
+            cur[:, :3] += rng.normal(0, 0.3, (cur.shape[0], 3)).astype(np.float32)
+            q = cur[:, 3:] + rng.normal(0, 0.2, (cur.shape[0], 4)).astype(np.float32)
+            cur[:, 3:] = q / np.linalg.norm(q, axis=1, keepdims=True)
+            ags.ags_scene_update_poses(ctx, two, cur, ags.AGS_UPDATE_REFIT)
+            moved = S.SceneBatch(batch.vertices, batch.indices, batch.sub_vert, batch.sub_tri, batch.sub_seg,
+                                 batch.env_sub, cur.copy())
+            d, s = render(ctx, two, spec, poses[0])
+            check_all(moved, spec, poses[0], d, s, tag="two-level after moves 48x36")
+        p = torch.as_tensor(poses[0]).cuda()
+        dd = torch.empty((3, 36, 48), device="cuda")
+        ss = torch.empty((3, 36, 48), dtype=torch.int32, device="cuda")
+        with pytest.raises(ags.AgsError):
+            ags.ags_render_ex(ctx, two, spec, p, dd, ss, face=torch.empty((3, 36, 48), dtype=torch.int32,
+                                                                          device="cuda"))
+        with pytest.raises(ags.AgsError):
+            ags.ags_render_count(ctx, two, spec, p)
+        with pytest.raises(ags.AgsError):
+            ags.ags_scene_build(ctx, batch, ags.AGS_BUILD_INSTANCED | ags.AGS_BVH_Q8)
+        cfg = ags.ags_autotune(ctx, two, spec, p, dd, ss, 1).as_dict()
+        assert cfg["tile_w"] == 8 and cfg["rays_per_lane"] == 1
+        hd, hs = ags.ags_render_host(ctx, two, spec, np.ascontiguousarray(poses[0]))
+        d, s = render(ctx, two, spec, poses[0])
+        assert np.array_equal(hd, d) and np.array_equal(hs, s)
+    finally:
+        ags.ags_scene_destroy(two)
+
+
+def test_two_level_empty_and_tiny(ctx):
+    tri = (np.array([[3, -3, -3], [3, 3, -3], [3, 0, 3]], np.float32), np.array([[0, 1, 2]], np.int32),
+           S.IDENTITY_POSE, 7)
+    empty_obj = (np.zeros((0, 3), np.float32), np.zeros((0, 3), np.int32), S.IDENTITY_POSE, 3)
+    batch = S.scene_from_lists([[], [tri], [tri, empty_obj, tri]])
+    spec = S.pinhole(5, 3, 90.0, 0.1, 10.0)
+    poses = np.tile(S.IDENTITY_POSE, (3, 1))
+    two = ags.ags_scene_build(ctx, batch, ags.AGS_BUILD_INSTANCED)
+    try:
+        d, s = render(ctx, two, spec, poses)
+        assert (s[0] == -1).all() and (d[0] == np.float32(10.0)).all()
+        check_all(batch, spec, poses, d, s)
+    finally:
+        ags.ags_scene_destroy(two)
+    batch, spec, poses = S.tiny_room()
+    two = ags.ags_scene_build(ctx, batch, ags.AGS_BUILD_INSTANCED)
+    try:
+        for k in range(0, 16, 5):
+            d, s = render(ctx, two, spec, poses[k:k + 1])
+            check_all(batch, spec, poses[k:k + 1], d, s, tag="two-level tiny room 64x48")
+    finally:
+        ags.ags_scene_destroy(two)
