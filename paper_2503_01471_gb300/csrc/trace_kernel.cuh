@@ -1033,8 +1033,8 @@ __device__ __forceinline__ void trace_tile_inst(const TraceArgs& a, const Sensor
   a.out_seg[o] = seg;
 }
 
-// two world-to-object levels hold two rays: a larger register budget (4 blocks per SM) than k_trace
-__global__ void __launch_bounds__(kTraceThreads, 4) k_trace_inst(const TraceArgs a) {
+// two levels hold two rays: a larger register budget than k_trace (6 blocks per SM measured best of 4..8)
+__global__ void __launch_bounds__(kTraceThreads, 6) k_trace_inst(const TraceArgs a) {
   const int lane = threadIdx.x & 31;
   int2 stack[kStackSize];
   while (true) {
