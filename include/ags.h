@@ -298,6 +298,22 @@ ags_status ags_render_count(ags_context* ctx, const ags_scene* scene, const ags_
                             const float* sensor_poses_dev, uint64_t counts_host[3]);
 
 /*
+ * ags_scene_validate -- structural checks of the scene's BVH, a test and
+ * debugging aid (the paper has no counterpart), run on the host from the
+ * device data the render kernel reads: every wide node and every reference
+ * reached exactly once from its environment's root, every index in range,
+ * each packed triangle copy equal to its source triangle (vertices, segment
+ * ID, environment-local index), and every point of a 28-point barycentric
+ * grid on every triangle inside all the boxes on the path to one of its
+ * references, with boxes decoded from the scene's node format (so a ray that
+ * meets a triangle reaches a leaf holding it). Two-level scenes are checked
+ * level by level. counts[0] = wide nodes, [1] = points checked, [2] =
+ * violations (the first few are described by ags_last_error), [3] = deepest
+ * path in nodes. Synchronous; copies the scene to host memory.
+ */
+ags_status ags_scene_validate(const ags_scene* scene, int64_t counts[4]);
+
+/*
  * ags_autotune_build -- build-time tuning of the reference splitting (the
  * AGS_SPLIT_CELLS setting, 0 = the default 16 cells, 1 = off): the scene is
  * rebuilt, from its kept inputs and current object poses, with each listed

@@ -57,7 +57,7 @@ EXPORTS = [
     "ags_set_launch_config", "ags_get_launch_config", "ags_memcpy_d2h", "ags_server_create", "ags_server_destroy",
     "ags_server_submit", "ags_server_poll", "ags_server_release", "ags_server_stats", "ags_server_replay",
     "ags_replay_sequential", "ags_scene_update_poses", "ags_render_graph_create", "ags_render_graph_launch",
-    "ags_render_graph_destroy", "ags_render_channels", "ags_render_ex", "ags_autotune_build",
+    "ags_render_graph_destroy", "ags_render_channels", "ags_render_ex", "ags_autotune_build", "ags_scene_validate",
 ]
 
 
@@ -195,6 +195,7 @@ def lib() -> ctypes.CDLL:
                                       ctypes.POINTER(ags_hit_channels), vp]),
         "ags_render_ex": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), vp, vp, vp,
                                 ctypes.POINTER(ags_render_options), vp]),
+        "ags_scene_validate": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
         "ags_autotune_build": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), vp, vp, vp,
                                      ctypes.POINTER(ctypes.c_uint32), i32, i32, ctypes.POINTER(ctypes.c_uint32)]),
     }
@@ -550,3 +551,14 @@ def ags_autotune_build(ctx: int, scene: int, spec, sensor_poses, out_depth, out_
     _check(lib().ags_autotune_build(ctx, scene, ctypes.byref(s), _ptr(sensor_poses), _ptr(out_depth), _ptr(out_seg),
                                     c, len(split_cells), int(repeats), ctypes.byref(best)), "ags_autotune_build")
     return int(best.value)
+
+
+def ags_scene_validate(scene: int) -> dict:
+    """Structural BVH checks; returns nodes, points, violations, depth (and the first problems if any)."""
+    c = (ctypes.c_int64 * 4)()
+    _check(lib().ags_scene_validate(scene, c), "ags_scene_validate")
+    out = {"nodes": c[0], "points": c[1], "violations": c[2], "depth": c[3]}
+    if c[2]:
+        msg = lib().ags_last_error()
+        out["problems"] = msg.decode() if msg else ""
+    return out

@@ -838,3 +838,101 @@ def test_two_level_empty_and_tiny(ctx):
             check_all(batch, spec, poses[k:k + 1], d, s, tag="two-level tiny room 64x48")
     finally:
         ags.ags_scene_destroy(two)
+
+
+# ---------------------------------------------------------------- watertightness
+@pytest.mark.parametrize("mesh", ["icosphere", "cylinder", "box", "cone"])
+def test_no_ray_slips_through_closed_meshes(ctx, mesh):
+    """From inside a closed mesh every ray must hit, including rays aimed exactly at its vertices and at the
+    midpoints of its edges (where a test that is not watertight lets rays through cracks); the hits also
+    match the oracle. Ray tables carry the aimed directions."""
+    if mesh == "icosphere":
+        v, f = S.icosphere(1.7, level=3)
+        centre = np.array([0.11, -0.07, 0.05])
+    elif mesh == "cylinder":
+        v, f = S.cylinder(0.9, 2.5, 48)
+        centre = np.array([0.05, 0.1, -0.3])
+    elif mesh == "box":
+        v, f = S.box(2.0, 1.4, 3.1)
+        centre = np.array([0.2, -0.1, 0.3])
+    else:
+        v, f = S.cone(1.2, 2.0, 40)
+        centre = np.array([0.05, -0.02, 0.4])
+    batch = S.scene_from_lists([[(v, f, S.IDENTITY_POSE, 4)]])
+    scene = ags.ags_scene_build(ctx, batch)
+    try:
+        v64 = v.astype(np.float64)
+        edges = set()
+        for a, b, c in f:
+            for x, y in ((a, b), (b, c), (c, a)):
+                edges.add((min(x, y), max(x, y)))
+        targets = [v64] + [np.array([(v64[x] + v64[y]) / 2 for x, y in sorted(edges)])]
+        rng = np.random.default_rng(26)
+        targets.append(rng.normal(size=(512, 3)) + centre)
+        dirs = np.concatenate(targets) - centre
+        n = dirs.shape[0]
+        W = 64
+        H = (n + W - 1) // W
+        table = np.zeros((H * W, 3), np.float32)
+        table[:n] = dirs
+        table[n:] = dirs[0]
+        table = table.reshape(H, W, 3)
+        spec = S.ray_table_spec(W, H, 0.01, 100.0)
+        pose = np.concatenate([centre, [0, 0, 0, 1]]).astype(np.float32)[None]
+        p = torch.as_tensor(pose).cuda()
+        d = torch.empty((1, H, W), device="cuda")
+        sg = torch.empty((1, H, W), dtype=torch.int32, device="cuda")
+        ags.ags_render_ex(ctx, scene, spec, p, d, sg, ray_table=torch.as_tensor(table).cuda())
+        ags.ags_stream_status(ctx)
+        d, sg = d.cpu().numpy().reshape(-1), sg.cpu().numpy().reshape(-1)
+        assert (sg == 4).all(), f"{int((sg != 4).sum())} of {sg.size} rays slipped through"
+        tris, tseg = oracle_env(batch, 0)
+        s = oracle_sensor(spec)
+        s.dirs = table.astype(np.float64)
+        rays = np.arange(H * W, dtype=np.int64)
+        res = O.render(tris, tseg, s, pose[0].astype(np.float64), rays)
+        ok, counted = O.check(res, d, sg, s.max_range)
+        assert ok.all(), describe_failures(ok, res, d, sg, rays)
+        print(f"[parity] watertight {mesh}: {n} aimed rays ({v.shape[0]} vertices, {len(edges)} edge midpoints), "
+              f"all hit, {int(counted.sum())} counted")
+    finally:
+        ags.ags_scene_destroy(scene)
+
+
+# ---------------------------------------------------------------- BVH structure
+def test_bvh_structure_of_every_variant(ctx):
+    """Every node and reference reached once, copies equal to their triangles, and every point of every
+    triangle inside the boxes of a path to one of its references: all builders, formats, leaf sizes and
+    splitting settings, a two-level scene, a refitted scene and a LiDAR forest."""
+    batch, spec, poses = S.obstacle_rooms(4, steps=1, width=8, height=8)
+    variants = [0, ags.AGS_BVH_FP16, ags.AGS_BVH_Q8, ags.AGS_LEAF_SIZE(1), ags.AGS_LEAF_SIZE(4),
+                ags.AGS_SPLIT_CELLS(1), ags.AGS_SPLIT_CELLS(64), ags.AGS_BUILD_LBVH,
+                ags.AGS_BUILD_LBVH | ags.AGS_BVH_Q8 | ags.AGS_LEAF_SIZE(3), ags.AGS_BUILD_INSTANCED]
+    for flags in variants:
+        scene = ags.ags_scene_build(ctx, batch, flags)
+        try:
+            r = ags.ags_scene_validate(scene)
+            assert r["violations"] == 0 and r["points"] > 0, (flags, r.get("problems"), r)
+            assert r["depth"] * 7 <= 64 or flags & ags.AGS_BUILD_INSTANCED, (flags, r)
+        finally:
+            ags.ags_scene_destroy(scene)
+    scene = ags.ags_scene_build(ctx, batch)
+    try:
+        rng = np.random.default_rng(27)
+        new = batch.poses.copy()
+        new[:, :3] += rng.normal(0, 0.4, (new.shape[0], 3)).astype(np.float32)
+        q = new[:, 3:] + rng.normal(0, 0.3, (new.shape[0], 4)).astype(np.float32)
+        new[:, 3:] = q / np.linalg.norm(q, axis=1, keepdims=True)
+        ags.ags_scene_update_poses(ctx, scene, new, ags.AGS_UPDATE_REFIT)
+        r = ags.ags_scene_validate(scene)
+        assert r["violations"] == 0, r
+    finally:
+        ags.ags_scene_destroy(scene)
+    fb, _, _ = S.lidar_forests(1, steps=1, trees=(5, 8), tris=(2000, 3000))
+    scene = ags.ags_scene_build(ctx, fb, ags.AGS_SPLIT_CELLS(48))
+    try:
+        r = ags.ags_scene_validate(scene)
+        assert r["violations"] == 0, r
+        print(f"[structure] forest: {r}")
+    finally:
+        ags.ags_scene_destroy(scene)
