@@ -56,7 +56,8 @@ typedef enum {
   AGS_ERR_TRAVERSAL_LIMIT = 4,/* a ray hit the stack or iteration limit, or met an out-of-range
                                  index; that ray's output is NaN */
   AGS_ERR_NOT_READY = 5,
-  AGS_ERR_BUSY = 6
+  AGS_ERR_BUSY = 6,
+  AGS_ERR_CANCELLED = 7       /* a served request cancelled before it was batched */
 } ags_status;
 
 typedef struct ags_context ags_context;
@@ -402,6 +403,11 @@ ags_status ags_server_submit(ags_server* server, const ags_request* request, uin
 ags_status ags_server_poll(ags_server* server, ags_completion* out, int32_t max, int32_t* n_out);
 /* Free a completed request's outputs in the arena. Thread-safe. */
 ags_status ags_server_release(ags_server* server, uint64_t request_id);
+
+/* Cancel a request that is still queued (not yet in a batch): it leaves the
+ * queue and completes at once with status AGS_ERR_CANCELLED and no outputs.
+ * AGS_ERR_BUSY if it is already batched, done or unknown. */
+ags_status ags_server_cancel(ags_server* server, uint64_t request_id);
 /* Counters; any pointer may be NULL. */
 ags_status ags_server_stats(ags_server* server, int64_t* submitted, int64_t* completed, int64_t* batches,
                             int64_t* arena_free_bytes);

@@ -26,8 +26,9 @@ AGS_ERR_CUDA = 3
 AGS_ERR_TRAVERSAL_LIMIT = 4
 AGS_ERR_NOT_READY = 5
 AGS_ERR_BUSY = 6
+AGS_ERR_CANCELLED = 7
 STATUS_NAMES = {0: "AGS_OK", 1: "AGS_ERR_INVALID_ARG", 2: "AGS_ERR_OUT_OF_MEMORY", 3: "AGS_ERR_CUDA",
-                4: "AGS_ERR_TRAVERSAL_LIMIT", 5: "AGS_ERR_NOT_READY", 6: "AGS_ERR_BUSY"}
+                4: "AGS_ERR_TRAVERSAL_LIMIT", 5: "AGS_ERR_NOT_READY", 6: "AGS_ERR_BUSY", 7: "AGS_ERR_CANCELLED"}
 
 AGS_PINHOLE = 0
 AGS_LIDAR = 1
@@ -58,6 +59,7 @@ EXPORTS = [
     "ags_server_submit", "ags_server_poll", "ags_server_release", "ags_server_stats", "ags_server_replay",
     "ags_replay_sequential", "ags_scene_update_poses", "ags_render_graph_create", "ags_render_graph_launch",
     "ags_render_graph_destroy", "ags_render_channels", "ags_render_ex", "ags_autotune_build", "ags_scene_validate",
+    "ags_server_cancel",
 ]
 
 
@@ -196,6 +198,7 @@ def lib() -> ctypes.CDLL:
         "ags_render_ex": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), vp, vp, vp,
                                 ctypes.POINTER(ags_render_options), vp]),
         "ags_scene_validate": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
+        "ags_server_cancel": (i32, [vp, ctypes.c_uint64]),
         "ags_autotune_build": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), vp, vp, vp,
                                      ctypes.POINTER(ctypes.c_uint32), i32, i32, ctypes.POINTER(ctypes.c_uint32)]),
     }
@@ -562,3 +565,14 @@ def ags_scene_validate(scene: int) -> dict:
         msg = lib().ags_last_error()
         out["problems"] = msg.decode() if msg else ""
     return out
+
+
+def ags_server_cancel(server: int, request_id: int) -> bool:
+    """Cancel a queued request; False if it is already batched, done or unknown."""
+    rc = lib().ags_server_cancel(server, int(request_id))
+    if rc == 0:
+        return True
+    if rc == AGS_ERR_BUSY:
+        return False
+    _check(rc, "ags_server_cancel")
+    return False

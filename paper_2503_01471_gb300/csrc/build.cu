@@ -832,6 +832,7 @@ unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1
 
 ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_h, const int32_t* tri_vidx_h,
                        const int32_t* sub_vert_off_h, const float* poses_h, const int32_t* sub_env_h) {
+  NvtxRange range("ags build_scene");
   cudaStream_t s = ctx->stream;
   const int32_t E = sc->n_envs;
   const int32_t F = (int32_t)sc->n_tris;
@@ -1308,6 +1309,7 @@ ags_status transform_vertices(const float* base_dev, int32_t V, const int32_t* s
 }
 
 ags_status refit_scene(ags_context* ctx, ags_scene* sc, const float* poses_h) {
+  NvtxRange range("ags refit_scene");
   cudaStream_t s = ctx->stream;
   if (!sc->d.nodes_build && sc->n_nodes > 0) {
     AGS_CHECK(cudaMalloc(&sc->d.nodes_build, (size_t)sc->n_nodes * sizeof(WideNode)));

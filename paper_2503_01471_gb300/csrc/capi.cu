@@ -154,6 +154,7 @@ ags_status fill_trace_args(ags_context* ctx, const ags_scene* sc, const ags_sens
 }
 
 ags_status launch(ags_context* ctx, TraceArgs& a, cudaStream_t s, bool count, int blocks_per_sm = 0) {
+  NvtxRange range(count ? "ags render (count)" : "ags render");
   unsigned int* counter = tile_counter(ctx, s);
   if (!counter) {
     set_error("cannot allocate the tile counter");

@@ -249,6 +249,7 @@ ags_status build_instanced(ags_context* ctx, ags_scene* sc, const float* base_h,
 }
 
 ags_status update_instanced(ags_context* ctx, ags_scene* sc, const float* poses_h) {
+  NvtxRange range("ags two-level update");
   ags_scene* top = nullptr;
   ags_status st = build_top(ctx, sc, poses_h, &top);
   if (st != AGS_OK) return st;

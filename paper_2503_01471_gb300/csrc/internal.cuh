@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/ags.h"
 
 namespace ags {
@@ -152,6 +154,14 @@ cudaError_t sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* alt_keys, uint3
 // exclusive scan of n int32 values in place; returns the total in *total_dev (device int)
 size_t scan_temp_bytes(int64_t n);
 cudaError_t exclusive_scan(int32_t* data, int64_t n, int32_t* total_dev, void* temp, cudaStream_t s);
+
+// An NVTX range over a scope (shown by profilers that record NVTX; free when none is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // device scratch freed when the holder goes out of scope
 struct DevBufs {

@@ -211,6 +211,7 @@ int blocks_of(int64_t n, int t) { return (int)((n + t - 1) / t); }
 ags_status build_ploc(const uint64_t* keys, uint32_t* vals, int32_t R, int key_shift, const int32_t* env_ref_off,
                       int32_t E, const Box* ref_box, Box* leaf_box, int32_t* left, int32_t* right, int32_t* first,
                       int32_t* last, Box* inner_box, std::vector<int32_t>& roots, cudaStream_t s) {
+  NvtxRange range("ags clustering");
   roots.assign(E, -1);
   if (R <= 0) return AGS_OK;
   DevBufs tmp;

@@ -150,6 +150,7 @@ void retire(ags_server* sv) {
 }
 
 bool launch_batch(ags_server* sv) {
+  NvtxRange range("ags serving batch");
   int lane = -1;
   for (int k = 0; k < sv->max_inflight; ++k)
     if (!sv->lane_busy[k]) {
@@ -404,6 +405,26 @@ ags_status ags_server_release(ags_server* sv, uint64_t request_id) {
   }
   sv->cv.notify_one();
   return AGS_OK;
+}
+
+ags_status ags_server_cancel(ags_server* sv, uint64_t request_id) {
+  if (!sv) return invalid_arg("server is NULL");
+  std::lock_guard<std::mutex> lk(sv->m);
+  for (auto it = sv->pending.begin(); it != sv->pending.end(); ++it) {
+    if (it->id != request_id) continue;
+    ags_completion c{};
+    c.request_id = it->id;
+    c.tag = it->req.tag;
+    c.status = AGS_ERR_CANCELLED;
+    c.t_submit = it->t_submit;
+    c.t_start = c.t_done = now_s();
+    sv->pending.erase(it);
+    sv->done.push_back(c);
+    ++sv->completed;
+    return AGS_OK;
+  }
+  set_error("request is not queued (already batched, done or unknown)");
+  return AGS_ERR_BUSY;
 }
 
 ags_status ags_server_stats(ags_server* sv, int64_t* submitted, int64_t* completed, int64_t* batches,

@@ -141,3 +141,31 @@ def test_replay_and_sequential_baseline(setup):
     seq = ags.ags_replay_sequential(ctx, scene, specs, reqs[:100], arrival[:100])
     assert (seq["status"] == 0).all()
     assert ((seq["t_done"] - seq["t_submit"]) > 0).all()
+
+
+def test_cancel_queued_requests(setup):
+    """A queued request can be cancelled (it completes at once, cancelled, with no outputs); a request
+    already served cannot."""
+    ctx, batch, scene, specs, poses = setup
+    # an arena that holds one request at a time keeps the rest queued
+    req_bytes = 64 * 48 * 8
+    server = ags.ags_server_create(ctx, scene, specs[:1], max_slots=4, max_inflight=1, arena_bytes=req_bytes + 64)
+    try:
+        ids = [ags.ags_server_submit(server, e % 6, 0, poses[e % 6]) for e in range(6)]
+        first = _wait(server, ids[:1])
+        cancelled = [rid for rid in ids[2:] if ags.ags_server_cancel(server, rid)]
+        assert len(cancelled) >= 3
+        assert not ags.ags_server_cancel(server, ids[0])  # already done
+        got = _wait(server, cancelled)
+        for rid in cancelled:
+            c = got[rid]
+            assert int(c["status"]) == ags.AGS_ERR_CANCELLED and int(c["depth_dev"]) == 0
+        ags.ags_server_release(server, ids[0])
+        rest = [rid for rid in ids[1:] if rid not in cancelled]
+        done = _wait(server, rest)
+        for rid in rest:
+            assert int(done[rid]["status"]) == 0
+            ags.ags_server_release(server, rid)
+        assert first
+    finally:
+        ags.ags_server_destroy(server)
