@@ -299,6 +299,17 @@ ags_status ags_render_count(ags_context* ctx, const ags_scene* scene, const ags_
                             const float* sensor_poses_dev, uint64_t counts_host[3]);
 
 /*
+ * Test hooks of two building blocks of ags_scene_build (no counterpart in the
+ * paper): the stable LSD radix sort of (uint64 key, uint32 value) pairs on
+ * key bits [0, end_bit) (1 <= end_bit <= 64), in place on device buffers, and
+ * the exclusive scan of int32 values in place on a device buffer, with the
+ * total written to *total_host. Both synchronise the context's stream.
+ */
+ags_status ags_test_sort_pairs(ags_context* ctx, uint64_t* keys_dev, uint32_t* vals_dev, int64_t n,
+                               int32_t end_bit);
+ags_status ags_test_exclusive_scan(ags_context* ctx, int32_t* data_dev, int64_t n, int32_t* total_host);
+
+/*
  * ags_scene_validate -- structural checks of the scene's BVH, a test and
  * debugging aid (the paper has no counterpart), run on the host from the
  * device data the render kernel reads: every wide node and every reference

@@ -59,7 +59,7 @@ EXPORTS = [
     "ags_server_submit", "ags_server_poll", "ags_server_release", "ags_server_stats", "ags_server_replay",
     "ags_replay_sequential", "ags_scene_update_poses", "ags_render_graph_create", "ags_render_graph_launch",
     "ags_render_graph_destroy", "ags_render_channels", "ags_render_ex", "ags_autotune_build", "ags_scene_validate",
-    "ags_server_cancel",
+    "ags_server_cancel", "ags_test_sort_pairs", "ags_test_exclusive_scan",
 ]
 
 
@@ -199,6 +199,8 @@ def lib() -> ctypes.CDLL:
                                 ctypes.POINTER(ags_render_options), vp]),
         "ags_scene_validate": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
         "ags_server_cancel": (i32, [vp, ctypes.c_uint64]),
+        "ags_test_sort_pairs": (i32, [vp, vp, vp, ctypes.c_int64, i32]),
+        "ags_test_exclusive_scan": (i32, [vp, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)]),
         "ags_autotune_build": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), vp, vp, vp,
                                      ctypes.POINTER(ctypes.c_uint32), i32, i32, ctypes.POINTER(ctypes.c_uint32)]),
     }
@@ -576,3 +578,17 @@ def ags_server_cancel(server: int, request_id: int) -> bool:
         return False
     _check(rc, "ags_server_cancel")
     return False
+
+
+def ags_test_sort_pairs(ctx: int, keys, vals, end_bit: int = 64) -> None:
+    """Stable radix sort of device (uint64 key, uint32 value) pairs in place (test hook)."""
+    _check(lib().ags_test_sort_pairs(ctx, _ptr(keys), _ptr(vals), int(keys.numel()), int(end_bit)),
+           "ags_test_sort_pairs")
+
+
+def ags_test_exclusive_scan(ctx: int, data) -> int:
+    """Exclusive scan of a device int32 buffer in place; returns the total (test hook)."""
+    t = ctypes.c_int32()
+    _check(lib().ags_test_exclusive_scan(ctx, _ptr(data), int(data.numel()), ctypes.byref(t)),
+           "ags_test_exclusive_scan")
+    return int(t.value)

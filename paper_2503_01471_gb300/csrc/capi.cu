@@ -911,6 +911,48 @@ ags_status time_render(ags_context* ctx, const ags_scene* sc, const ags_sensor_s
 
 extern "C" {
 
+ags_status ags_test_sort_pairs(ags_context* ctx, uint64_t* keys, uint32_t* vals, int64_t n, int32_t end_bit) {
+  AGS_API_BEGIN
+  if (!ctx) return invalid("ctx is NULL");
+  if (n < 0 || n >= (1ll << 31)) return invalid("n must be in [0, 2^31)");
+  if (n > 0 && (!keys || !vals)) return invalid("keys or vals is NULL");
+  if (end_bit < 1 || end_bit > 64) return invalid("end_bit must be in [1, 64]");
+  DeviceGuard g(ctx->device);
+  DevBufs tmp;
+  uint64_t* k2 = nullptr;
+  uint32_t* v2 = nullptr;
+  char* t = nullptr;
+  cudaError_t e;
+  if ((e = tmp.alloc(&k2, (size_t)n)) != cudaSuccess || (e = tmp.alloc(&v2, (size_t)n)) != cudaSuccess ||
+      (e = tmp.alloc(&t, sort_temp_bytes(n))) != cudaSuccess)
+    return cuda_fail(e, "sort scratch");
+  if ((e = sort_pairs(keys, vals, k2, v2, n, end_bit, t, ctx->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
+    return cuda_fail(e, "sort_pairs");
+  return AGS_OK;
+  AGS_API_END
+}
+
+ags_status ags_test_exclusive_scan(ags_context* ctx, int32_t* data, int64_t n, int32_t* total_host) {
+  AGS_API_BEGIN
+  if (!ctx || !total_host) return invalid("ctx or total is NULL");
+  if (n < 0 || n >= (1ll << 31)) return invalid("n must be in [0, 2^31)");
+  if (n > 0 && !data) return invalid("data is NULL");
+  DeviceGuard g(ctx->device);
+  DevBufs tmp;
+  int32_t* total = nullptr;
+  char* t = nullptr;
+  cudaError_t e;
+  if ((e = tmp.alloc(&total, 1)) != cudaSuccess || (e = tmp.alloc(&t, scan_temp_bytes(n))) != cudaSuccess)
+    return cuda_fail(e, "scan scratch");
+  if ((e = exclusive_scan(data, n, total, t, ctx->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(total_host, total, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(ctx->stream)) != cudaSuccess)
+    return cuda_fail(e, "exclusive_scan");
+  return AGS_OK;
+  AGS_API_END
+}
+
 ags_status ags_autotune_build(ags_context* ctx, ags_scene* sc, const ags_sensor_spec* spec, const float* poses,
                               float* depth, int32_t* seg, const uint32_t* cells, int32_t n_cells, int32_t repeats,
                               uint32_t* best_cells) {

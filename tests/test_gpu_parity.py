@@ -936,3 +936,33 @@ def test_bvh_structure_of_every_variant(ctx):
         print(f"[structure] forest: {r}")
     finally:
         ags.ags_scene_destroy(scene)
+
+
+# ---------------------------------------------------------------- building blocks
+@pytest.mark.parametrize("n,end_bit", [(0, 64), (1, 64), (1000, 12), (257 * 1024 + 3, 40), (3_000_001, 64)])
+def test_radix_sort_is_a_stable_sort(ctx, n, end_bit):
+    """The device radix sort against numpy's stable argsort on keys with many ties, on the low end_bit bits."""
+    rng = np.random.default_rng(28 + n)
+    keys = rng.integers(0, 1 << 62, n, dtype=np.int64).astype(np.uint64)
+    keys[: n // 2] = keys[: n // 2] % 97  # plenty of equal keys
+    keys = rng.permutation(keys) if n else keys
+    mask = np.uint64((1 << end_bit) - 1) if end_bit < 64 else np.uint64(0xFFFFFFFFFFFFFFFF)
+    keys &= mask
+    vals = np.arange(n, dtype=np.uint32)
+    kd = torch.as_tensor(keys.view(np.int64)).cuda()
+    vd = torch.as_tensor(vals.view(np.int32)).cuda()
+    ags.ags_test_sort_pairs(ctx, kd, vd, end_bit)
+    order = np.argsort(keys, kind="stable")
+    assert np.array_equal(kd.cpu().numpy().view(np.uint64), keys[order])
+    assert np.array_equal(vd.cpu().numpy().view(np.uint32), vals[order])
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 1023, 1024, 1025, 1_000_003])
+def test_exclusive_scan(ctx, n):
+    rng = np.random.default_rng(29 + n)
+    x = rng.integers(0, 50, n).astype(np.int32)
+    d = torch.as_tensor(x).cuda()
+    total = ags.ags_test_exclusive_scan(ctx, d)
+    ref = np.concatenate([[0], np.cumsum(x)[:-1]]).astype(np.int64) if n else np.zeros(0, np.int64)
+    assert np.array_equal(d.cpu().numpy().astype(np.int64), ref)
+    assert total == int(x.sum())
