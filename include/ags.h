@@ -140,6 +140,12 @@ typedef struct {
 ags_status ags_context_create(int device, ags_context** out);
 void ags_context_destroy(ags_context* ctx);
 
+/* The context's device: its name (NUL-terminated, truncated to name_len
+ * bytes), SM count and compute capability (major * 10 + minor). Any output
+ * pointer may be NULL. */
+ags_status ags_context_device(const ags_context* ctx, char* name, int32_t name_len, int32_t* sm_count,
+                              int32_t* compute_capability);
+
 /*
  * ags_scene_build -- Sec. III-D.1: transform every sub-mesh by its pose and
  * build one BVH per environment ("a bounding volume hierarchy is calculated

@@ -59,7 +59,7 @@ EXPORTS = [
     "ags_server_submit", "ags_server_poll", "ags_server_release", "ags_server_stats", "ags_server_replay",
     "ags_replay_sequential", "ags_scene_update_poses", "ags_render_graph_create", "ags_render_graph_launch",
     "ags_render_graph_destroy", "ags_render_channels", "ags_render_ex", "ags_autotune_build", "ags_scene_validate",
-    "ags_server_cancel", "ags_test_sort_pairs", "ags_test_exclusive_scan",
+    "ags_server_cancel", "ags_test_sort_pairs", "ags_test_exclusive_scan", "ags_context_device",
 ]
 
 
@@ -199,6 +199,8 @@ def lib() -> ctypes.CDLL:
                                 ctypes.POINTER(ags_render_options), vp]),
         "ags_scene_validate": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
         "ags_server_cancel": (i32, [vp, ctypes.c_uint64]),
+        "ags_context_device": (i32, [vp, ctypes.c_char_p, i32, ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.POINTER(ctypes.c_int32)]),
         "ags_test_sort_pairs": (i32, [vp, vp, vp, ctypes.c_int64, i32]),
         "ags_test_exclusive_scan": (i32, [vp, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)]),
         "ags_autotune_build": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), vp, vp, vp,
@@ -592,3 +594,11 @@ def ags_test_exclusive_scan(ctx: int, data) -> int:
     _check(lib().ags_test_exclusive_scan(ctx, _ptr(data), int(data.numel()), ctypes.byref(t)),
            "ags_test_exclusive_scan")
     return int(t.value)
+
+
+def ags_context_device(ctx: int) -> dict:
+    """Name, SM count and compute capability of the context's device."""
+    buf = ctypes.create_string_buffer(256)
+    sm, cc = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().ags_context_device(ctx, buf, 256, ctypes.byref(sm), ctypes.byref(cc)), "ags_context_device")
+    return {"name": buf.value.decode(), "sm_count": sm.value, "compute_capability": cc.value}

@@ -368,6 +368,23 @@ void ags_scene_destroy(ags_scene* sc) {
 
 int32_t ags_scene_n_envs(const ags_scene* sc) { return sc ? sc->n_envs : -1; }
 
+ags_status ags_context_device(const ags_context* ctx, char* name, int32_t name_len, int32_t* sm_count,
+                              int32_t* compute_capability) {
+  AGS_API_BEGIN
+  if (!ctx) return invalid("ctx is NULL");
+  cudaDeviceProp prop{};
+  cudaError_t e = cudaGetDeviceProperties(&prop, ctx->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+  if (name && name_len > 0) {
+    std::strncpy(name, prop.name, (size_t)name_len - 1);
+    name[name_len - 1] = '\0';
+  }
+  if (sm_count) *sm_count = ctx->sm_count;
+  if (compute_capability) *compute_capability = prop.major * 10 + prop.minor;
+  return AGS_OK;
+  AGS_API_END
+}
+
 }  // extern "C"
 
 namespace {

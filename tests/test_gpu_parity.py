@@ -966,3 +966,27 @@ def test_exclusive_scan(ctx, n):
     ref = np.concatenate([[0], np.cumsum(x)[:-1]]).astype(np.int64) if n else np.zeros(0, np.int64)
     assert np.array_equal(d.cpu().numpy().astype(np.int64), ref)
     assert total == int(x.sum())
+
+
+def test_launch_shape_cache(ctx, tmp_path):
+    """A tuned shape is stored under the device, sensor shape and scene size, and a later lookup applies it
+    without tuning; outputs do not depend on it."""
+    from paper_2503_01471_gb300 import tuning
+    batch, spec, poses = S.obstacle_rooms(2, steps=1, width=40, height=30)
+    dev = ags.ags_context_device(ctx)
+    assert dev["sm_count"] > 0 and dev["compute_capability"] >= 100 and dev["name"]
+    path = str(tmp_path / "shapes.json")
+    scene = ags.ags_scene_build(ctx, batch)
+    try:
+        p = torch.as_tensor(poses[0]).cuda()
+        d = torch.empty((2, 30, 40), device="cuda")
+        s = torch.empty((2, 30, 40), dtype=torch.int32, device="cuda")
+        a = tuning.autotune_cached(ctx, scene, spec, p, d, s, path, 1)
+        assert a["cached"] is False
+        ags.ags_set_launch_config(ctx, scene, spec, None)
+        b = tuning.autotune_cached(ctx, scene, spec, p, d, s, path, 1)
+        assert b["cached"] is True and b["tile_w"] == a["tile_w"] and b["rays_per_lane"] == a["rays_per_lane"]
+        got = ags.ags_get_launch_config(ctx, scene, spec)
+        assert got["tile_w"] == a["tile_w"] and got["rays_per_lane"] == a["rays_per_lane"]
+    finally:
+        ags.ags_scene_destroy(scene)
