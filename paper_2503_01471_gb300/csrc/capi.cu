@@ -991,23 +991,21 @@ ags_status ags_autotune_build(ags_context* ctx, ags_scene* sc, const ags_sensor_
   float best_ms = 0.0f;
   if ((st = time_render(ctx, sc, spec, poses, depth, seg, repeats, &best_ms)) != AGS_OK) return st;
   uint32_t best = current;
-  ScenePtr best_scene;
   const float* h_poses = sc->n_subs > 0 ? sc->h_poses.data() : nullptr;
   for (int32_t k = 0; k < n_cells; ++k) {
-    if (cells[k] == current) continue;
+    if (cells[k] == best) continue;
     ScenePtr cand;
     st = rebuild_like(ctx, sc, h_poses, (sc->flags & ~split_mask) | (cells[k] << 12), cand);
-    if (st == AGS_ERR_OUT_OF_MEMORY) continue;  // this setting does not fit: skip it
+    if (st == AGS_ERR_OUT_OF_MEMORY) continue;  // this setting does not fit beside the scene: skip it
     if (st != AGS_OK) return st;
     float ms = 0.0f;
     if ((st = time_render(ctx, cand.get(), spec, poses, depth, seg, repeats, &ms)) != AGS_OK) return st;
-    if (ms < best_ms) {
+    if (ms < best_ms) {  // keep the faster BVH at once, so at most two are held during tuning
       best_ms = ms;
       best = cells[k];
-      best_scene = std::move(cand);
+      adopt(sc, cand, false);
     }
   }
-  if (best_scene) adopt(sc, best_scene, false);
   *best_cells = best;
   return AGS_OK;
   AGS_API_END
