@@ -222,7 +222,7 @@ def serving_measure(ags, ctx, scene, n_envs, poses_step, specs, loads=(0.5, 1.0)
     def pct(x, q):
         return float(np.percentile(x, q)) if len(x) else None
 
-    server = ags.ags_server_create(ctx, scene, specs, max_slots=512, max_inflight=3, arena_bytes=4 << 30)
+    server = ags.ags_server_create(ctx, scene, specs, max_slots=512, max_inflight=4, arena_bytes=4 << 30)
     try:
         reqs, arr = trace(burst, None)
         out = ags.ags_server_replay(server, reqs, arr)
@@ -230,7 +230,7 @@ def serving_measure(ags, ctx, scene, n_envs, poses_step, specs, loads=(0.5, 1.0)
         cap = burst / span
         res = {"capacity_req_per_s": cap, "capacity_mrays_per_s": float(rays[reqs["spec"]].sum()) / span / 1e6,
                "sensors": [f"{'camera' if sp.type == 0 else 'lidar'} {sp.height}x{sp.width}" for sp in specs],
-               "max_slots": 512, "max_inflight": 3, "loads": []}
+               "max_slots": 512, "max_inflight": 4, "loads": []}
         for f in loads:
             rate = f * cap
             n = max(100, int(rate * duration))
