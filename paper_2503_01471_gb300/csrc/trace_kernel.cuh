@@ -559,7 +559,31 @@ __device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParam
       node = child_base + (__ffs(inner_hits) - 1);
       continue;
     }
-    if (n_inner > 1) {
+    if (n_inner == 2) {
+      // two children: the nearer is taken, the farther pushed (keys: tmin bits, slot in the low 3 bits)
+      uint32_t kmin = 0xFFFFFFFFu, kx = 0u;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const uint32_t key = (__float_as_uint(tmins[k]) & ~7u) | (uint32_t)k;
+        const bool v = (inner_hits >> k) & 1u;
+        kmin = v ? min(kmin, key) : kmin;
+        kx ^= v ? key : 0u;
+      }
+      const uint32_t kfar = kx ^ kmin;
+      const uint32_t key_cull = __float_as_uint(t_best * kCullSlack);
+      if ((kfar & ~7u) <= key_cull) {
+        if (sp >= kStackSize) {
+          atomicOr(status, kStatusStackOverflow);
+          failed = true;
+          break;
+        }
+        stack[sp++] = make_int2(child_base + (int32_t)(kfar & 7u), (int32_t)(kfar & ~7u));
+      }
+      if ((kmin & ~7u) <= key_cull) {
+        node = child_base + (int32_t)(kmin & 7u);
+        continue;
+      }
+    } else if (n_inner > 1) {
       // nearest first (sorting network on keys: tmin bits with the slot in the low 3 bits)
       uint32_t keys[8];
 #pragma unroll
