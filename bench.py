@@ -39,7 +39,7 @@ WORKLOADS = {
     "features": {"envs": 1024, "metric": "Mrays/s at 1024 rooms per sensor feature (hit channels, stereo, projection models)"},
 }
 PAPER_MRAYS = 340.5  # Table II, 1024 envs x 270x480 (RTX 3090; context)
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "k_trace_rooms_1024x270x480_traffic.md")
+PROFILE_DIR = os.path.join(ROOT, "profiles")
 
 
 def parse():
@@ -97,12 +97,14 @@ def profiled_counters(workload, kernel):
     """(DRAM bytes, warp instructions) per launch of the render kernel from the committed ncu summary, if its
     row matches this workload, this kernel instance and the current kernel and builder sources; else None."""
     try:
-        with open(PROFILE_TRAFFIC) as fh:
-            for line in fh:
-                cells = [c.strip() for c in line.strip().strip("|").split("|")]
-                if len(cells) == 7 and cells[0] == workload and cells[1] == kernel \
-                        and cells[2] == kernel_source_hash():
-                    return float(cells[5]), float(cells[6])
+        names = sorted(f for f in os.listdir(PROFILE_DIR) if f.startswith("k_trace_") and f.endswith("_traffic.md"))
+        for name in names:
+            with open(os.path.join(PROFILE_DIR, name)) as fh:
+                for line in fh:
+                    cells = [c.strip() for c in line.strip().strip("|").split("|")]
+                    if len(cells) == 7 and cells[0] == workload and cells[1] == kernel \
+                            and cells[2] == kernel_source_hash():
+                        return float(cells[5]), float(cells[6])
     except (OSError, ValueError):
         pass
     return None
@@ -733,7 +735,7 @@ def bench_ours(args, rank, world, local):
     workload = workload_name(args, spec, E)
     lc = ags.ags_get_launch_config(ctx, scene, spec)
     fmt = args.build_flags & 0xFF
-    counters = profiled_counters(f"{args.workload}:{E}x{spec.height}x{spec.width}",
+    counters = profiled_counters(f"{args.workload}:{E}x{spec.height}x{spec.width}:cells{split_cells or 16}",
                                  f"k_trace<0, {lc['tile_w']}, {lc['rays_per_lane']}, 0, {fmt}, 0>")
     traffic = counters[0] if counters else None
     line = {
