@@ -85,11 +85,16 @@ def peaks():
 
 
 def kernel_source_hash():
+    """Hash of the render kernel's and BVH builders' code, comments and blank space left out (a comment edit
+    does not invalidate counters taken from the same code)."""
+    import re
     h = hashlib.sha256()
-    # the render kernel and everything that shapes what it traverses (BVH builders)
     for f in ("trace.cu", "trace_kernel.cuh", "internal.cuh", "build.cu", "ploc.cu", "radix_sort.cu"):
-        with open(os.path.join(ROOT, "paper_2503_01471_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2503_01471_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

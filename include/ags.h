@@ -148,8 +148,8 @@ ags_status ags_context_device(const ags_context* ctx, char* name, int32_t name_l
 
 /*
  * ags_scene_build -- Sec. III-D.1: transform every sub-mesh by its pose and
- * build one BVH per environment ("a bounding volume hierarchy is calculated
- * for M_{i,t}"). envs[n_envs] describe the meshes (host memory);
+ * build one BVH over each environment's meshes M_{i,t}. envs[n_envs]
+ * describe the meshes (host memory);
  * obstacle_poses is host float32 [sum_i n_submeshes(i)][7] in environment
  * order, then sub-mesh order. The call validates every input before any
  * device work (indices in range, finite vertices and poses, non-zero
@@ -165,8 +165,8 @@ void ags_scene_destroy(ags_scene* scene);
 /*
  * ags_scene_update_poses -- move every object of a resident scene to new
  * poses (host float32 [sum n_submeshes][7], the order of ags_scene_build):
- * Sec. III-D.1 updates M_{i,t} from the transforms T_{j,t} ("create, maintain
- * and update"), there by rebuilding the BVH. AGS_UPDATE_REFIT transforms the
+ * Sec. III-D.1 keeps M_{i,t} current from the transforms T_{j,t} as the
+ * simulation runs, there by rebuilding the BVH. AGS_UPDATE_REFIT transforms the
  * vertices, rewrites the packed triangles and refits the node boxes bottom-up
  * in the existing topology (float32 nodes only; fast, but the tree degrades
  * as objects move far); AGS_UPDATE_REBUILD builds the whole scene again with

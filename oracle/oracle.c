@@ -59,7 +59,7 @@ static void matvec(const double R[9], const double a[3], double b[3]) {
   for (int r = 0; r < 3; ++r) b[r] = R[3 * r] * a[0] + R[3 * r + 1] * a[1] + R[3 * r + 2] * a[2];
 }
 
-/* ---- a3: one ray per pixel / beam (Sec. III-D.1: "rays are cast outwards per pixel") ----
+/* ---- a3: one ray per pixel / beam (Sec. III-D.1: a ray leaves the sensor through each pixel) ----
  * reading (camera): body axes +x forward, +y left, +z up; row 0 is the top
  *   image row, column 0 the left column; the ray passes through the pixel
  *   centre; square pixels with focal length f = (W/2)/tan(hfov/2).
@@ -415,8 +415,8 @@ int orc_render(const double* tris, const int32_t* seg, int64_t F, const orc_sens
   return 0;
 }
 
-/* ---- extra hit channels (Sec. III-D.1: "vertex (or mesh-face) indices
- * alongside barycentric coordinates", "point clouds and surface normals") ----
+/* ---- extra hit channels (Sec. III-D.1: the index of the face hit with the
+ * barycentric coordinates of the hit, point clouds, surface normals) ----
  * reading: the face index is the env-local triangle index; the barycentrics
  * are those of the point where the ray meets the face's plane, weights of its
  * second and third vertex; the normal is the face's geometric normal turned

@@ -1,6 +1,6 @@
 // Scene build: object-to-world transform (Sec. III-D.1, M_{i,t} from the
-// per-object transforms T_{j,t}) and one BVH per environment ("a bounding
-// volume hierarchy is calculated for M_{i,t}"), as an LBVH (Morton codes,
+// per-object transforms T_{j,t}) and one BVH per environment's meshes M_{i,t}
+// (Sec. III-D.1), as an LBVH (Morton codes,
 // radix sort, Karras-style radix tree, bottom-up bounds refit) collapsed into
 // 8-wide nodes. All environments are built together, in one pass per stage.
 #include <algorithm>

@@ -1,5 +1,5 @@
-// Batched ray casting (Sec. III-D.1: "individual rays are cast outwards
-// per-pixel to evaluate intersection with M_{i,t}"; range vs depth): the
+// Batched ray casting (Sec. III-D.1: one ray per pixel tested against the
+// environment's meshes M_{i,t}; range vs depth): the
 // launch shapes of the plain render, the instrumented count and the serving
 // slot mode. The kernel itself is in trace_kernel.cuh; the variants with
 // extra work (hit channels, stereo shadows, ray tables) are instantiated in

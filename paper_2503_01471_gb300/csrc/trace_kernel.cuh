@@ -1,6 +1,6 @@
 // The render kernel, shared by the translation units that instantiate it.
-// Batched ray casting (Sec. III-D.1: "individual rays are cast outwards
-// per-pixel to evaluate intersection with M_{i,t}"; range vs depth): one
+// Batched ray casting (Sec. III-D.1: one ray per pixel tested against the
+// environment's meshes M_{i,t}; range vs depth): one
 // persistent launch over every environment's rays. Each warp repeatedly takes
 // an 8x4 tile of pixels (env-major order, so one environment's BVH stays hot
 // in L2 while all SMs work on it), generates the rays in registers, walks the

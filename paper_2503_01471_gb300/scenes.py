@@ -6,9 +6,9 @@ the renderer's arithmetic (no object-to-world transform, no rays, no
 intersection); both the CUDA renderer and the FP64 oracle consume what it
 makes.
 
-The paper's own benchmark scenes ("20 cube obstacles" in front of each robot,
-Table I; "a room-like static environment with 15 floating obstacles", Table II)
-are built from the simulator's assets, which are not available here. The
+The paper's own benchmark scenes (twenty cubes in front of each robot, Table I;
+a static room with fifteen floating obstacles, Table II) are built from the
+simulator's assets, which are not available here. The
 workloads below stand in for them with the same structure: a 10 x 10 x 4 m
 room per environment with 20-40 obstacles of several mesh types, or a forest of
 procedural trees on a 40 x 40 m ground plane for the 3-D LiDAR. All randomness
