@@ -1,0 +1,39 @@
+"""bench.py's contract on the CPU: the reference arm (the FP64 oracle timed on the host cores) prints one
+JSON line with the keys the driver reads, and the ncu counter tables parse."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_prints_one_json_line():
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "1",
+                          "--envs", "4"], cwd=ROOT, capture_output=True, text=True, timeout=600, check=True)
+    lines = [l for l in out.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "Mrays/s" and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert d["metric"].startswith("Mrays/s at 1024 envs x 270x480")
+
+
+def test_counter_tables_parse():
+    sys.path.insert(0, ROOT)
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+    assert len(b.kernel_source_hash()) == 16
+    rows = 0
+    for name in os.listdir(b.PROFILE_DIR):
+        if name.startswith("k_trace_") and name.endswith("_traffic.md"):
+            for line in open(os.path.join(b.PROFILE_DIR, name)):
+                cells = [c.strip() for c in line.strip().strip("|").split("|")]
+                if len(cells) == 7 and ":" in cells[0] and cells[1].startswith("k_trace<"):
+                    assert int(cells[3]) + int(cells[4]) == int(cells[5]) and int(cells[6]) > 0
+                    rows += 1
+    assert rows >= 2
