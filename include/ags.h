@@ -305,6 +305,20 @@ ags_status ags_render_count(ags_context* ctx, const ags_scene* scene, const ags_
                             const float* sensor_poses_dev, uint64_t counts_host[3]);
 
 /*
+ * ags_render_bruteforce -- a test and debugging aid (no counterpart in the
+ * paper): the render of ags_render (same outputs, same layouts) with every
+ * ray tested against every BVH reference of its environment, no tree, using
+ * the render kernel's own ray set-up and triangle test. The BVH walk culls
+ * conservatively and breaks ties the same way, so ags_render must match it
+ * bit for bit. Cost grows with rays x triangles: meant for checks at reduced
+ * resolution. Single-level scenes; camera and LiDAR sensors. Synchronises
+ * `cuda_stream`.
+ */
+ags_status ags_render_bruteforce(ags_context* ctx, const ags_scene* scene, const ags_sensor_spec* spec,
+                                 const float* sensor_poses_dev, float* out_depth_dev, int32_t* out_seg_dev,
+                                 void* cuda_stream);
+
+/*
  * Test hooks of two building blocks of ags_scene_build (no counterpart in the
  * paper): the stable LSD radix sort of (uint64 key, uint32 value) pairs on
  * key bits [0, end_bit) (1 <= end_bit <= 64), in place on device buffers, and

@@ -60,6 +60,7 @@ EXPORTS = [
     "ags_replay_sequential", "ags_scene_update_poses", "ags_render_graph_create", "ags_render_graph_launch",
     "ags_render_graph_destroy", "ags_render_channels", "ags_render_ex", "ags_autotune_build", "ags_scene_validate",
     "ags_server_cancel", "ags_test_sort_pairs", "ags_test_exclusive_scan", "ags_context_device",
+    "ags_render_bruteforce",
 ]
 
 
@@ -199,6 +200,7 @@ def lib() -> ctypes.CDLL:
                                 ctypes.POINTER(ags_render_options), vp]),
         "ags_scene_validate": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
         "ags_server_cancel": (i32, [vp, ctypes.c_uint64]),
+        "ags_render_bruteforce": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), vp, vp, vp, vp]),
         "ags_context_device": (i32, [vp, ctypes.c_char_p, i32, ctypes.POINTER(ctypes.c_int32),
                                      ctypes.POINTER(ctypes.c_int32)]),
         "ags_test_sort_pairs": (i32, [vp, vp, vp, ctypes.c_int64, i32]),
@@ -602,3 +604,10 @@ def ags_context_device(ctx: int) -> dict:
     sm, cc = ctypes.c_int32(), ctypes.c_int32()
     _check(lib().ags_context_device(ctx, buf, 256, ctypes.byref(sm), ctypes.byref(cc)), "ags_context_device")
     return {"name": buf.value.decode(), "sm_count": sm.value, "compute_capability": cc.value}
+
+
+def ags_render_bruteforce(ctx: int, scene: int, spec, sensor_poses, out_depth, out_seg, stream=None) -> None:
+    """Every ray against every reference of its environment, no tree (a test aid; synchronous)."""
+    s = make_spec(spec)
+    _check(lib().ags_render_bruteforce(ctx, scene, ctypes.byref(s), _ptr(sensor_poses), _ptr(out_depth),
+                                       _ptr(out_seg), _stream(stream)), "ags_render_bruteforce")

@@ -11,6 +11,13 @@
 
 namespace ags {
 
+// brute.cu: every triangle copy of each ray's environment, no tree (a test aid). env_ref_dev and
+// env_tri_dev are the [E+1] reference and triangle offsets, leaf_tri_dev the [R] input triangle of each
+// leaf-order copy; temp holds brute_temp_bytes(R) bytes.
+cudaError_t launch_brute(const TraceArgs& a, const int32_t* env_ref_dev, const int32_t* env_tri_dev,
+                         const int32_t* leaf_tri_dev, int32_t E, int32_t R, void* temp, cudaStream_t s);
+size_t brute_temp_bytes(int32_t R);
+
 SensorParams sensor_params(const ags_sensor_spec* spec, int tile_w, int tile_h) {
   SensorParams p;
   p.W = spec->width;
@@ -927,6 +934,41 @@ ags_status time_render(ags_context* ctx, const ags_scene* sc, const ags_sensor_s
 }  // namespace
 
 extern "C" {
+
+ags_status ags_render_bruteforce(ags_context* ctx, const ags_scene* sc, const ags_sensor_spec* spec,
+                                 const float* poses, float* depth, int32_t* seg, void* stream) {
+  AGS_API_BEGIN
+  if (!ctx || !sc) return invalid("ctx or scene is NULL");
+  if (sc->ctx != ctx) return invalid("scene belongs to another context");
+  if (sc->objects) return invalid("brute force needs a single-level scene");
+  ags_status st = check_spec(spec, false);
+  if (st != AGS_OK) return st;
+  if (!poses || !depth || !seg) return invalid("poses/depth/seg pointer is NULL");
+  DeviceGuard g(ctx->device);
+  TraceArgs a{};
+  if ((st = fill_trace_args(ctx, sc, spec, sc->n_envs, nullptr, poses, depth, seg, a, default_config())) != AGS_OK)
+    return st;
+  const int32_t E = sc->n_envs, R = (int32_t)sc->n_refs;
+  if ((int64_t)sc->env_ref_off.size() != E + 1 || (int64_t)sc->env_tri_off.size() != E + 1)
+    return invalid("scene offsets are missing");
+  std::vector<int32_t> off(2 * ((size_t)E + 1));
+  for (int32_t e = 0; e <= E; ++e) {
+    off[e] = (int32_t)sc->env_ref_off[e];
+    off[E + 1 + e] = (int32_t)sc->env_tri_off[e];
+  }
+  DevBufs tmp;
+  int32_t* d_off = nullptr;
+  char* d_temp = nullptr;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if ((e = tmp.alloc(&d_off, off.size())) != cudaSuccess || (e = tmp.alloc(&d_temp, brute_temp_bytes(R))) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_off, off.data(), off.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = launch_brute(a, d_off, d_off + E + 1, sc->d.leaf_tri, E, R, d_temp, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return cuda_fail(e, "brute-force render");
+  return AGS_OK;
+  AGS_API_END
+}
 
 ags_status ags_test_sort_pairs(ags_context* ctx, uint64_t* keys, uint32_t* vals, int64_t n, int32_t end_bit) {
   AGS_API_BEGIN
