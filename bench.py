@@ -247,9 +247,13 @@ def serving_measure(ags, ctx, scene, n_envs, poses_step, specs, loads=(0.5, 1.0)
             m = min(seq_max, n)
             seq = ags.ags_replay_sequential(ctx, scene, specs, reqs[:m], arr[:m])
             slat = (seq["t_done"] - seq["t_submit"]) * 1e3
+            by_sensor = [{"sensor": res["sensors"][k], "requests": int((reqs["spec"] == k).sum()),
+                          "p50_ms": pct(lat[reqs["spec"] == k], 50), "p99_ms": pct(lat[reqs["spec"] == k], 99)}
+                         for k in range(len(specs))]
             res["loads"].append({"load": f, "req_per_s": rate, "requests": n, "p50_ms": pct(lat, 50),
                                  "p99_ms": pct(lat, 99), "mrays_per_s": float(rays[reqs["spec"]].sum()) /
                                  float(out["t_done"].max() - out["t_submit"].min()) / 1e6,
+                                 "by_sensor": by_sensor,
                                  "sequential": {"requests": m, "p50_ms": pct(slat, 50), "p99_ms": pct(slat, 99)}})
         # a load the sequential launch can sustain: half its own capacity, same trace for both
         reqs, arr = trace(300, None)

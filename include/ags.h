@@ -114,6 +114,12 @@ typedef struct {
  * bit selects the Morton radix tree instead (faster build). Results are
  * identical either way. */
 #define AGS_BUILD_LBVH (1u << 20)
+/* Wide nodes from the clustered binary tree: by default each node's eight
+ * slots are the subtrees of least surface-area cost (a dynamic program over
+ * the binary tree); this bit selects the greedy collapse instead (open the
+ * largest child until eight slots). The Morton radix tree always uses the
+ * greedy collapse. Results are identical either way. */
+#define AGS_BUILD_GREEDY_COLLAPSE (1u << 22)
 /* Two-level scene: every object (sub-mesh) gets its own BVH, built once in its
  * own frame, and each environment a small BVH over its objects' world boxes;
  * rays are moved into an object's frame to walk its BVH. ags_scene_update_poses

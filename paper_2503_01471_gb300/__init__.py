@@ -40,6 +40,7 @@ AGS_BVH_FP16 = 1
 AGS_BVH_Q8 = 2
 AGS_BUILD_LBVH = 1 << 20
 AGS_BUILD_INSTANCED = 1 << 21
+AGS_BUILD_GREEDY_COLLAPSE = 1 << 22
 
 
 def AGS_LEAF_SIZE(n: int) -> int:

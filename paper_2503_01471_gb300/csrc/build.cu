@@ -582,13 +582,15 @@ __device__ __forceinline__ float box_area(const Box& b) {
 constexpr int32_t kSlotEmpty = (int32_t)0x80000000;
 
 // Phase A: open the binary subtree below each queued node into up to 8
-// slots (largest surface area first), classify them and count.
+// slots, classify them and count. With `choice` (the clustered tree's
+// least-cost slots, from build_ploc) the slots follow its decisions;
+// otherwise the largest child by surface area is opened until 8 slots.
 __global__ void k_collapse_expand(const QueueItem* __restrict__ items, int32_t n_items,
                                   const int32_t* __restrict__ left, const int32_t* __restrict__ right,
                                   const int32_t* __restrict__ first, const int32_t* __restrict__ last,
                                   const Box* __restrict__ inner_box, int leaf_max, int32_t* __restrict__ slots,
                                   int32_t* __restrict__ n_inner, int32_t* __restrict__ n_leaf_tris, int32_t F,
-                                  int* __restrict__ err) {
+                                  int* __restrict__ err, const uint32_t* __restrict__ choice) {
   int32_t it = blockIdx.x * blockDim.x + threadIdx.x;
   if (it >= n_items) return;
   int32_t ref = items[it].ref;
@@ -616,7 +618,33 @@ __global__ void k_collapse_expand(const QueueItem* __restrict__ items, int32_t n
     atomicOr(err, 1);
     ns = 0;
   }
-  while (ns < 8) {
+  if (choice && ns == 2) {
+    // follow the least-cost decomposition of the 8 slots: (node, budget) pairs
+    int32_t pn[8];
+    int pb[8], np = 0;
+    const int k8 = (int)((choice[ref] >> 18) & 7u) + 1;
+    pn[np] = s[1], pb[np++] = 8 - k8;
+    pn[np] = s[0], pb[np++] = k8;
+    ns = 0;
+    while (np > 0) {
+      const int32_t c = pn[--np];
+      const int b = pb[np];
+      const uint32_t ch = c >= 0 ? choice[c] : 0u;
+      if (c < 0 || b <= 1 || ((ch >> (21 + b - 2)) & 1u) || ns + np >= 7) {
+        s[ns++] = c;  // one slot (the last guard only bounds a corrupt choice)
+        continue;
+      }
+      if (bad(left[c]) || bad(right[c])) {
+        atomicOr(err, 1);
+        s[ns++] = c;
+        continue;
+      }
+      const int k = (int)((ch >> (3 * (b - 2))) & 7u) + 1;
+      pn[np] = right[c], pb[np++] = b - k;
+      pn[np] = left[c], pb[np++] = k;
+    }
+  }
+  while (ns < 8 && !choice) {
     int best = -1;
     float best_area = -1.0f;
     for (int k = 0; k < ns; ++k) {
@@ -1006,6 +1034,8 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
   Box *d_leaf_box, *d_inner_box;
   AGS_CHECK(tmp.alloc(&d_leaf_box, (size_t)R));
   AGS_CHECK(tmp.alloc(&d_inner_box, (size_t)R));
+  const int leaf_max = ((sc->flags >> 8) & 0xFu) ? (int)((sc->flags >> 8) & 0xFu) : kDefaultLeafTris;
+  uint32_t* d_choice = nullptr;  // least-cost wide-node slots (clustered tree only)
   if (sc->flags & AGS_BUILD_LBVH) {
     // Morton radix tree (Karras 2012) and an atomic bottom-up refit
     k_karras<<<blocks_for(R, 256), 256, 0, s>>>(d_keys, R, key_shift, d_env_ref, d_left, d_right, d_pin, d_pleaf,
@@ -1016,8 +1046,9 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
   } else {
     // locally-ordered clustering (default): lower surface-area cost
     std::vector<int32_t> roots;
+    if (!(sc->flags & AGS_BUILD_GREEDY_COLLAPSE)) AGS_CHECK(tmp.alloc(&d_choice, (size_t)R));
     ags_status st = build_ploc(d_keys, d_vals, R, key_shift, d_env_ref, E, d_ref_box, d_leaf_box, d_left, d_right,
-                               d_first, d_last, d_inner_box, roots, s);
+                               d_first, d_last, d_inner_box, roots, s, d_choice, leaf_max);
     if (st != AGS_OK) return st;
     for (QueueItem& q : q0) {
       if (q.ref < 0) continue;  // a single reference: the leaf keeps its position
@@ -1033,7 +1064,6 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
   // wide nodes: at most R/(L+1) + E without inner children (each covers more
   // than L references, or is a root), and every node with inner children has
   // 8 slots, which bounds those by (R + R/(L+1) + E)/7
-  const int leaf_max = ((sc->flags >> 8) & 0xFu) ? (int)((sc->flags >> 8) & 0xFu) : kDefaultLeafTris;
   const double leafonly = (double)R / (leaf_max + 1) + E;
   int64_t node_cap = (int64_t)(leafonly + ((double)R + leafonly) / 7.0) + 2 * (int64_t)E + 64;
   WideNode* d_nodes_tmp = nullptr;
@@ -1045,7 +1075,6 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
   int32_t *d_slots, *d_ninner, *d_ntris, *d_perm, *d_tot;
   int* d_err = nullptr;
   AGS_CHECK(tmp.alloc(&d_err, 1));
-  AGS_CHECK(cudaMemsetAsync(d_err, 0, sizeof(int), s));
   AGS_CHECK(tmp.alloc(&d_slots, 8 * (size_t)q_cap));
   AGS_CHECK(tmp.alloc(&d_ninner, (size_t)q_cap));
   AGS_CHECK(tmp.alloc(&d_ntris, (size_t)q_cap));
@@ -1055,11 +1084,18 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
   AGS_CHECK(tmp.alloc(reinterpret_cast<char**>(&d_scan_tmp), scan_temp_bytes(q_cap)));
   unsigned long long* d_env_nodes = nullptr;
   AGS_CHECK(tmp.alloc(&d_env_nodes, (size_t)E));
+
+  // the least-cost slots may leave nodes with fewer than 8 slots; should they
+  // outgrow the bound above, the collapse is redone greedily
+  int32_t level_base = 0, tri_level_base = 0;
+  for (bool again = true; again;) {
+  again = false;
+  AGS_CHECK(cudaMemsetAsync(d_err, 0, sizeof(int), s));
   AGS_CHECK(cudaMemsetAsync(d_env_nodes, 0, (size_t)E * sizeof(unsigned long long), s));
   AGS_CHECK(cudaMemcpyAsync(d_q, q0.data(), q0.size() * sizeof(QueueItem), cudaMemcpyHostToDevice, s));
-
   int32_t n_items = (int32_t)q0.size();
-  int32_t level_base = 0, tri_level_base = 0;
+  level_base = 0;
+  tri_level_base = 0;
   int levels = 0;
   sc->level_off.assign(1, 0);
   while (n_items > 0) {
@@ -1069,7 +1105,7 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
     }
     k_collapse_expand<<<blocks_for(n_items, 128), 128, 0, s>>>(d_q, n_items, d_left, d_right, d_first, d_last,
                                                               d_inner_box, leaf_max, d_slots, d_ninner, d_ntris,
-                                                              R, d_err);
+                                                              R, d_err, d_choice);
     AGS_CHECK(cudaGetLastError());
     AGS_CHECK(exclusive_scan(d_ninner, n_items, d_tot, d_scan_tmp, s));
     AGS_CHECK(exclusive_scan(d_ntris, n_items, d_tot + 1, d_scan_tmp, s));
@@ -1087,6 +1123,11 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
     }
     int32_t next_base = level_base + n_items;
     if ((int64_t)next_base + tot[0] > node_cap) {
+      if (d_choice) {
+        d_choice = nullptr;
+        again = true;
+        break;
+      }
       set_error("BVH node capacity exceeded");
       return AGS_ERR_CUDA;
     }
@@ -1099,6 +1140,7 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
     sc->level_off.push_back(level_base);
     tri_level_base += tot[1];
     n_items = tot[0];
+  }
   }
   if (tri_level_base != R) {
     set_error("BVH collapse lost references");

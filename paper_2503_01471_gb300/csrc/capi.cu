@@ -262,7 +262,7 @@ ags_status ags_scene_build(ags_context* ctx, const ags_env_mesh* envs, int32_t n
   if (!envs) return invalid("envs is NULL");
   if (n_envs < 1 || n_envs > 65536) return invalid("n_envs must be in [1, 65536]");
   if ((build_flags & 0xFFu) > AGS_BVH_Q8) return invalid("unsupported BVH node format in build_flags");
-  if ((build_flags & ~(0xFFFFFu | AGS_BUILD_LBVH | AGS_BUILD_INSTANCED)) != 0) return invalid("unknown bits in build_flags");
+  if ((build_flags & ~(0xFFFFFu | AGS_BUILD_LBVH | AGS_BUILD_INSTANCED | AGS_BUILD_GREEDY_COLLAPSE)) != 0) return invalid("unknown bits in build_flags");
   if ((build_flags & AGS_BUILD_INSTANCED) && (build_flags & 0xFFu) != AGS_BVH_FP32)
     return invalid("two-level scenes use float32 nodes");
   if (((build_flags >> 8) & 0xFu) > (uint32_t)kMaxLeafTris) return invalid("leaf size must be 1..4");

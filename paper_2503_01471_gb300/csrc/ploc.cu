@@ -204,13 +204,78 @@ __global__ void k_ploc_relabel(int32_t n_inner, int32_t R, int32_t* __restrict__
   if (r < 0 && ~r < R) right[id] = ~newpos[~r];
 }
 
+// ---- wide-node slots of least surface-area cost (the collapse's choice)
+// Cost of a wide tree under the surface-area heuristic: a ray that enters a
+// box of area A' enters a child box of area A with probability A / A', so a
+// wide node costs kCostNode * A (its eight child tests) and a leaf of c
+// references kCostTri * c * A (its triangle tests). For an inner node n of
+// the binary tree and a budget of i = 1..8 slots of one wide node, D(n, i) is
+// the least cost of covering n's subtree with at most i slots:
+//   D(n, 1) = kCostTri * c(n) * A(n)          when c(n) <= leaf_max (a leaf)
+//           = kCostNode * A(n) + S(n, 8)      otherwise (a wide node of its own)
+//   S(n, i) = min over k = 1..i-1 of D(left, k) + D(right, i - k)
+//   D(n, i) = min(D(n, 1), S(n, i))           for i >= 2
+// (a single reference is a leaf slot at every budget). Children are made in
+// earlier clustering rounds than their parent, so the rounds in order give a
+// bottom-up pass. choice[n] packs, for i = 2..8, the k of S(n, i) less one
+// (3 bits at 3 (i - 2)) and whether D(n, i) keeps n as one slot (bit 21 + i - 2).
+#ifndef AGS_SAH_TRI_COST
+#define AGS_SAH_TRI_COST 0.3f
+#endif
+constexpr float kCostNode = 1.0f, kCostTri = AGS_SAH_TRI_COST;
+
+__global__ void k_collapse_cost(int32_t b, int32_t e, const int32_t* __restrict__ left,
+                                const int32_t* __restrict__ right, const int32_t* __restrict__ first,
+                                const int32_t* __restrict__ last, const Box* __restrict__ inner_box,
+                                const Box* __restrict__ leaf_box, int leaf_max, float* __restrict__ cost,
+                                uint32_t* __restrict__ choice) {
+  const int32_t id = b + (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (id >= e) return;
+  float dl[8], dr[8];
+  const int32_t l = left[id], r = right[id];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    dl[k] = l >= 0 ? cost[8 * (int64_t)l + k] : kCostTri * half_area(leaf_box[~l]);
+    dr[k] = r >= 0 ? cost[8 * (int64_t)r + k] : kCostTri * half_area(leaf_box[~r]);
+  }
+  float split[9];
+  uint32_t ch = 0;
+#pragma unroll
+  for (int i = 2; i <= 8; ++i) {
+    float best = INFINITY;
+    int bk = 1;
+#pragma unroll
+    for (int k = 1; k < i; ++k) {
+      const float c = dl[k - 1] + dr[i - k - 1];
+      if (c < best) {
+        best = c;
+        bk = k;
+      }
+    }
+    split[i] = best;
+    ch |= (uint32_t)(bk - 1) << (3 * (i - 2));
+  }
+  const int32_t cnt = last[id] - first[id] + 1;
+  const float area = half_area(inner_box[id]);
+  const float one = cnt <= leaf_max ? kCostTri * (float)cnt * area : kCostNode * area + split[8];
+  cost[8 * (int64_t)id] = one;
+#pragma unroll
+  for (int i = 2; i <= 8; ++i) {
+    const bool keep = one <= split[i];
+    cost[8 * (int64_t)id + i - 1] = keep ? one : split[i];
+    ch |= keep ? (1u << (21 + i - 2)) : 0u;
+  }
+  choice[id] = ch;
+}
+
 int blocks_of(int64_t n, int t) { return (int)((n + t - 1) / t); }
 
 }  // namespace
 
 ags_status build_ploc(const uint64_t* keys, uint32_t* vals, int32_t R, int key_shift, const int32_t* env_ref_off,
                       int32_t E, const Box* ref_box, Box* leaf_box, int32_t* left, int32_t* right, int32_t* first,
-                      int32_t* last, Box* inner_box, std::vector<int32_t>& roots, cudaStream_t s) {
+                      int32_t* last, Box* inner_box, std::vector<int32_t>& roots, cudaStream_t s,
+                      uint32_t* choice, int leaf_max) {
   NvtxRange range("ags clustering");
   roots.assign(E, -1);
   if (R <= 0) return AGS_OK;
@@ -287,6 +352,15 @@ ags_status build_ploc(const uint64_t* keys, uint32_t* vals, int32_t R, int key_s
   if (n_inner > 0) k_ploc_relabel<<<blocks_of(n_inner, 256), 256, 0, s>>>(n_inner, R, left, right, newpos);
   AGS_CHECK(cudaGetLastError());
   AGS_CHECK(cudaMemcpyAsync(vals, vals2, (size_t)R * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+  if (choice && n_inner > 0) {
+    float* cost = nullptr;
+    AGS_CHECK(tmp.alloc(&cost, 8 * (size_t)n_inner));
+    for (const auto& rd : rounds)
+      k_collapse_cost<<<blocks_of(rd.second - rd.first, 256), 256, 0, s>>>(rd.first, rd.second, left, right, first,
+                                                                         last, inner_box, leaf_box, leaf_max, cost,
+                                                                         choice);
+    AGS_CHECK(cudaGetLastError());
+  }
   int h_err = 0;
   AGS_CHECK(cudaMemcpyAsync(roots.data(), d_roots, (size_t)E * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
   AGS_CHECK(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, s));

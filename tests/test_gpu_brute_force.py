@@ -61,7 +61,8 @@ def test_rooms_1024_envs_every_variant(ctx):
     spec = S.pinhole(96, 54)
     for flags, tag in [(0, "default"), (ags.AGS_BVH_Q8, "8-bit nodes"), (ags.AGS_BVH_FP16, "16-bit nodes"),
                        (ags.AGS_BUILD_LBVH | ags.AGS_LEAF_SIZE(4), "Morton tree, leaves of 4"),
-                       (ags.AGS_SPLIT_CELLS(64) | ags.AGS_LEAF_SIZE(1), "64 split cells, leaves of 1")]:
+                       (ags.AGS_SPLIT_CELLS(64) | ags.AGS_LEAF_SIZE(1), "64 split cells, leaves of 1"),
+                       (ags.AGS_BUILD_GREEDY_COLLAPSE, "greedy collapse"), (ags.AGS_LEAF_SIZE(4), "leaves of 4")]:
         scene = ags.ags_scene_build(ctx, batch, flags)
         try:
             assert assert_same(both(ctx, scene, spec, poses[0]), f"1024 rooms 96x54, {tag}") > 0.5

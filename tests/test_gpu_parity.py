@@ -311,6 +311,9 @@ def test_bit_exact_across_bvh_variants(ctx):
     # the Morton radix tree instead of clustering, alone and with the other options
     variants += [ags.AGS_BUILD_LBVH, ags.AGS_BUILD_LBVH | ags.AGS_LEAF_SIZE(4) | ags.AGS_SPLIT_CELLS(1),
                  ags.AGS_BUILD_LBVH | ags.AGS_BVH_Q8]
+    # the greedy collapse instead of the least-cost slots
+    variants += [ags.AGS_BUILD_GREEDY_COLLAPSE, ags.AGS_BUILD_GREEDY_COLLAPSE | ags.AGS_LEAF_SIZE(4),
+                 ags.AGS_LEAF_SIZE(4) | ags.AGS_BVH_FP16]
     for flags in variants:
         scene = ags.ags_scene_build(ctx, batch, flags)
         try:
@@ -907,7 +910,8 @@ def test_bvh_structure_of_every_variant(ctx):
     batch, spec, poses = S.obstacle_rooms(4, steps=1, width=8, height=8)
     variants = [0, ags.AGS_BVH_FP16, ags.AGS_BVH_Q8, ags.AGS_LEAF_SIZE(1), ags.AGS_LEAF_SIZE(4),
                 ags.AGS_SPLIT_CELLS(1), ags.AGS_SPLIT_CELLS(64), ags.AGS_BUILD_LBVH,
-                ags.AGS_BUILD_LBVH | ags.AGS_BVH_Q8 | ags.AGS_LEAF_SIZE(3), ags.AGS_BUILD_INSTANCED]
+                ags.AGS_BUILD_LBVH | ags.AGS_BVH_Q8 | ags.AGS_LEAF_SIZE(3), ags.AGS_BUILD_INSTANCED,
+                ags.AGS_BUILD_GREEDY_COLLAPSE, ags.AGS_LEAF_SIZE(3) | ags.AGS_SPLIT_CELLS(64)]
     for flags in variants:
         scene = ags.ags_scene_build(ctx, batch, flags)
         try:
