@@ -372,7 +372,9 @@ ags_status ags_autotune_build(ags_context* ctx, ags_scene* scene, const ags_sens
  * launch shape (tiles 8x4, 4x8, 8x8, 16x4, 16x8; full or reduced grid),
  * `repeats` timed renders each after one warm-up, on the context's
  * stream, writing into the caller's buffers (as ags_render). The fastest shape
- * is stored with the scene for this sensor shape (type, width, height) and
+ * (the default 8x4 tile with the full grid is timed first, and another shape
+ * replaces the best so far only when more than 1% faster, so near ties keep
+ * the default) is stored with the scene for this sensor shape (type, width, height) and
  * used by every later ags_render / ags_render_envs of that shape; it is also
  * returned in *best. Synchronous. The paper has no counterpart (its renderer
  * is Warp's); the shape does not change any output bit.

@@ -889,7 +889,9 @@ ags_status ags_autotune(ags_context* ctx, const ags_scene* sc, const ags_sensor_
         break;
       }
       c.ms = ms / repeats;
-      if (top.ms < 0.0f || c.ms < top.ms) top = c;
+      // the default shape is timed first; another replaces the best only when
+      // more than 1% faster, so near ties (within run-to-run noise) keep it
+      if (top.ms < 0.0f || c.ms < 0.99f * top.ms) top = c;
     }
   }
   cudaEventDestroy(e0);
