@@ -185,11 +185,13 @@ def run_oracle(batch, spec, poses_step, envs, rays_per_env, seed=7):
         rays = np.sort(rng.choice(n_pix, min(rays_per_env, n_pix), replace=False)).astype(np.int64)
         work.append((tris, tseg, np.asarray(poses_step[e], np.float64), rays))
     t0 = time.perf_counter()
-    n = 0
+    n = tests = 0
     for tris, tseg, pose, rays in work:
         O.render(tris, tseg, s, pose, rays)
         n += rays.shape[0]
+        tests += rays.shape[0] * tris.shape[0]
     dt = time.perf_counter() - t0
+    run_oracle.last_tests = tests
     return n, dt, O.num_threads()
 
 
@@ -201,9 +203,12 @@ def cpu_baseline(batch, spec, poses, budget_s=12.0):
     per_ray = dt / max(n, 1)
     k = int(max(64, min(spec.width * spec.height, budget_s / per_ray / len(envs))))
     n, dt, cores = run_oracle(batch, spec, poses[0], envs, k, seed=8)
+    rays_per_step = E * spec.width * spec.height
     return {"value": n / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n} random rays ({k} from each of envs {envs}) at step 0, FP64 brute force "
-                      f"over every triangle of the env, {dt:.1f} s"}
+                      f"over every triangle of the env, {dt:.1f} s",
+            "ray_tri_tests_per_s": run_oracle.last_tests / dt,
+            "full_step_s_extrapolated": rays_per_step * dt / max(n, 1)}
 
 
 # ---------------------------------------------------------------- serving
@@ -583,9 +588,9 @@ def bench_reference(args, rank, world):
         e = (it * 131) % E
         n, dt, cores = run_oracle(batch, spec, poses[it % poses.shape[0]], [e], rays_per_step, seed=it)
         if it >= args.warmup:
-            times.append((n, dt))
-    n_tot = sum(n for n, _ in times)
-    t_tot = sum(dt for _, dt in times)
+            times.append((n, dt, run_oracle.last_tests))
+    n_tot = sum(t[0] for t in times)
+    t_tot = sum(t[1] for t in times)
     value = n_tot / t_tot / 1e6
     line = {
         "impl": "reference", "metric": WORKLOADS[args.workload]["metric"], "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -594,7 +599,9 @@ def bench_reference(args, rank, world):
         "config": {"workload": workload_name(args, spec, E), "envs": E, "width": spec.width, "height": spec.height},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"each step: {rays_per_step} random rays of one env (env cycles), FP64 brute "
-                                   f"force over every triangle"},
+                                   f"force over every triangle",
+                         "ray_tri_tests_per_s": sum(t[2] for t in times) / t_tot,
+                         "full_step_s_extrapolated": E * spec.width * spec.height * t_tot / n_tot},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

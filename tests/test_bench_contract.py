@@ -17,6 +17,7 @@ def test_reference_arm_prints_one_json_line():
     assert d["impl"] == "reference" and d["unit"] == "Mrays/s" and d["higher_is_better"] is True
     assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["ray_tri_tests_per_s"] > 0 and d["cpu_baseline"]["full_step_s_extrapolated"] > 0
     assert d["e2e"] == {"value": d["value"], "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["metric"].startswith("Mrays/s at 1024 envs x 270x480")
 
@@ -28,7 +29,7 @@ def test_counter_tables_parse():
     b = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(b)
     assert len(b.kernel_source_hash()) == 16
-    rows = 0
+    rows = current = 0
     for name in os.listdir(b.PROFILE_DIR):
         if name.startswith("k_trace_") and name.endswith("_traffic.md"):
             for line in open(os.path.join(b.PROFILE_DIR, name)):
@@ -36,4 +37,8 @@ def test_counter_tables_parse():
                 if len(cells) == 7 and ":" in cells[0] and cells[1].startswith("k_trace<"):
                     assert int(cells[3]) + int(cells[4]) == int(cells[5]) and int(cells[6]) > 0
                     rows += 1
+                    current += cells[2] == b.kernel_source_hash()
     assert rows >= 2
+    # the committed counters were taken on the current kernel and builder sources (else the bench reports
+    # traffic as null): recapture them after changing either
+    assert current >= 2
