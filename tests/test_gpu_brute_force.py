@@ -157,3 +157,80 @@ def test_empty_and_invalid(ctx):
             ags.ags_render_bruteforce(ctx, inst, spec, p, d, s)
     finally:
         ags.ags_scene_destroy(inst)
+
+
+def same_or_oracle(out, batch, spec, poses, tag, max_frac=1e-4):
+    """Bit-identical, except on at most max_frac of the rays, where the BVH render must then agree with the
+    FP64 oracle. A float32 triangle test on a ray within ~1e-7 rad of a sliver's plane can accept the sliver
+    at a t outside the sliver's box along the ray (its barycentric weights are rounding noise, so t is any
+    depth of its vertices); whether such a hit is found then depends on the order of the tests, and the
+    FP64 oracle places it elsewhere or nowhere."""
+    (d, s), (bd, bs) = out
+    bad = (d.view(np.uint32) != bd.view(np.uint32)) | (s != bs)
+    n_bad = int(bad.sum())
+    assert n_bad <= max(1, max_frac * bad.size), f"{tag}: {n_bad} of {bad.size} rays differ"
+    W = spec.width
+    for e, r, c in np.argwhere(bad):
+        ray = np.array([r * W + c], np.int64)
+        ok, _, res = compare_env(batch, int(e), spec, poses[e], d[e], s[e], ray)
+        assert ok.all(), f"{tag}: env {e}: " + describe_failures(ok, res, d[e].reshape(-1)[ray], s[e].reshape(-1)[ray], ray)
+    print(f"[brute] {tag}: {bad.size - n_bad} of {bad.size} rays bit-identical, {n_bad} differing "
+          f"(the BVH render's value checked against the oracle)")
+
+
+def _soup(rng, n, scale, offset):
+    """n random triangles: mixed sizes, some degenerate (repeated or collinear vertices), some duplicated
+    exactly (equal t: the smaller triangle id must win) and some axis-aligned (flat boxes)."""
+    c = offset + rng.uniform(-scale, scale, (n, 1, 3))
+    size = scale * 10.0 ** rng.uniform(-3, -0.3, (n, 1, 1))
+    v = (c + size * rng.normal(size=(n, 3, 3))).astype(np.float32)
+    k = rng.random(n)
+    v[k < 0.05, 2] = v[k < 0.05, 1]                                     # repeated vertex
+    col = (k >= 0.05) & (k < 0.1)
+    v[col, 2] = (2.0 * v[col, 1] - v[col, 0]).astype(np.float32)       # (nearly) collinear
+    flat = (k >= 0.1) & (k < 0.3)
+    axis = rng.integers(0, 3, int(flat.sum()))
+    v[np.where(flat)[0], :, axis] = v[np.where(flat)[0], 0:1, axis]    # axis-aligned plane
+    dup = rng.random(n) < 0.05
+    v[dup] = v[np.roll(np.arange(n), 1)][dup]                          # exact copies of a neighbour
+    return v.reshape(-1, 3), np.arange(3 * n, dtype=np.int32).reshape(-1, 3)
+
+
+@pytest.mark.parametrize("offset", [0.0, 1000.0, -5000.0])
+def test_random_soups_far_from_the_origin(ctx, offset):
+    """Random triangle soups (degenerate, duplicated and axis-aligned triangles) at growing distances from
+    the origin, seen by cameras with axis-aligned and random poses and by a LiDAR: every ray bit-identical
+    to brute force under three builds, and a sample within the tolerance of the FP64 oracle."""
+    rng = np.random.default_rng(int(abs(offset)) + 50)
+    o = np.array([offset, -0.5 * offset, 0.25 * offset])
+    envs = []
+    for e in range(48):
+        objs = []
+        for j in range(int(rng.integers(1, 5))):
+            v, f = _soup(rng, int(rng.integers(50, 800)), 8.0, o)
+            objs.append((v, f, S.IDENTITY_POSE, int(rng.integers(0, 5))))
+        envs.append(objs)
+    batch = S.scene_from_lists(envs)
+    poses = np.zeros((48, 7), np.float32)
+    poses[:, :3] = o + rng.uniform(-6, 6, (48, 3))
+    poses[:, 3:] = S.random_unit_quat(rng, 48)
+    poses[::4, 3:] = S.IDENTITY_POSE[3:]                                # exact axis directions
+    poses[1::8, 3:] = np.array([0.0, 0.0, np.sqrt(0.5), np.sqrt(0.5)], np.float32)  # 90 degrees about z
+    for spec in (S.pinhole(64, 48, max_range=30.0), S.lidar(128, 16, max_range=40.0)):
+        outs = []
+        for flags in (0, ags.AGS_BUILD_LBVH | ags.AGS_LEAF_SIZE(4), ags.AGS_BVH_Q8 | ags.AGS_SPLIT_CELLS(32)):
+            scene = ags.ags_scene_build(ctx, batch, flags)
+            try:
+                out = both(ctx, scene, spec, poses)
+                tag = f"soups at {offset:g} m, {'camera' if spec.type == 0 else 'LiDAR'}, flags {flags}"
+                same_or_oracle(out, batch, spec, poses, tag)
+                outs.append(out[0])
+            finally:
+                ags.ags_scene_destroy(scene)
+        for d, s in outs[1:]:
+            same_or_oracle([(d, s), outs[0]], batch, spec, poses, f"soups at {offset:g} m, builds")
+        d, s = outs[0]
+        for e in (0, 17, 47):
+            rays = np.sort(rng.choice(spec.width * spec.height, 48, replace=False)).astype(np.int64)
+            ok, _, res = compare_env(batch, e, spec, poses[e], d[e], s[e], rays)
+            assert ok.all(), describe_failures(ok, res, d[e].reshape(-1)[rays], s[e].reshape(-1)[rays], rays)
