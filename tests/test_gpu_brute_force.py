@@ -200,7 +200,8 @@ def _soup(rng, n, scale, offset):
 def test_random_soups_far_from_the_origin(ctx, offset):
     """Random triangle soups (degenerate, duplicated and axis-aligned triangles) at growing distances from
     the origin, seen by cameras with axis-aligned and random poses and by a LiDAR: every ray bit-identical
-    to brute force under three builds, and a sample within the tolerance of the FP64 oracle."""
+    to brute force under three builds (but for rare grazing slivers, see same_or_oracle), and every ray
+    within the tolerance of the FP64 oracle."""
     rng = np.random.default_rng(int(abs(offset)) + 50)
     o = np.array([offset, -0.5 * offset, 0.25 * offset])
     envs = []
@@ -230,7 +231,11 @@ def test_random_soups_far_from_the_origin(ctx, offset):
         for d, s in outs[1:]:
             same_or_oracle([(d, s), outs[0]], batch, spec, poses, f"soups at {offset:g} m, builds")
         d, s = outs[0]
-        for e in (0, 17, 47):
-            rays = np.sort(rng.choice(spec.width * spec.height, 48, replace=False)).astype(np.int64)
-            ok, _, res = compare_env(batch, e, spec, poses[e], d[e], s[e], rays)
-            assert ok.all(), describe_failures(ok, res, d[e].reshape(-1)[rays], s[e].reshape(-1)[rays], rays)
+        n = counted = 0
+        for e in range(batch.n_envs):  # every ray against the oracle
+            ok, cnt, res = compare_env(batch, e, spec, poses[e], d[e], s[e])
+            rays = np.arange(spec.width * spec.height)
+            assert ok.all(), f"env {e}: " + describe_failures(ok, res, d[e].reshape(-1), s[e].reshape(-1), rays)
+            n += ok.size
+            counted += int(cnt.sum())
+        print(f"[parity] soups at {offset:g} m, {'camera' if spec.type == 0 else 'LiDAR'}: {n} rays, {counted} counted")
