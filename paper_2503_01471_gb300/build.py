@@ -2,7 +2,7 @@
 
 Each translation unit is compiled by nvcc in parallel, then linked into one
 shared library with the CUDA runtime linked statically, so the library only
-needs the driver at run time.
+needs the CUDA driver library at run time.
 """
 from __future__ import annotations
 

@@ -1,5 +1,5 @@
 """bench.py's contract on the CPU: the reference arm (the FP64 oracle timed on the host cores) prints one
-JSON line with the keys the driver reads, and the ncu counter tables parse."""
+JSON line with the keys of the benchmark contract, and the ncu counter tables parse."""
 import json
 import os
 import subprocess
