@@ -438,9 +438,15 @@ def bench_dynamic(args, rank, world, local):
     refit = ags.ags_scene_build(ctx, batch)
     rebuilt = ags.ags_scene_build(ctx, batch)
     two = ags.ags_scene_build(ctx, batch, ags.AGS_BUILD_INSTANCED)
+    auto = ags.ags_scene_build(ctx, batch)
     cur = batch.poses.copy()
     rows = []
-    t_refit, t_rebuild, t_two = [], [], []
+    t_refit, t_rebuild, t_two, t_auto = [], [], [], []
+    auto_rebuilds = 0
+
+    def cost_ratio(scene):
+        now, built = ags.ags_scene_tree_cost(ctx, scene)
+        return now / built if built > 0 else None
     for step in range(args.steps + 1):
         if step > 0:  # obstacles drift: 5 cm and 0.05 rad per step
             cur[movable, :3] += rng.normal(0, 0.05, (movable.sum(), 3)).astype(np.float32)
@@ -456,10 +462,18 @@ def bench_dynamic(args, rank, world, local):
             t0 = time.perf_counter()
             ags.ags_scene_update_poses(ctx, two, cur, ags.AGS_UPDATE_REBUILD)
             t_two.append((time.perf_counter() - t0) * 1e3)
+            built_before = ags.ags_scene_tree_cost(ctx, auto)[1]
+            t0 = time.perf_counter()
+            ags.ags_scene_update_poses(ctx, auto, cur, ags.AGS_UPDATE_AUTO)
+            t_auto.append((time.perf_counter() - t0) * 1e3)
+            auto_rebuilds += int(ags.ags_scene_tree_cost(ctx, auto)[1] != built_before)
         if step in (0, 1, args.steps // 2, args.steps):
             rows.append({"step": step, "refit_mrays_per_s": rays / render_ms(refit) / 1e3,
                          "rebuild_mrays_per_s": rays / render_ms(rebuilt) / 1e3,
-                         "two_level_mrays_per_s": rays / render_ms(two) / 1e3})
+                         "two_level_mrays_per_s": rays / render_ms(two) / 1e3,
+                         "auto_mrays_per_s": rays / render_ms(auto) / 1e3,
+                         "refit_tree_cost_ratio": cost_ratio(refit), "auto_tree_cost_ratio": cost_ratio(auto),
+                         "auto_rebuilds_so_far": auto_rebuilds})
     line = {"metric": WORKLOADS["dynamic"]["metric"], "value": float(np.median(t_refit)), "unit": "ms",
             "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"obstacle rooms, {E} envs, 270x480 camera; every obstacle moves each step",
@@ -467,9 +481,11 @@ def bench_dynamic(args, rank, world, local):
             "refit_ms": {"median": float(np.median(t_refit)), "max": float(np.max(t_refit))},
             "rebuild_ms": {"median": float(np.median(t_rebuild)), "max": float(np.max(t_rebuild))},
             "two_level_update_ms": {"median": float(np.median(t_two)), "max": float(np.max(t_two))},
+            "auto_update_ms": {"median": float(np.median(t_auto)), "max": float(np.max(t_auto)),
+                               "rebuilds": auto_rebuilds, "rebuild_ratio": 1.25},
             "render_after_updates": rows}
     print(json.dumps(line), flush=True)
-    for sc in (refit, rebuilt, two):
+    for sc in (refit, rebuilt, two, auto):
         ags.ags_scene_destroy(sc)
     ags.ags_context_destroy(ctx)
 

@@ -181,7 +181,25 @@ void ags_scene_destroy(ags_scene* scene);
  */
 #define AGS_UPDATE_REFIT 0
 #define AGS_UPDATE_REBUILD 1
+/* AGS_UPDATE_AUTO refits, then rebuilds when the refitted tree's surface-area
+ * cost (ags_scene_tree_cost) exceeds the tree's cost as built (or last
+ * rebuilt) by more than the scene's rebuild ratio (1.25 unless set); scenes
+ * with compressed nodes are rebuilt, two-level scenes update as in the other
+ * modes. */
+#define AGS_UPDATE_AUTO 2
 ags_status ags_scene_update_poses(ags_context* ctx, ags_scene* scene, const float* obstacle_poses, int32_t mode);
+
+/*
+ * ags_scene_tree_cost -- the surface-area cost of a single-level scene's
+ * float32 BVH under the model its collapse minimises: summed over every wide
+ * node, the area (dx dy + dy dz + dz dx) of each inner child box plus 0.3 x
+ * triangles x area of each leaf child box. out[0] = now, out[1] = as built or
+ * last rebuilt (-1 when not measured). Synchronous. The paper has no
+ * counterpart; it tracks how far refits have degraded the tree.
+ */
+ags_status ags_scene_tree_cost(ags_context* ctx, const ags_scene* scene, double out[2]);
+/* The multiple of the built cost above which AGS_UPDATE_AUTO rebuilds (>= 1). */
+ags_status ags_scene_set_rebuild_ratio(ags_scene* scene, double ratio);
 
 /*
  * ags_render -- Sec. III-D.1: cast one ray per pixel / beam of `spec` from

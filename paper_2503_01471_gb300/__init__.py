@@ -61,7 +61,7 @@ EXPORTS = [
     "ags_replay_sequential", "ags_scene_update_poses", "ags_render_graph_create", "ags_render_graph_launch",
     "ags_render_graph_destroy", "ags_render_channels", "ags_render_ex", "ags_autotune_build", "ags_scene_validate",
     "ags_server_cancel", "ags_test_sort_pairs", "ags_test_exclusive_scan", "ags_context_device",
-    "ags_render_bruteforce",
+    "ags_render_bruteforce", "ags_scene_tree_cost", "ags_scene_set_rebuild_ratio",
 ]
 
 
@@ -202,6 +202,8 @@ def lib() -> ctypes.CDLL:
         "ags_scene_validate": (i32, [vp, ctypes.POINTER(ctypes.c_int64)]),
         "ags_server_cancel": (i32, [vp, ctypes.c_uint64]),
         "ags_render_bruteforce": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), vp, vp, vp, vp]),
+        "ags_scene_tree_cost": (i32, [vp, vp, ctypes.POINTER(ctypes.c_double)]),
+        "ags_scene_set_rebuild_ratio": (i32, [vp, ctypes.c_double]),
         "ags_context_device": (i32, [vp, ctypes.c_char_p, i32, ctypes.POINTER(ctypes.c_int32),
                                      ctypes.POINTER(ctypes.c_int32)]),
         "ags_test_sort_pairs": (i32, [vp, vp, vp, ctypes.c_int64, i32]),
@@ -303,6 +305,7 @@ def ags_scene_build(ctx: int, batch, build_flags: int = AGS_BVH_FP32) -> int:
 
 AGS_UPDATE_REFIT = 0
 AGS_UPDATE_REBUILD = 1
+AGS_UPDATE_AUTO = 2
 
 
 def ags_scene_update_poses(ctx: int, scene: int, obstacle_poses, mode: int = AGS_UPDATE_REFIT) -> None:
@@ -612,3 +615,14 @@ def ags_render_bruteforce(ctx: int, scene: int, spec, sensor_poses, out_depth, o
     s = make_spec(spec)
     _check(lib().ags_render_bruteforce(ctx, scene, ctypes.byref(s), _ptr(sensor_poses), _ptr(out_depth),
                                        _ptr(out_seg), _stream(stream)), "ags_render_bruteforce")
+
+
+def ags_scene_tree_cost(ctx: int, scene: int):
+    """(surface-area cost of the BVH now, as built or last rebuilt; -1 when not measured)."""
+    c = (ctypes.c_double * 2)()
+    _check(lib().ags_scene_tree_cost(ctx, scene, c), "ags_scene_tree_cost")
+    return float(c[0]), float(c[1])
+
+
+def ags_scene_set_rebuild_ratio(scene: int, ratio: float) -> None:
+    _check(lib().ags_scene_set_rebuild_ratio(scene, float(ratio)), "ags_scene_set_rebuild_ratio")

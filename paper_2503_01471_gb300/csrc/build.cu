@@ -1171,6 +1171,7 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
                             cudaMemcpyDeviceToHost, s));
   AGS_CHECK(cudaStreamSynchronize(s));
   for (int32_t e = 0; e < E; ++e) sc->env_nodes[e] = (int64_t)env_nodes[e];
+  if (sc->node_format == kNodeFp32) return tree_cost(ctx, sc, &sc->tree_cost_built);
   return AGS_OK;
 }
 
@@ -1347,6 +1348,45 @@ ags_status transform_vertices(const float* base_dev, int32_t V, const int32_t* s
                                                             world_dev);
   AGS_CHECK(cudaGetLastError());
   AGS_CHECK(cudaStreamSynchronize(s));  // the scratch is freed on return
+  return AGS_OK;
+}
+
+namespace {
+// Per node: the collapse's cost of its child boxes (inner: node weight x area; leaf: triangle weight x
+// count x area; area as in the collapse, dx dy + dy dz + dz dx), summed in double.
+__global__ void k_tree_cost(const WideNode* __restrict__ nodes, int32_t n, double* __restrict__ out) {
+  double c = 0.0;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const WideNode& nd = nodes[i];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t m = ((k < 4 ? nd.meta_lo : nd.meta_hi) >> (8 * (k & 3))) & 0xFFu;
+      if (m == kMetaEmpty) continue;
+      const double dx = (double)nd.hix[k] - nd.lox[k], dy = (double)nd.hiy[k] - nd.loy[k],
+                   dz = (double)nd.hiz[k] - nd.loz[k];
+      const double area = dx * dy + dy * dz + dz * dx;
+      c += (m & 0x80u) ? (double)kSahNodeCost * area : (double)kSahTriCost * (double)((m & 3u) + 1) * area;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c != 0.0) atomicAdd(out, c);
+}
+}  // namespace
+
+ags_status tree_cost(ags_context* ctx, const ags_scene* sc, double* cost) {
+  *cost = 0.0;
+  if (sc->node_format != kNodeFp32 || sc->n_nodes <= 0) return AGS_OK;
+  cudaStream_t s = ctx->stream;
+  DevBufs tmp;
+  double* d_cost = nullptr;
+  AGS_CHECK(tmp.alloc(&d_cost, 1));
+  AGS_CHECK(cudaMemsetAsync(d_cost, 0, sizeof(double), s));
+  const int blocks = (int)std::min<int64_t>(blocks_for(sc->n_nodes, 256), 4096);
+  k_tree_cost<<<blocks, 256, 0, s>>>(static_cast<const WideNode*>(sc->d.nodes), (int32_t)sc->n_nodes, d_cost);
+  AGS_CHECK(cudaGetLastError());
+  AGS_CHECK(cudaMemcpyAsync(cost, d_cost, sizeof(double), cudaMemcpyDeviceToHost, s));
+  AGS_CHECK(cudaStreamSynchronize(s));
   return AGS_OK;
 }
 

@@ -433,6 +433,7 @@ void adopt(ags_scene* sc, ScenePtr& fresh, bool keep_launch) {
   fresh->h_sub_vert.swap(sc->h_sub_vert);
   fresh->h_sub_env.swap(sc->h_sub_env);
   fresh->h_poses.swap(sc->h_poses);
+  fresh->rebuild_ratio = sc->rebuild_ratio;
   if (keep_launch) fresh->launch = sc->launch;
   std::swap(*sc, *fresh);
   fresh.reset();
@@ -445,7 +446,8 @@ ags_status ags_scene_update_poses(ags_context* ctx, ags_scene* sc, const float* 
   AGS_API_BEGIN
   if (!ctx || !sc) return invalid("ctx or scene is NULL");
   if (sc->ctx != ctx) return invalid("scene belongs to another context");
-  if (mode != AGS_UPDATE_REFIT && mode != AGS_UPDATE_REBUILD) return invalid("mode must be AGS_UPDATE_REFIT or AGS_UPDATE_REBUILD");
+  if (mode != AGS_UPDATE_REFIT && mode != AGS_UPDATE_REBUILD && mode != AGS_UPDATE_AUTO)
+    return invalid("mode must be AGS_UPDATE_REFIT, AGS_UPDATE_REBUILD or AGS_UPDATE_AUTO");
   if (sc->n_subs > 0 && !poses) return invalid("poses is NULL");
   for (int64_t j = 0; j < sc->n_subs; ++j) {
     const float* p = poses + 7 * j;
@@ -462,9 +464,18 @@ ags_status ags_scene_update_poses(ags_context* ctx, ags_scene* sc, const float* 
     if (sc->node_format != kNodeFp32) return invalid("refit needs float32 nodes; use AGS_UPDATE_REBUILD");
     st = refit_scene(ctx, sc, poses);
   } else {
-    // rebuild: a fresh scene from the kept inputs, then swap it in
-    ScenePtr fresh;
-    if ((st = rebuild_like(ctx, sc, poses, sc->flags, fresh)) == AGS_OK) adopt(sc, fresh, true);
+    bool rebuild = true;
+    if (mode == AGS_UPDATE_AUTO && sc->node_format == kNodeFp32 && sc->tree_cost_built > 0.0) {
+      // refit, and keep the refitted tree unless its cost outgrew the built tree's by rebuild_ratio
+      double cost = 0.0;
+      if ((st = refit_scene(ctx, sc, poses)) != AGS_OK || (st = tree_cost(ctx, sc, &cost)) != AGS_OK) return st;
+      rebuild = cost > sc->rebuild_ratio * sc->tree_cost_built;
+    }
+    if (rebuild) {
+      // a fresh scene from the kept inputs, then swap it in (with its own built cost)
+      ScenePtr fresh;
+      if ((st = rebuild_like(ctx, sc, poses, sc->flags, fresh)) == AGS_OK) adopt(sc, fresh, true);
+    }
   }
   if (st == AGS_OK && sc->n_subs > 0) sc->h_poses.assign(poses, poses + 7 * sc->n_subs);
   return st;
@@ -472,6 +483,29 @@ ags_status ags_scene_update_poses(ags_context* ctx, ags_scene* sc, const float* 
 }
 
 int32_t ags_scene_node_bytes(const ags_scene* sc) { return sc ? node_bytes_of(sc->node_format) : -1; }
+
+ags_status ags_scene_tree_cost(ags_context* ctx, const ags_scene* sc, double out[2]) {
+  AGS_API_BEGIN
+  if (!ctx || !sc || !out) return invalid("ctx, scene or out is NULL");
+  if (sc->ctx != ctx) return invalid("scene belongs to another context");
+  if (sc->objects || sc->node_format != kNodeFp32) return invalid("tree cost needs a single-level scene with float32 nodes");
+  DeviceGuard g(ctx->device);
+  double c = 0.0;
+  ags_status st = tree_cost(ctx, sc, &c);
+  out[0] = c;
+  out[1] = sc->tree_cost_built;
+  return st;
+  AGS_API_END
+}
+
+ags_status ags_scene_set_rebuild_ratio(ags_scene* sc, double ratio) {
+  AGS_API_BEGIN
+  if (!sc) return invalid("scene is NULL");
+  if (!(ratio >= 1.0) || !std::isfinite(ratio)) return invalid("rebuild ratio must be a finite number >= 1");
+  sc->rebuild_ratio = ratio;
+  return AGS_OK;
+  AGS_API_END
+}
 
 ags_status ags_render(ags_context* ctx, const ags_scene* sc, const ags_sensor_spec* spec, const float* poses,
                       float* depth, int32_t* seg, void* stream) {

@@ -39,6 +39,12 @@ constexpr int kNodeQ8 = 2;    // 80 B: child bounds as 8-bit steps of a power-of
 inline int node_bytes_of(int fmt) { return fmt == kNodeFp16 ? 128 : (fmt == kNodeQ8 ? 80 : 208); }
 
 constexpr int kMaxLeafTris = 4;      // largest wide-BVH leaf (2-bit count field)
+// weights of the surface-area cost model of the wide tree (ploc.cu's collapse and tree_cost): a wide
+// node visit against a triangle test, about the ratio of their instructions
+#ifndef AGS_SAH_TRI_COST
+#define AGS_SAH_TRI_COST 0.3f
+#endif
+constexpr float kSahNodeCost = 1.0f, kSahTriCost = AGS_SAH_TRI_COST;
 constexpr int kDefaultLeafTris = 2;  // default leaf size (fewest instructions per ray on room scenes)
 constexpr uint8_t kMetaEmpty = 0xFF;
 constexpr float kEmptyBoxCoord = 1e30f;  // empty slots hold a far-away point box
@@ -138,6 +144,10 @@ struct ags_scene {
   ags::InstanceDev* d_inst = nullptr;  // [J]
   int32_t* d_env_sub = nullptr;        // [E+1]
   std::vector<double> h_obj_box;       // [J][6] object-frame bounds of each object's vertices
+  // AGS_UPDATE_AUTO: surface-area cost of the float32 tree as built (tree_cost; -1 when not measured)
+  // and the multiple of it above which a refitted tree is rebuilt instead
+  double tree_cost_built = -1.0;
+  double rebuild_ratio = 1.25;
 };
 
 namespace ags {
@@ -221,6 +231,9 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
                        const float* poses_h, const int32_t* sub_env_h);
 
 ags_status refit_scene(ags_context* ctx, ags_scene* sc, const float* poses_h);
+// surface-area cost of a float32 tree under the collapse's model (kSahNodeCost x area of every inner
+// child box + kSahTriCost x count x area of every leaf child box, all nodes); synchronous
+ags_status tree_cost(ags_context* ctx, const ags_scene* sc, double* cost);
 
 // trace.cu
 // Ray pattern of one sensor shape (derived from ags_sensor_spec on the host).

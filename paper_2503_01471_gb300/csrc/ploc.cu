@@ -219,10 +219,7 @@ __global__ void k_ploc_relabel(int32_t n_inner, int32_t R, int32_t* __restrict__
 // earlier clustering rounds than their parent, so the rounds in order give a
 // bottom-up pass. choice[n] packs, for i = 2..8, the k of S(n, i) less one
 // (3 bits at 3 (i - 2)) and whether D(n, i) keeps n as one slot (bit 21 + i - 2).
-#ifndef AGS_SAH_TRI_COST
-#define AGS_SAH_TRI_COST 0.3f
-#endif
-constexpr float kCostNode = 1.0f, kCostTri = AGS_SAH_TRI_COST;
+constexpr float kCostNode = kSahNodeCost, kCostTri = kSahTriCost;
 
 __global__ void k_collapse_cost(int32_t b, int32_t e, const int32_t* __restrict__ left,
                                 const int32_t* __restrict__ right, const int32_t* __restrict__ first,

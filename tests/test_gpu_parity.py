@@ -467,6 +467,65 @@ def test_refit_after_moving_every_object_including_split_walls(ctx):
         ags.ags_scene_destroy(refit)
 
 
+def test_auto_update_refits_then_rebuilds_when_the_tree_degrades(ctx):
+    """AGS_UPDATE_AUTO keeps a refitted tree while its surface-area cost stays within the rebuild ratio of the
+    built tree's, and rebuilds past it; either way the images equal a fresh build's."""
+    batch, spec, poses = S.obstacle_rooms(6, steps=1, width=48, height=36)
+    scene = ags.ags_scene_build(ctx, batch)
+    q8 = ags.ags_scene_build(ctx, batch, ags.AGS_BVH_Q8)
+    try:
+        now, built = ags.ags_scene_tree_cost(ctx, scene)
+        assert built > 0 and abs(now - built) <= 1e-9 * built
+        rng = np.random.default_rng(23)
+        movable = np.ones(batch.poses.shape[0], bool)
+        movable[batch.env_sub[:-1]] = False
+        cur = batch.poses.copy()
+
+        def fresh_images(p):
+            moved = S.SceneBatch(batch.vertices, batch.indices, batch.sub_vert, batch.sub_tri, batch.sub_seg,
+                                 batch.env_sub, p.copy())
+            f = ags.ags_scene_build(ctx, moved)
+            try:
+                return render(ctx, f, spec, poses[0])
+            finally:
+                ags.ags_scene_destroy(f)
+
+        # a small move: refitted, kept (the built cost stays that of the build)
+        cur[movable, :3] += rng.normal(0, 0.01, (movable.sum(), 3)).astype(np.float32)
+        ags.ags_scene_update_poses(ctx, scene, cur, ags.AGS_UPDATE_AUTO)
+        now1, built1 = ags.ags_scene_tree_cost(ctx, scene)
+        assert built1 == built and now1 != built and now1 <= 1.25 * built
+        ref = fresh_images(cur)
+        out = render(ctx, scene, spec, poses[0])
+        assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1])
+        # a large move past a tight ratio: rebuilt (a new built cost, equal to the tree's own)
+        ags.ags_scene_set_rebuild_ratio(scene, 1.0)
+        cur[movable, :3] += rng.normal(0, 1.0, (movable.sum(), 3)).astype(np.float32)
+        ags.ags_scene_update_poses(ctx, scene, cur, ags.AGS_UPDATE_AUTO)
+        now2, built2 = ags.ags_scene_tree_cost(ctx, scene)
+        assert built2 != built and abs(now2 - built2) <= 1e-9 * built2
+        ref = fresh_images(cur)
+        out = render(ctx, scene, spec, poses[0])
+        assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1])
+        moved = S.SceneBatch(batch.vertices, batch.indices, batch.sub_vert, batch.sub_tri, batch.sub_seg,
+                             batch.env_sub, cur.copy())
+        check_all(moved, spec, poses[0], out[0], out[1], envs=[0, 5], tag="automatic refit or rebuild 48x36")
+        # compressed nodes cannot refit: AUTO rebuilds them; their cost is not defined
+        ags.ags_scene_update_poses(ctx, q8, cur, ags.AGS_UPDATE_AUTO)
+        out = render(ctx, q8, spec, poses[0])
+        assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1])
+        with pytest.raises(ags.AgsError):
+            ags.ags_scene_tree_cost(ctx, q8)
+        for bad in (0.5, float("nan"), float("inf")):
+            with pytest.raises(ags.AgsError):
+                ags.ags_scene_set_rebuild_ratio(scene, bad)
+        with pytest.raises(ags.AgsError):
+            ags.ags_scene_update_poses(ctx, scene, cur, 3)
+    finally:
+        ags.ags_scene_destroy(scene)
+        ags.ags_scene_destroy(q8)
+
+
 def test_step_graph_replays_the_render(ctx):
     batch, spec, poses = S.obstacle_rooms(3, steps=3, width=48, height=36)
     scene = ags.ags_scene_build(ctx, batch)
