@@ -42,3 +42,26 @@ def test_counter_tables_parse():
     # the committed counters were taken on the current kernel and builder sources (else the bench reports
     # traffic as null): recapture them after changing either
     assert current >= 2
+
+
+def test_clock_samples_summary():
+    """The clock record of the timed region: median SM clock, max clock and every active throttle reason."""
+    import importlib.util
+    import tempfile
+    spec = importlib.util.spec_from_file_location("bench_mod2", os.path.join(ROOT, "bench.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+    rows = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 2055, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 1980, 2070, 1400.0, 0x8, Active, Not Active, Not Active, Active"]
+    fd, path = tempfile.mkstemp(suffix=".csv")
+    with os.fdopen(fd, "w") as fh:
+        fh.write("\n".join(rows) + "\n")
+    c = b.ClockSampler(0)
+    c.path = path
+    out = c.summary()
+    assert out == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["hw_slowdown", "sw_power_cap"], "samples": 3}
+    assert not os.path.exists(path)
+    c2 = b.ClockSampler(0)
+    c2.path = os.path.join(tempfile.gettempdir(), "does-not-exist.csv")
+    assert c2.summary()["reasons"] == ["unsampled"]
