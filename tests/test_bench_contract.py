@@ -65,3 +65,17 @@ def test_clock_samples_summary():
     c2 = b.ClockSampler(0)
     c2.path = os.path.join(tempfile.gettempdir(), "does-not-exist.csv")
     assert c2.summary()["reasons"] == ["unsampled"]
+
+
+def test_clock_rejection_rule():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod3", os.path.join(ROOT, "bench.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+    ok = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}
+    assert not b.clocks_rejected(ok)
+    assert not b.clocks_rejected(dict(ok, reasons=["sw_power_cap"], sm_mhz=1700.0))  # power cap: kept
+    for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
+        assert b.clocks_rejected(dict(ok, reasons=[r]))
+    assert b.clocks_rejected(dict(ok, sm_mhz=1400.0))          # well below max with no reason: a lock
+    assert not b.clocks_rejected({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]})
