@@ -705,6 +705,8 @@ def bench_ours(args, rank, world, local):
         return ms, clk.summary()
 
     ms, clocks = timed_steps()
+    start = torch.cuda.Event(enable_timing=True)  # for the plain-launch and step-graph timings below
+    stop = torch.cuda.Event(enable_timing=True)
     first_clocks = None
     bad = clocks_rejected(clocks)
     if dist is not None:
