@@ -37,6 +37,28 @@ def test_library_exports_every_declared_symbol(lib):
         assert hasattr(lib, name), name
 
 
+def header_constants():
+    """Integer constants of include/ags.h: object-like #defines and enum members."""
+    text = open(os.path.join(ROOT, "include", "ags.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for name, expr in re.findall(r"^#define\s+(AGS_[A-Z0-9_]+)\s+([^\n(][^\n]*|\([^\n]*\))$", text, flags=re.M):
+        expr = re.sub(r"(\d+)u\b", r"\1", expr.strip())
+        if re.fullmatch(r"[\d\s()<x|a-fA-F]+", expr):
+            out[name] = eval(expr)  # noqa: S307 (digits, shifts and or only)
+    for name, val in re.findall(r"\b(AGS_[A-Z0-9_]+)\s*=\s*(\d+)", text):
+        out[name] = int(val)
+    return out
+
+
+def test_binding_constants_match_the_header():
+    consts = header_constants()
+    assert len(consts) >= 20
+    for name, val in consts.items():
+        assert getattr(ags, name) == val, name
+    assert ags.AGS_LEAF_SIZE(3) == 3 << 8 and ags.AGS_SPLIT_CELLS(64) == 64 << 12
+
+
 def test_struct_layouts_match_the_header():
     assert ctypes.sizeof(ags.ags_submesh) == 32
     assert ctypes.sizeof(ags.ags_env_mesh) == 16
