@@ -138,6 +138,8 @@ typedef struct {
   double t_exact;
   int possible, sure, edge, grazing;
   double t_lo, t_hi;
+  double cosn;       /* |n.d| (0 for a zero-area triangle) */
+  double vert;       /* the vertex band: how far rounding may move the triangle's plane */
 } orc_tri_eval;
 
 static void eval_triangle(const double* tri, const double o[3], const double d[3],
@@ -192,6 +194,7 @@ static void eval_triangle(const double* tri, const double o[3], const double d[3
   }
   rmax = fmax(sqrt(dot3(a, a)), fmax(sqrt(dot3(b, b)), sqrt(dot3(c, c))));
   double vert = sqrt(3.0) * bands->vert_rel * cmax + vert_extra;
+  r->vert = vert;
   double eps = vert + (bands->dir_rel + bands->arith_rel) * rmax;
   double len0 = hypot(pc[0] - pb[0], pc[1] - pb[1]);
   double len1 = hypot(pa[0] - pc[0], pa[1] - pc[1]);
@@ -209,7 +212,12 @@ static void eval_triangle(const double* tri, const double o[3], const double d[3
    * and also shifts t along the ray directly (the same amount); moving the
    * plane by vert along its normal moves t by vert / cos(n, d). */
   double cosn = fabs(dot3(n, d)) / nn;
-  double zmin = fmin(za, fmin(zb, zc)) - vert, zmax = fmax(za, fmax(zb, zc)) + vert;
+  r->cosn = cosn;
+  /* the hit lies in the triangle, so its t is within the vertices' depths,
+   * widened by what the bands do to those depths: the vertex band, the
+   * direction band over the vertex distance, and the arithmetic band's shift
+   * along the ray (together: eps) */
+  double zmin = fmin(za, fmin(zb, zc)) - eps, zmax = fmax(za, fmax(zb, zc)) + eps;
   double t_lo = zmin, t_hi = zmax;
   if (area2 != 0.0 && cosn > 0.0) {
     double tc = (e0 * za + e1 * zb + e2 * zc) / area2;
@@ -266,6 +274,7 @@ static void render_one(const double* tris, const int32_t* seg, int64_t F, const 
 
   double best_t = INFINITY;
   int64_t best_i = -1;
+  double best_cos = 0.0, best_lo = 0.0, best_hi = 0.0, best_vert = 0.0;
   double sure_thi = INFINITY;
   int n_list = 0, list_overflow = 0;
 
@@ -275,6 +284,10 @@ static void render_one(const double* tris, const int32_t* seg, int64_t F, const 
     if (ev.exact_hit && (ev.t_exact < best_t || (ev.t_exact == best_t && i < best_i))) {
       best_t = ev.t_exact;
       best_i = i;
+      best_cos = ev.cosn;
+      best_vert = ev.vert;
+      best_lo = ev.t_lo;
+      best_hi = ev.t_hi;
     }
     if (!ev.possible) continue;
     if (ev.sure && ev.t_hi < sure_thi) sure_thi = ev.t_hi;
@@ -303,6 +316,10 @@ static void render_one(const double* tris, const int32_t* seg, int64_t F, const 
 
   /* exact answer (a6): value, clamp, miss */
   res->t_hit = best_i >= 0 ? best_t : INFINITY;
+  if (best_i >= 0) {
+    res->cos_hit = best_cos;
+    res->hit_dev = fmax(best_t - best_lo, best_hi - best_t) * scale;
+  }
   if (best_i >= 0) {
     double v = best_t * scale;
     if (v > s->max_range) v = s->max_range;
@@ -334,7 +351,9 @@ static void render_one(const double* tris, const int32_t* seg, int64_t F, const 
     orc_cand* c = &list[k];
     if (c->t_lo > bound) continue;
     if (c->edge) flags |= ORC_F_SILHOUETTE;
-    if (c->grazing) flags |= ORC_F_GRAZING;
+    /* geometrically sure but its t band crosses the sensor's origin or the
+     * far limit: hit vs miss is open there */
+    if (!c->sure && !c->edge) flags |= ORC_F_RANGE_EDGE;
     if (c->sure) {
       if (n_sure_segs == 0) {
         sure_seg0 = c->seg;
@@ -381,9 +400,26 @@ static void render_one(const double* tris, const int32_t* seg, int64_t F, const 
   if (n_sure_segs > 1) flags |= ORC_F_NEAR_TIE;
   if (miss_ok) flags |= ORC_F_MISS_OK;
   int outcomes = res->n_cand + (miss_ok ? 1 : 0);
-  if (outcomes > 1) flags |= ORC_F_COUNTED;
   for (int g = 0; g < res->n_cand; ++g)
     if (res->cand_hi[g] - res->cand_lo[g] > 2.0 * tolv(res->cand_hi[g])) flags |= ORC_F_WIDE;
+
+  /* Counting. A ray is held to the tolerance around the exact answer unless
+   * one of these reasons applies; then any outcome the bands allow is
+   * accepted and the ray is counted:
+   *  - several outcomes (a silhouette, a near tie or a range edge above);
+   *  - grazing: the exact hit surface meets the ray so obliquely that the
+   *    direction band alone moves the hit by more than the relative
+   *    tolerance: a tilt of dir_rel moves it by t dir_rel tan(theta), above
+   *    1e-5 t once tan(theta) > 1e-5 / dir_rel (|n.d| < 0.06 for 6e-7);
+   *  - coarse: the vertex band of the hit triangle (the float32 spacing of
+   *    its coordinates) is above the tolerance at the hit's value, so no
+   *    float32 scene can place that surface within it, at any incidence. */
+  if (outcomes > 1) flags |= ORC_F_COUNTED;
+  if (best_i >= 0 && res->seg >= 0) {
+    const double cos_graze = s->dir_rel / sqrt(s->dir_rel * s->dir_rel + 1e-10);
+    if (best_cos < cos_graze) flags |= ORC_F_GRAZING | ORC_F_COUNTED;
+    if (best_vert * scale > tolv(res->v)) flags |= ORC_F_COARSE | ORC_F_COUNTED;
+  }
   res->flags = flags;
 }
 

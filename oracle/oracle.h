@@ -15,8 +15,10 @@
  *     (distance of the hit from the image plane) for the camera, and the
  *     segment ID of the object hit; misses report max_range and -1.
  * On top of the exact answer it classifies each ray's tolerance-ambiguous
- * outcomes (edge/silhouette, near-tie, range boundary, grazing) so that a
- * single-precision implementation can be judged element by element.
+ * outcomes (edge/silhouette, near-tie, range boundary, grazing incidence,
+ * coarse coordinates) so that a single-precision implementation can be judged
+ * element by element: a ray none of these applies to must match the exact
+ * answer within the tolerance.
  */
 #ifndef AGS_ORACLE_H
 #define AGS_ORACLE_H
@@ -38,15 +40,16 @@ extern "C" {
 #define ORC_MAX_TRI 8
 
 /* flag bits of orc_result.flags */
-#define ORC_F_COUNTED 1      /* more than one outcome (segment, or hit vs miss) is acceptable */
+#define ORC_F_COUNTED 1      /* judged against the listed outcomes, not the tolerance (a reason below holds) */
 #define ORC_F_SILHOUETTE 2   /* a candidate lies within eps of a triangle edge */
 #define ORC_F_NEAR_TIE 4     /* two surely-hit triangles of different segments within tol */
-#define ORC_F_RANGE_EDGE 8   /* a candidate lies within tol of a range limit */
-#define ORC_F_GRAZING 16     /* a candidate has |n.d| < 1e-3 */
+#define ORC_F_RANGE_EDGE 8   /* a candidate lies within tol of a range limit or of the sensor's origin */
+#define ORC_F_GRAZING 16     /* the exact hit surface has |n.d| below the grazing bound (counted) */
 #define ORC_F_OVERFLOW 32    /* more than ORC_MAX_CAND segment groups (test must fail) */
 #define ORC_F_MISS_OK 64     /* "miss" (max_range, -1) is an acceptable outcome */
-#define ORC_F_WIDE 128       /* the error bands widen an outcome's value range beyond +-tol */
+#define ORC_F_WIDE 128       /* the error bands widen an outcome's value range beyond +-tol (information only) */
 #define ORC_F_TRI_OVERFLOW 256 /* more than ORC_MAX_TRI candidate triangles */
+#define ORC_F_COARSE 512     /* the hit triangle's vertex band exceeds the tolerance (counted) */
 
 typedef struct {
   int32_t type;        /* ORC_PINHOLE or ORC_LIDAR */
@@ -78,6 +81,9 @@ typedef struct {
   int32_t n_tri;       /* triangles a single-precision renderer may report (within the bands) */
   int32_t cand_tri[ORC_MAX_TRI];
   double t_hit;        /* exact distance to the nearest hit along the unit ray (INFINITY: none) */
+  double cos_hit;      /* |n.d| of the exact nearest triangle (0 on a miss) */
+  double hit_dev;      /* how far the error bands move that triangle's own hit, in reported units
+                          (the larger side of its band around the exact value; 0 on a miss) */
 } orc_result;
 
 /* Rotation matrix of the unit quaternion q/|q| (x, y, z, w order), row-major. */

@@ -348,11 +348,31 @@ def ags_transform_vertices_noalloc(ctx: int, base_vertices, submesh_vertex_offse
     """Object-to-world transform into caller-owned device buffers, allocating nothing.
 
     base_vertices float32 [V,3], submesh_vertex_offsets int32 [J+1], poses
-    float32 [J,7], world_vertices float32 [V,4] (all CUDA tensors or device
-    pointers; pass sizes through the tensors' shapes).
+    float32 [J,7], world_vertices float32 [>=V,4]: CUDA tensors, whose shapes
+    give the sizes. Dtypes and shapes are checked here on the host (a short
+    offsets array or a small output would make the kernels read or write out
+    of bounds); a mismatch raises ValueError before anything is launched.
     """
+    def _need(t, name, dtype, ndim, cols=None):
+        if not (hasattr(t, "dtype") and hasattr(t, "shape") and hasattr(t, "is_cuda")):
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if not t.is_cuda or t.dtype != dtype or t.dim() != ndim or (cols is not None and t.shape[1] != cols):
+            raise ValueError(f"{name} must be a CUDA {dtype} tensor of {ndim} dims"
+                             + (f" with {cols} columns" if cols is not None else "") + f", got {t.dtype} "
+                             f"{tuple(t.shape)} on {t.device}")
+
+    import torch
+    _need(base_vertices, "base_vertices", torch.float32, 2, 3)
+    _need(submesh_vertex_offsets, "submesh_vertex_offsets", torch.int32, 1)
+    _need(poses, "poses", torch.float32, 2, 7)
+    _need(world_vertices, "world_vertices", torch.float32, 2, 4)
     V = int(base_vertices.shape[0])
     J = int(poses.shape[0])
+    if int(submesh_vertex_offsets.shape[0]) != J + 1:
+        raise ValueError(f"submesh_vertex_offsets must hold J+1 = {J + 1} entries, got "
+                         f"{int(submesh_vertex_offsets.shape[0])}")
+    if int(world_vertices.shape[0]) < V:
+        raise ValueError(f"world_vertices must have at least V = {V} rows, got {int(world_vertices.shape[0])}")
     _check(lib().ags_transform_vertices_noalloc(ctx, _ptr(base_vertices), V, _ptr(submesh_vertex_offsets), J,
                                                 _ptr(poses), _ptr(world_vertices), _stream(stream)),
            "ags_transform_vertices_noalloc")

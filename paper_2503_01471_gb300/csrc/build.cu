@@ -1468,6 +1468,15 @@ ags_status noalloc_scratch(int device, float** out) {
   }
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (!g_noalloc_ptr[device]) {
+    // the address is only valid on the device current at the lookup: never
+    // cache one taken with another device current
+    int cur = -1;
+    cudaError_t ce = cudaGetDevice(&cur);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
+    if (cur != device) {
+      set_error("ags_transform_vertices_noalloc: the context's device is not current");
+      return AGS_ERR_CUDA;
+    }
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, ags_noalloc_rot_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(ags_noalloc_rot_scratch)");
@@ -1508,7 +1517,10 @@ extern "C" ags_status ags_transform_vertices_noalloc(ags_context* ctx, const flo
   }
   int prev = -1;
   if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-  if (prev != ctx->device) cudaSetDevice(ctx->device);
+  if (prev != ctx->device) {
+    const cudaError_t se = cudaSetDevice(ctx->device);
+    if (se != cudaSuccess) return cuda_fail(se, "ags_transform_vertices_noalloc: cudaSetDevice");
+  }
   float* rot = nullptr;
   ags_status st = noalloc_scratch(ctx->device, &rot);
   if (st == AGS_OK) {

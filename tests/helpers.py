@@ -28,19 +28,22 @@ def compare_env(batch, e, spec, pose, depth, seg, rays=None):
     res = O.render(tris, tseg, s, np.asarray(pose, np.float32).astype(np.float64), rays)
     d = np.asarray(depth, np.float32).reshape(-1)[rays]
     g = np.asarray(seg, np.int32).reshape(-1)[rays]
-    ok, counted, strict = O.check(res, d, g, s.max_range, with_strict=True)
-    compare_env.last_strict = strict
-    compare_env.last_wide = (res["flags"] & O.F_WIDE) != 0
+    ok, counted = O.check(res, d, g, s.max_range)
     return ok, counted, res
 
 
 def describe_failures(ok, res, depth, seg, rays, limit=5):
+    """The first failing rays: renderer vs exact value and segment, the error in tolerances, the hit surface's
+    incidence |n.d|, how far the float32 bands move its hit (in tolerances), the flags and the listed outcomes."""
     bad = np.nonzero(~ok)[0][:limit]
     lines = []
     for i in bad:
         r = res[i]
+        t = O.tol(r["v"])
         lines.append(f"ray {int(rays[i])}: gpu=({float(depth[i])!r}, {int(seg[i])}) oracle v={r['v']!r} seg={r['seg']} "
-                     f"flags={r['flags']} cand={list(zip(r['cand_seg'][:r['n_cand']], r['cand_lo'][:r['n_cand']], r['cand_hi'][:r['n_cand']]))}")
+                     f"err={abs(float(depth[i]) - r['v']) / t:.2f} tol |n.d|={r['cos_hit']:.4f} "
+                     f"band={r['hit_dev'] / t:.2f} tol flags={r['flags']} "
+                     f"cand={list(zip(r['cand_seg'][:r['n_cand']], r['cand_lo'][:r['n_cand']], r['cand_hi'][:r['n_cand']]))}")
     return "\n".join(lines)
 
 

@@ -632,3 +632,170 @@ ALL_PINS = [
     pin_shadow_plate_closed_form, pin_shadow_zero_baseline_and_open_scene, pin_shadow_linear_solve,
     pin_ray_table_reproduces_builtin_models, pin_ray_table_wall_units,
 ]
+
+
+# ---------------------------------------------------------------- error bands (counting and acceptance)
+# The oracle judges a float32 renderer with three stated error bands: each world vertex coordinate off by up
+# to VERT_REL * cmax (cmax: the largest |coordinate| of the ray origin and the triangle, at least 1), the ray
+# direction tilted by up to DIR_REL, and the intersection arithmetic moving the ray sideways by up to
+# ARITH_REL * rmax (rmax: the farthest vertex) and its distance along the ray by as much. The pins below
+# apply those perturbations to the exact geometry, intersect in FP64, and hold the oracle's bands, edge
+# flags and counting reasons to what the perturbed rays actually do: every perturbed hit must fall inside
+# the band (sound) and the band may be at most twice as wide as the largest perturbed deviation (tight).
+
+def _one_ray(d):
+    """A 1x1 ray-table sensor casting unit direction d (reported value = distance along the ray)."""
+    d = np.asarray(d, float) / np.linalg.norm(d)
+    return O.Sensor(O.RAY_TABLE, 1, 1, 0.0, 1e-9, 1e6, dirs=d.reshape(1, 1, 3))
+
+
+def _frame(d):
+    """Unit d and two unit vectors spanning the plane orthogonal to it."""
+    d = np.asarray(d, float) / np.linalg.norm(d)
+    a = np.array([1.0, 0, 0]) if abs(d[0]) < 0.9 else np.array([0, 1.0, 0])
+    u = np.cross(d, a)
+    u /= np.linalg.norm(u)
+    return d, u, np.cross(d, u)
+
+
+def _perturbed(tri, o, d, rng, n_random=400):
+    """(t, barycentrics) of the ray's meet with the triangle's plane under the band perturbations: every
+    combination of extreme signs along the plane normal's in-ray-plane direction, plus random extremes."""
+    tri = np.asarray(tri, float).reshape(3, 3)
+    cmax = max(1.0, np.abs(tri).max(), np.abs(o).max())
+    vert = O.VERT_REL * cmax
+    rmax = np.linalg.norm(tri - o, axis=1).max()
+    ar = O.ARITH_REL * rmax
+    n = np.cross(tri[1] - tri[0], tri[2] - tri[0])
+    n /= np.linalg.norm(n)
+    e = n - (n @ d) * d  # the sideways direction that moves the hit most
+    e = e / np.linalg.norm(e) if np.linalg.norm(e) > 1e-12 else _frame(d)[1]
+    cases = []
+    for sv in (-1, 1):
+        for st in (-1, 1):
+            for ss in (-1, 1):
+                for sa in (-1, 1):
+                    cases.append((np.tile(sv * np.sign(n), (3, 1)), st * e, ss * e, sa))
+    for _ in range(n_random):
+        dv = rng.choice([-1.0, 1.0], size=(3, 3))
+        r1, r2 = rng.normal(size=3), rng.normal(size=3)
+        r1 -= (r1 @ d) * d
+        r2 -= (r2 @ d) * d
+        cases.append((dv, r1 / np.linalg.norm(r1), r2 / np.linalg.norm(r2), rng.choice([-1, 1])))
+    out = []
+    for dv, tilt, side, along in cases:
+        T = tri + vert * dv
+        dd = np.cos(O.DIR_REL) * d + np.sin(O.DIR_REL) * tilt
+        oo = o + ar * side
+        # o + t dd = T0 + b1 (T1 - T0) + b2 (T2 - T0)
+        A = np.column_stack([dd, T[0] - T[1], T[0] - T[2]])
+        t, b1, b2 = np.linalg.solve(A, T[0] - oo)
+        out.append((t + along * ar, 1 - b1 - b2, b1, b2))
+    return np.array(out)
+
+
+def _tilted_triangle(o, d, D, theta, rng, size=2.0):
+    """A large triangle whose plane meets the ray at distance D with incidence angle theta (|n.d| = cos)."""
+    d, u, w = _frame(d)
+    phi = rng.uniform(0, 2 * np.pi)
+    a = np.cos(phi) * u + np.sin(phi) * w  # the tilt axis, orthogonal to the ray
+    n = np.cos(theta) * d + np.sin(theta) * np.cross(a, d)
+    b1 = a
+    b2 = np.cross(n, b1)
+    c = o + D * d
+    return np.array([c + size * b1 - size * b2, c - size * b1 - size * b2, c + 1.3 * size * b2])
+
+
+def pin_band_width_against_perturbations(lib):
+    """Sound and tight t bands across incidences, near the origin (direction and arithmetic bands dominate)
+    and 200 m from it (the vertex band dominates)."""
+    rng = np.random.default_rng(31)
+    for o in (np.array([0.3, -0.2, 0.1]), np.array([180.0, -140.0, 95.0])):
+        for theta_deg in (0.0, 40.0, 70.0, 82.0, 87.0):
+            d = _frame(rng.normal(size=3))[0]
+            D = rng.uniform(2.0, 6.0)
+            tri = _tilted_triangle(o, d, D, math.radians(theta_deg), rng)
+            res = O.render(tri.reshape(1, 9), np.array([1], np.int32), _one_ray(d),
+                           np.concatenate([o, [0, 0, 0, 1]]), lib=lib)[0]
+            assert res["seg"] == 1 and res["n_cand"] == 1, (theta_deg, res)
+            t0 = res["v"]
+            pert = _perturbed(tri, o, d, rng)
+            assert np.all(pert[:, 1:] > 0)  # every perturbed ray still meets the triangle inside
+            lo, hi = res["cand_lo"][0], res["cand_hi"][0]
+            dev = np.abs(pert[:, 0] - t0).max()
+            assert lo <= pert[:, 0].min() + 1e-12 * t0 and pert[:, 0].max() <= hi + 1e-12 * t0, \
+                (theta_deg, lo, hi, pert[:, 0].min(), pert[:, 0].max())
+            assert (hi - lo) / 2 <= 2.0 * dev, (theta_deg, (hi - lo) / 2, dev)
+            assert abs(res["hit_dev"] - max(t0 - lo, hi - t0)) <= 1e-12 * t0
+
+
+def pin_silhouette_band_against_perturbations(lib):
+    """A ray passing an edge at sideways distance s is flagged (and counted) when a band perturbation can
+    carry it across the edge, and not once s is 1.6 times the largest such displacement."""
+    rng = np.random.default_rng(32)
+    o = np.array([0.2, 0.1, -0.3])
+    d, u, w = _frame([1.0, 0.3, 0.2])
+    D, a, h = 5.0, 0.03, 0.04
+    # the edge v0-v1 runs along u at sideways offset s0 (along w) from the ray; v2 lies at s0 + h
+    def tri_at(s0):
+        c = o + D * d + (rng.uniform(-1, 1) * 0.002) * d
+        return np.array([c + a * u + s0 * w, c - a * u + s0 * w, c + (s0 + h) * w])
+    base = tri_at(0.0)
+    pert = _perturbed(base, o, d, rng)
+    s_flip = np.abs(pert[:, 3] * h).max()  # how far the perturbations move the ray across the edge
+    assert s_flip > 0
+    pose = np.concatenate([o, [0, 0, 0, 1]])
+    for frac, inside in ((0.8, True), (0.8, False), (1.6, True), (1.6, False)):
+        s0 = -frac * s_flip if inside else frac * s_flip
+        res = O.render(tri_at(s0).reshape(1, 9), np.array([2], np.int32), _one_ray(d), pose, lib=lib)[0]
+        sil = bool(res["flags"] & O.F_SILHOUETTE)
+        counted = bool(res["flags"] & O.F_COUNTED)
+        if frac < 1:
+            assert sil and counted and (res["flags"] & O.F_MISS_OK), (frac, inside, res["flags"])
+        else:
+            assert not sil and not counted, (frac, inside, res["flags"], s_flip)
+            assert res["seg"] == (2 if inside else -1)
+
+
+def pin_grazing_and_coarse_reasons(lib):
+    """Counted for incidence: when the direction band alone can move the hit by more than the relative
+    tolerance (grazing), and when the vertex band alone exceeds the tolerance at normal incidence (coarse
+    coordinates, far from the origin). Not counted when every band perturbation stays within the tolerance."""
+    rng = np.random.default_rng(33)
+    o = np.array([0.4, 0.7, -0.2])
+    for theta_deg in (30.0, 60.0, 80.0, 86.0, 87.5, 88.5):
+        d = _frame(rng.normal(size=3))[0]
+        D = 3.0
+        tri = _tilted_triangle(o, d, D, math.radians(theta_deg), rng)
+        res = O.render(tri.reshape(1, 9), np.array([5], np.int32), _one_ray(d),
+                       np.concatenate([o, [0, 0, 0, 1]]), lib=lib)[0]
+        # deviation from the direction tilt alone, in the plane of the ray and the normal
+        n = np.cross(tri[1] - tri[0], tri[2] - tri[0])
+        n /= np.linalg.norm(n)
+        e = n - (n @ d) * d
+        e /= np.linalg.norm(e)
+        tilt = [np.linalg.solve(np.column_stack([np.cos(O.DIR_REL) * d + s * np.sin(O.DIR_REL) * e,
+                                                 tri[0] - tri[1], tri[0] - tri[2]]), tri[0] - o)[0]
+                for s in (-1, 1)]
+        dev_tilt = max(abs(t - res["v"]) for t in tilt)
+        dev_all = np.abs(_perturbed(tri, o, d, rng)[:, 0] - res["v"]).max()
+        graze = bool(res["flags"] & O.F_GRAZING)
+        if dev_tilt > 1e-5 * res["v"] * 1.02:
+            assert graze and (res["flags"] & O.F_COUNTED), (theta_deg, dev_tilt, res["flags"])
+        if dev_all < O.tol(res["v"]):
+            assert not (res["flags"] & O.F_COUNTED), (theta_deg, dev_all, res["flags"])
+    # a wall 5 km from the origin seen head on from 3 m: its coordinates' float32 spacing alone exceeds the
+    # tolerance; the same wall near the origin is judged by the tolerance
+    for centre, coarse in ((np.array([5000.0, -3000.0, 2000.0]), True), (np.array([2.0, 1.0, 0.5]), False)):
+        d = np.array([1.0, 0.0, 0.0])
+        oc = centre - 3.0 * d + np.array([0.0, 1.1, -0.7])  # off the diagonal shared by the two triangles
+        wall = np.array(_rect(centre[0], centre[1] - 5, centre[1] + 5, centre[2] - 5, centre[2] + 5), float)
+        res = O.render(wall, np.array([0, 0], np.int32), _one_ray(d), np.concatenate([oc, [0, 0, 0, 1]]),
+                       lib=lib)[0]
+        dev_vert = O.VERT_REL * max(1.0, np.abs(wall).max(), np.abs(oc).max())  # a wall coordinate moved
+        assert (dev_vert > O.tol(res["v"])) == coarse
+        assert bool(res["flags"] & O.F_COARSE) == coarse and bool(res["flags"] & O.F_COUNTED) == coarse
+
+
+ALL_PINS += [pin_band_width_against_perturbations, pin_silhouette_band_against_perturbations,
+             pin_grazing_and_coarse_reasons]

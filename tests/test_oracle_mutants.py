@@ -55,6 +55,21 @@ MUTANTS = {
     "shadow_segment_too_long": ("    double t_far = (1.0 - eps) * L;", "    double t_far = 2.0 * L;"),
     "ray_table_scale_inverted": ("    *scale = 1.0 / n;", "    *scale = n;"),
     "ray_table_not_normalised": ("    for (int k = 0; k < 3; ++k) local[k] = g[k] / n;", "    for (int k = 0; k < 3; ++k) local[k] = g[k];"),
+    # the error bands and the counting reasons
+    "band_delta_inflated": ("double delta = (bands->dir_rel * fabs(tc) + ar) * fmin(tan_n, bary) + ar + vert / cosn;",
+                            "double delta = 10.0 * ((bands->dir_rel * fabs(tc) + ar) * fmin(tan_n, bary) + ar + vert / cosn);"),
+    "band_vertex_term_without_cos": ("* fmin(tan_n, bary) + ar + vert / cosn;", "* fmin(tan_n, bary) + ar + vert;"),
+    "band_without_sideways_slope": ("* fmin(tan_n, bary) + ar + vert / cosn;", "* 0.0 + ar + vert / cosn;"),
+    "band_without_direction_term": ("double delta = (bands->dir_rel * fabs(tc) + ar)", "double delta = (ar)"),
+    "band_depth_clamp_without_eps": ("double zmin = fmin(za, fmin(zb, zc)) - eps, zmax = fmax(za, fmax(zb, zc)) + eps;",
+                                     "double zmin = fmin(za, fmin(zb, zc)) - vert, zmax = fmax(za, fmax(zb, zc)) + vert;"),
+    "eps_doubled": ("double eps = vert + (bands->dir_rel + bands->arith_rel) * rmax;",
+                    "double eps = 2.0 * (vert + (bands->dir_rel + bands->arith_rel) * rmax);"),
+    "eps_halved": ("double eps = vert + (bands->dir_rel + bands->arith_rel) * rmax;",
+                   "double eps = 0.5 * (vert + (bands->dir_rel + bands->arith_rel) * rmax);"),
+    "grazing_reason_dropped": ("if (best_cos < cos_graze) flags |=", "if (best_cos < 0.0) flags |="),
+    "grazing_bound_tenfold": ("if (best_cos < cos_graze) flags |=", "if (best_cos < 10.0 * cos_graze) flags |="),
+    "coarse_reason_dropped": ("if (best_vert * scale > tolv(res->v)) flags |=", "if (best_vert * scale > 1e9) flags |="),
 }
 
 

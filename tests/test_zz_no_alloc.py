@@ -83,3 +83,28 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(ctx):
     out = torch.zeros((4, 4), device="cuda")
     with pytest.raises(ags.AgsError, match="65536"):
         ags.ags_transform_vertices_noalloc(ctx, base, offs, poses, out)
+
+
+def test_noalloc_checks_shapes_and_dtypes_on_the_host(ctx):
+    base = torch.zeros((8, 3), device="cuda")
+    offs = torch.tensor([0, 4, 8], dtype=torch.int32, device="cuda")
+    poses = torch.zeros((2, 7), device="cuda")
+    poses[:, 6] = 1.0
+    out = torch.zeros((8, 4), device="cuda")
+    bad = [
+        dict(submesh_vertex_offsets=offs[:2]),                     # J entries instead of J+1
+        dict(submesh_vertex_offsets=offs.to(torch.int64)),         # wrong dtype
+        dict(world_vertices=out[:7]),                              # fewer rows than vertices
+        dict(world_vertices=torch.zeros((8, 3), device="cuda")),   # not [V,4]
+        dict(poses=torch.zeros((2, 6), device="cuda")),            # not [J,7]
+        dict(base_vertices=base.double()),                         # wrong dtype
+        dict(base_vertices=base.cpu()),                            # host tensor
+    ]
+    for kw in bad:
+        args = dict(base_vertices=base, submesh_vertex_offsets=offs, poses=poses, world_vertices=out)
+        args.update(kw)
+        with pytest.raises(ValueError):
+            ags.ags_transform_vertices_noalloc(ctx, **args)
+    ags.ags_transform_vertices_noalloc(ctx, base, offs, poses, out)  # the well-formed call still runs
+    torch.cuda.synchronize()
+    assert torch.equal(out[:, :3], base)
