@@ -136,8 +136,8 @@ typedef struct {
  * pixels (or beams) of one environment, each lane tracing rays_per_lane rays
  * of it; the grid holds blocks_per_sm blocks per SM (0: as many as fit). */
 typedef struct {
-  int32_t tile_w;         /* with rays_per_lane, one of the compiled shapes: */
-  int32_t rays_per_lane;  /* (8,1) 8x4, (4,1) 4x8, (8,2) 8x8, (16,2) 16x4, (16,4) 16x8 */
+  int32_t tile_w;         /* with rays_per_lane, one of the compiled shapes: (8,1) 8x4, */
+  int32_t rays_per_lane;  /* (4,1) 4x8, (16,1) 16x2, (32,1) 32x1, (8,2) 8x8, (16,2) 16x4, (16,4) 16x8 */
   int32_t blocks_per_sm;  /* 0, or 1 .. the kernel's occupancy limit */
   float ms;               /* ags_autotune: measured time of one render; else 0 */
 } ags_launch_config;

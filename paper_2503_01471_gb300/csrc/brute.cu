@@ -41,28 +41,14 @@ __global__ void k_brute(const TraceArgs a, const int32_t* __restrict__ env_ref, 
     return;
   }
   const float* P = a.poses + 7 * (int64_t)slot;
-  const float px = __ldg(P), py = __ldg(P + 1), pz = __ldg(P + 2);
-  const float qx = __ldg(P + 3), qy = __ldg(P + 4), qz = __ldg(P + 5), qw = __ldg(P + 6);
-  const float n2 = qx * qx + qy * qy + qz * qz + qw * qw;
-  if (!(n2 >= 1e-30f) || !isfinite(n2) || !isfinite(px + py + pz)) {
+  Ray r;
+  float R[9], lx, ly, lz;
+  if (!make_ray<false>(sen, P, row, col, r, R, lx, ly, lz)) {
     atomicOr(a.status, kStatusBadPose);
     a.out_depth[i] = __int_as_float(0x7fc00000);
     a.out_seg[i] = -1;
     return;
   }
-  const float s = 2.0f / n2;
-  const float R00 = 1.0f - s * (qy * qy + qz * qz), R01 = s * (qx * qy - qz * qw), R02 = s * (qx * qz + qy * qw);
-  const float R10 = s * (qx * qy + qz * qw), R11 = 1.0f - s * (qx * qx + qz * qz), R12 = s * (qy * qz - qx * qw);
-  const float R20 = s * (qx * qz - qy * qw), R21 = s * (qy * qz + qx * qw), R22 = 1.0f - s * (qx * qx + qy * qy);
-  float lx, ly, lz;
-  sensor_dir<false>(sen, row, col, lx, ly, lz);
-  Ray r;
-  r.ox = px;
-  r.oy = py;
-  r.oz = pz;
-  setup_ray(r, __fmaf_rn(R02, lz, __fmaf_rn(R01, ly, __fmul_rn(R00, lx))),
-            __fmaf_rn(R12, lz, __fmaf_rn(R11, ly, __fmul_rn(R10, lx))),
-            __fmaf_rn(R22, lz, __fmaf_rn(R21, ly, __fmul_rn(R20, lx))));
   float t_best = sen.max_range;
   int32_t best_id = 0x7fffffff, best_seg = -1, best_k = -1;
   const int32_t k0 = __ldg(env_ref + env), k1 = __ldg(env_ref + env + 1);

@@ -105,7 +105,8 @@ int max_blocks_per_sm(ags_context* ctx) { return ctx->sm_count > 0 ? ctx->trace_
 ags_status check_config(ags_context* ctx, const ags_launch_config* c) {
   if (!c) return invalid("launch config is NULL");
   if (!trace_shape_supported(c->tile_w, c->rays_per_lane))
-    return invalid("unsupported launch shape: (tile_w, rays_per_lane) must be one of (8,1) (4,1) (8,2) (16,2) (16,4)");
+    return invalid("unsupported launch shape: (tile_w, rays_per_lane) must be one of (8,1) (4,1) (16,1) (32,1) "
+                   "(8,2) (16,2) (16,4)");
   if (c->blocks_per_sm < 0 || c->blocks_per_sm > max_blocks_per_sm(ctx))
     return invalid("blocks_per_sm must be 0 .. the kernel's occupancy limit");
   return AGS_OK;

@@ -308,8 +308,8 @@ cudaError_t launch_trace(const TraceArgs& a, int blocks, bool count, cudaStream_
 cudaError_t launch_trace_extra(const TraceArgs& a, int blocks, cudaStream_t s);  // a.extra != 0
 cudaError_t launch_trace_inst(const TraceArgs& a, int blocks, cudaStream_t s);   // a.instanced != 0
 // compiled launch shapes of the render kernel: {tile width, rays per lane}
-constexpr int kTraceShapes = 5;
-constexpr int kTraceShape[kTraceShapes][2] = {{8, 1}, {4, 1}, {8, 2}, {16, 2}, {16, 4}};
+constexpr int kTraceShapes = 7;
+constexpr int kTraceShape[kTraceShapes][2] = {{8, 1}, {4, 1}, {8, 2}, {16, 2}, {16, 4}, {16, 1}, {32, 1}};
 bool trace_shape_supported(int tile_w, int rays_per_lane);
 // host: ray pattern of a validated spec for tiles of tile_w x tile_h
 SensorParams sensor_params(const ags_sensor_spec* spec, int tile_w, int tile_h);

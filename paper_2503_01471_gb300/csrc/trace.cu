@@ -43,6 +43,10 @@ cudaError_t launch_fmt(const TraceArgs& a, int blocks, bool count, cudaStream_t 
     k_trace<false, 16, 2, false, kFmt><<<blocks, kTraceThreads, 0, s>>>(a);
   } else if (w == 16 && r == 4) {
     k_trace<false, 16, 4, false, kFmt><<<blocks, kTraceThreads, 0, s>>>(a);
+  } else if (w == 16 && r == 1) {
+    k_trace<false, 16, 1, false, kFmt><<<blocks, kTraceThreads, 0, s>>>(a);
+  } else if (w == 32 && r == 1) {
+    k_trace<false, 32, 1, false, kFmt><<<blocks, kTraceThreads, 0, s>>>(a);
   } else {
     return cudaErrorInvalidValue;
   }

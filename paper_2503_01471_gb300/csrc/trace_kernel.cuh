@@ -179,16 +179,17 @@ __device__ __forceinline__ void hit_normal(const float4* __restrict__ tris, int3
   const float4 a = __ldg(tris + 3 * (int64_t)k);
   const float4 b = __ldg(tris + 3 * (int64_t)k + 1);
   const float4 c = __ldg(tris + 3 * (int64_t)k + 2);
-  const float e1x = b.x - a.x, e1y = b.y - a.y, e1z = b.z - a.z;
-  const float e2x = c.x - a.x, e2y = c.y - a.y, e2z = c.z - a.z;
-  nx = e1y * e2z - e1z * e2y;
-  ny = e1z * e2x - e1x * e2z;
-  nz = e1x * e2y - e1y * e2x;
-  float s = rsqrtf(nx * nx + ny * ny + nz * nz);
-  if (nx * dx + ny * dy + nz * dz > 0.0f) s = -s;
-  nx *= s;
-  ny *= s;
-  nz *= s;
+  // explicitly rounded, so that every kernel variant gives the same bits
+  const float e1x = __fsub_rn(b.x, a.x), e1y = __fsub_rn(b.y, a.y), e1z = __fsub_rn(b.z, a.z);
+  const float e2x = __fsub_rn(c.x, a.x), e2y = __fsub_rn(c.y, a.y), e2z = __fsub_rn(c.z, a.z);
+  nx = __fmaf_rn(e1y, e2z, -__fmul_rn(e1z, e2y));
+  ny = __fmaf_rn(e1z, e2x, -__fmul_rn(e1x, e2z));
+  nz = __fmaf_rn(e1x, e2y, -__fmul_rn(e1y, e2x));
+  float s = rsqrtf(__fmaf_rn(nz, nz, __fmaf_rn(ny, ny, __fmul_rn(nx, nx))));
+  if (__fmaf_rn(nz, dz, __fmaf_rn(ny, dy, __fmul_rn(nx, dx))) > 0.0f) s = -s;
+  nx = __fmul_rn(nx, s);
+  ny = __fmul_rn(ny, s);
+  nz = __fmul_rn(nz, s);
 }
 
 // The rays of one warp tile: sensor shape `sen`, environment `env`, tile
@@ -430,10 +431,10 @@ __device__ __forceinline__ void sensor_dir(const SensorParams& sen, int32_t row,
     lz = __fmul_rn(0.5f * (float)sen.H - ((float)row + 0.5f), sen.inv_f);
   } else {
     float sin_el, cos_el, sin_az, cos_az;
-    sincosf(sen.vmax - (float)row * sen.dv, &sin_el, &cos_el);
-    sincosf(sen.hfov * ((float)col / (float)sen.W), &sin_az, &cos_az);
-    lx = cos_el * cos_az;
-    ly = cos_el * sin_az;
+    sincosf(__fmaf_rn(-(float)row, sen.dv, sen.vmax), &sin_el, &cos_el);
+    sincosf(__fmul_rn(sen.hfov, __fdiv_rn((float)col, (float)sen.W)), &sin_az, &cos_az);
+    lx = __fmul_rn(cos_el, cos_az);
+    ly = __fmul_rn(cos_el, sin_az);
     lz = sin_el;
   }
 }
@@ -447,6 +448,186 @@ template <bool kSlots>
 __device__ __forceinline__ int64_t slot_out(const TraceArgs& a, const SensorParams& sen, int32_t slot) {
   if constexpr (kSlots) return __ldg(&a.slots[slot].out_offset);
   else return (int64_t)slot * sen.H * sen.W;
+}
+
+// One step of a ray's nearest-hit traversal (a4-a6): test the eight children
+// of `node`, the triangles of its hit leaves (they tighten t_best before any
+// descent), then pick the next node: the nearest hit inner child (the
+// others pushed, farthest deepest), else the nearest stacked node still
+// within the cull distance. Returns -1 when the ray is done; sets `failed`
+// (and the status word) on an out-of-range triangle range or a full stack.
+template <bool kCount, int kFmt, bool kChannels>
+__device__ __forceinline__ int32_t visit_node(const TraceArgs& a, const Ray& r, int32_t node, float& t_best,
+                                              int32_t& best_id, int32_t& best_seg, int32_t& best_k, int2* stack,
+                                              int& sp, bool& failed, unsigned long long& n_tris) {
+  int32_t* __restrict__ status = a.status;
+  const float t_cull = t_best * kCullSlack;
+  int32_t child_base, tri_base;
+  uint32_t meta_lo, meta_hi;
+  float tmins[8];
+  uint32_t hit_mask;
+  test_node<kFmt>(a.nodes, node, r, t_cull, child_base, tri_base, meta_lo, meta_hi, tmins, hit_mask);
+  const uint32_t b0 = meta_lo & 0xFFu;
+  const int ni = (b0 & 0x80u) ? (int)min(b0 & 0xFu, 8u) : 0;
+  const uint32_t inner_bits = (1u << ni) - 1u;
+  uint32_t leaf_mask = hit_mask & ~inner_bits;
+  const uint32_t inner_hits = hit_mask & inner_bits;
+  // leaves of this node first: they tighten t_best before descending
+  while (leaf_mask) {
+    const int k = __ffs(leaf_mask) - 1;
+    leaf_mask &= leaf_mask - 1;
+    const uint32_t m = ((k < 4 ? meta_lo : meta_hi) >> (8 * (k & 3))) & 0xFFu;
+    if (m == kMetaEmpty) continue;
+    const int32_t start = tri_base + (int32_t)(m >> 2);
+    const int32_t cnt = (int32_t)(m & 3u) + 1;
+    if (start < 0 || start + cnt > a.n_tris) {
+      atomicOr(status, kStatusBadIndex);
+      failed = true;
+      return -1;
+    }
+    for (int32_t x = 0; x < cnt; ++x)
+      test_triangle<kChannels>(r, a.tris, start + x, t_best, best_id, best_seg, best_k);
+    if (kCount) n_tris += cnt;
+  }
+  const int n_inner = __popc(inner_hits);
+  if (n_inner == 1) return child_base + (__ffs(inner_hits) - 1);  // the common case: no ordering needed
+  if (n_inner == 2) {
+    // two children: the nearer is taken, the farther pushed (keys: tmin bits, slot in the low 3 bits)
+    uint32_t kmin = 0xFFFFFFFFu, kx = 0u;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t key = (__float_as_uint(tmins[k]) & ~7u) | (uint32_t)k;
+      const bool v = (inner_hits >> k) & 1u;
+      kmin = v ? min(kmin, key) : kmin;
+      kx ^= v ? key : 0u;
+    }
+    const uint32_t kfar = kx ^ kmin;
+    const uint32_t key_cull = __float_as_uint(t_best * kCullSlack);
+    if ((kfar & ~7u) <= key_cull) {
+      if (sp >= kStackSize) {
+        atomicOr(status, kStatusStackOverflow);
+        failed = true;
+        return -1;
+      }
+      stack[sp++] = make_int2(child_base + (int32_t)(kfar & 7u), (int32_t)(kfar & ~7u));
+    }
+    if ((kmin & ~7u) <= key_cull) return child_base + (int32_t)(kmin & 7u);
+  } else if (n_inner > 1) {
+    // nearest first (sorting network on keys: tmin bits with the slot in the low 3 bits)
+    uint32_t keys[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      keys[k] = ((inner_hits >> k) & 1u) ? ((__float_as_uint(tmins[k]) & ~7u) | (uint32_t)k) : 0xFFFFFFFFu;
+#define AGS_CSWAP(i, j)                         \
+  {                                             \
+  const uint32_t lo_ = min(keys[i], keys[j]); \
+  const uint32_t hi_ = max(keys[i], keys[j]); \
+  keys[i] = lo_;                              \
+  keys[j] = hi_;                              \
+  }
+    AGS_CSWAP(0, 1) AGS_CSWAP(2, 3) AGS_CSWAP(4, 5) AGS_CSWAP(6, 7)
+    AGS_CSWAP(0, 2) AGS_CSWAP(1, 3) AGS_CSWAP(4, 6) AGS_CSWAP(5, 7)
+    AGS_CSWAP(1, 2) AGS_CSWAP(5, 6) AGS_CSWAP(0, 4) AGS_CSWAP(3, 7)
+    AGS_CSWAP(1, 5) AGS_CSWAP(2, 6)
+    AGS_CSWAP(1, 4) AGS_CSWAP(3, 6)
+    AGS_CSWAP(2, 4) AGS_CSWAP(3, 5)
+    AGS_CSWAP(3, 4)
+#undef AGS_CSWAP
+    const uint32_t key_cull = __float_as_uint(t_best * kCullSlack);
+#pragma unroll
+    for (int k = 7; k >= 1; --k) {
+      if (keys[k] != 0xFFFFFFFFu && (keys[k] & ~7u) <= key_cull) {
+        if (sp >= kStackSize) {
+          atomicOr(status, kStatusStackOverflow);
+          failed = true;
+        } else {
+          stack[sp++] = make_int2(child_base + (int32_t)(keys[k] & 7u), (int32_t)(keys[k] & ~7u));
+        }
+      }
+    }
+    if (failed) return -1;
+    if ((keys[0] & ~7u) <= key_cull) return child_base + (int32_t)(keys[0] & 7u);
+  }
+  const float t_pop = t_best * kCullSlack;
+  while (sp > 0) {
+    const int2 e = stack[--sp];
+    if (__int_as_float(e.y) <= t_pop) return e.x;
+  }
+  return -1;
+}
+
+// The rotation R(q) (rows R[0..8]) of the sensor pose P = (p, q), q
+// normalised. Every operation is explicitly rounded, so the compiler has no
+// freedom to fuse a multiply and an add differently in different kernels:
+// every kernel variant casts exactly the same rays. False for a pose the
+// method cannot use (q near zero, or anything non-finite).
+__device__ __forceinline__ bool pose_rotation(const float* P, float* R) {
+  const float px = __ldg(P), py = __ldg(P + 1), pz = __ldg(P + 2);
+  const float qx = __ldg(P + 3), qy = __ldg(P + 4), qz = __ldg(P + 5), qw = __ldg(P + 6);
+  const float n2 = __fmaf_rn(qw, qw, __fmaf_rn(qz, qz, __fmaf_rn(qy, qy, __fmul_rn(qx, qx))));
+  if (!(n2 >= 1e-30f) || !isfinite(n2) || !isfinite(__fadd_rn(__fadd_rn(px, py), pz))) return false;
+  const float s = __fdiv_rn(2.0f, n2);
+  const float xx = __fmul_rn(qx, qx), yy = __fmul_rn(qy, qy), zz = __fmul_rn(qz, qz);
+  R[0] = __fmaf_rn(-s, __fadd_rn(yy, zz), 1.0f);
+  R[4] = __fmaf_rn(-s, __fadd_rn(xx, zz), 1.0f);
+  R[8] = __fmaf_rn(-s, __fadd_rn(xx, yy), 1.0f);
+  R[1] = __fmul_rn(s, __fmaf_rn(qx, qy, -__fmul_rn(qz, qw)));
+  R[3] = __fmul_rn(s, __fmaf_rn(qx, qy, __fmul_rn(qz, qw)));
+  R[2] = __fmul_rn(s, __fmaf_rn(qx, qz, __fmul_rn(qy, qw)));
+  R[6] = __fmul_rn(s, __fmaf_rn(qx, qz, -__fmul_rn(qy, qw)));
+  R[5] = __fmul_rn(s, __fmaf_rn(qy, qz, -__fmul_rn(qx, qw)));
+  R[7] = __fmul_rn(s, __fmaf_rn(qy, qz, __fmul_rn(qx, qw)));
+  return true;
+}
+
+// R l for sensor-frame l, explicitly rounded.
+__device__ __forceinline__ void rotate(const float* R, float lx, float ly, float lz, float& dx, float& dy,
+                                       float& dz) {
+  dx = __fmaf_rn(R[2], lz, __fmaf_rn(R[1], ly, __fmul_rn(R[0], lx)));
+  dy = __fmaf_rn(R[5], lz, __fmaf_rn(R[4], ly, __fmul_rn(R[3], lx)));
+  dz = __fmaf_rn(R[8], lz, __fmaf_rn(R[7], ly, __fmul_rn(R[6], lx)));
+}
+
+// a3: the world ray of pixel / beam (row, col) from the sensor pose P =
+// (p, q): origin p, direction R(q) l with l the sensor-frame direction, and
+// R itself. False for a pose or table row the method cannot use. The same
+// bits whether l comes from the camera model (lx = 1 folded) or a table.
+template <bool kTable>
+__device__ __forceinline__ bool make_ray(const SensorParams& sen, const float* P, int32_t row, int32_t col, Ray& r,
+                                         float* R, float& lx, float& ly, float& lz) {
+  if (!pose_rotation(P, R)) return false;
+  sensor_dir<kTable>(sen, row, col, lx, ly, lz);
+  if (kTable && (!isfinite(lx + ly + lz) || (lx == 0.0f && ly == 0.0f && lz == 0.0f))) return false;
+  r.ox = __ldg(P);
+  r.oy = __ldg(P + 1);
+  r.oz = __ldg(P + 2);
+  float dx, dy, dz;
+  rotate(R, lx, ly, lz, dx, dy, dz);
+  setup_ray(r, dx, dy, dz);
+  return true;
+}
+
+// a6: the reported value and segment of a finished ray (failed: NaN, -1).
+__device__ __forceinline__ void resolve_hit(const SensorParams& sen, bool failed, float t_best, int32_t best_id,
+                                            int32_t best_seg, float& v, int32_t& seg) {
+  if (failed) {
+    v = __int_as_float(0x7fc00000);
+    seg = -1;
+  } else if (best_id != 0x7fffffff) {
+    v = t_best;
+    seg = best_seg;
+    if (v < sen.min_range) {
+      if (sen.near_mode == AGS_NEAR_CLAMP) {
+        v = sen.min_range;
+      } else {
+        v = sen.max_range;
+        seg = -1;
+      }
+    }
+  } else {
+    v = sen.max_range;
+    seg = -1;
+  }
 }
 
 template <bool kCount, int kTileW, int kRaysPerLane, bool kSlots, int kFmt, int kExtra>
@@ -468,44 +649,18 @@ __device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParam
   // ---- a3: ray generation from the sensor pose (p, q); recomputed per ray
   // (L1-resident) so that nothing of it stays live during the traversal
   const float* P = slot_pose<kSlots>(a, slot);
-  const float px = __ldg(P), py = __ldg(P + 1), pz = __ldg(P + 2);
-  const float qx = __ldg(P + 3), qy = __ldg(P + 4), qz = __ldg(P + 5), qw = __ldg(P + 6);
-  const float n2 = qx * qx + qy * qy + qz * qz + qw * qw;
-  if (!(n2 >= 1e-30f) || !isfinite(n2) || !isfinite(px + py + pz)) {
-    // a pose the method cannot use: flag it and report NaN for this ray
-    atomicOr(status, kStatusBadPose);
-    if (!kCount) {
-      const int64_t o = slot_out<kSlots>(a, sen, slot) + (int64_t)row * W + col;
-      a.out_depth[o] = __int_as_float(0x7fc00000);
-      a.out_seg[o] = -1;
-    }
-    continue;
-  }
-  const float s = 2.0f / n2;
-  const float R00 = 1.0f - s * (qy * qy + qz * qz), R01 = s * (qx * qy - qz * qw), R02 = s * (qx * qz + qy * qw);
-  const float R10 = s * (qx * qy + qz * qw), R11 = 1.0f - s * (qx * qx + qz * qz), R12 = s * (qy * qz - qx * qw);
-  const float R20 = s * (qx * qz - qy * qw), R21 = s * (qy * qz + qx * qw), R22 = 1.0f - s * (qx * qx + qy * qy);
-  float lx, ly, lz;
-  sensor_dir<(kExtra & kExtraTable) != 0>(sen, row, col, lx, ly, lz);
-  if ((kExtra & kExtraTable) != 0 && (!isfinite(lx + ly + lz) || (lx == 0.0f && ly == 0.0f && lz == 0.0f))) {
-    // a table row the method cannot cast: flagged like an unusable pose
-    atomicOr(status, kStatusBadPose);
-    if (!kCount) {
-      const int64_t o = slot_out<kSlots>(a, sen, slot) + (int64_t)row * W + col;
-      a.out_depth[o] = __int_as_float(0x7fc00000);
-      a.out_seg[o] = -1;
-    }
-    continue;
-  }
   Ray r;
-  r.ox = px;
-  r.oy = py;
-  r.oz = pz;
-  // world direction R l with explicitly rounded operations: the same bits
-  // whether l comes from the camera model (lx = 1 folded) or from a table
-  setup_ray(r, __fmaf_rn(R02, lz, __fmaf_rn(R01, ly, __fmul_rn(R00, lx))),
-            __fmaf_rn(R12, lz, __fmaf_rn(R11, ly, __fmul_rn(R10, lx))),
-            __fmaf_rn(R22, lz, __fmaf_rn(R21, ly, __fmul_rn(R20, lx))));
+  float R[9], lx, ly, lz;
+  if (!make_ray<(kExtra & kExtraTable) != 0>(sen, P, row, col, r, R, lx, ly, lz)) {
+    // a pose (or table row) the method cannot use: flag it and report NaN for this ray
+    atomicOr(status, kStatusBadPose);
+    if (!kCount) {
+      const int64_t o = slot_out<kSlots>(a, sen, slot) + (int64_t)row * W + col;
+      a.out_depth[o] = __int_as_float(0x7fc00000);
+      a.out_seg[o] = -1;
+    }
+    continue;
+  }
 
   // ---- a4-a6: traversal, triangle tests, nearest hit
   float t_best = sen.max_range;  // camera: depth limit; LiDAR: range limit (unit direction)
@@ -525,112 +680,9 @@ __device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParam
       break;
     }
     if (kCount) ++n_nodes;
-    const float t_cull = t_best * kCullSlack;
-    int32_t child_base, tri_base;
-    uint32_t meta_lo, meta_hi;
-    float tmins[8];
-    uint32_t hit_mask;
-    test_node<kFmt>(a.nodes, node, r, t_cull, child_base, tri_base, meta_lo, meta_hi, tmins, hit_mask);
-    const uint32_t b0 = meta_lo & 0xFFu;
-    const int ni = (b0 & 0x80u) ? (int)min(b0 & 0xFu, 8u) : 0;
-    const uint32_t inner_bits = (1u << ni) - 1u;
-    uint32_t leaf_mask = hit_mask & ~inner_bits;
-    const uint32_t inner_hits = hit_mask & inner_bits;
-    // leaves of this node first: they tighten t_best before descending
-    while (leaf_mask) {
-      const int k = __ffs(leaf_mask) - 1;
-      leaf_mask &= leaf_mask - 1;
-      const uint32_t m = ((k < 4 ? meta_lo : meta_hi) >> (8 * (k & 3))) & 0xFFu;
-      if (m == kMetaEmpty) continue;
-      const int32_t start = tri_base + (int32_t)(m >> 2);
-      const int32_t cnt = (int32_t)(m & 3u) + 1;
-      if (start < 0 || start + cnt > a.n_tris) {
-        atomicOr(status, kStatusBadIndex);
-        failed = true;
-        break;
-      }
-      for (int32_t x = 0; x < cnt; ++x)
-        test_triangle<(kExtra & kExtraChannels) != 0>(r, a.tris, start + x, t_best, best_id, best_seg, best_k);
-      if (kCount) n_tris += cnt;
-    }
+    node = visit_node<kCount, kFmt, (kExtra & kExtraChannels) != 0>(a, r, node, t_best, best_id, best_seg, best_k,
+                                                                    stack, sp, failed, n_tris);
     if (failed) break;
-    const int n_inner = __popc(inner_hits);
-    if (n_inner == 1) {  // the common case: no ordering needed
-      node = child_base + (__ffs(inner_hits) - 1);
-      continue;
-    }
-    if (n_inner == 2) {
-      // two children: the nearer is taken, the farther pushed (keys: tmin bits, slot in the low 3 bits)
-      uint32_t kmin = 0xFFFFFFFFu, kx = 0u;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const uint32_t key = (__float_as_uint(tmins[k]) & ~7u) | (uint32_t)k;
-        const bool v = (inner_hits >> k) & 1u;
-        kmin = v ? min(kmin, key) : kmin;
-        kx ^= v ? key : 0u;
-      }
-      const uint32_t kfar = kx ^ kmin;
-      const uint32_t key_cull = __float_as_uint(t_best * kCullSlack);
-      if ((kfar & ~7u) <= key_cull) {
-        if (sp >= kStackSize) {
-          atomicOr(status, kStatusStackOverflow);
-          failed = true;
-          break;
-        }
-        stack[sp++] = make_int2(child_base + (int32_t)(kfar & 7u), (int32_t)(kfar & ~7u));
-      }
-      if ((kmin & ~7u) <= key_cull) {
-        node = child_base + (int32_t)(kmin & 7u);
-        continue;
-      }
-    } else if (n_inner > 1) {
-      // nearest first (sorting network on keys: tmin bits with the slot in the low 3 bits)
-      uint32_t keys[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k)
-        keys[k] = ((inner_hits >> k) & 1u) ? ((__float_as_uint(tmins[k]) & ~7u) | (uint32_t)k) : 0xFFFFFFFFu;
-#define AGS_CSWAP(i, j)                         \
-  {                                             \
-  const uint32_t lo_ = min(keys[i], keys[j]); \
-  const uint32_t hi_ = max(keys[i], keys[j]); \
-  keys[i] = lo_;                              \
-  keys[j] = hi_;                              \
-  }
-      AGS_CSWAP(0, 1) AGS_CSWAP(2, 3) AGS_CSWAP(4, 5) AGS_CSWAP(6, 7)
-      AGS_CSWAP(0, 2) AGS_CSWAP(1, 3) AGS_CSWAP(4, 6) AGS_CSWAP(5, 7)
-      AGS_CSWAP(1, 2) AGS_CSWAP(5, 6) AGS_CSWAP(0, 4) AGS_CSWAP(3, 7)
-      AGS_CSWAP(1, 5) AGS_CSWAP(2, 6)
-      AGS_CSWAP(1, 4) AGS_CSWAP(3, 6)
-      AGS_CSWAP(2, 4) AGS_CSWAP(3, 5)
-      AGS_CSWAP(3, 4)
-#undef AGS_CSWAP
-      const uint32_t key_cull = __float_as_uint(t_best * kCullSlack);
-#pragma unroll
-      for (int k = 7; k >= 1; --k) {
-        if (keys[k] != 0xFFFFFFFFu && (keys[k] & ~7u) <= key_cull) {
-          if (sp >= kStackSize) {
-            atomicOr(status, kStatusStackOverflow);
-            failed = true;
-          } else {
-            stack[sp++] = make_int2(child_base + (int32_t)(keys[k] & 7u), (int32_t)(keys[k] & ~7u));
-          }
-        }
-      }
-      if (failed) break;
-      if ((keys[0] & ~7u) <= key_cull) {
-        node = child_base + (int32_t)(keys[0] & 7u);
-        continue;
-      }
-    }
-    node = -1;
-    const float t_pop = t_best * kCullSlack;
-    while (sp > 0) {
-      const int2 e = stack[--sp];
-      if (__int_as_float(e.y) <= t_pop) {
-        node = e.x;
-        break;
-      }
-    }
   }
 
   if (kCount) {
@@ -639,39 +691,21 @@ __device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParam
   }
   float v;
   int32_t seg;
-  if (failed) {
-    v = __int_as_float(0x7fc00000);
-    seg = -1;
-  } else if (best_id != 0x7fffffff) {
-    v = t_best;
-    seg = best_seg;
-    if (v < sen.min_range) {
-      if (sen.near_mode == AGS_NEAR_CLAMP) {
-        v = sen.min_range;
-      } else {
-        v = sen.max_range;
-        seg = -1;
-      }
-    }
-  } else {
-    v = sen.max_range;
-    seg = -1;
-  }
+  resolve_hit(sen, failed, t_best, best_id, best_seg, v, seg);
   if constexpr ((kExtra & kExtraShadow) != 0) {
     if (!failed && seg >= 0) {
       // the hit point P and the second sensor o2 = p + R b, both in the world
       float sx, sy, sz;
       sensor_dir<(kExtra & kExtraTable) != 0>(sen, row, col, sx, sy, sz);
-      const float dwx = __fmaf_rn(R02, sz, __fmaf_rn(R01, sy, __fmul_rn(R00, sx))),
-                  dwy = __fmaf_rn(R12, sz, __fmaf_rn(R11, sy, __fmul_rn(R10, sx))),
-                  dwz = __fmaf_rn(R22, sz, __fmaf_rn(R21, sy, __fmul_rn(R20, sx)));
-      const float Px = px + t_best * dwx, Py = py + t_best * dwy, Pz = pz + t_best * dwz;
-      const float bx = a.baseline[0], by = a.baseline[1], bz = a.baseline[2];
-      const float o2x = px + (R00 * bx + R01 * by + R02 * bz), o2y = py + (R10 * bx + R11 * by + R12 * bz),
-                  o2z = pz + (R20 * bx + R21 * by + R22 * bz);
+      float dwx, dwy, dwz, bwx, bwy, bwz;
+      rotate(R, sx, sy, sz, dwx, dwy, dwz);
+      rotate(R, a.baseline[0], a.baseline[1], a.baseline[2], bwx, bwy, bwz);
+      const float px = r.ox, py = r.oy, pz = r.oz;
+      const float Px = __fmaf_rn(t_best, dwx, px), Py = __fmaf_rn(t_best, dwy, py), Pz = __fmaf_rn(t_best, dwz, pz);
+      const float o2x = __fadd_rn(px, bwx), o2y = __fadd_rn(py, bwy), o2z = __fadd_rn(pz, bwz);
       bool sfail = false;
-      const bool shadowed = occluded<kFmt>(a, env, o2x, o2y, o2z, Px - o2x, Py - o2y, Pz - o2z, 0.0f,
-                                           1.0f - a.shadow_eps, stack, sfail);
+      const bool shadowed = occluded<kFmt>(a, env, o2x, o2y, o2z, __fsub_rn(Px, o2x), __fsub_rn(Py, o2y),
+                                           __fsub_rn(Pz, o2z), 0.0f, __fsub_rn(1.0f, a.shadow_eps), stack, sfail);
       if (sfail) {
         failed = true;
         v = __int_as_float(0x7fc00000);
@@ -708,9 +742,9 @@ __device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParam
     if (a.out_point) {
       // the hit in the sensor frame: reported value along the sensor-frame direction
       sensor_dir<(kExtra & kExtraTable) != 0>(sen, row, col, lx, ly, lz);
-      a.out_point[3 * o] = v * lx;
-      a.out_point[3 * o + 1] = v * ly;
-      a.out_point[3 * o + 2] = v * lz;
+      a.out_point[3 * o] = __fmul_rn(v, lx);
+      a.out_point[3 * o + 1] = __fmul_rn(v, ly);
+      a.out_point[3 * o + 2] = __fmul_rn(v, lz);
     }
   }
   }  // rays of this lane in the tile
@@ -946,25 +980,18 @@ __device__ __forceinline__ void trace_tile_inst(const TraceArgs& a, const Sensor
   const int32_t W = sen.W, H = sen.H;
   if (col >= W || row >= H) return;
   const float* P = a.poses + 7 * (int64_t)slot;
-  const float px = __ldg(P), py = __ldg(P + 1), pz = __ldg(P + 2);
-  const float qx = __ldg(P + 3), qy = __ldg(P + 4), qz = __ldg(P + 5), qw = __ldg(P + 6);
   const int64_t o = (int64_t)slot * H * W + (int64_t)row * W + col;
-  const float n2 = qx * qx + qy * qy + qz * qz + qw * qw;
-  if (!(n2 >= 1e-30f) || !isfinite(n2) || !isfinite(px + py + pz)) {
+  float R[9];
+  if (!pose_rotation(P, R)) {
     atomicOr(a.status, kStatusBadPose);
     a.out_depth[o] = __int_as_float(0x7fc00000);
     a.out_seg[o] = -1;
     return;
   }
-  const float s = 2.0f / n2;
-  const float R00 = 1.0f - s * (qy * qy + qz * qz), R01 = s * (qx * qy - qz * qw), R02 = s * (qx * qz + qy * qw);
-  const float R10 = s * (qx * qy + qz * qw), R11 = 1.0f - s * (qx * qx + qz * qz), R12 = s * (qy * qz - qx * qw);
-  const float R20 = s * (qx * qz - qy * qw), R21 = s * (qy * qz + qx * qw), R22 = 1.0f - s * (qx * qx + qy * qy);
-  float lx, ly, lz;
+  const float px = __ldg(P), py = __ldg(P + 1), pz = __ldg(P + 2);
+  float lx, ly, lz, dx, dy, dz;
   sensor_dir<false>(sen, row, col, lx, ly, lz);
-  const float dx = __fmaf_rn(R02, lz, __fmaf_rn(R01, ly, __fmul_rn(R00, lx)));
-  const float dy = __fmaf_rn(R12, lz, __fmaf_rn(R11, ly, __fmul_rn(R10, lx)));
-  const float dz = __fmaf_rn(R22, lz, __fmaf_rn(R21, ly, __fmul_rn(R20, lx)));
+  rotate(R, lx, ly, lz, dx, dy, dz);
   Ray r;
   r.ox = px;
   r.oy = py;

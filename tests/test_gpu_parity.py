@@ -359,12 +359,22 @@ def test_launch_shapes_and_autotune_keep_results(ctx):
     scene = ags.ags_scene_build(ctx, batch)
     try:
         ref = render(ctx, scene, spec, poses[0])
-        for w, rpl, b in [(8, 1, 0), (4, 1, 0), (8, 2, 1), (16, 2, 0), (16, 4, 2)]:
+        for w, rpl, b in [(8, 1, 0), (4, 1, 0), (8, 2, 1), (16, 2, 0), (16, 4, 2), (16, 1, 0), (32, 1, 3)]:
             ags.ags_set_launch_config(ctx, scene, spec, w, rpl, b)
-            assert ags.ags_get_launch_config(ctx, scene, spec)["tile_w"] == w
+            cfg = ags.ags_get_launch_config(ctx, scene, spec)
+            assert cfg["tile_w"] == w and cfg["rays_per_lane"] == rpl and cfg["blocks_per_sm"] == b
             out = render(ctx, scene, spec, poses[0])
             assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1]), (w, rpl, b)
-        for bad in [(3, 1, 0), (8, 3, 0), (64, 1, 0), (32, 1, 0), (8, 1, 10_000)]:
+            # a subset of the environments, in another order, through the same launch shape
+            ids = torch.tensor([3, 0, 4], dtype=torch.int32, device="cuda")
+            p = torch.as_tensor(poses[0][[3, 0, 4]]).cuda()
+            d = torch.empty((3, 45, 70), device="cuda")
+            sg = torch.empty((3, 45, 70), dtype=torch.int32, device="cuda")
+            ags.ags_render_envs(ctx, scene, spec, ids, p, d, sg)
+            ags.ags_stream_status(ctx)
+            assert np.array_equal(d.cpu().numpy(), ref[0][[3, 0, 4]]) and np.array_equal(sg.cpu().numpy(),
+                                                                                        ref[1][[3, 0, 4]])
+        for bad in [(3, 1, 0), (8, 3, 0), (64, 1, 0), (32, 2, 0), (8, 1, 10_000), (8, 1, -1)]:
             with pytest.raises(ags.AgsError):
                 ags.ags_set_launch_config(ctx, scene, spec, *bad)
         ags.ags_set_launch_config(ctx, scene, spec, None)
@@ -393,7 +403,7 @@ def test_compressed_nodes_bit_exact_on_lidar_forest_and_launch_shapes(ctx, fmt):
     try:
         assert ags.ags_scene_node_bytes(scene) == (128 if fmt == "fp16" else 80)
         ref = render(ctx, ref_scene, spec, poses[0])
-        for w, rpl in [(8, 1), (4, 1), (8, 2), (16, 2), (16, 4)]:
+        for w, rpl in [(8, 1), (4, 1), (8, 2), (16, 2), (16, 4), (16, 1), (32, 1)]:
             ags.ags_set_launch_config(ctx, scene, spec, w, rpl, 0)
             out = render(ctx, scene, spec, poses[0])
             assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1]), (w, rpl)
