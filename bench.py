@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--build-flags", type=int, default=0, help="ags_scene_build flags")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape")
     ap.add_argument("--no-serving", action="store_true", help="skip the served-latency measurement")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="Poisson arrivals per load in --workload serving (seconds)")
+    ap.add_argument("--no-sub-records", action="store_true",
+                    help="skip the forest and node-format records of the default line")
     args = ap.parse_args()
     if args.envs is None:
         args.envs = WORKLOADS[args.workload]["envs"]
@@ -126,8 +130,50 @@ def clocks_rejected(c) -> bool:
     return bool(sm and mx and sm < 0.85 * mx and not c.get("reasons"))
 
 
-# instruction issue limit of one GB300: 152 SMs x 4 schedulers x 1 warp instruction per cycle x 2.07 GHz
-ISSUE_PEAK_G = 152 * 4 * 2.07
+def issue_peak_g(sm_count: int, sm_max_mhz: float) -> float:
+    """Warp-instruction issue limit of the device in G/s: every SM has 4 schedulers, each issuing at most one
+    warp instruction per cycle, at the maximum SM clock."""
+    return sm_count * 4 * sm_max_mhz / 1e3
+
+
+def sm_max_mhz(clocks) -> float:
+    """The maximum SM clock: as sampled by nvidia-smi during the run, else the measured peaks file."""
+    if clocks and clocks.get("sm_max_mhz"):
+        return float(clocks["sm_max_mhz"])
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["sm_max_mhz"])
+    except Exception:
+        return 2070.0
+
+
+def rooflines(counters, ms_step, b_ray, rays, hbm, peak_kind, sm_count, mhz, nodes_per_ray, tris_per_ray,
+              node_bytes):
+    """The lead roofline of the render kernel and the algorithmic-bytes one beside it.
+
+    The BVHs and triangles of an environment stay in L1/L2 while all SMs work on it, so what bounds the kernel
+    is instruction issue, not DRAM: the lead block is the issue roofline (warp instructions per launch from the
+    committed ncu capture of this kernel and these sources, per second, against SMs x 4 x max clock), with the
+    DRAM traffic of that capture beside it. The algorithmic block is the survey's B_ray roofline: nodes and
+    triangles a ray fetches, per second, against the HBM copy bandwidth; it exceeds 1 because those bytes are
+    served mostly from L1/L2."""
+    algo_gbs = b_ray * rays / (ms_step * 1e-3) / 1e9
+    algorithmic = {"bound": "hbm", "achieved": algo_gbs, "peak": hbm, "unit": "GB/s", "frac": algo_gbs / hbm,
+                   "peak_kind": peak_kind + " hbm_gbs (copy)",
+                   "achieved_is": "algorithmic bytes served (node and triangle fetches per ray, mostly from L1/L2)",
+                   "bytes_per_ray": b_ray, "nodes_per_ray": nodes_per_ray, "tris_per_ray": tris_per_ray,
+                   "node_bytes": node_bytes}
+    peak_g = issue_peak_g(sm_count, mhz)
+    if counters is None:
+        return dict(algorithmic, traffic=None, kernel="k_trace"), None
+    dram_gbs = counters[0] / (ms_step * 1e-3) / 1e9
+    achieved = counters[1] / (ms_step * 1e-3) / 1e9
+    lead = {"bound": "alu", "achieved": achieved, "peak": peak_g, "unit": "G warp instructions/s",
+            "frac": achieved / peak_g, "traffic": counters[0], "kernel": "k_trace",
+            "peak_kind": f"{sm_count} SMs x 4 schedulers x 1 warp instruction/cycle x {mhz:.0f} MHz (max SM clock)",
+            "instructions_per_launch": counters[1], "dram_gbs": dram_gbs, "dram_frac": dram_gbs / hbm,
+            "dram_peak_kind": peak_kind + " hbm_gbs (copy)", "algorithmic": algorithmic}
+    return lead, algorithmic
 
 
 class ClockSampler:
@@ -229,9 +275,10 @@ def serving_specs():
 
 
 def serving_measure(ags, ctx, scene, n_envs, poses_step, specs, loads=(0.5, 1.0), duration=0.5, seq_max=2000,
-                    burst=20000, seed=5):
+                    burst=20000, seed=5, use_graph=True, sequential=True):
     """Continuous-batching server under a burst (capacity) and Poisson arrivals at fractions of it, and the
-    sequential one-request-at-a-time launch on the same traces (first seq_max requests)."""
+    sequential one-request-at-a-time launch on the same traces (first seq_max requests). use_graph: each
+    stream replays its captured batch graph (else three calls per batch)."""
     rng = np.random.default_rng(seed)
     rays = np.array([sp.width * sp.height for sp in specs])
 
@@ -245,7 +292,8 @@ def serving_measure(ags, ctx, scene, n_envs, poses_step, specs, loads=(0.5, 1.0)
     def pct(x, q):
         return float(np.percentile(x, q)) if len(x) else None
 
-    server = ags.ags_server_create(ctx, scene, specs, max_slots=512, max_inflight=4, arena_bytes=4 << 30)
+    server = ags.ags_server_create(ctx, scene, specs, max_slots=512, max_inflight=4, arena_bytes=4 << 30,
+                                   use_graph=use_graph)
     try:
         reqs, arr = trace(burst, None)
         out = ags.ags_server_replay(server, reqs, arr)
@@ -253,7 +301,8 @@ def serving_measure(ags, ctx, scene, n_envs, poses_step, specs, loads=(0.5, 1.0)
         cap = burst / span
         res = {"capacity_req_per_s": cap, "capacity_mrays_per_s": float(rays[reqs["spec"]].sum()) / span / 1e6,
                "sensors": [f"{'camera' if sp.type == 0 else 'lidar'} {sp.height}x{sp.width}" for sp in specs],
-               "max_slots": 512, "max_inflight": 4, "loads": []}
+               "max_slots": 512, "max_inflight": 4, "use_graph": use_graph, "seconds_per_load": duration,
+               "loads": []}
         for f in loads:
             rate = f * cap
             n = max(100, int(rate * duration))
@@ -261,8 +310,10 @@ def serving_measure(ags, ctx, scene, n_envs, poses_step, specs, loads=(0.5, 1.0)
             out = ags.ags_server_replay(server, reqs, arr)
             lat = (out["t_done"] - out["t_submit"]) * 1e3
             m = min(seq_max, n)
-            seq = ags.ags_replay_sequential(ctx, scene, specs, reqs[:m], arr[:m])
-            slat = (seq["t_done"] - seq["t_submit"]) * 1e3
+            slat = np.zeros(0)
+            if sequential:
+                seq = ags.ags_replay_sequential(ctx, scene, specs, reqs[:m], arr[:m])
+                slat = (seq["t_done"] - seq["t_submit"]) * 1e3
             by_sensor = [{"sensor": res["sensors"][k], "requests": int((reqs["spec"] == k).sum()),
                           "p50_ms": pct(lat[reqs["spec"] == k], 50), "p99_ms": pct(lat[reqs["spec"] == k], 99)}
                          for k in range(len(specs))]
@@ -270,7 +321,10 @@ def serving_measure(ags, ctx, scene, n_envs, poses_step, specs, loads=(0.5, 1.0)
                                  "p99_ms": pct(lat, 99), "mrays_per_s": float(rays[reqs["spec"]].sum()) /
                                  float(out["t_done"].max() - out["t_submit"].min()) / 1e6,
                                  "by_sensor": by_sensor,
-                                 "sequential": {"requests": m, "p50_ms": pct(slat, 50), "p99_ms": pct(slat, 99)}})
+                                 "sequential": {"requests": int(slat.shape[0]), "p50_ms": pct(slat, 50),
+                                                "p99_ms": pct(slat, 99)}})
+        if not sequential:
+            return res
         # a load the sequential launch can sustain: half its own capacity, same trace for both
         reqs, arr = trace(300, None)
         seq = ags.ags_replay_sequential(ctx, scene, specs, reqs, arr)
@@ -312,7 +366,9 @@ def bench_serving(args, rank, world, local):
     specs = serving_specs()
     with ClockSampler(torch.cuda.current_device()) as clk:
         res = serving_measure(ags, ctx, scene, batch.n_envs, poses[0], specs,
-                              loads=(0.5, 0.75, 1.0, 1.25, 1.5), duration=1.0)
+                              loads=(0.5, 0.75, 1.0, 1.25, 1.5), duration=args.serve_seconds)
+        res["without_graph"] = serving_measure(ags, ctx, scene, batch.n_envs, poses[0], specs, loads=(0.5, 1.0),
+                                               duration=args.serve_seconds, use_graph=False, sequential=False)
     line = {"metric": WORKLOADS["serving"]["metric"], "value": res["capacity_mrays_per_s"], "unit": UNIT,
             "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"serving: {batch.n_envs} rooms, triangles log-uniform 1k-200k "
@@ -587,6 +643,131 @@ def bench_features(args, rank, world, local):
     ags.ags_context_destroy(ctx)
 
 
+# ---------------------------------------------------------------- sub-records of the default line
+def timed_renders(ags, ctx, scene, spec, poses_d, depth, seg, stream, steps, warmup):
+    """ms per render over `steps` renders after `warmup`, CUDA events on the render stream, clocks sampled."""
+    import torch
+    walk = poses_d.shape[0]
+    for i in range(warmup):
+        ags.ags_render(ctx, scene, spec, poses_d[i % walk], depth, seg, stream)
+    st, en = torch.cuda.Event(True), torch.cuda.Event(True)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        st.record(stream)
+        for i in range(steps):
+            ags.ags_render(ctx, scene, spec, poses_d[(warmup + i) % walk], depth, seg, stream)
+        en.record(stream)
+        torch.cuda.synchronize()
+    ags.ags_stream_status(ctx, stream)
+    return st.elapsed_time(en) / steps, clk.summary()
+
+
+def forest_record(ags, ctx, dev, stream, steps, warmup, envs=64, cells=64, check_rays=256):
+    """A bounded run of the LiDAR-forest workload: 64 forests (50-200 trees of 2k-10k triangles), the 64x512
+    LiDAR, references split at a fixed 64 cells (the forest setting the build tuner keeps; no tuning here),
+    the default launch shape, and a sample of beams checked against the FP64 oracle."""
+    import torch
+
+    import oracle as O
+    from paper_2503_01471_gb300 import scenes as S
+    batch, spec, poses = S.lidar_forests(envs, steps=max(steps + warmup, 4))
+    t0 = time.perf_counter()
+    scene = ags.ags_scene_build(ctx, batch, ags.AGS_SPLIT_CELLS(cells))
+    build_s = time.perf_counter() - t0
+    try:
+        poses_d = torch.as_tensor(poses).to(dev)
+        E = batch.n_envs
+        depth = torch.empty((E, spec.height, spec.width), device=dev)
+        seg = torch.empty((E, spec.height, spec.width), dtype=torch.int32, device=dev)
+        ms, clocks = timed_renders(ags, ctx, scene, spec, poses_d, depth, seg, stream, steps, warmup)
+        r_c, n_c, t_c = ags.ags_render_count(ctx, scene, spec, poses_d[0])
+        ags.ags_render(ctx, scene, spec, poses_d[0], depth, seg, stream)
+        ags.ags_stream_status(ctx, stream)
+        d, g = depth.cpu().numpy(), seg.cpu().numpy()
+        s_or = O.Sensor(type=1, width=spec.width, height=spec.height, hfov=float(np.float32(spec.hfov)),
+                        min_range=float(np.float32(spec.min_range)), max_range=float(np.float32(spec.max_range)),
+                        vfov_min=float(np.float32(spec.vfov_min)), vfov_max=float(np.float32(spec.vfov_max)))
+        rng = np.random.default_rng(13)
+        n_ok = n_cnt = 0
+        for e in (0, E - 1):
+            vs, ix, ps, sg = batch.env_submeshes(e)
+            tris, tseg = O.world_triangles(vs, ix, ps, sg)
+            rr = np.sort(rng.choice(spec.width * spec.height, check_rays // 2, replace=False)).astype(np.int64)
+            res = O.render(tris, tseg, s_or, poses[0][e].astype(np.float64), rr)
+            ok, cnt = O.check(res, d[e].reshape(-1)[rr], g[e].reshape(-1)[rr], s_or.max_range)
+            if not ok.all():
+                raise RuntimeError(f"forest record: env {e}: {int((~ok).sum())} beams outside the oracle's outcomes")
+            n_ok += int(ok.sum())
+            n_cnt += int(cnt.sum())
+        rays = E * spec.width * spec.height
+        return {"workload": f"LiDAR forests, {E} envs (50-200 trees of 2k-10k triangles), 64x512 LiDAR, "
+                            f"references split at {cells} cells",
+                "mrays_per_s": rays / ms / 1e3, "ms_per_step": ms, "steps": steps, "warmup": warmup,
+                "tris": int(batch.env_tri_counts().sum()), "bvh_bytes": ags.ags_scene_stats(scene)[2],
+                "build_ms": build_s * 1e3, "nodes_per_ray": n_c / r_c, "tris_per_ray": t_c / r_c,
+                "bytes_per_ray": (n_c * ags.ags_scene_node_bytes(scene) + t_c * 48) / r_c + 8.0,
+                "launch_config": ags.ags_get_launch_config(ctx, scene, spec), "clocks": clocks,
+                "oracle_check": {"beams": n_ok, "counted": n_cnt, "envs": [0, E - 1],
+                                 "rule": "uncounted beams within 1e-5*d + 1e-6 m of the FP64 range, exact segment"}}
+    finally:
+        ags.ags_scene_destroy(scene)
+
+
+def precision_record(ags, ctx, dev, stream, batch, spec, poses, poses_d, steps, warmup, n_envs_checked=48,
+                     rays_per_env=256):
+    """Node formats on the benchmark's own scene: float32, float16 and 8-bit child bounds (rounded outward),
+    each timed at the benchmark's sensor shape and compared bit for bit with float32; and the depth error of
+    the (common) output against the FP64 oracle on a sample of rays."""
+    import torch
+
+    import oracle as O
+    E = batch.n_envs
+    depth = torch.empty((E, spec.height, spec.width), device=dev)
+    seg = torch.empty((E, spec.height, spec.width), dtype=torch.int32, device=dev)
+    out, ref = {}, None
+    for name, flag in (("fp32", 0), ("fp16", ags.AGS_BVH_FP16), ("q8", ags.AGS_BVH_Q8)):
+        scene = ags.ags_scene_build(ctx, batch, flag)
+        try:
+            ms, clocks = timed_renders(ags, ctx, scene, spec, poses_d, depth, seg, stream, steps, warmup)
+            ags.ags_render(ctx, scene, spec, poses_d[0], depth, seg, stream)
+            ags.ags_stream_status(ctx, stream)
+            o = (depth.cpu().numpy(), seg.cpu().numpy())
+            if ref is None:
+                ref = o
+            out[name] = {"mrays_per_s": E * spec.width * spec.height / ms / 1e3, "ms_per_step": ms,
+                         "node_bytes": ags.ags_scene_node_bytes(scene), "bvh_bytes": ags.ags_scene_stats(scene)[2],
+                         "bit_identical_to_fp32": bool(np.array_equal(o[0], ref[0]) and np.array_equal(o[1], ref[1])),
+                         "clocks_sm_mhz": clocks.get("sm_mhz")}
+        finally:
+            ags.ags_scene_destroy(scene)
+    s_or = O.Sensor(type=0, width=spec.width, height=spec.height, hfov=float(np.float32(spec.hfov)),
+                    min_range=float(np.float32(spec.min_range)), max_range=float(np.float32(spec.max_range)))
+    rng = np.random.default_rng(17)
+    abs_e, rel_e, n_s, counted = [], [], 0, 0
+    for e in rng.choice(E, min(E, n_envs_checked), replace=False):
+        vs, ix, ps, sg = batch.env_submeshes(int(e))
+        tris, tseg = O.world_triangles(vs, ix, ps, sg)
+        rr = np.sort(rng.choice(spec.width * spec.height, rays_per_env, replace=False)).astype(np.int64)
+        res = O.render(tris, tseg, s_or, poses[0][e].astype(np.float64), rr)
+        d = ref[0][e].reshape(-1)[rr].astype(np.float64)
+        g = ref[1][e].reshape(-1)[rr]
+        ok, cnt = O.check(res, d, g, s_or.max_range)
+        if not ok.all():
+            raise RuntimeError(f"precision record: env {e}: {int((~ok).sum())} rays outside the oracle's outcomes")
+        hit = (~cnt) & (res["seg"] >= 0)
+        abs_e.append(np.abs(d - res["v"])[hit])
+        rel_e.append((np.abs(d - res["v"]) / res["v"])[hit])
+        counted += int(cnt.sum())
+        n_s += rr.shape[0]
+    a, r = np.concatenate(abs_e), np.concatenate(rel_e)
+    return {"workload": f"the benchmark scene ({E} obstacle rooms, {spec.height}x{spec.width} camera) per node format",
+            "formats": out,
+            "depth_error_vs_fp64": {"sampled_rays": n_s, "single_outcome_hits": int(a.shape[0]), "counted": counted,
+                                    "max_abs_m": float(a.max()), "p999_abs_m": float(np.percentile(a, 99.9)),
+                                    "max_rel": float(r.max()), "p999_rel": float(np.percentile(r, 99.9)),
+                                    "tolerance": "1e-5*d + 1e-6 m (every uncounted ray within it)"}}
+
+
 # ---------------------------------------------------------------- workload
 def make_workload(args, rank, world=1):
     from paper_2503_01471_gb300 import scenes as S
@@ -790,13 +971,14 @@ def bench_ours(args, rank, world, local):
                   "api": "ags_render_graph_launch (tile-counter reset + k_trace captured once)"}
 
     hbm, peak_kind = peaks()
-    achieved_gbs = b_ray * rays_per_step / (ms_step * 1e-3) / 1e9
     workload = workload_name(args, spec, E)
     lc = ags.ags_get_launch_config(ctx, scene, spec)
     fmt = args.build_flags & 0xFF
     counters = profiled_counters(f"{args.workload}:{E}x{spec.height}x{spec.width}:cells{split_cells or 16}",
                                  f"k_trace<0, {lc['tile_w']}, {lc['rays_per_lane']}, 0, {fmt}, 0>")
-    traffic = counters[0] if counters else None
+    sm_count = ags.ags_context_device(ctx)["sm_count"]
+    lead, algorithmic = rooflines(counters, ms_step, b_ray, rays_per_step, hbm, peak_kind, sm_count,
+                                  sm_max_mhz(clocks), nodes_c / rays_c, tris_c / rays_c, node_b)
     line = {
         "metric": WORKLOADS[args.workload]["metric"], "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -809,16 +991,8 @@ def bench_ours(args, rank, world, local):
                    "bvh_bytes": ags.ags_scene_stats(scene)[2], "build_flags": args.build_flags,
                    "split_cells": split_cells or 16,
                    "parallelism": f"env-sharded x{world}, no collective on the data path"},
-        "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved_gbs / hbm, "traffic": traffic,
-                     "peak_kind": peak_kind + " hbm_gbs (copy)",
-                     "bytes_per_ray": b_ray, "nodes_per_ray": nodes_c / rays_c, "tris_per_ray": tris_c / rays_c,
-                     "node_bytes": node_b, "kernel": "k_trace"},
-        "roofline_issue": None if counters is None else {
-            "bound": "alu", "achieved": counters[1] / (ms_step * 1e-3) / 1e9, "peak": ISSUE_PEAK_G,
-            "unit": "G warp instructions/s", "frac": counters[1] / (ms_step * 1e-3) / 1e9 / ISSUE_PEAK_G,
-            "instructions_per_launch": counters[1],
-            "peak_kind": "152 SMs x 4 schedulers x 1 warp instruction/cycle x 2.07 GHz (max SM clock)"},
+        "roofline": lead,
+        "roofline_hbm_algorithmic": algorithmic,
         "clocks": clocks if first_clocks is None else dict(clocks, first_run_rejected=first_clocks),
         "e2e": e2e,
         "gpu_launches": args.steps,
@@ -832,6 +1006,13 @@ def bench_ours(args, rank, world, local):
     if args.workload == "rooms" and not args.no_serving:
         # served latency on the same resident scene, mixed camera and LiDAR requests
         line["serving"] = serving_measure(ags, ctx, scene, E, poses[0], serving_specs())
+        line["serving"]["without_graph"] = serving_measure(ags, ctx, scene, E, poses[0], serving_specs(),
+                                                           use_graph=False, sequential=False)
+    if args.workload == "rooms" and not args.no_sub_records and rank == 0:
+        # the other workloads' figures in the same run: a bounded LiDAR-forest run and the node formats
+        sub_steps = max(3, min(args.steps, 10))
+        line["forest"] = forest_record(ags, ctx, dev, stream, sub_steps, 3)
+        line["precision"] = precision_record(ags, ctx, dev, stream, batch, spec, poses, poses_d, sub_steps, 3)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(batch, spec, poses)
     if rank == 0:

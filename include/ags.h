@@ -429,6 +429,9 @@ typedef struct {
   const ags_sensor_spec* specs;  /* sensor shapes requests may use (copied) */
   int32_t n_specs;            /* 1..256 */
   int32_t auto_release;       /* nonzero: free a request's outputs as soon as it completes */
+  int32_t use_graph;          /* nonzero: each stream replays one CUDA graph per batch (slot-table copy,
+                                 tile-counter reset, render), captured at creation, instead of three calls */
+  int32_t pad0;
 } ags_server_config;
 
 typedef struct {

@@ -105,7 +105,8 @@ class ags_launch_config(ctypes.Structure):
 
 class ags_server_config(ctypes.Structure):
     _fields_ = [("max_slots", ctypes.c_int32), ("max_inflight", ctypes.c_int32), ("arena_bytes", ctypes.c_int64),
-                ("specs", ctypes.c_void_p), ("n_specs", ctypes.c_int32), ("auto_release", ctypes.c_int32)]
+                ("specs", ctypes.c_void_p), ("n_specs", ctypes.c_int32), ("auto_release", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32), ("pad0", ctypes.c_int32)]
 
 
 class ags_request(ctypes.Structure):
@@ -461,10 +462,10 @@ def _spec_array(specs):
 
 
 def ags_server_create(ctx: int, scene: int, specs, max_slots: int = 256, max_inflight: int = 2,
-                      arena_bytes: int = 0, auto_release: bool = False) -> int:
+                      arena_bytes: int = 0, auto_release: bool = False, use_graph: bool = False) -> int:
     arr = _spec_array(specs)
     cfg = ags_server_config(int(max_slots), int(max_inflight), int(arena_bytes), ctypes.cast(arr, ctypes.c_void_p),
-                            len(specs), 1 if auto_release else 0)
+                            len(specs), 1 if auto_release else 0, 1 if use_graph else 0, 0)
     h = ctypes.c_void_p()
     _check(lib().ags_server_create(ctx, scene, ctypes.byref(cfg), ctypes.byref(h)), "ags_server_create")
     return h.value

@@ -297,6 +297,7 @@ struct TraceArgs {
   int32_t n_specs;
   const SlotEntry* slots;    // slot mode when non-null
   int32_t n_slots;
+  const int32_t* slot_header;  // slot mode: when non-null, {n_slots, total_tiles} are read here (device)
   int32_t log2_tile_w, tile_h, rays_per_lane;  // a warp's tile: (1 << log2_tile_w) x tile_h pixels
   int64_t total_tiles;
   int32_t max_visits;

@@ -74,6 +74,12 @@ struct ags_server {
   std::vector<ags::SlotEntry*> h_slots;  // pinned staging
   std::vector<bool> lane_busy;
   std::vector<unsigned int*> counters;
+  // use_graph: per lane, the batch step (slot-table copy, counter reset, render) as one captured graph whose
+  // copy size is set per batch
+  bool use_graph = false;
+  std::vector<cudaGraph_t> graphs;
+  std::vector<cudaGraphExec_t> gexec;
+  std::vector<cudaGraphNode_t> gcopy;
   // queues
   std::mutex m;
   std::condition_variable cv;
@@ -149,6 +155,74 @@ void retire(ags_server* sv) {
   while (!sv->inflight.empty() && sv->inflight.front().done) sv->inflight.pop_front();
 }
 
+// The render arguments of one lane's batches: the slot table follows a
+// one-entry header {n_slots, total_tiles} that the kernel reads from device
+// memory, so the same arguments serve every batch (and a captured graph).
+TraceArgs batch_args(ags_server* sv, int lane) {
+  TraceArgs a{};
+  a.nodes = sv->scene->d.nodes;
+  a.node_format = sv->scene->node_format;
+  a.tris = sv->scene->d.tris;
+  a.env_root = sv->scene->d.env_root;
+  a.n_nodes = (int32_t)sv->scene->n_nodes;
+  a.n_tris = (int32_t)sv->scene->n_refs;
+  a.n_scene_envs = sv->scene->n_envs;
+  a.out_depth = sv->arena_depth;
+  a.out_seg = sv->arena_seg;
+  a.specs = sv->d_specs;
+  a.n_specs = (int32_t)sv->params.size();
+  a.slots = sv->d_slots[lane] + 1;
+  a.slot_header = reinterpret_cast<const int32_t*>(sv->d_slots[lane]);
+  a.n_slots = 0;
+  a.log2_tile_w = 3;
+  a.tile_h = 4;
+  a.rays_per_lane = 1;
+  a.total_tiles = 0;
+  a.max_visits = sv->ctx->max_node_visits;
+  a.status = sv->ctx->d_status;
+  a.counts = sv->ctx->d_counts;
+  a.tile_counter = sv->counters[lane];
+  return a;
+}
+
+// Capture lane k's batch step into a graph (at server creation, before the worker starts).
+cudaError_t capture_lane(ags_server* sv, int k) {
+  cudaStream_t s = sv->streams[k];
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaMemcpyAsync(sv->d_slots[k], sv->h_slots[k], sizeof(SlotEntry), cudaMemcpyHostToDevice, s);
+  cudaMemsetAsync(sv->counters[k], 0, sizeof(unsigned int), s);
+  const cudaError_t le = launch_trace(batch_args(sv, k), sv->ctx->trace_blocks, false, s);
+  e = cudaStreamEndCapture(s, &g);
+  if (e == cudaSuccess && le != cudaSuccess) e = le;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphNode_t copy = nullptr;
+  if (e == cudaSuccess) {
+    size_t n = 0;
+    e = cudaGraphGetNodes(g, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (e == cudaSuccess) e = cudaGraphGetNodes(g, nodes.data(), &n);
+    for (size_t i = 0; e == cudaSuccess && i < n; ++i) {
+      cudaGraphNodeType t;
+      e = cudaGraphNodeGetType(nodes[i], &t);
+      if (e == cudaSuccess && t == cudaGraphNodeTypeMemcpy) copy = nodes[i];
+    }
+    if (e == cudaSuccess && !copy) e = cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) {
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return e;
+  }
+  sv->graphs[k] = g;
+  sv->gexec[k] = ge;
+  sv->gcopy[k] = copy;
+  return cudaSuccess;
+}
+
 bool launch_batch(ags_server* sv) {
   NvtxRange range("ags serving batch");
   int lane = -1;
@@ -161,7 +235,7 @@ bool launch_batch(ags_server* sv) {
   InFlight b;
   b.lane = lane;
   int64_t tiles = 0;
-  SlotEntry* hs = sv->h_slots[lane];
+  SlotEntry* hs = sv->h_slots[lane] + 1;  // entry 0 is the header
   while (!sv->pending.empty() && (int32_t)b.reqs.size() < sv->max_slots) {
     Pending& p = sv->pending.front();
     int64_t off = 0;
@@ -183,32 +257,20 @@ bool launch_batch(ags_server* sv) {
   if (b.reqs.empty()) return false;
   cudaStream_t s = sv->streams[lane];
   const int n = (int)b.reqs.size();
-  cudaMemcpyAsync(sv->d_slots[lane], hs, n * sizeof(SlotEntry), cudaMemcpyHostToDevice, s);
-  TraceArgs a{};
-  a.nodes = sv->scene->d.nodes;
-  a.node_format = sv->scene->node_format;
-  a.tris = sv->scene->d.tris;
-  a.env_root = sv->scene->d.env_root;
-  a.n_nodes = (int32_t)sv->scene->n_nodes;
-  a.n_tris = (int32_t)sv->scene->n_refs;
-  a.n_scene_envs = sv->scene->n_envs;
-  a.out_depth = sv->arena_depth;
-  a.out_seg = sv->arena_seg;
-  a.specs = sv->d_specs;
-  a.n_specs = (int32_t)sv->params.size();
-  a.slots = sv->d_slots[lane];
-  a.n_slots = n;
-  a.log2_tile_w = 3;
-  a.tile_h = 4;
-  a.rays_per_lane = 1;
-  a.total_tiles = tiles;
-  a.max_visits = sv->ctx->max_node_visits;
-  a.status = sv->ctx->d_status;
-  a.counts = sv->ctx->d_counts;
-  unsigned int* counter = sv->counters[lane];
-  a.tile_counter = counter;
-  cudaMemsetAsync(counter, 0, sizeof(unsigned int), s);
-  if (launch_trace(a, sv->ctx->trace_blocks, false, s) != cudaSuccess) sv->status_error = 1;
+  int32_t* hdr = reinterpret_cast<int32_t*>(sv->h_slots[lane]);
+  hdr[0] = n;
+  hdr[1] = (int32_t)tiles;
+  const size_t bytes = (size_t)(n + 1) * sizeof(SlotEntry);
+  if (sv->use_graph) {
+    cudaError_t e = cudaGraphExecMemcpyNodeSetParams1D(sv->gexec[lane], sv->gcopy[lane], sv->d_slots[lane],
+                                                       sv->h_slots[lane], bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaGraphLaunch(sv->gexec[lane], s);
+    if (e != cudaSuccess) sv->status_error = 1;
+  } else {
+    cudaMemcpyAsync(sv->d_slots[lane], sv->h_slots[lane], bytes, cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(sv->counters[lane], 0, sizeof(unsigned int), s);
+    if (launch_trace(batch_args(sv, lane), sv->ctx->trace_blocks, false, s) != cudaSuccess) sv->status_error = 1;
+  }
   cudaEventRecord(sv->events[lane], s);
   b.t_launch = now_s();
   sv->lane_busy[lane] = true;
@@ -301,8 +363,8 @@ ags_status ags_server_create(ags_context* ctx, const ags_scene* scene, const ags
       SlotEntry *ds, *hs;
       if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess ||
           (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess ||
-          (e = cudaMalloc(&ds, sv->max_slots * sizeof(SlotEntry))) != cudaSuccess ||
-          (e = cudaHostAlloc(&hs, sv->max_slots * sizeof(SlotEntry), cudaHostAllocDefault)) != cudaSuccess) {
+          (e = cudaMalloc(&ds, (sv->max_slots + 1) * sizeof(SlotEntry))) != cudaSuccess ||
+          (e = cudaHostAlloc(&hs, (sv->max_slots + 1) * sizeof(SlotEntry), cudaHostAllocDefault)) != cudaSuccess) {
         ags_server* raw = sv.release();
         ags_server_destroy(raw);
         return cuda_fail(e, "server lane setup");
@@ -319,6 +381,20 @@ ags_status ags_server_create(ags_context* ctx, const ags_scene* scene, const ags
         return cuda_fail(e, "server tile counter");
       }
       sv->counters.push_back(counter);
+    }
+    sv->use_graph = cfg->use_graph != 0;
+    sv->graphs.assign(sv->max_inflight, nullptr);
+    sv->gexec.assign(sv->max_inflight, nullptr);
+    sv->gcopy.assign(sv->max_inflight, nullptr);
+    if (sv->use_graph) {
+      for (int k = 0; k < sv->max_inflight; ++k) {
+        std::memset(sv->h_slots[k], 0, sizeof(SlotEntry));
+        if ((e = capture_lane(sv.get(), k)) != cudaSuccess) {
+          ags_server* raw = sv.release();
+          ags_server_destroy(raw);
+          return cuda_fail(e, "server graph capture");
+        }
+      }
     }
     ags_server* raw = sv.release();
     raw->worker = std::thread(worker_main, raw);
@@ -343,8 +419,12 @@ void ags_server_destroy(ags_server* sv) {
   sv->cv.notify_all();
   if (sv->worker.joinable()) sv->worker.join();
   cudaSetDevice(sv->ctx->device);
+  for (size_t k = 0; k < sv->streams.size(); ++k) cudaStreamSynchronize(sv->streams[k]);
+  for (size_t k = 0; k < sv->gexec.size(); ++k) {
+    if (sv->gexec[k]) cudaGraphExecDestroy(sv->gexec[k]);
+    if (sv->graphs[k]) cudaGraphDestroy(sv->graphs[k]);
+  }
   for (size_t k = 0; k < sv->streams.size(); ++k) {
-    cudaStreamSynchronize(sv->streams[k]);
     if (k < sv->counters.size()) cudaFree(sv->counters[k]);
     cudaStreamDestroy(sv->streams[k]);
     cudaEventDestroy(sv->events[k]);

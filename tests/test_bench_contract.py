@@ -79,3 +79,26 @@ def test_clock_rejection_rule():
         assert b.clocks_rejected(dict(ok, reasons=[r]))
     assert b.clocks_rejected(dict(ok, sm_mhz=1400.0))          # well below max with no reason: a lock
     assert not b.clocks_rejected({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]})
+
+
+def test_rooflines_follow_from_their_inputs():
+    """The lead roofline is the issue one (bound alu) when counters exist, with the DRAM fraction beside it;
+    the algorithmic-bytes block is labelled as such; every fraction is its achieved value over its peak."""
+    sys.path.insert(0, ROOT)
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+    assert abs(b.issue_peak_g(152, 2070.0) - 1258.56) < 1e-9
+    lead, algo = b.rooflines((1.2e9, 1.19e10), 12.4, 1790.0, 132710400, 6789.6, "measured", 152, 2070.0, 7.67,
+                             3.89, 208)
+    assert lead["bound"] == "alu" and lead["unit"] == "G warp instructions/s"
+    assert abs(lead["achieved"] - 1.19e10 / 12.4e-3 / 1e9) < 1e-6
+    assert abs(lead["frac"] - lead["achieved"] / lead["peak"]) < 1e-12 and lead["peak"] == b.issue_peak_g(152, 2070.0)
+    assert abs(lead["dram_gbs"] - 1.2e9 / 12.4e-3 / 1e9) < 1e-6 and abs(lead["dram_frac"] - lead["dram_gbs"] / 6789.6) < 1e-12
+    assert lead["traffic"] == 1.2e9 and lead["algorithmic"] is algo
+    assert algo["bound"] == "hbm" and "L1/L2" in algo["achieved_is"]
+    assert abs(algo["achieved"] - 1790.0 * 132710400 / 12.4e-3 / 1e9) < 1e-6
+    assert abs(algo["frac"] - algo["achieved"] / 6789.6) < 1e-12
+    lead2, algo2 = b.rooflines(None, 12.4, 1790.0, 132710400, 6789.6, "measured", 152, 2070.0, 7.67, 3.89, 208)
+    assert algo2 is None and lead2["bound"] == "hbm" and lead2["traffic"] is None

@@ -67,6 +67,7 @@ def test_struct_layouts_match_the_header():
     assert ctypes.sizeof(ags.ags_stereo) == 16
     assert ctypes.sizeof(ags.ags_render_options) == 24
     assert ctypes.sizeof(ags.ags_launch_config) == 16
+    assert ctypes.sizeof(ags.ags_server_config) == 40
 
 
 def test_null_arguments_are_rejected_without_a_device(lib):
@@ -106,9 +107,9 @@ int main(void) {{
   ags_status st = ags_context_create(0, &ctx);
   if (st == AGS_OK) ags_context_destroy(ctx);
   printf("%d %d\\n", (int)(sizeof table / sizeof table[0]), (int)st);
-  printf("%d %d %d %d %d %d %d\\n", (int)sizeof(ags_submesh), (int)sizeof(ags_env_mesh), (int)sizeof(ags_sensor_spec),
-         (int)sizeof(ags_hit_channels), (int)sizeof(ags_stereo), (int)sizeof(ags_render_options),
-         (int)sizeof(ags_launch_config));
+  printf("%d %d %d %d %d %d %d %d\\n", (int)sizeof(ags_submesh), (int)sizeof(ags_env_mesh),
+         (int)sizeof(ags_sensor_spec), (int)sizeof(ags_hit_channels), (int)sizeof(ags_stereo),
+         (int)sizeof(ags_render_options), (int)sizeof(ags_launch_config), (int)sizeof(ags_server_config));
   return 0;
 }}
 """)
@@ -122,8 +123,8 @@ int main(void) {{
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
     assert int(out[0]) == len(names)
     # the C compiler's struct sizes equal the binding's
-    assert [int(x) for x in out[2:9]] == [ctypes.sizeof(t) for t in (
+    assert [int(x) for x in out[2:10]] == [ctypes.sizeof(t) for t in (
         ags.ags_submesh, ags.ags_env_mesh, ags.ags_sensor_spec, ags.ags_hit_channels, ags.ags_stereo,
-        ags.ags_render_options, ags.ags_launch_config)]
+        ags.ags_render_options, ags.ags_launch_config, ags.ags_server_config)]
     if not torch.cuda.is_available():
         assert int(out[1]) != 0  # no device here: an error status

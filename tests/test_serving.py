@@ -55,10 +55,14 @@ def _wait(server, ids, timeout=20.0):
     return got
 
 
-def test_alone_equals_in_the_mix(setup):
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_alone_equals_in_the_mix(setup, use_graph):
+    """Each result is the same served alone and inside a burst of other requests, with the batch step
+    launched call by call or replayed from each stream's captured graph."""
     ctx, batch, scene, specs, poses = setup
     rng = np.random.default_rng(3)
-    server = ags.ags_server_create(ctx, scene, specs, max_slots=64, max_inflight=2, arena_bytes=64 << 20)
+    server = ags.ags_server_create(ctx, scene, specs, max_slots=64, max_inflight=2, arena_bytes=64 << 20,
+                                   use_graph=use_graph)
     try:
         probe = [(2, 0), (5, 2), (0, 1)]
         alone = {}
