@@ -40,6 +40,9 @@ struct Ray {
   float cnx, cny, cnz;       // near-bound constants: -o/d, lowered
   float cfx, cfy, cfz;       // far-bound constants: -o/d, raised
   int onx, ony, onz;         // float4 offsets of the near-bound arrays in a node (octant)
+  // the inverse direction and the near / far constants again, each held twice as a register pair for the
+  // packed arithmetic of the float32 node test (two children per instruction)
+  float2 ix2, iy2, iz2, cnx2, cfx2, cny2, cfy2, cnz2, cfz2;
   // watertight test: rows of the shear that maps (v - o) to the ray's frame
   float m0x, m0y, m0z, m1x, m1y, m1z, m2x, m2y, m2z;
 };
@@ -48,6 +51,26 @@ __device__ __forceinline__ float nonzero(float d) {
   // an exactly-zero direction component is replaced by a tiny one of the same
   // sign for both the box and the triangle test, keeping them consistent
   return fabsf(d) < 1e-30f ? copysignf(1e-30f, d) : d;
+}
+
+// Packed FP32 arithmetic of Blackwell (fma.rn.f32x2 / mul.rn.f32x2, sm_100 and later): one instruction
+// performs two IEEE round-to-nearest operations, the same as two scalar __fmaf_rn / __fmul_rn, bit for bit.
+// The node test applies them to two children at once.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
 }
 
 __device__ __forceinline__ float max3f(float a, float b, float c) {
@@ -77,6 +100,15 @@ __device__ __forceinline__ void setup_ray(Ray& r, float dx, float dy, float dz) 
   r.cnz = pz - ez;
   r.cfz = pz + ez;
   // node layout (float4 units): header, lox[2], hix[2], loy[2], hiy[2], loz[2], hiz[2]
+  r.ix2 = make_float2(r.ix, r.ix);
+  r.iy2 = make_float2(r.iy, r.iy);
+  r.iz2 = make_float2(r.iz, r.iz);
+  r.cnx2 = make_float2(r.cnx, r.cnx);
+  r.cfx2 = make_float2(r.cfx, r.cfx);
+  r.cny2 = make_float2(r.cny, r.cny);
+  r.cfy2 = make_float2(r.cfy, r.cfy);
+  r.cnz2 = make_float2(r.cnz, r.cnz);
+  r.cfz2 = make_float2(r.cfz, r.cfz);
   r.onx = r.ix >= 0.0f ? 1 : 3;
   r.ony = r.iy >= 0.0f ? 5 : 7;
   r.onz = r.iz >= 0.0f ? 9 : 11;
@@ -207,6 +239,19 @@ __device__ __forceinline__ void child_test(int k, float tnx, float tfx, float tn
   if (tmin <= fminf(tmax, t_cull)) hit_mask |= 1u << k;
 }
 
+// Two children k, k+1 at once: their slab distances come in register pairs (packed arithmetic); the
+// exits are scaled up by the slack with one packed multiply. Same results as two child_test calls.
+__device__ __forceinline__ void child_test2(int k, float2 tnx, float2 tfx, float2 tny, float2 tfy, float2 tnz,
+                                            float2 tfz, float t_cull, float* tmins, uint32_t& hit_mask) {
+  const float tmin0 = max3f(tnx.x, tny.x, fmaxf(tnz.x, 0.0f)), tmin1 = max3f(tnx.y, tny.y, fmaxf(tnz.y, 0.0f));
+  const float2 tmax = mul2(make_float2(min3f(tfx.x, tfy.x, tfz.x), min3f(tfx.y, tfy.y, tfz.y)),
+                           make_float2(kSlabSlack, kSlabSlack));
+  tmins[k] = tmin0;
+  tmins[k + 1] = tmin1;
+  if (tmin0 <= fminf(tmax.x, t_cull)) hit_mask |= 1u << k;
+  if (tmin1 <= fminf(tmax.y, t_cull)) hit_mask |= 2u << k;
+}
+
 // near / far constants of one axis for a node whose bounds are origin + b:
 // c = (origin - o) / d, computed as one fma from the ray's lowered / raised
 // constants, then moved away again by the rounding of that fma
@@ -237,10 +282,16 @@ __device__ __forceinline__ void test_node(const void* __restrict__ nodes, int32_
       const float nys[4] = {ny4.x, ny4.y, ny4.z, ny4.w}, fys[4] = {fy4.x, fy4.y, fy4.z, fy4.w};
       const float nzs[4] = {nz4.x, nz4.y, nz4.z, nz4.w}, fzs[4] = {fz4.x, fz4.y, fz4.z, fz4.w};
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        child_test(4 * half + q, __fmaf_rn(nxs[q], r.ix, r.cnx), __fmaf_rn(fxs[q], r.ix, r.cfx),
-                   __fmaf_rn(nys[q], r.iy, r.cny), __fmaf_rn(fys[q], r.iy, r.cfy), __fmaf_rn(nzs[q], r.iz, r.cnz),
-                   __fmaf_rn(fzs[q], r.iz, r.cfz), t_cull, tmins, hit_mask);
+      for (int q = 0; q < 4; q += 2) {
+        // children q, q+1 of this half: adjacent words of one 16-byte load form each register pair
+        const float2 tnx = fma2(make_float2(nxs[q], nxs[q + 1]), r.ix2, r.cnx2);
+        const float2 tfx = fma2(make_float2(fxs[q], fxs[q + 1]), r.ix2, r.cfx2);
+        const float2 tny = fma2(make_float2(nys[q], nys[q + 1]), r.iy2, r.cny2);
+        const float2 tfy = fma2(make_float2(fys[q], fys[q + 1]), r.iy2, r.cfy2);
+        const float2 tnz = fma2(make_float2(nzs[q], nzs[q + 1]), r.iz2, r.cnz2);
+        const float2 tfz = fma2(make_float2(fzs[q], fzs[q + 1]), r.iz2, r.cfz2);
+        child_test2(4 * half + q, tnx, tfx, tny, tfy, tnz, tfz, t_cull, tmins, hit_mask);
+      }
     }
   } else if constexpr (kFmt == kNodeFp16) {
     // 128 B: header, origin, then lo_x, hi_x, lo_y, hi_y, lo_z, hi_z as 8 halves each
@@ -261,20 +312,19 @@ __device__ __forceinline__ void test_node(const void* __restrict__ nodes, int32_
     const float nxw[4] = {nx.x, nx.y, nx.z, nx.w}, fxw[4] = {fx.x, fx.y, fx.z, fx.w};
     const float nyw[4] = {ny.x, ny.y, ny.z, ny.w}, fyw[4] = {fy.x, fy.y, fy.z, fy.w};
     const float nzw[4] = {nz.x, nz.y, nz.z, nz.w}, fzw[4] = {fz.x, fz.y, fz.z, fz.w};
+    const float2 cnx2 = make_float2(cnx, cnx), cfx2 = make_float2(cfx, cfx), cny2 = make_float2(cny, cny),
+                 cfy2 = make_float2(cfy, cfy), cnz2 = make_float2(cnz, cnz), cfz2 = make_float2(cfz, cfz);
 #pragma unroll
     for (int w = 0; w < 4; ++w) {
+      // the two halves of a word are children 2w and 2w+1
       const float2 bnx = __half22float2(*reinterpret_cast<const __half2*>(&nxw[w]));
       const float2 bfx = __half22float2(*reinterpret_cast<const __half2*>(&fxw[w]));
       const float2 bny = __half22float2(*reinterpret_cast<const __half2*>(&nyw[w]));
       const float2 bfy = __half22float2(*reinterpret_cast<const __half2*>(&fyw[w]));
       const float2 bnz = __half22float2(*reinterpret_cast<const __half2*>(&nzw[w]));
       const float2 bfz = __half22float2(*reinterpret_cast<const __half2*>(&fzw[w]));
-      child_test(2 * w, __fmaf_rn(bnx.x, r.ix, cnx), __fmaf_rn(bfx.x, r.ix, cfx), __fmaf_rn(bny.x, r.iy, cny),
-                 __fmaf_rn(bfy.x, r.iy, cfy), __fmaf_rn(bnz.x, r.iz, cnz), __fmaf_rn(bfz.x, r.iz, cfz), t_cull, tmins,
-                 hit_mask);
-      child_test(2 * w + 1, __fmaf_rn(bnx.y, r.ix, cnx), __fmaf_rn(bfx.y, r.ix, cfx), __fmaf_rn(bny.y, r.iy, cny),
-                 __fmaf_rn(bfy.y, r.iy, cfy), __fmaf_rn(bnz.y, r.iz, cnz), __fmaf_rn(bfz.y, r.iz, cfz), t_cull, tmins,
-                 hit_mask);
+      child_test2(2 * w, fma2(bnx, r.ix2, cnx2), fma2(bfx, r.ix2, cfx2), fma2(bny, r.iy2, cny2),
+                  fma2(bfy, r.iy2, cfy2), fma2(bnz, r.iz2, cnz2), fma2(bfz, r.iz2, cfz2), t_cull, tmins, hit_mask);
     }
   } else {
     // 80 B: origin + per-axis power-of-two scale exponents, header, then per
