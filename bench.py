@@ -644,12 +644,20 @@ def bench_features(args, rank, world, local):
 
 
 # ---------------------------------------------------------------- sub-records of the default line
-def timed_renders(ags, ctx, scene, spec, poses_d, depth, seg, stream, steps, warmup):
-    """ms per render over `steps` renders after `warmup`, CUDA events on the render stream, clocks sampled."""
+def timed_renders(ags, ctx, scene, spec, poses_d, depth, seg, stream, steps, warmup, min_seconds=0.5):
+    """ms per render over at least `steps` renders after `warmup`, CUDA events on the render stream, clocks
+    sampled. Short renders are repeated until the timed region lasts about min_seconds, so that the clock
+    record (sampled every 100 ms) covers it."""
     import torch
     walk = poses_d.shape[0]
+    st, en = torch.cuda.Event(True), torch.cuda.Event(True)
+    st.record(stream)
     for i in range(warmup):
         ags.ags_render(ctx, scene, spec, poses_d[i % walk], depth, seg, stream)
+    en.record(stream)
+    torch.cuda.synchronize()
+    per = st.elapsed_time(en) / max(warmup, 1)
+    steps = int(min(5000, max(steps, math.ceil(min_seconds * 1e3 / max(per, 1e-3)))))
     st, en = torch.cuda.Event(True), torch.cuda.Event(True)
     torch.cuda.synchronize()
     with ClockSampler(torch.cuda.current_device()) as clk:
@@ -659,7 +667,7 @@ def timed_renders(ags, ctx, scene, spec, poses_d, depth, seg, stream, steps, war
         en.record(stream)
         torch.cuda.synchronize()
     ags.ags_stream_status(ctx, stream)
-    return st.elapsed_time(en) / steps, clk.summary()
+    return st.elapsed_time(en) / steps, dict(clk.summary(), timed_steps=steps)
 
 
 def forest_record(ags, ctx, dev, stream, steps, warmup, envs=64, cells=64, check_rays=256):
@@ -702,7 +710,8 @@ def forest_record(ags, ctx, dev, stream, steps, warmup, envs=64, cells=64, check
         rays = E * spec.width * spec.height
         return {"workload": f"LiDAR forests, {E} envs (50-200 trees of 2k-10k triangles), 64x512 LiDAR, "
                             f"references split at {cells} cells",
-                "mrays_per_s": rays / ms / 1e3, "ms_per_step": ms, "steps": steps, "warmup": warmup,
+                "mrays_per_s": rays / ms / 1e3, "ms_per_step": ms, "steps": clocks.get("timed_steps", steps),
+                "warmup": warmup,
                 "tris": int(batch.env_tri_counts().sum()), "bvh_bytes": ags.ags_scene_stats(scene)[2],
                 "build_ms": build_s * 1e3, "nodes_per_ray": n_c / r_c, "tris_per_ray": t_c / r_c,
                 "bytes_per_ray": (n_c * ags.ags_scene_node_bytes(scene) + t_c * 48) / r_c + 8.0,
