@@ -53,7 +53,7 @@ __device__ __forceinline__ float nonzero(float d) {
   return fabsf(d) < 1e-30f ? copysignf(1e-30f, d) : d;
 }
 
-// Packed FP32 arithmetic of Blackwell (fma.rn.f32x2 / mul.rn.f32x2, sm_100 and later): one instruction
+// Packed FP32 arithmetic of Blackwell (fma / add / mul .rn.f32x2, sm_100 and later): one instruction
 // performs two IEEE round-to-nearest operations, the same as two scalar __fmaf_rn / __fmul_rn, bit for bit.
 // The node test applies them to two children at once.
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
@@ -62,6 +62,14 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
       "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
       : "=f"(d.x), "=f"(d.y)
       : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
   return d;
 }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) {
@@ -224,23 +232,12 @@ __device__ __forceinline__ void hit_normal(const float4* __restrict__ tris, int3
   nz = __fmul_rn(nz, s);
 }
 
-// The rays of one warp tile: sensor shape `sen`, environment `env`, tile
-// index t_in within it; `slot` locates the pose and the outputs (the
-// environment's index in the launch, or the request's slot in the table).
 // ---- one wide node: header, and per child the entry distance and whether
 // the ray's slab interval meets [0, t_cull]. Every bound t = b * ix + c is a
 // single fma whose constant is already lowered (near) or raised (far) by more
-// than the rounding of c, as for the float32 node.
-__device__ __forceinline__ void child_test(int k, float tnx, float tfx, float tny, float tfy, float tnz, float tfz,
-                                           float t_cull, float* tmins, uint32_t& hit_mask) {
-  const float tmin = max3f(tnx, tny, fmaxf(tnz, 0.0f));
-  const float tmax = min3f(tfx, tfy, tfz) * kSlabSlack;
-  tmins[k] = tmin;
-  if (tmin <= fminf(tmax, t_cull)) hit_mask |= 1u << k;
-}
-
-// Two children k, k+1 at once: their slab distances come in register pairs (packed arithmetic); the
-// exits are scaled up by the slack with one packed multiply. Same results as two child_test calls.
+// than the rounding of c. Children k and k+1 are tested together: their slab
+// distances come in register pairs (packed arithmetic), and one packed
+// multiply scales both exits up by the slack.
 __device__ __forceinline__ void child_test2(int k, float2 tnx, float2 tfx, float2 tny, float2 tfy, float2 tnz,
                                             float2 tfz, float t_cull, float* tmins, uint32_t& hit_mask) {
   const float tmin0 = max3f(tnx.x, tny.x, fmaxf(tnz.x, 0.0f)), tmin1 = max3f(tnx.y, tny.y, fmaxf(tnz.y, 0.0f));
@@ -351,16 +348,23 @@ __device__ __forceinline__ void test_node(const void* __restrict__ nodes, int32_
     const uint32_t nx0 = sx ? qx.z : qx.x, nx1 = sx ? qx.w : qx.y, fx0 = sx ? qx.x : qx.z, fx1 = sx ? qx.y : qx.w;
     const uint32_t ny0 = sy ? qy.z : qy.x, ny1 = sy ? qy.w : qy.y, fy0 = sy ? qy.x : qy.z, fy1 = sy ? qy.y : qy.w;
     const uint32_t nz0 = sz ? qz.z : qz.x, nz1 = sz ? qz.w : qz.y, fz0 = sz ? qz.x : qz.z, fz1 = sz ? qz.y : qz.w;
+    // children k, k+1 together (packed arithmetic, as for float32 nodes)
+    const float2 ax2 = make_float2(ax, ax), ay2 = make_float2(ay, ay), az2 = make_float2(az, az);
+    const float2 cnx2 = make_float2(cnx, cnx), cfx2 = make_float2(cfx, cfx), cny2 = make_float2(cny, cny),
+                 cfy2 = make_float2(cfy, cfy), cnz2 = make_float2(cnz, cnz), cfz2 = make_float2(cfz, cfz);
+    const float2 m23 = make_float2(-8388608.0f, -8388608.0f);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      // byte k of the word as the exact float q: bits 0x4B000000 | q = 2^23 + q
-      const uint32_t sel = 0x7440u | (uint32_t)(k & 3);
-      auto qf = [&](uint32_t w0, uint32_t w1) {
-        return __uint_as_float(__byte_perm(k < 4 ? w0 : w1, 0x4B000000u, sel)) - 8388608.0f;
+    for (int k = 0; k < 8; k += 2) {
+      // bytes k, k+1 of the word as exact floats q: bits 0x4B000000 | q = 2^23 + q, less 2^23
+      auto q2 = [&](uint32_t w0, uint32_t w1) {
+        const uint32_t w = k < 4 ? w0 : w1;
+        return add2(make_float2(__uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u | (uint32_t)(k & 3))),
+                                __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7440u | (uint32_t)((k + 1) & 3)))),
+                    m23);
       };
-      child_test(k, __fmaf_rn(qf(nx0, nx1), ax, cnx), __fmaf_rn(qf(fx0, fx1), ax, cfx),
-                 __fmaf_rn(qf(ny0, ny1), ay, cny), __fmaf_rn(qf(fy0, fy1), ay, cfy),
-                 __fmaf_rn(qf(nz0, nz1), az, cnz), __fmaf_rn(qf(fz0, fz1), az, cfz), t_cull, tmins, hit_mask);
+      child_test2(k, fma2(q2(nx0, nx1), ax2, cnx2), fma2(q2(fx0, fx1), ax2, cfx2), fma2(q2(ny0, ny1), ay2, cny2),
+                  fma2(q2(fy0, fy1), ay2, cfy2), fma2(q2(nz0, nz1), az2, cnz2), fma2(q2(fz0, fz1), az2, cfz2), t_cull,
+                  tmins, hit_mask);
     }
   }
 }
@@ -680,6 +684,9 @@ __device__ __forceinline__ void resolve_hit(const SensorParams& sen, bool failed
   }
 }
 
+// The rays of one warp tile: sensor shape `sen`, environment `env`, tile
+// index t_in within it; `slot` locates the pose and the outputs (the
+// environment's index in the launch, or the request's slot in the table).
 template <bool kCount, int kTileW, int kRaysPerLane, bool kSlots, int kFmt, int kExtra>
 __device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParams& sen, int32_t env, int32_t t_in,
                                            int32_t slot, int lane, int2* stack, unsigned long long& n_nodes,
