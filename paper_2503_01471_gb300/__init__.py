@@ -380,9 +380,43 @@ def ags_transform_vertices_noalloc(ctx: int, base_vertices, submesh_vertex_offse
 
 
 # ---------------------------------------------------------------- render
+def _device_buffer(x, name: str, dtype: str, numel: int) -> None:
+    """Host-side check of one device-buffer argument before any launch: a CUDA tensor of ``dtype`` ("float32"
+    or "int32") holding at least ``numel`` elements. A raw device address (an int) or None passes unchecked
+    (the caller vouches for it); a host array is refused, since a kernel would write through its address."""
+    if x is None or isinstance(x, int):
+        return
+    if isinstance(x, np.ndarray):
+        raise ValueError(f"{name} must be a device buffer (a CUDA tensor or a device address), not a host array")
+    if hasattr(x, "is_cuda") and hasattr(x, "numel"):
+        if not x.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor, not one on {x.device}")
+        if str(x.dtype) != "torch." + dtype:
+            raise ValueError(f"{name} must hold {dtype}, not {x.dtype}")
+        if int(x.numel()) < numel:
+            raise ValueError(f"{name} holds {int(x.numel())} elements, fewer than the {numel} the render writes or reads")
+
+
+def _render_buffers(spec, n: int, sensor_poses, out_depth, out_seg, face=None, bary=None, normal=None, point=None,
+                    ray_table=None) -> None:
+    """The buffers of a render of n environments with ``spec`` (validated spec fields only: an invalid spec is
+    left to the library, which rejects it)."""
+    w, h = int(spec.width), int(spec.height)
+    pix = n * w * h if w > 0 and h > 0 else 0
+    _device_buffer(sensor_poses, "sensor_poses", "float32", 7 * n)
+    _device_buffer(out_depth, "out_depth", "float32", pix)
+    _device_buffer(out_seg, "out_seg", "int32", pix)
+    _device_buffer(face, "face", "int32", pix)
+    _device_buffer(bary, "bary", "float32", 2 * pix)
+    _device_buffer(normal, "normal", "float32", 3 * pix)
+    _device_buffer(point, "point", "float32", 3 * pix)
+    _device_buffer(ray_table, "ray_table", "float32", 3 * w * h if w > 0 and h > 0 else 0)
+
+
 def ags_render(ctx: int, scene: int, spec, sensor_poses, out_depth, out_seg, stream=None) -> None:
     """Enqueue a render of every environment; tensors are CUDA tensors (or device pointers)."""
     s = make_spec(spec)
+    _render_buffers(s, ags_scene_n_envs(scene), sensor_poses, out_depth, out_seg)
     _check(lib().ags_render(ctx, scene, ctypes.byref(s), _ptr(sensor_poses), _ptr(out_depth), _ptr(out_seg),
                             _stream(stream)), "ags_render")
 
@@ -390,6 +424,8 @@ def ags_render(ctx: int, scene: int, spec, sensor_poses, out_depth, out_seg, str
 def ags_render_envs(ctx: int, scene: int, spec, env_ids, sensor_poses, out_depth, out_seg, stream=None) -> None:
     s = make_spec(spec)
     n = int(env_ids.numel() if hasattr(env_ids, "numel") else len(env_ids))
+    _device_buffer(env_ids, "env_ids", "int32", n)
+    _render_buffers(s, n, sensor_poses, out_depth, out_seg)
     _check(lib().ags_render_envs(ctx, scene, ctypes.byref(s), _ptr(env_ids), n, _ptr(sensor_poses), _ptr(out_depth),
                                  _ptr(out_seg), _stream(stream)), "ags_render_envs")
 
@@ -410,6 +446,7 @@ def ags_render_host(ctx: int, scene: int, spec, sensor_poses_host, out_depth_hos
 def ags_render_count(ctx: int, scene: int, spec, sensor_poses):
     """(rays, wide nodes visited, triangles tested) of one render."""
     s = make_spec(spec)
+    _render_buffers(s, ags_scene_n_envs(scene), sensor_poses, None, None)
     c = (ctypes.c_uint64 * 3)()
     _check(lib().ags_render_count(ctx, scene, ctypes.byref(s), _ptr(sensor_poses), c), "ags_render_count")
     return int(c[0]), int(c[1]), int(c[2])
@@ -418,6 +455,7 @@ def ags_render_count(ctx: int, scene: int, spec, sensor_poses):
 def ags_autotune(ctx: int, scene: int, spec, sensor_poses, out_depth, out_seg, repeats: int = 3):
     """Pick (and remember for this scene and sensor shape) the fastest launch shape; returns it."""
     s = make_spec(spec)
+    _render_buffers(s, ags_scene_n_envs(scene), sensor_poses, out_depth, out_seg)
     best = ags_launch_config()
     _check(lib().ags_autotune(ctx, scene, ctypes.byref(s), _ptr(sensor_poses), _ptr(out_depth), _ptr(out_seg),
                               int(repeats), ctypes.byref(best)), "ags_autotune")
@@ -531,6 +569,7 @@ def ags_replay_sequential(ctx: int, scene: int, specs, requests: np.ndarray, arr
 # ---------------------------------------------------------------- step graph
 def ags_render_graph_create(ctx: int, scene: int, spec, sensor_poses, out_depth, out_seg) -> int:
     s = make_spec(spec)
+    _render_buffers(s, ags_scene_n_envs(scene), sensor_poses, out_depth, out_seg)
     h = ctypes.c_void_p()
     _check(lib().ags_render_graph_create(ctx, scene, ctypes.byref(s), _ptr(sensor_poses), _ptr(out_depth),
                                          _ptr(out_seg), ctypes.byref(h)), "ags_render_graph_create")
@@ -550,6 +589,7 @@ def ags_render_channels(ctx: int, scene: int, spec, sensor_poses, out_depth, out
                         normal=None, point=None, stream=None) -> None:
     """ags_render plus the extra hit channels given (device tensors; None = not written)."""
     s = make_spec(spec)
+    _render_buffers(s, ags_scene_n_envs(scene), sensor_poses, out_depth, out_seg, face, bary, normal, point)
     ch = ags_hit_channels(_ptr(face) or None, _ptr(bary) or None, _ptr(normal) or None, _ptr(point) or None)
     _check(lib().ags_render_channels(ctx, scene, ctypes.byref(s), _ptr(sensor_poses), _ptr(out_depth),
                                      _ptr(out_seg), ctypes.byref(ch), _stream(stream)), "ags_render_channels")
@@ -561,6 +601,8 @@ def ags_render_ex(ctx: int, scene: int, spec, sensor_poses, out_depth, out_seg, 
     sensor at ``baseline`` (3 floats, sensor frame), and, for an AGS_RAY_TABLE spec, its device direction
     table ``ray_table`` [height, width, 3]."""
     s = make_spec(spec)
+    _render_buffers(s, ags_scene_n_envs(scene), sensor_poses, out_depth, out_seg, face, bary, normal, point,
+                    ray_table)
     chans = (face, bary, normal, point)
     ch = None
     if any(c is not None for c in chans):
@@ -580,6 +622,7 @@ def ags_autotune_build(ctx: int, scene: int, spec, sensor_poses, out_depth, out_
                        repeats: int = 2) -> int:
     """Rebuild the scene with each reference-splitting setting, keep the fastest; returns its cell count."""
     s = make_spec(spec)
+    _render_buffers(s, ags_scene_n_envs(scene), sensor_poses, out_depth, out_seg)
     c = (ctypes.c_uint32 * len(split_cells))(*[int(x) for x in split_cells])
     best = ctypes.c_uint32()
     _check(lib().ags_autotune_build(ctx, scene, ctypes.byref(s), _ptr(sensor_poses), _ptr(out_depth), _ptr(out_seg),
@@ -634,6 +677,7 @@ def ags_context_device(ctx: int) -> dict:
 def ags_render_bruteforce(ctx: int, scene: int, spec, sensor_poses, out_depth, out_seg, stream=None) -> None:
     """Every ray against every reference of its environment, no tree (a test aid; synchronous)."""
     s = make_spec(spec)
+    _render_buffers(s, ags_scene_n_envs(scene), sensor_poses, out_depth, out_seg)
     _check(lib().ags_render_bruteforce(ctx, scene, ctypes.byref(s), _ptr(sensor_poses), _ptr(out_depth),
                                        _ptr(out_seg), _stream(stream)), "ags_render_bruteforce")
 

@@ -128,3 +128,21 @@ int main(void) {{
         ags.ags_render_options, ags.ags_launch_config, ags.ags_server_config)]
     if not torch.cuda.is_available():
         assert int(out[1]) != 0  # no device here: an error status
+
+
+def test_render_wrappers_refuse_host_buffers_before_any_call():
+    """A kernel would write through a host array's address: the binding refuses host arrays and CPU tensors as
+    device buffers, on the host, before the library is asked to launch anything."""
+    import numpy as np
+    import torch
+
+    from paper_2503_01471_gb300 import scenes as S
+    spec = S.pinhole(4, 4)
+    dev_like = [np.zeros((1, 4, 4), np.float32), torch.zeros((1, 4, 4))]
+    for bad in dev_like:
+        with pytest.raises(ValueError):
+            ags.ags_render(0, None, spec, None, bad, None)
+    with pytest.raises(ValueError):
+        ags.ags_render_ex(0, None, spec, None, None, None, normal=np.zeros(3, np.float32))
+    with pytest.raises(ValueError):
+        ags.ags_render_envs(0, None, spec, np.zeros(1, np.int32), None, None, None)

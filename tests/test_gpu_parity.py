@@ -268,6 +268,14 @@ def test_host_validation_errors(ctx):
             with pytest.raises(ags.AgsError) as ei:
                 ags.ags_render(ctx, scene, bad, p, out, seg)
             assert ei.value.status == ags.AGS_ERR_INVALID_ARG
+        # buffers too small, of the wrong type or on the host are refused before anything is launched
+        spec8 = S.pinhole(8, 8)
+        for args in ((p[:, :6].contiguous(), out, seg), (p, out[:, :7].contiguous(), seg),
+                     (p, out, seg.float()), (p, out.cpu(), seg)):
+            with pytest.raises(ValueError):
+                ags.ags_render(ctx, scene, spec8, *args)
+        with pytest.raises(ValueError):
+            ags.ags_render_ex(ctx, scene, spec8, p, out, seg, normal=torch.empty((1, 8, 8, 2), device="cuda"))
         assert ags.ags_stream_status(ctx) == ags.AGS_OK
     finally:
         ags.ags_scene_destroy(scene)
