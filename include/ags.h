@@ -134,12 +134,18 @@ typedef struct {
 /* Launch shape of the persistent render kernel for one (scene, sensor shape):
  * each warp repeatedly takes a tile of tile_w x (32 * rays_per_lane / tile_w)
  * pixels (or beams) of one environment, each lane tracing rays_per_lane rays
- * of it; the grid holds blocks_per_sm blocks per SM (0: as many as fit). */
+ * of it; the grid holds blocks_per_sm blocks per SM (0: as many as fit).
+ * stack_depth 16 or 32 (8x4 tile, plain renders) walks each ray with a short
+ * traversal stack; a ray that outgrows it is listed and walked again, after
+ * the launch, with the full 64-entry stack, so results are the same; the list
+ * holds ags_context_set_retry_capacity rays (1048576 by default), beyond which
+ * rays report NaN / -1 and AGS_ERR_TRAVERSAL_LIMIT. 0 or 64: the full stack. */
 typedef struct {
   int32_t tile_w;         /* with rays_per_lane, one of the compiled shapes: (8,1) 8x4, */
   int32_t rays_per_lane;  /* (4,1) 4x8, (16,1) 16x2, (32,1) 32x1, (8,2) 8x8, (16,2) 16x4, (16,4) 16x8 */
   int32_t blocks_per_sm;  /* 0, or 1 .. the kernel's occupancy limit */
   float ms;               /* ags_autotune: measured time of one render; else 0 */
+  int32_t stack_depth;    /* 0 or 64 (full stack), 32 or 16 (short stack with retries) */
 } ags_launch_config;
 
 /* Create a context on CUDA device `device`. */
@@ -515,6 +521,12 @@ ags_status ags_stream_status(ags_context* ctx, void* cuda_stream);
  * it stops, reports NaN / segment -1 and makes the next ags_stream_status
  * return AGS_ERR_TRAVERSAL_LIMIT. Values below 1 are rejected. */
 ags_status ags_context_set_traversal_cap(ags_context* ctx, int32_t max_node_visits);
+
+/* Rays a short-stack render (ags_launch_config.stack_depth 16 or 32) may hand
+ * to its full-stack retry pass, 0..1048576 (the default; the list's memory is
+ * held by the context). Rays beyond it report NaN / segment -1 and make the
+ * next ags_stream_status return AGS_ERR_TRAVERSAL_LIMIT. */
+ags_status ags_context_set_retry_capacity(ags_context* ctx, int32_t rays);
 
 /*
  * ags_transform_vertices_noalloc -- the object-to-world vertex transform of

@@ -61,7 +61,7 @@ EXPORTS = [
     "ags_replay_sequential", "ags_scene_update_poses", "ags_render_graph_create", "ags_render_graph_launch",
     "ags_render_graph_destroy", "ags_render_channels", "ags_render_ex", "ags_autotune_build", "ags_scene_validate",
     "ags_server_cancel", "ags_test_sort_pairs", "ags_test_exclusive_scan", "ags_context_device",
-    "ags_render_bruteforce", "ags_scene_tree_cost", "ags_scene_set_rebuild_ratio",
+    "ags_render_bruteforce", "ags_scene_tree_cost", "ags_scene_set_rebuild_ratio", "ags_context_set_retry_capacity",
 ]
 
 
@@ -96,11 +96,12 @@ class ags_render_options(ctypes.Structure):
 
 class ags_launch_config(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("rays_per_lane", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("ms", ctypes.c_float)]
+                ("ms", ctypes.c_float), ("stack_depth", ctypes.c_int32)]
 
     def as_dict(self):
         return {"tile_w": self.tile_w, "tile_h": 32 * self.rays_per_lane // self.tile_w,
-                "rays_per_lane": self.rays_per_lane, "blocks_per_sm": self.blocks_per_sm, "ms": self.ms}
+                "rays_per_lane": self.rays_per_lane, "blocks_per_sm": self.blocks_per_sm, "ms": self.ms,
+                "stack_depth": self.stack_depth}
 
 
 class ags_server_config(ctypes.Structure):
@@ -177,6 +178,7 @@ def lib() -> ctypes.CDLL:
         "ags_scene_stats": (i32, [vp, i32, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "ags_scene_node_bytes": (i32, [vp]),
         "ags_context_set_traversal_cap": (i32, [vp, i32]),
+        "ags_context_set_retry_capacity": (i32, [vp, i32]),
         "ags_transform_vertices_noalloc": (i32, [vp, vp, i32, vp, i32, vp, vp, vp]),
         "ags_autotune": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), vp, vp, vp, i32,
                                ctypes.POINTER(ags_launch_config)]),
@@ -279,6 +281,11 @@ def ags_context_set_traversal_cap(ctx: int, max_node_visits: int) -> None:
 
 
 # ---------------------------------------------------------------- scene
+
+def ags_context_set_retry_capacity(ctx: int, rays: int) -> None:
+    """Rays a short-stack render may hand to its full-stack retry pass (0..1048576)."""
+    _check(lib().ags_context_set_retry_capacity(ctx, int(rays)), "ags_context_set_retry_capacity")
+
 def ags_scene_build(ctx: int, batch, build_flags: int = AGS_BVH_FP32) -> int:
     """Build per-environment BVHs from a ``scenes.SceneBatch`` (host arrays)."""
     verts = np.ascontiguousarray(batch.vertices, np.float32)
@@ -462,11 +469,12 @@ def ags_autotune(ctx: int, scene: int, spec, sensor_poses, out_depth, out_seg, r
     return best
 
 
-def ags_set_launch_config(ctx: int, scene: int, spec, tile_w=None, rays_per_lane=1, blocks_per_sm=0) -> None:
+def ags_set_launch_config(ctx: int, scene: int, spec, tile_w=None, rays_per_lane=1, blocks_per_sm=0,
+                          stack_depth=0) -> None:
     """Set the launch shape for this scene and sensor shape (tile_w None clears it)."""
     s = make_spec(spec)
     cfg = None if tile_w is None else ctypes.byref(ags_launch_config(int(tile_w), int(rays_per_lane),
-                                                                     int(blocks_per_sm), 0.0))
+                                                                     int(blocks_per_sm), 0.0, int(stack_depth)))
     _check(lib().ags_set_launch_config(ctx, scene, ctypes.byref(s), cfg), "ags_set_launch_config")
 
 

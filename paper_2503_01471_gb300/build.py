@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libags.so")
-SOURCES = ["capi.cu", "build.cu", "ploc.cu", "radix_sort.cu", "trace.cu", "trace_extra.cu", "trace_inst.cu", "instanced.cu", "validate.cu", "brute.cu", "server.cu"]
+SOURCES = ["capi.cu", "build.cu", "ploc.cu", "radix_sort.cu", "trace.cu", "trace_short.cu", "trace_extra.cu", "trace_inst.cu", "instanced.cu", "validate.cu", "brute.cu", "server.cu"]
 HEADERS = [os.path.join(CSRC, "internal.cuh"), os.path.join(CSRC, "trace_kernel.cuh"), os.path.join(ROOT, "include", "ags.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -93,7 +93,7 @@ unsigned int* tile_counter(ags_context* ctx, cudaStream_t s) {
   return p;
 }
 
-ags_launch_config default_config() { return {8, 1, 0, 0.0f}; }
+ags_launch_config default_config() { return {8, 1, 0, 0.0f, 0}; }
 
 ags_launch_config lookup_config(const ags_scene* sc, const ags_sensor_spec* spec) {
   auto it = sc->launch.find({spec->type, spec->width, spec->height});
@@ -109,6 +109,10 @@ ags_status check_config(ags_context* ctx, const ags_launch_config* c) {
                    "(8,2) (16,2) (16,4)");
   if (c->blocks_per_sm < 0 || c->blocks_per_sm > max_blocks_per_sm(ctx))
     return invalid("blocks_per_sm must be 0 .. the kernel's occupancy limit");
+  if (c->stack_depth != 0 && c->stack_depth != 16 && c->stack_depth != 32 && c->stack_depth != 64)
+    return invalid("stack_depth must be 0 (64), 16, 32 or 64");
+  if ((c->stack_depth == 16 || c->stack_depth == 32) && (c->tile_w != 8 || c->rays_per_lane != 1))
+    return invalid("a short stack (16 or 32) renders with the 8x4 tile");
   return AGS_OK;
 }
 
@@ -150,6 +154,10 @@ ags_status fill_trace_args(ags_context* ctx, const ags_scene* sc, const ags_sens
   while ((1 << lw) < cfg.tile_w) ++lw;
   a.log2_tile_w = lw;
   a.rays_per_lane = cfg.rays_per_lane;
+  a.stack_depth = (sc->objects || cfg.stack_depth == 0) ? 64 : cfg.stack_depth;
+  a.retry_list = ctx->d_retry_list;
+  a.retry_count = ctx->d_retry_count;
+  a.retry_cap = ctx->retry_cap;
   a.tile_h = 32 * cfg.rays_per_lane / cfg.tile_w;
   a.sensor = sensor_params(spec, cfg.tile_w, a.tile_h);
   int64_t total = (int64_t)a.sensor.tiles_per_env * n;
@@ -174,6 +182,14 @@ ags_status launch(ags_context* ctx, TraceArgs& a, cudaStream_t s, bool count, in
   if (a.total_tiles == 0) return AGS_OK;
   const int blocks = count ? ctx->trace_count_blocks
                            : (blocks_per_sm > 0 ? ctx->sm_count * blocks_per_sm : ctx->trace_blocks);
+  if (!count && a.stack_depth < 64 && !a.slots && !a.extra && !a.instanced) {
+    // short stack: its overflows go to the retry list, walked again with the full stack
+    e = cudaMemsetAsync(a.retry_count, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(retry count)");
+    e = launch_trace_short(a, blocks, ctx->sm_count * 4, s);
+    if (e != cudaSuccess) return cuda_fail(e, "k_trace_short launch");
+    return AGS_OK;
+  }
   e = launch_trace(a, blocks, count, s);
   if (e != cudaSuccess) return cuda_fail(e, "k_trace launch");
   return AGS_OK;
@@ -223,11 +239,14 @@ ags_status ags_context_create(int device, ags_context** out) {
   if ((e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking)) != cudaSuccess ||
       (e = cudaMalloc(&ctx->d_status, sizeof(int))) != cudaSuccess ||
       (e = cudaMalloc(&ctx->d_counts, 3 * sizeof(unsigned long long))) != cudaSuccess ||
+      (e = cudaMalloc(&ctx->d_retry_list, (size_t)kRetryAlloc * sizeof(int64_t))) != cudaSuccess ||
+      (e = cudaMalloc(&ctx->d_retry_count, sizeof(unsigned int))) != cudaSuccess ||
       (e = cudaMemset(ctx->d_status, 0, sizeof(int))) != cudaSuccess) {
     ags_status st = cuda_fail(e, "context setup");
     ags_context_destroy(ctx);
     return st;
   }
+  ctx->retry_cap = kRetryAlloc;
   ctx->trace_blocks = ctx->sm_count * trace_blocks_per_sm(false);
   ctx->trace_count_blocks = ctx->sm_count * trace_blocks_per_sm(true);
   *out = ctx;
@@ -242,6 +261,8 @@ void ags_context_destroy(ags_context* ctx) {
   for (auto& kv : ctx->tile_counters) cudaFree(kv.second);
   cudaFree(ctx->d_status);
   cudaFree(ctx->d_counts);
+  cudaFree(ctx->d_retry_list);
+  cudaFree(ctx->d_retry_count);
   cudaFree(ctx->stage);
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -251,6 +272,13 @@ ags_status ags_context_set_traversal_cap(ags_context* ctx, int32_t max_node_visi
   if (!ctx) return invalid("ctx is NULL");
   if (max_node_visits < 1) return invalid("max_node_visits must be >= 1");
   ctx->max_node_visits = max_node_visits;
+  return AGS_OK;
+}
+
+ags_status ags_context_set_retry_capacity(ags_context* ctx, int32_t rays) {
+  if (!ctx) return invalid("ctx is NULL");
+  if (rays < 0 || rays > kRetryAlloc) return invalid("rays must be in [0, 1048576]");
+  ctx->retry_cap = rays;
   return AGS_OK;
 }
 
@@ -862,8 +890,9 @@ ags_status ags_set_launch_config(ags_context* ctx, const ags_scene* sc, const ag
     return AGS_OK;
   }
   if ((st = check_config(ctx, config)) != AGS_OK) return st;
-  if (sc->objects && (config->tile_w != 8 || config->rays_per_lane != 1))
-    return invalid("two-level scenes render with the 8x4 tile");
+  if (sc->objects && (config->tile_w != 8 || config->rays_per_lane != 1 ||
+                      (config->stack_depth != 0 && config->stack_depth != 64)))
+    return invalid("two-level scenes render with the 8x4 tile and the full stack");
   sc->launch[{spec->type, spec->width, spec->height}] = *config;
   return AGS_OK;
   AGS_API_END
@@ -928,6 +957,45 @@ ags_status ags_autotune(ags_context* ctx, const ags_scene* sc, const ags_sensor_
       // more than 1% faster, so near ties (within run-to-run noise) keep it
       if (top.ms < 0.0f || c.ms < 0.99f * top.ms) top = c;
     }
+  }
+  // the stack depth: the 8x4 tile with 32 and 16 stack entries (rays that need more are walked again with
+  // 64, so results do not change); a candidate whose retry list overflowed is skipped
+  for (int sd : {32, 16}) {
+    if (st != AGS_OK || sc->objects) break;
+    ags_launch_config c = {8, 1, 0, 0.0f, sd};
+    TraceArgs a{};
+    if ((st = fill_trace_args(ctx, sc, spec, sc->n_envs, nullptr, poses, depth, seg, a, c)) != AGS_OK) break;
+    if ((st = launch(ctx, a, s, false, 0)) != AGS_OK) break;
+    unsigned int listed = 0;
+    if ((e = cudaMemcpyAsync(&listed, ctx->d_retry_count, sizeof(unsigned int), cudaMemcpyDeviceToHost, s)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+      st = cuda_fail(e, "autotune retry count");
+      break;
+    }
+    if (listed > (unsigned int)ctx->retry_cap) {
+      int word = 0;  // clear the overflow this candidate reported
+      if ((e = cudaMemcpy(&word, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+          (e = cudaMemset(ctx->d_status, 0, sizeof(int))) != cudaSuccess) {
+        st = cuda_fail(e, "autotune status");
+        break;
+      }
+      continue;
+    }
+    if ((e = cudaEventRecord(e0, s)) != cudaSuccess) {
+      st = cuda_fail(e, "cudaEventRecord");
+      break;
+    }
+    for (int r = 0; r < repeats && st == AGS_OK; ++r) st = launch(ctx, a, s, false, 0);
+    if (st != AGS_OK) break;
+    float ms = 0.0f;
+    if ((e = cudaEventRecord(e1, s)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+        (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) {
+      st = cuda_fail(e, "autotune timing");
+      break;
+    }
+    c.ms = ms / repeats;
+    if (c.ms < 0.99f * top.ms) top = c;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

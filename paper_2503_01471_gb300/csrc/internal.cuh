@@ -58,6 +58,7 @@ constexpr int kTriFloat4 = 3;
 constexpr int kStatusStackOverflow = 1;
 constexpr int kStatusIterationCap = 2;
 constexpr int kStatusBadIndex = 4;
+constexpr int32_t kRetryAlloc = 1 << 20;  // retry-list entries each context holds (8 MiB)
 constexpr int kStatusBadPose = 8;
 
 // ----------------------------------------------------------------- scene
@@ -103,6 +104,10 @@ struct ags_context {
   std::map<cudaStream_t, unsigned int*> tile_counters;
   int trace_blocks = 0;                // persistent grid size
   int32_t max_node_visits = 1 << 20;   // per-ray traversal cap
+  // short-stack renders: rays whose stack ran out, walked again with the full stack
+  int64_t* d_retry_list = nullptr;
+  unsigned int* d_retry_count = nullptr;
+  int32_t retry_cap = 0;               // in use (<= the allocated kRetryAlloc)
   int trace_count_blocks = 0;
   // staging for ags_render_host
   void* stage = nullptr;
@@ -299,6 +304,10 @@ struct TraceArgs {
   int32_t n_slots;
   const int32_t* slot_header;  // slot mode: when non-null, {n_slots, total_tiles} are read here (device)
   int32_t log2_tile_w, tile_h, rays_per_lane;  // a warp's tile: (1 << log2_tile_w) x tile_h pixels
+  int32_t stack_depth;       // plain renders: 16 or 32 walk with a short stack (its overflows retried); else 64
+  int64_t* retry_list;       // short stack: output index of every ray to walk again with the full stack
+  unsigned int* retry_count;
+  int32_t retry_cap;
   int64_t total_tiles;
   int32_t max_visits;
   unsigned int* tile_counter;
@@ -308,6 +317,9 @@ struct TraceArgs {
 cudaError_t launch_trace(const TraceArgs& a, int blocks, bool count, cudaStream_t s);
 cudaError_t launch_trace_extra(const TraceArgs& a, int blocks, cudaStream_t s);  // a.extra != 0
 cudaError_t launch_trace_inst(const TraceArgs& a, int blocks, cudaStream_t s);   // a.instanced != 0
+// a plain render with a short stack (a.stack_depth 16 or 32, 8x4 tiles) and its retry pass; the caller has
+// zeroed *a.retry_count on the stream
+cudaError_t launch_trace_short(const TraceArgs& a, int blocks, int retry_blocks, cudaStream_t s);
 // compiled launch shapes of the render kernel: {tile width, rays per lane}
 constexpr int kTraceShapes = 7;
 constexpr int kTraceShape[kTraceShapes][2] = {{8, 1}, {4, 1}, {8, 2}, {16, 2}, {16, 4}, {16, 1}, {32, 1}};

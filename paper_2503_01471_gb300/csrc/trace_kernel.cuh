@@ -510,7 +510,7 @@ __device__ __forceinline__ int64_t slot_out(const TraceArgs& a, const SensorPara
 // others pushed, farthest deepest), else the nearest stacked node still
 // within the cull distance. Returns -1 when the ray is done; sets `failed`
 // (and the status word) on an out-of-range triangle range or a full stack.
-template <bool kCount, int kFmt, bool kChannels>
+template <bool kCount, int kFmt, bool kChannels, int kStack = kStackSize>
 __device__ __forceinline__ int32_t visit_node(const TraceArgs& a, const Ray& r, int32_t node, float& t_best,
                                               int32_t& best_id, int32_t& best_seg, int32_t& best_k, int2* stack,
                                               int& sp, bool& failed, unsigned long long& n_tris) {
@@ -558,8 +558,10 @@ __device__ __forceinline__ int32_t visit_node(const TraceArgs& a, const Ray& r, 
     const uint32_t kfar = kx ^ kmin;
     const uint32_t key_cull = __float_as_uint(t_best * kCullSlack);
     if ((kfar & ~7u) <= key_cull) {
-      if (sp >= kStackSize) {
-        atomicOr(status, kStatusStackOverflow);
+      if (sp >= kStack) {
+        // the full stack reports an overflow; a short one marks the ray for the full-stack retry pass
+        if (kStack == kStackSize) atomicOr(status, kStatusStackOverflow);
+        else sp = kStack + 1;
         failed = true;
         return -1;
       }
@@ -591,8 +593,9 @@ __device__ __forceinline__ int32_t visit_node(const TraceArgs& a, const Ray& r, 
 #pragma unroll
     for (int k = 7; k >= 1; --k) {
       if (keys[k] != 0xFFFFFFFFu && (keys[k] & ~7u) <= key_cull) {
-        if (sp >= kStackSize) {
-          atomicOr(status, kStatusStackOverflow);
+        if (sp >= kStack) {
+          if (kStack == kStackSize) atomicOr(status, kStatusStackOverflow);
+          else sp = kStack + 1;
           failed = true;
         } else {
           stack[sp++] = make_int2(child_base + (int32_t)(keys[k] & 7u), (int32_t)(keys[k] & ~7u));
@@ -684,10 +687,43 @@ __device__ __forceinline__ void resolve_hit(const SensorParams& sen, bool failed
   }
 }
 
+// a4-a6 for one ray: the nearest-hit walk of environment env's BVH from its
+// root. On return `failed` says whether a limit stopped it; with a short
+// stack (kStack < kStackSize), sp == kStack + 1 says the stack ran out.
+template <bool kCount, int kFmt, bool kChannels, int kStack>
+__device__ __forceinline__ void walk_ray(const TraceArgs& a, const Ray& r, int32_t env, float& t_best,
+                                         int32_t& best_id, int32_t& best_seg, int32_t& best_k, int2* stack, int& sp,
+                                         bool& failed, unsigned long long& n_nodes, unsigned long long& n_tris) {
+  int32_t* __restrict__ status = a.status;
+  int32_t node = __ldg(a.env_root + env);
+  int visits = 0;
+  sp = 0;
+  failed = false;
+  while (node >= 0) {
+    if (++visits > a.max_visits) {
+      atomicOr(status, kStatusIterationCap);
+      failed = true;
+      break;
+    }
+    if (node >= a.n_nodes) {
+      atomicOr(status, kStatusBadIndex);
+      failed = true;
+      break;
+    }
+    if (kCount) ++n_nodes;
+    node = visit_node<kCount, kFmt, kChannels, kStack>(a, r, node, t_best, best_id, best_seg, best_k, stack, sp,
+                                                       failed, n_tris);
+    if (failed) break;
+  }
+}
+
 // The rays of one warp tile: sensor shape `sen`, environment `env`, tile
 // index t_in within it; `slot` locates the pose and the outputs (the
 // environment's index in the launch, or the request's slot in the table).
-template <bool kCount, int kTileW, int kRaysPerLane, bool kSlots, int kFmt, int kExtra>
+// A short stack (kStack < kStackSize, plain renders only) hands each ray
+// that outgrows it to the retry list, which k_trace_retry walks again with
+// the full stack; such a ray writes no output here.
+template <bool kCount, int kTileW, int kRaysPerLane, bool kSlots, int kFmt, int kExtra, int kStack = kStackSize>
 __device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParams& sen, int32_t env, int32_t t_in,
                                            int32_t slot, int lane, int2* stack, unsigned long long& n_nodes,
                                            unsigned long long& n_tris, unsigned long long& n_rays) {
@@ -722,29 +758,25 @@ __device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParam
   // ---- a4-a6: traversal, triangle tests, nearest hit
   float t_best = sen.max_range;  // camera: depth limit; LiDAR: range limit (unit direction)
   int32_t best_id = 0x7fffffff, best_seg = -1, best_k = -1;
-  int32_t node = __ldg(a.env_root + env);
-  int sp = 0, visits = 0;
-  bool failed = false;
-  while (node >= 0) {
-    if (++visits > a.max_visits) {
-      atomicOr(status, kStatusIterationCap);
-      failed = true;
-      break;
-    }
-    if (node >= a.n_nodes) {
-      atomicOr(status, kStatusBadIndex);
-      failed = true;
-      break;
-    }
-    if (kCount) ++n_nodes;
-    node = visit_node<kCount, kFmt, (kExtra & kExtraChannels) != 0>(a, r, node, t_best, best_id, best_seg, best_k,
-                                                                    stack, sp, failed, n_tris);
-    if (failed) break;
-  }
+  int sp;
+  bool failed;
+  walk_ray<kCount, kFmt, (kExtra & kExtraChannels) != 0, kStack>(a, r, env, t_best, best_id, best_seg, best_k, stack,
+                                                                  sp, failed, n_nodes, n_tris);
 
   if (kCount) {
     ++n_rays;
     continue;
+  }
+  if constexpr (kStack < kStackSize) {
+    if (sp > kStack) {
+      // the short stack ran out: the full-stack retry pass renders this ray
+      const unsigned int i = atomicAdd(a.retry_count, 1u);
+      if (i < (unsigned int)a.retry_cap) {
+        a.retry_list[i] = slot_out<kSlots>(a, sen, slot) + (int64_t)row * W + col;
+        continue;
+      }
+      atomicOr(status, kStatusStackOverflow);  // the retry list is full: reported like an overflow
+    }
   }
   float v;
   int32_t seg;
@@ -807,13 +839,12 @@ __device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParam
   }  // rays of this lane in the tile
 }
 
-// kSlots: each tile belongs to one slot of a table (serving: every request has
-// its own environment, sensor shape, pose and output offset); otherwise all
-// environments of the launch share one sensor shape.
-template <bool kCount, int kTileW, int kRaysPerLane, bool kSlots, int kFmt, int kExtra = 0>
-__global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) k_trace(const TraceArgs a) {
+// The persistent tile loop of the render kernels: each warp takes tiles from
+// the global counter until none is left.
+template <bool kCount, int kTileW, int kRaysPerLane, bool kSlots, int kFmt, int kExtra, int kStack>
+__device__ __forceinline__ void run_tiles(const TraceArgs& a) {
   const int lane = threadIdx.x & 31;
-  int2 stack[kStackSize];
+  int2 stack[kStack];
   unsigned long long n_nodes = 0, n_tris = 0, n_rays = 0;
   int64_t total_tiles = a.total_tiles;
   int32_t n_slots = a.n_slots;
@@ -856,11 +887,11 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) k_trace(const 
       continue;
     }
     if constexpr (kSlots) {
-      trace_tile<kCount, kTileW, kRaysPerLane, true, kFmt, kExtra>(a, a.specs[slot_spec], env, t_in, slot, lane,
-                                                                   stack, n_nodes, n_tris, n_rays);
+      trace_tile<kCount, kTileW, kRaysPerLane, true, kFmt, kExtra, kStack>(a, a.specs[slot_spec], env, t_in, slot,
+                                                                           lane, stack, n_nodes, n_tris, n_rays);
     } else {
-      trace_tile<kCount, kTileW, kRaysPerLane, false, kFmt, kExtra>(a, a.sensor, env, t_in, slot, lane, stack,
-                                                                    n_nodes, n_tris, n_rays);
+      trace_tile<kCount, kTileW, kRaysPerLane, false, kFmt, kExtra, kStack>(a, a.sensor, env, t_in, slot, lane,
+                                                                            stack, n_nodes, n_tris, n_rays);
     }
   }
   if (kCount) {
@@ -878,6 +909,57 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) k_trace(const 
   }
 }
 
+// kSlots: each tile belongs to one slot of a table (serving: every request has
+// its own environment, sensor shape, pose and output offset); otherwise all
+// environments of the launch share one sensor shape.
+template <bool kCount, int kTileW, int kRaysPerLane, bool kSlots, int kFmt, int kExtra = 0>
+__global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) k_trace(const TraceArgs a) {
+  run_tiles<kCount, kTileW, kRaysPerLane, kSlots, kFmt, kExtra, kStackSize>(a);
+}
+
+// The plain render (8x4 tiles) with a kStack-entry stack; rays that need more
+// go to the retry list (a short stack is a tuning choice: results are those
+// of the full stack).
+template <int kFmt, int kStack>
+__global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) k_trace_short(const TraceArgs a) {
+  run_tiles<false, 8, 1, false, kFmt, 0, kStack>(a);
+}
+
+// The retry pass after k_trace_short: one thread per listed ray, walked with
+// the full stack, output written as k_trace would.
+template <int kFmt>
+__global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) k_trace_retry(const TraceArgs a) {
+  const SensorParams& sen = a.sensor;
+  const unsigned int n = min(*a.retry_count, (unsigned int)a.retry_cap);
+  const int64_t per = (int64_t)sen.W * sen.H;
+  int2 stack[kStackSize];
+  unsigned long long no_count = 0;
+  for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int64_t o = a.retry_list[i];
+    const int32_t slot = (int32_t)(o / per);
+    const int32_t pix = (int32_t)(o - (int64_t)slot * per);
+    const int32_t row = pix / sen.W, col = pix - row * sen.W;
+    const int32_t env = a.env_ids ? __ldg(a.env_ids + slot) : slot;
+    Ray r;
+    float R[9], lx, ly, lz;
+    if (slot < 0 || slot >= a.n || (unsigned)env >= (unsigned)a.n_scene_envs ||
+        !make_ray<false>(sen, a.poses + 7 * (int64_t)slot, row, col, r, R, lx, ly, lz)) {
+      atomicOr(a.status, kStatusBadIndex);  // the first pass listed only rays it could cast
+      continue;
+    }
+    float t_best = sen.max_range;
+    int32_t best_id = 0x7fffffff, best_seg = -1, best_k = -1;
+    int sp;
+    bool failed;
+    walk_ray<false, kFmt, false, kStackSize>(a, r, env, t_best, best_id, best_seg, best_k, stack, sp, failed, no_count,
+                                             no_count);
+    float v;
+    int32_t seg;
+    resolve_hit(sen, failed, t_best, best_id, best_seg, v, seg);
+    a.out_depth[o] = v;
+    a.out_seg[o] = seg;
+  }
+}
 
 }  // namespace
 

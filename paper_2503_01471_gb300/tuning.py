@@ -30,7 +30,8 @@ def autotune_cached(ctx: int, scene: int, spec, sensor_poses, out_depth, out_seg
             cache = json.load(fh)
     if key in cache:
         c = cache[key]
-        ags_set_launch_config(ctx, scene, spec, int(c["tile_w"]), int(c["rays_per_lane"]), int(c["blocks_per_sm"]))
+        ags_set_launch_config(ctx, scene, spec, int(c["tile_w"]), int(c["rays_per_lane"]), int(c["blocks_per_sm"]),
+                              int(c.get("stack_depth", 0)))
         return dict(c, cached=True)
     c = ags_autotune(ctx, scene, spec, sensor_poses, out_depth, out_seg, repeats).as_dict()
     cache[key] = c

@@ -66,7 +66,7 @@ def test_struct_layouts_match_the_header():
     assert ctypes.sizeof(ags.ags_hit_channels) == 32
     assert ctypes.sizeof(ags.ags_stereo) == 16
     assert ctypes.sizeof(ags.ags_render_options) == 24
-    assert ctypes.sizeof(ags.ags_launch_config) == 16
+    assert ctypes.sizeof(ags.ags_launch_config) == 20
     assert ctypes.sizeof(ags.ags_server_config) == 40
 
 

@@ -421,6 +421,75 @@ def test_compressed_nodes_bit_exact_on_lidar_forest_and_launch_shapes(ctx, fmt):
         ags.ags_scene_destroy(ref_scene)
 
 
+@pytest.mark.parametrize("fmt", ["fp32", "fp16", "q8"])
+def test_short_stack_retries_give_the_full_stack_results(ctx, fmt):
+    """A 16- or 32-entry stack hands every ray that outgrows it to the full-stack retry pass: images equal the
+    full stack's bit for bit (LiDAR forests, whose long beams do outgrow 16 entries, and rooms), also for an
+    env subset and a captured step graph. With no room in the retry list the outgrown rays report NaN and the
+    status says so, which shows the retry pass is what renders them."""
+    flag = {"fp32": 0, "fp16": ags.AGS_BVH_FP16, "q8": ags.AGS_BVH_Q8}[fmt]
+    batch, spec, poses = S.lidar_forests(2, steps=1, trees=(180, 200))  # dense: some beams need > 16 entries
+    spec.width = 256
+    scene = ags.ags_scene_build(ctx, batch, flag | ags.AGS_SPLIT_CELLS(64))
+    try:
+        ref = render(ctx, scene, spec, poses[0])
+        for depth in (16, 32, 64):
+            ags.ags_set_launch_config(ctx, scene, spec, 8, 1, 0, depth)
+            assert ags.ags_get_launch_config(ctx, scene, spec)["stack_depth"] == depth
+            out = render(ctx, scene, spec, poses[0])
+            assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1]), depth
+        ags.ags_set_launch_config(ctx, scene, spec, 8, 1, 0, 16)
+        ids = torch.tensor([1], dtype=torch.int32, device="cuda")
+        p = torch.as_tensor(poses[0][[1]]).cuda()
+        d = torch.empty((1, spec.height, spec.width), device="cuda")
+        sg = torch.empty((1, spec.height, spec.width), dtype=torch.int32, device="cuda")
+        ags.ags_render_envs(ctx, scene, spec, ids, p, d, sg)
+        ags.ags_stream_status(ctx)
+        assert np.array_equal(d.cpu().numpy(), ref[0][[1]]) and np.array_equal(sg.cpu().numpy(), ref[1][[1]])
+        gp = torch.as_tensor(poses[0]).cuda()
+        gd = torch.empty((2, spec.height, spec.width), device="cuda")
+        gs = torch.empty((2, spec.height, spec.width), dtype=torch.int32, device="cuda")
+        g = ags.ags_render_graph_create(ctx, scene, spec, gp, gd, gs)
+        try:
+            gd.fill_(-1.0)
+            ags.ags_render_graph_launch(g)
+            ags.ags_stream_status(ctx)
+            assert np.array_equal(gd.cpu().numpy(), ref[0]) and np.array_equal(gs.cpu().numpy(), ref[1])
+        finally:
+            ags.ags_render_graph_destroy(g)
+        ags.ags_context_set_retry_capacity(ctx, 0)
+        try:
+            p2 = torch.as_tensor(poses[0]).cuda()
+            d2 = torch.empty((2, spec.height, spec.width), device="cuda")
+            s2 = torch.empty((2, spec.height, spec.width), dtype=torch.int32, device="cuda")
+            ags.ags_render(ctx, scene, spec, p2, d2, s2)
+            with pytest.raises(ags.AgsError) as ei:
+                ags.ags_stream_status(ctx)
+            assert ei.value.status == ags.AGS_ERR_TRAVERSAL_LIMIT
+            lost = torch.isnan(d2).cpu().numpy()
+            assert lost.any() and not lost.all()
+            keep = ~lost
+            assert np.array_equal(d2.cpu().numpy()[keep], ref[0][keep])
+        finally:
+            ags.ags_context_set_retry_capacity(ctx, 1 << 20)
+        for bad in ((4, 1, 0, 16), (8, 1, 0, 8), (8, 1, 0, 48)):
+            with pytest.raises(ags.AgsError):
+                ags.ags_set_launch_config(ctx, scene, spec, *bad)
+    finally:
+        ags.ags_scene_destroy(scene)
+    # rooms: the short stacks rarely run out; same images
+    batch, spec, poses = S.obstacle_rooms(3, steps=1, width=70, height=45)
+    scene = ags.ags_scene_build(ctx, batch, flag)
+    try:
+        ref = render(ctx, scene, spec, poses[0])
+        for depth in (16, 32):
+            ags.ags_set_launch_config(ctx, scene, spec, 8, 1, 0, depth)
+            out = render(ctx, scene, spec, poses[0])
+            assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1]), depth
+    finally:
+        ags.ags_scene_destroy(scene)
+
+
 def test_update_poses_refit_and_rebuild_match_a_fresh_build(ctx):
     """Moving the obstacles by refit or by rebuild gives exactly the images of a scene built with the new
     poses (the traversal is exact, so the tree shape cannot change a result), and they match the oracle."""
