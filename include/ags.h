@@ -121,8 +121,12 @@ typedef struct {
  * greedy collapse. Results are identical either way. */
 #define AGS_BUILD_GREEDY_COLLAPSE (1u << 22)
 /* Two-level scene: every object (sub-mesh) gets its own BVH, built once in its
- * own frame, and each environment a small BVH over its objects' world boxes;
- * rays are moved into an object's frame to walk its BVH. ags_scene_update_poses
+ * own frame without reference splitting (the flags' splitting setting applies
+ * to nothing here), and each environment a small BVH over its objects' world
+ * boxes (an object whose box has at least a quarter of its environment's box
+ * surface, such as a room around the others, enters it as the children of its
+ * root, each under its own box); rays are moved into an object's frame to walk
+ * its BVH. ags_scene_update_poses
  * then only rebuilds the small top level (either mode). Float32 nodes only; at
  * most 65536 objects; renders through ags_render / ags_render_envs /
  * ags_render_host / step graphs with the 8x4 tile; not with extra channels,

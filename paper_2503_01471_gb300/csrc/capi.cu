@@ -136,6 +136,7 @@ ags_status fill_trace_args(ags_context* ctx, const ags_scene* sc, const ags_sens
     a.obj_tris = sc->objects->d.tris;
     a.obj_n_nodes = (int32_t)sc->objects->n_nodes;
     a.obj_n_tris = (int32_t)sc->objects->n_refs;
+    a.parts = sc->top->d_parts;
   } else {
     a.nodes = sc->d.nodes;
     a.node_format = sc->node_format;

@@ -93,6 +93,16 @@ struct InstanceDev {
 };
 static_assert(sizeof(InstanceDev) == 64, "InstanceDev layout");
 
+// One entry of a two-level scene's top level: a part of object j's BVH that
+// the top level holds under its own world box (the object's root, or one
+// child of the root when the root is opened into the top level). node >= 0:
+// the walk starts at that node of the object-level pool; node < 0: the part
+// is a leaf, triangles leaf_start .. leaf_start + leaf_cnt - 1 of the pool.
+struct ObjPart {
+  double box[6];  // object-frame bounds
+  int32_t node, leaf_start, leaf_cnt;
+};
+
 }  // namespace ags
 
 struct ags_context {
@@ -149,6 +159,10 @@ struct ags_scene {
   ags::InstanceDev* d_inst = nullptr;  // [J]
   int32_t* d_env_sub = nullptr;        // [E+1]
   std::vector<double> h_obj_box;       // [J][6] object-frame bounds of each object's vertices
+  std::vector<ags::ObjPart> h_parts;   // the top level's entries of every object, object-major
+  std::vector<int64_t> h_part_off;     // [J+1]
+  int4* d_parts = nullptr;             // top level of a two-level scene: per leaf reference {object, node,
+                                       // leaf start, leaf count}, in leaf order
   // AGS_UPDATE_AUTO: surface-area cost of the float32 tree as built (tree_cost; -1 when not measured)
   // and the multiple of it above which a refitted tree is rebuilt instead
   double tree_cost_built = -1.0;
@@ -294,6 +308,7 @@ struct TraceArgs {
   const void* obj_nodes;     // object-level pool (float32 nodes)
   const float4* obj_tris;
   int32_t obj_n_nodes, obj_n_tris;
+  const int4* parts;         // per top-level leaf reference: {object, node, leaf start, leaf count}
   float baseline[3];         // stereo: second sensor's origin in the sensor frame
   float shadow_eps;          // stereo: the shadow segment starts at this fraction
   int32_t n;                 // environments rendered

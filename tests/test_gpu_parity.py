@@ -970,6 +970,38 @@ def test_two_level_scene_updates_and_limits(ctx):
         ags.ags_scene_destroy(two)
 
 
+def test_two_level_opened_roots(ctx):
+    """Objects whose box spans their environment have their roots opened into the top level: a sphere of
+    1280 triangles around the sensor (its root's children are inner nodes) and a room (its root's children
+    are leaves), each with smaller objects inside, turned and moved; every ray against the oracle."""
+    rng = np.random.default_rng(41)
+    sv, sf = S.icosphere(4.0, 3)
+    rv, rf = S.room()
+    inner = [(*S.box(0.6, 0.8, 1.0), np.array([1.5, 0.2, 0.3, *S.random_unit_quat(rng)], np.float32), 2),
+             (*S.icosphere(0.5, 2), np.array([-1.0, 1.2, -0.4, 0, 0, 0, 1], np.float32), 3)]
+    turned = np.array([0.1, -0.2, 0.05, *S.random_unit_quat(rng)], np.float32)
+    room_inner = [(*S.box(1.0, 0.5, 0.7), np.array([2.0, 1.0, 1.5, *S.random_unit_quat(rng)], np.float32), 2)]
+    batch = S.scene_from_lists([[(sv, sf, S.IDENTITY_POSE, 1)] + inner, [(sv, sf, turned, 1)] + inner,
+                                [(rv, rf, S.IDENTITY_POSE, 0)] + room_inner])
+    spec = S.pinhole(64, 48, 100.0, 0.1, 12.0)
+    poses = np.array([[0, 0, 0, 0, 0, 0, 1], [0.3, 0.1, -0.2, *S.random_unit_quat(rng)],
+                      [-1.0, -2.0, 2.0, *S.quat_from_euler_zyx(0.4, 0.1, 0.0)]], np.float32)
+    two = ags.ags_scene_build(ctx, batch, ags.AGS_BUILD_INSTANCED)
+    try:
+        d, s = render(ctx, two, spec, poses)
+        assert (s >= 0).all()  # closed sphere and room: every ray hits
+        check_all(batch, spec, poses, d, s, tag="two-level opened roots 64x48")
+        cur = batch.poses.copy()
+        cur[:, :3] += rng.normal(0, 0.05, (cur.shape[0], 3)).astype(np.float32)
+        ags.ags_scene_update_poses(ctx, two, cur, ags.AGS_UPDATE_REBUILD)
+        moved = S.SceneBatch(batch.vertices, batch.indices, batch.sub_vert, batch.sub_tri, batch.sub_seg,
+                             batch.env_sub, cur.copy())
+        d, s = render(ctx, two, spec, poses)
+        check_all(moved, spec, poses, d, s, tag="two-level opened roots after a move")
+    finally:
+        ags.ags_scene_destroy(two)
+
+
 def test_two_level_empty_and_tiny(ctx):
     tri = (np.array([[3, -3, -3], [3, 3, -3], [3, 0, 3]], np.float32), np.array([[0, 1, 2]], np.int32),
            S.IDENTITY_POSE, 7)
