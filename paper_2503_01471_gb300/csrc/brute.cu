@@ -27,7 +27,11 @@ __global__ void k_copy_env(const int32_t* __restrict__ leaf_tri, int32_t R, cons
   vals[k] = (uint32_t)k;
 }
 
-__global__ void k_brute(const TraceArgs a, const int32_t* __restrict__ env_ref, const uint32_t* __restrict__ copies) {
+constexpr int kBruteThreads = 256;
+
+__global__ void __launch_bounds__(kBruteThreads) k_brute(const TraceArgs a, const int32_t* __restrict__ env_ref,
+                                                         const uint32_t* __restrict__ copies) {
+  __shared__ float4 s_frames[kBruteThreads * 3];
   const SensorParams& sen = a.sensor;
   const int64_t per = (int64_t)sen.W * sen.H;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -42,6 +46,7 @@ __global__ void k_brute(const TraceArgs a, const int32_t* __restrict__ env_ref, 
   }
   const float* P = a.poses + 7 * (int64_t)slot;
   Ray r;
+  r.frame = s_frames + 3 * threadIdx.x;
   float R[9], lx, ly, lz;
   if (!make_ray<false>(sen, P, row, col, r, R, lx, ly, lz)) {
     atomicOr(a.status, kStatusBadPose);
@@ -101,7 +106,7 @@ cudaError_t launch_brute(const TraceArgs& a, const int32_t* env_ref_dev, const i
   }
   const int64_t n = (int64_t)a.sensor.W * a.sensor.H * a.n;
   if (n == 0) return cudaSuccess;
-  k_brute<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, env_ref_dev, vals);
+  k_brute<<<(unsigned)((n + kBruteThreads - 1) / kBruteThreads), kBruteThreads, 0, s>>>(a, env_ref_dev, vals);
   return cudaGetLastError();
 }
 

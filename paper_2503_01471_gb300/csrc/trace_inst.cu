@@ -18,10 +18,11 @@ __device__ __forceinline__ void test_object_triangle(const Ray& r, const float4*
   const float4 a = __ldg(tris + 3 * (int64_t)k);
   const float4 b = __ldg(tris + 3 * (int64_t)k + 1);
   const float4 c = __ldg(tris + 3 * (int64_t)k + 2);
+  const float4 f[3] = {r.frame[0], r.frame[1], r.frame[2]};
   float Ax, Ay, Az, Bx, By, Bz, Cx, Cy, Cz;
-  shear(r, a, Ax, Ay, Az);
-  shear(r, b, Bx, By, Bz);
-  shear(r, c, Cx, Cy, Cz);
+  shear(f, a, Ax, Ay, Az);
+  shear(f, b, Bx, By, Bz);
+  shear(f, c, Cx, Cy, Cz);
   const float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
   const float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
   const float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
@@ -124,10 +125,10 @@ __device__ __forceinline__ void object_ray(const InstanceDev* I, float ox, float
   for (int k = 0; k < 9; ++k) rt[k] = __ldg(&I->rt[k]);
   const float ax = __fsub_rn(ox, __ldg(&I->p[0])), ay = __fsub_rn(oy, __ldg(&I->p[1])),
               az = __fsub_rn(oz, __ldg(&I->p[2]));
-  r.ox = __fmaf_rn(rt[2], az, __fmaf_rn(rt[1], ay, __fmul_rn(rt[0], ax)));
-  r.oy = __fmaf_rn(rt[5], az, __fmaf_rn(rt[4], ay, __fmul_rn(rt[3], ax)));
-  r.oz = __fmaf_rn(rt[8], az, __fmaf_rn(rt[7], ay, __fmul_rn(rt[6], ax)));
-  setup_ray(r, __fmaf_rn(rt[2], dz, __fmaf_rn(rt[1], dy, __fmul_rn(rt[0], dx))),
+  setup_ray(r, __fmaf_rn(rt[2], az, __fmaf_rn(rt[1], ay, __fmul_rn(rt[0], ax))),
+            __fmaf_rn(rt[5], az, __fmaf_rn(rt[4], ay, __fmul_rn(rt[3], ax))),
+            __fmaf_rn(rt[8], az, __fmaf_rn(rt[7], ay, __fmul_rn(rt[6], ax))),
+            __fmaf_rn(rt[2], dz, __fmaf_rn(rt[1], dy, __fmul_rn(rt[0], dx))),
             __fmaf_rn(rt[5], dz, __fmaf_rn(rt[4], dy, __fmul_rn(rt[3], dx))),
             __fmaf_rn(rt[8], dz, __fmaf_rn(rt[7], dy, __fmul_rn(rt[6], dx))));
 }
@@ -208,7 +209,7 @@ __device__ __forceinline__ void walk_part(const TraceArgs& a, const int4 part, c
 // same object) and walks the part. Stack entries: an inner node (>= 0) or
 // part q (-2 - q). Nearest hit, ties, clamping and misses as in trace_tile.
 __device__ __forceinline__ void trace_tile_inst(const TraceArgs& a, const SensorParams& sen, int32_t env,
-                                                int32_t t_in, int32_t slot, int lane, int2* stack) {
+                                                int32_t t_in, int32_t slot, int lane, int2* stack, float4* frames) {
   constexpr int kTileW = 8, kTileH = 4;
   const int32_t col = (t_in % sen.tiles_x) * kTileW + (lane % kTileW);
   const int32_t row = (t_in / sen.tiles_x) * kTileH + (lane / kTileW);
@@ -227,17 +228,16 @@ __device__ __forceinline__ void trace_tile_inst(const TraceArgs& a, const Sensor
   float lx, ly, lz, dx, dy, dz;
   sensor_dir<false>(sen, row, col, lx, ly, lz);
   rotate(R, lx, ly, lz, dx, dy, dz);
-  Ray r;
-  r.ox = px;
-  r.oy = py;
-  r.oz = pz;
-  setup_ray(r, dx, dy, dz);
+  Ray r;  // the world ray meets only the top level's boxes
+  r.frame = nullptr;
+  setup_ray<false>(r, px, py, pz, dx, dy, dz);
 
   float t_best = sen.max_range;
   int32_t best_id = 0x7fffffff, best_seg = -1;
   int32_t e = __ldg(a.env_root + env);
   const int32_t j0 = __ldg(a.env_sub + env), j1 = __ldg(a.env_sub + env + 1);
   Ray ro;                       // the ray in the frame of object cur_j
+  ro.frame = frames;
   int32_t cur_j = -1, tri_base = 0;
   int sp = 0, visits = 0;
   bool failed = false;
@@ -341,6 +341,9 @@ __device__ __forceinline__ void trace_tile_inst(const TraceArgs& a, const Sensor
 __global__ void __launch_bounds__(kTraceThreads, 7) k_trace_inst(const TraceArgs a) {
   const int lane = threadIdx.x & 31;
   int2 stack[kStackSize];
+  // each thread's slot for the triangle-test constants of its ray in an object's frame
+  __shared__ float4 s_frames[kTraceThreads * 3];
+  float4* frames = s_frames + 3 * threadIdx.x;
   while (true) {
     unsigned int tile = 0;
     if (lane == 0) tile = atomicAdd(a.tile_counter, 1u);
@@ -353,7 +356,7 @@ __global__ void __launch_bounds__(kTraceThreads, 7) k_trace_inst(const TraceArgs
       if (lane == 0) atomicOr(a.status, kStatusBadIndex);
       continue;
     }
-    trace_tile_inst(a, a.sensor, env, t_in, slot, lane, stack);
+    trace_tile_inst(a, a.sensor, env, t_in, slot, lane, stack, frames);
   }
 }
 

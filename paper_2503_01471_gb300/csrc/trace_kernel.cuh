@@ -35,7 +35,6 @@ constexpr float kCullSlack = 1.0f + 2.44140625e-4f;
 constexpr float kSlabEps = 4.0f * 5.96046448e-8f;
 
 struct Ray {
-  float ox, oy, oz;
   float ix, iy, iz;          // 1 / direction
   float cnx, cny, cnz;       // near-bound constants: -o/d, lowered
   float cfx, cfy, cfz;       // far-bound constants: -o/d, raised
@@ -43,8 +42,10 @@ struct Ray {
   // the inverse direction and the near / far constants again, each held twice as a register pair for the
   // packed arithmetic of the float32 node test (two children per instruction)
   float2 ix2, iy2, iz2, cnx2, cfx2, cny2, cfy2, cnz2, cfz2;
-  // watertight test: rows of the shear that maps (v - o) to the ray's frame
-  float m0x, m0y, m0z, m1x, m1y, m1z, m2x, m2y, m2z;
+  // the watertight test's constants, in this thread's slot of shared memory (three float4: the rows of the
+  // shear that maps v - o to the ray's frame, each with one origin coordinate in w). They are read only by
+  // triangle tests, so keeping them out of registers leaves the traversal more registers.
+  float4* frame;
 };
 
 __device__ __forceinline__ float nonzero(float d) {
@@ -92,14 +93,18 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
   return r;
 }
 
-__device__ __forceinline__ void setup_ray(Ray& r, float dx, float dy, float dz) {
+// The ray o + t d: its slab constants in registers and (kTri) its
+// triangle-test constants in r.frame, which the caller points at the
+// thread's slot. A ray that only meets boxes skips the latter.
+template <bool kTri = true>
+__device__ __forceinline__ void setup_ray(Ray& r, float ox, float oy, float oz, float dx, float dy, float dz) {
   dx = nonzero(dx);
   dy = nonzero(dy);
   dz = nonzero(dz);
   r.ix = 1.0f / dx;
   r.iy = 1.0f / dy;
   r.iz = 1.0f / dz;
-  const float px = -r.ox * r.ix, py = -r.oy * r.iy, pz = -r.oz * r.iz;
+  const float px = -ox * r.ix, py = -oy * r.iy, pz = -oz * r.iz;
   const float ex = kSlabEps * fabsf(px), ey = kSlabEps * fabsf(py), ez = kSlabEps * fabsf(pz);
   r.cnx = px - ex;
   r.cfx = px + ex;
@@ -120,6 +125,7 @@ __device__ __forceinline__ void setup_ray(Ray& r, float dx, float dy, float dz) 
   r.onx = r.ix >= 0.0f ? 1 : 3;
   r.ony = r.iy >= 0.0f ? 5 : 7;
   r.onz = r.iz >= 0.0f ? 9 : 11;
+  if (!kTri) return;
   // watertight shear: z axis = largest |d| component, x/y the next two in
   // cyclic order (swapped when d_z < 0 to keep the winding)
   const float ax = fabsf(dx), ay = fabsf(dy), az = fabsf(dz);
@@ -135,15 +141,13 @@ __device__ __forceinline__ void setup_ray(Ray& r, float dx, float dy, float dz) 
   const float dkx = kx == 0 ? dx : (kx == 1 ? dy : dz);
   const float dky = ky == 0 ? dx : (ky == 1 ? dy : dz);
   const float Sx = dkx / dkz, Sy = dky / dkz, Sz = 1.0f / dkz;
-  r.m0x = (kx == 0 ? 1.0f : 0.0f) - (kz == 0 ? Sx : 0.0f);
-  r.m0y = (kx == 1 ? 1.0f : 0.0f) - (kz == 1 ? Sx : 0.0f);
-  r.m0z = (kx == 2 ? 1.0f : 0.0f) - (kz == 2 ? Sx : 0.0f);
-  r.m1x = (ky == 0 ? 1.0f : 0.0f) - (kz == 0 ? Sy : 0.0f);
-  r.m1y = (ky == 1 ? 1.0f : 0.0f) - (kz == 1 ? Sy : 0.0f);
-  r.m1z = (ky == 2 ? 1.0f : 0.0f) - (kz == 2 ? Sy : 0.0f);
-  r.m2x = kz == 0 ? Sz : 0.0f;
-  r.m2y = kz == 1 ? Sz : 0.0f;
-  r.m2z = kz == 2 ? Sz : 0.0f;
+  r.frame[0] = make_float4((kx == 0 ? 1.0f : 0.0f) - (kz == 0 ? Sx : 0.0f),
+                           (kx == 1 ? 1.0f : 0.0f) - (kz == 1 ? Sx : 0.0f),
+                           (kx == 2 ? 1.0f : 0.0f) - (kz == 2 ? Sx : 0.0f), ox);
+  r.frame[1] = make_float4((ky == 0 ? 1.0f : 0.0f) - (kz == 0 ? Sy : 0.0f),
+                           (ky == 1 ? 1.0f : 0.0f) - (kz == 1 ? Sy : 0.0f),
+                           (ky == 2 ? 1.0f : 0.0f) - (kz == 2 ? Sy : 0.0f), oy);
+  r.frame[2] = make_float4(kz == 0 ? Sz : 0.0f, kz == 1 ? Sz : 0.0f, kz == 2 ? Sz : 0.0f, oz);
 }
 
 // Watertight ray/triangle test (Woop, Benthin, Wald 2013), two-sided with
@@ -152,11 +156,11 @@ __device__ __forceinline__ void setup_ray(Ray& r, float dx, float dy, float dz) 
 // function is an explicitly rounded difference of two rounded products, so a
 // shared edge gives exactly opposite values in its two triangles and no ray
 // slips between them.
-__device__ __forceinline__ void shear(const Ray& r, const float4 v, float& X, float& Y, float& Z) {
-  const float ax = __fsub_rn(v.x, r.ox), ay = __fsub_rn(v.y, r.oy), az = __fsub_rn(v.z, r.oz);
-  X = __fmaf_rn(r.m0x, ax, __fmaf_rn(r.m0y, ay, __fmul_rn(r.m0z, az)));
-  Y = __fmaf_rn(r.m1x, ax, __fmaf_rn(r.m1y, ay, __fmul_rn(r.m1z, az)));
-  Z = __fmaf_rn(r.m2x, ax, __fmaf_rn(r.m2y, ay, __fmul_rn(r.m2z, az)));
+__device__ __forceinline__ void shear(const float4* f, const float4 v, float& X, float& Y, float& Z) {
+  const float ax = __fsub_rn(v.x, f[0].w), ay = __fsub_rn(v.y, f[1].w), az = __fsub_rn(v.z, f[2].w);
+  X = __fmaf_rn(f[0].x, ax, __fmaf_rn(f[0].y, ay, __fmul_rn(f[0].z, az)));
+  Y = __fmaf_rn(f[1].x, ax, __fmaf_rn(f[1].y, ay, __fmul_rn(f[1].z, az)));
+  Z = __fmaf_rn(f[2].x, ax, __fmaf_rn(f[2].y, ay, __fmul_rn(f[2].z, az)));
 }
 
 template <bool kChannels>
@@ -165,10 +169,11 @@ __device__ __forceinline__ void test_triangle(const Ray& r, const float4* __rest
   const float4 a = __ldg(tris + 3 * (int64_t)k);
   const float4 b = __ldg(tris + 3 * (int64_t)k + 1);
   const float4 c = __ldg(tris + 3 * (int64_t)k + 2);
+  const float4 f[3] = {r.frame[0], r.frame[1], r.frame[2]};
   float Ax, Ay, Az, Bx, By, Bz, Cx, Cy, Cz;
-  shear(r, a, Ax, Ay, Az);
-  shear(r, b, Bx, By, Bz);
-  shear(r, c, Cx, Cy, Cz);
+  shear(f, a, Ax, Ay, Az);
+  shear(f, b, Bx, By, Bz);
+  shear(f, c, Cx, Cy, Cz);
   const float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
   const float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
   const float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
@@ -200,10 +205,11 @@ __device__ __forceinline__ void hit_barycentrics(const Ray& r, const float4* __r
   const float4 a = __ldg(tris + 3 * (int64_t)k);
   const float4 b = __ldg(tris + 3 * (int64_t)k + 1);
   const float4 c = __ldg(tris + 3 * (int64_t)k + 2);
+  const float4 f[3] = {r.frame[0], r.frame[1], r.frame[2]};
   float Ax, Ay, Az, Bx, By, Bz, Cx, Cy, Cz;
-  shear(r, a, Ax, Ay, Az);
-  shear(r, b, Bx, By, Bz);
-  shear(r, c, Cx, Cy, Cz);
+  shear(f, a, Ax, Ay, Az);
+  shear(f, b, Bx, By, Bz);
+  shear(f, c, Cx, Cy, Cz);
   const float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
   const float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
   const float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
@@ -376,10 +382,11 @@ __device__ __forceinline__ bool segment_hits(const Ray& r, const float4* __restr
   const float4 a = __ldg(tris + 3 * (int64_t)k);
   const float4 b = __ldg(tris + 3 * (int64_t)k + 1);
   const float4 c = __ldg(tris + 3 * (int64_t)k + 2);
+  const float4 f[3] = {r.frame[0], r.frame[1], r.frame[2]};
   float Ax, Ay, Az, Bx, By, Bz, Cx, Cy, Cz;
-  shear(r, a, Ax, Ay, Az);
-  shear(r, b, Bx, By, Bz);
-  shear(r, c, Cx, Cy, Cz);
+  shear(f, a, Ax, Ay, Az);
+  shear(f, b, Bx, By, Bz);
+  shear(f, c, Cx, Cy, Cz);
   const float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
   const float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
   const float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
@@ -403,12 +410,10 @@ __device__ __forceinline__ bool segment_hits(const Ray& r, const float4* __restr
 // Limits set the status word and `failed`.
 template <int kFmt>
 __device__ bool occluded(const TraceArgs& a, int32_t env, float px, float py, float pz, float dx, float dy, float dz,
-                         float t0, float t1, int2* stack, bool& failed) {
+                         float t0, float t1, int2* stack, float4* frame, bool& failed) {
   Ray r;
-  r.ox = px;
-  r.oy = py;
-  r.oz = pz;
-  setup_ray(r, dx, dy, dz);
+  r.frame = frame;
+  setup_ray(r, px, py, pz, dx, dy, dz);
   int32_t node = __ldg(a.env_root + env);
   int sp = 0, visits = 0;
   const float t_cull = kCullSlack;
@@ -655,12 +660,9 @@ __device__ __forceinline__ bool make_ray(const SensorParams& sen, const float* P
   if (!pose_rotation(P, R)) return false;
   sensor_dir<kTable>(sen, row, col, lx, ly, lz);
   if (kTable && (!isfinite(lx + ly + lz) || (lx == 0.0f && ly == 0.0f && lz == 0.0f))) return false;
-  r.ox = __ldg(P);
-  r.oy = __ldg(P + 1);
-  r.oz = __ldg(P + 2);
   float dx, dy, dz;
   rotate(R, lx, ly, lz, dx, dy, dz);
-  setup_ray(r, dx, dy, dz);
+  setup_ray(r, __ldg(P), __ldg(P + 1), __ldg(P + 2), dx, dy, dz);
   return true;
 }
 
@@ -725,8 +727,9 @@ __device__ __forceinline__ void walk_ray(const TraceArgs& a, const Ray& r, int32
 // the full stack; such a ray writes no output here.
 template <bool kCount, int kTileW, int kRaysPerLane, bool kSlots, int kFmt, int kExtra, int kStack = kStackSize>
 __device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParams& sen, int32_t env, int32_t t_in,
-                                           int32_t slot, int lane, int2* stack, unsigned long long& n_nodes,
-                                           unsigned long long& n_tris, unsigned long long& n_rays) {
+                                           int32_t slot, int lane, int2* stack, float4* frames,
+                                           unsigned long long& n_nodes, unsigned long long& n_tris,
+                                           unsigned long long& n_rays) {
   constexpr int kTileH = 32 * kRaysPerLane / kTileW;
   int32_t* __restrict__ status = a.status;
   const int32_t tile_x0 = (t_in % sen.tiles_x) * kTileW;
@@ -743,6 +746,7 @@ __device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParam
   // (L1-resident) so that nothing of it stays live during the traversal
   const float* P = slot_pose<kSlots>(a, slot);
   Ray r;
+  r.frame = frames;
   float R[9], lx, ly, lz;
   if (!make_ray<(kExtra & kExtraTable) != 0>(sen, P, row, col, r, R, lx, ly, lz)) {
     // a pose (or table row) the method cannot use: flag it and report NaN for this ray
@@ -789,12 +793,13 @@ __device__ __forceinline__ void trace_tile(const TraceArgs& a, const SensorParam
       float dwx, dwy, dwz, bwx, bwy, bwz;
       rotate(R, sx, sy, sz, dwx, dwy, dwz);
       rotate(R, a.baseline[0], a.baseline[1], a.baseline[2], bwx, bwy, bwz);
-      const float px = r.ox, py = r.oy, pz = r.oz;
+      const float px = frames[0].w, py = frames[1].w, pz = frames[2].w;
       const float Px = __fmaf_rn(t_best, dwx, px), Py = __fmaf_rn(t_best, dwy, py), Pz = __fmaf_rn(t_best, dwz, pz);
       const float o2x = __fadd_rn(px, bwx), o2y = __fadd_rn(py, bwy), o2z = __fadd_rn(pz, bwz);
       bool sfail = false;
       const bool shadowed = occluded<kFmt>(a, env, o2x, o2y, o2z, __fsub_rn(Px, o2x), __fsub_rn(Py, o2y),
-                                           __fsub_rn(Pz, o2z), 0.0f, __fsub_rn(1.0f, a.shadow_eps), stack, sfail);
+                                           __fsub_rn(Pz, o2z), 0.0f, __fsub_rn(1.0f, a.shadow_eps), stack,
+                                           frames + 3, sfail);
       if (sfail) {
         failed = true;
         v = __int_as_float(0x7fc00000);
@@ -845,6 +850,10 @@ template <bool kCount, int kTileW, int kRaysPerLane, bool kSlots, int kFmt, int 
 __device__ __forceinline__ void run_tiles(const TraceArgs& a) {
   const int lane = threadIdx.x & 31;
   int2 stack[kStack];
+  // each thread's slot for its ray's triangle-test constants (a second one for the stereo shadow ray)
+  constexpr int kFrames = (kExtra & kExtraShadow) ? 2 : 1;
+  __shared__ float4 s_frames[kTraceThreads * 3 * kFrames];
+  float4* frames = s_frames + 3 * kFrames * threadIdx.x;
   unsigned long long n_nodes = 0, n_tris = 0, n_rays = 0;
   int64_t total_tiles = a.total_tiles;
   int32_t n_slots = a.n_slots;
@@ -888,10 +897,11 @@ __device__ __forceinline__ void run_tiles(const TraceArgs& a) {
     }
     if constexpr (kSlots) {
       trace_tile<kCount, kTileW, kRaysPerLane, true, kFmt, kExtra, kStack>(a, a.specs[slot_spec], env, t_in, slot,
-                                                                           lane, stack, n_nodes, n_tris, n_rays);
+                                                                           lane, stack, frames, n_nodes, n_tris,
+                                                                           n_rays);
     } else {
       trace_tile<kCount, kTileW, kRaysPerLane, false, kFmt, kExtra, kStack>(a, a.sensor, env, t_in, slot, lane,
-                                                                            stack, n_nodes, n_tris, n_rays);
+                                                                            stack, frames, n_nodes, n_tris, n_rays);
     }
   }
   if (kCount) {
@@ -933,6 +943,7 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) k_trace_retry(
   const unsigned int n = min(*a.retry_count, (unsigned int)a.retry_cap);
   const int64_t per = (int64_t)sen.W * sen.H;
   int2 stack[kStackSize];
+  __shared__ float4 s_frames[kTraceThreads * 3];
   unsigned long long no_count = 0;
   for (unsigned int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int64_t o = a.retry_list[i];
@@ -941,6 +952,7 @@ __global__ void __launch_bounds__(kTraceThreads, kTraceMinBlocks) k_trace_retry(
     const int32_t row = pix / sen.W, col = pix - row * sen.W;
     const int32_t env = a.env_ids ? __ldg(a.env_ids + slot) : slot;
     Ray r;
+    r.frame = s_frames + 3 * threadIdx.x;
     float R[9], lx, ly, lz;
     if (slot < 0 || slot >= a.n || (unsigned)env >= (unsigned)a.n_scene_envs ||
         !make_ray<false>(sen, a.poses + 7 * (int64_t)slot, row, col, r, R, lx, ly, lz)) {
