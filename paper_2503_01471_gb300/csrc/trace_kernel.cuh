@@ -551,16 +551,18 @@ __device__ __forceinline__ int32_t visit_node(const TraceArgs& a, const Ray& r, 
   const int n_inner = __popc(inner_hits);
   if (n_inner == 1) return child_base + (__ffs(inner_hits) - 1);  // the common case: no ordering needed
   if (n_inner == 2) {
-    // two children: the nearer is taken, the farther pushed (keys: tmin bits, slot in the low 3 bits)
-    uint32_t kmin = 0xFFFFFFFFu, kx = 0u;
+    // two children: the nearer is taken, the farther pushed (keys: tmin bits, slot in the low 3 bits); their
+    // entry distances picked out by slot with selects (keeping tmins in registers)
+    const int k1 = __ffs(inner_hits) - 1, k2 = 31 - __clz(inner_hits);
+    float t1 = tmins[0], t2 = tmins[0];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const uint32_t key = (__float_as_uint(tmins[k]) & ~7u) | (uint32_t)k;
-      const bool v = (inner_hits >> k) & 1u;
-      kmin = v ? min(kmin, key) : kmin;
-      kx ^= v ? key : 0u;
+    for (int k = 1; k < 8; ++k) {
+      t1 = k == k1 ? tmins[k] : t1;
+      t2 = k == k2 ? tmins[k] : t2;
     }
-    const uint32_t kfar = kx ^ kmin;
+    const uint32_t key1 = (__float_as_uint(t1) & ~7u) | (uint32_t)k1;
+    const uint32_t key2 = (__float_as_uint(t2) & ~7u) | (uint32_t)k2;
+    const uint32_t kmin = min(key1, key2), kfar = max(key1, key2);
     const uint32_t key_cull = __float_as_uint(t_best * kCullSlack);
     if ((kfar & ~7u) <= key_cull) {
       if (sp >= kStack) {
