@@ -154,7 +154,7 @@ def rooflines(counters, ms_step, b_ray, rays, hbm, peak_kind, sm_count, mhz, nod
     The BVHs and triangles of an environment stay in L1/L2 while all SMs work on it, so what bounds the kernel
     is instruction issue, not DRAM: the lead block is the issue roofline (warp instructions per launch from the
     committed ncu capture of this kernel and these sources, per second, against SMs x 4 x max clock), with the
-    DRAM traffic of that capture beside it. The algorithmic block is the survey's B_ray roofline: nodes and
+    DRAM traffic of that capture beside it. The algorithmic block is the B_ray roofline: the bytes of nodes and
     triangles a ray fetches, per second, against the HBM copy bandwidth; it exceeds 1 because those bytes are
     served mostly from L1/L2."""
     algo_gbs = b_ray * rays / (ms_step * 1e-3) / 1e9
