@@ -120,6 +120,13 @@ typedef struct {
  * largest child until eight slots). The Morton radix tree always uses the
  * greedy collapse. Results are identical either way. */
 #define AGS_BUILD_GREEDY_COLLAPSE (1u << 22)
+/* Search radius of the clustering (bits 23-24): each round every cluster
+ * looks for its partner among r positions on either side in Morton order,
+ * r = 16 (the default), 32, 64 or 128. A wider search finds pairs of smaller
+ * union boxes, so a tree of lower surface-area cost, at a cost per round
+ * proportional to r. Results are identical for every radius. */
+#define AGS_CLUSTER_RADIUS(r) \
+  ((uint32_t)((r) >= 128 ? 3u : ((r) >= 64 ? 2u : ((r) >= 32 ? 1u : 0u))) << 23)
 /* Two-level scene: every object (sub-mesh) gets its own BVH, built once in its
  * own frame without reference splitting (the flags' splitting setting applies
  * to nothing here), and each environment a small BVH over its objects' world
@@ -394,6 +401,20 @@ ags_status ags_scene_validate(const ags_scene* scene, int64_t counts[4]);
 ags_status ags_autotune_build(ags_context* ctx, ags_scene* scene, const ags_sensor_spec* spec,
                               const float* sensor_poses_dev, float* out_depth_dev, int32_t* out_seg_dev,
                               const uint32_t* split_cells, int32_t n_cells, int32_t repeats, uint32_t* best_cells);
+
+/*
+ * ags_autotune_build_flags -- the same tuning over whole build settings: each
+ * of the n_flags candidates (at most 64) is a build_flags word as for
+ * ags_scene_build (node format, leaf size, splitting, clustering radius,
+ * builder bits; not AGS_BUILD_INSTANCED), built and timed as above; the
+ * fastest BVH, the scene's own included, is kept and *best_flags receives its
+ * flags. A candidate with unknown bits is refused (AGS_ERR_INVALID_ARG)
+ * before anything is built. ags_autotune_build is this call over the scene's
+ * flags with each listed splitting setting.
+ */
+ags_status ags_autotune_build_flags(ags_context* ctx, ags_scene* scene, const ags_sensor_spec* spec,
+                                    const float* sensor_poses_dev, float* out_depth_dev, int32_t* out_seg_dev,
+                                    const uint32_t* flags, int32_t n_flags, int32_t repeats, uint32_t* best_flags);
 
 /*
  * ags_autotune -- time the render of `scene` with `spec` under each compiled

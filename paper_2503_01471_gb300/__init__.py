@@ -50,6 +50,11 @@ def AGS_LEAF_SIZE(n: int) -> int:
 def AGS_SPLIT_CELLS(n: int) -> int:
     return (int(n) & 0xFF) << 12
 
+
+def AGS_CLUSTER_RADIUS(r: int) -> int:
+    r = int(r)
+    return (3 if r >= 128 else 2 if r >= 64 else 1 if r >= 32 else 0) << 23
+
 # every symbol declared in include/ags.h
 EXPORTS = [
     "ags_context_create", "ags_context_destroy", "ags_scene_build", "ags_scene_destroy", "ags_render",
@@ -62,6 +67,7 @@ EXPORTS = [
     "ags_render_graph_destroy", "ags_render_channels", "ags_render_ex", "ags_autotune_build", "ags_scene_validate",
     "ags_server_cancel", "ags_test_sort_pairs", "ags_test_exclusive_scan", "ags_context_device",
     "ags_render_bruteforce", "ags_scene_tree_cost", "ags_scene_set_rebuild_ratio", "ags_context_set_retry_capacity",
+    "ags_autotune_build_flags",
 ]
 
 
@@ -213,6 +219,8 @@ def lib() -> ctypes.CDLL:
         "ags_test_exclusive_scan": (i32, [vp, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)]),
         "ags_autotune_build": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), vp, vp, vp,
                                      ctypes.POINTER(ctypes.c_uint32), i32, i32, ctypes.POINTER(ctypes.c_uint32)]),
+        "ags_autotune_build_flags": (i32, [vp, vp, ctypes.POINTER(ags_sensor_spec), vp, vp, vp,
+                                           ctypes.POINTER(ctypes.c_uint32), i32, i32, ctypes.POINTER(ctypes.c_uint32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -635,6 +643,19 @@ def ags_autotune_build(ctx: int, scene: int, spec, sensor_poses, out_depth, out_
     best = ctypes.c_uint32()
     _check(lib().ags_autotune_build(ctx, scene, ctypes.byref(s), _ptr(sensor_poses), _ptr(out_depth), _ptr(out_seg),
                                     c, len(split_cells), int(repeats), ctypes.byref(best)), "ags_autotune_build")
+    return int(best.value)
+
+
+def ags_autotune_build_flags(ctx: int, scene: int, spec, sensor_poses, out_depth, out_seg, flags,
+                             repeats: int = 2) -> int:
+    """Rebuild the scene with each candidate build_flags word, keep the fastest BVH; returns its flags."""
+    s = make_spec(spec)
+    _render_buffers(s, ags_scene_n_envs(scene), sensor_poses, out_depth, out_seg)
+    c = (ctypes.c_uint32 * max(len(flags), 1))(*[int(x) for x in flags])
+    best = ctypes.c_uint32()
+    _check(lib().ags_autotune_build_flags(ctx, scene, ctypes.byref(s), _ptr(sensor_poses), _ptr(out_depth),
+                                          _ptr(out_seg), c, len(flags), int(repeats), ctypes.byref(best)),
+           "ags_autotune_build_flags")
     return int(best.value)
 
 

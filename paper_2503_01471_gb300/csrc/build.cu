@@ -1048,7 +1048,8 @@ ags_status build_scene(ags_context* ctx, ags_scene* sc, const float* base_verts_
     std::vector<int32_t> roots;
     if (!(sc->flags & AGS_BUILD_GREEDY_COLLAPSE)) AGS_CHECK(tmp.alloc(&d_choice, (size_t)R));
     ags_status st = build_ploc(d_keys, d_vals, R, key_shift, d_env_ref, E, d_ref_box, d_leaf_box, d_left, d_right,
-                               d_first, d_last, d_inner_box, roots, s, d_choice, leaf_max);
+                               d_first, d_last, d_inner_box, roots, s, d_choice, leaf_max,
+                               16 << ((sc->flags >> 23) & 3u));
     if (st != AGS_OK) return st;
     for (QueueItem& q : q0) {
       if (q.ref < 0) continue;  // a single reference: the leaf keeps its position

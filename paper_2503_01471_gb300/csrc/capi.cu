@@ -292,7 +292,9 @@ ags_status ags_scene_build(ags_context* ctx, const ags_env_mesh* envs, int32_t n
   if (!envs) return invalid("envs is NULL");
   if (n_envs < 1 || n_envs > 65536) return invalid("n_envs must be in [1, 65536]");
   if ((build_flags & 0xFFu) > AGS_BVH_Q8) return invalid("unsupported BVH node format in build_flags");
-  if ((build_flags & ~(0xFFFFFu | AGS_BUILD_LBVH | AGS_BUILD_INSTANCED | AGS_BUILD_GREEDY_COLLAPSE)) != 0) return invalid("unknown bits in build_flags");
+  if ((build_flags & ~(0xFFFFFu | AGS_BUILD_LBVH | AGS_BUILD_INSTANCED | AGS_BUILD_GREEDY_COLLAPSE |
+                       AGS_CLUSTER_RADIUS(128))) != 0)
+    return invalid("unknown bits in build_flags");
   if ((build_flags & AGS_BUILD_INSTANCED) && (build_flags & 0xFFu) != AGS_BVH_FP32)
     return invalid("two-level scenes use float32 nodes");
   if (((build_flags >> 8) & 0xFu) > (uint32_t)kMaxLeafTris) return invalid("leaf size must be 1..4");
@@ -1118,43 +1120,68 @@ ags_status ags_test_exclusive_scan(ags_context* ctx, int32_t* data, int64_t n, i
   AGS_API_END
 }
 
-ags_status ags_autotune_build(ags_context* ctx, ags_scene* sc, const ags_sensor_spec* spec, const float* poses,
-                              float* depth, int32_t* seg, const uint32_t* cells, int32_t n_cells, int32_t repeats,
-                              uint32_t* best_cells) {
+ags_status ags_autotune_build_flags(ags_context* ctx, ags_scene* sc, const ags_sensor_spec* spec, const float* poses,
+                                    float* depth, int32_t* seg, const uint32_t* flags, int32_t n_flags, int32_t repeats,
+                                    uint32_t* best_flags) {
   AGS_API_BEGIN
   if (!ctx || !sc) return invalid("ctx or scene is NULL");
   if (sc->ctx != ctx) return invalid("scene belongs to another context");
-  if (sc->objects) return invalid("splitting tuning needs a single-level scene");
+  if (sc->objects) return invalid("build tuning needs a single-level scene");
   ags_status st = check_spec(spec, false);
   if (st != AGS_OK) return st;
-  if (!poses || !depth || !seg || !best_cells || (n_cells > 0 && !cells)) return invalid("NULL pointer argument");
-  if (n_cells < 0 || n_cells > 64) return invalid("n_cells must be in [0, 64]");
+  if (!poses || !depth || !seg || !best_flags || (n_flags > 0 && !flags)) return invalid("NULL pointer argument");
+  if (n_flags < 0 || n_flags > 64) return invalid("n_flags must be in [0, 64]");
   if (repeats < 1 || repeats > 1000) return invalid("repeats must be in [1, 1000]");
-  for (int32_t k = 0; k < n_cells; ++k)
-    if (cells[k] > 255u) return invalid("split cell counts must be in [0, 255]");
+  for (int32_t k = 0; k < n_flags; ++k) {
+    const uint32_t f = flags[k];
+    if ((f & 0xFFu) > AGS_BVH_Q8) return invalid("unsupported BVH node format in a candidate");
+    if ((f & ~(0xFFFFFu | AGS_BUILD_LBVH | AGS_BUILD_GREEDY_COLLAPSE | AGS_CLUSTER_RADIUS(128))) != 0)
+      return invalid("unknown bits in a candidate (two-level scenes are not tuned)");
+    if (((f >> 8) & 0xFu) > (uint32_t)kMaxLeafTris) return invalid("leaf size must be 1..4");
+  }
   if (sc->n_subs > 0 && sc->h_poses.size() != 7 * (size_t)sc->n_subs) return invalid("scene has no kept poses");
   DeviceGuard g(ctx->device);
-  const uint32_t split_mask = 0xFFu << 12;
-  const uint32_t current = (sc->flags >> 12) & 0xFFu;
   float best_ms = 0.0f;
   if ((st = time_render(ctx, sc, spec, poses, depth, seg, repeats, &best_ms)) != AGS_OK) return st;
-  uint32_t best = current;
+  uint32_t best = sc->flags;
   const float* h_poses = sc->n_subs > 0 ? sc->h_poses.data() : nullptr;
-  for (int32_t k = 0; k < n_cells; ++k) {
-    if (cells[k] == best) continue;
+  for (int32_t k = 0; k < n_flags; ++k) {
+    if (flags[k] == best) continue;
     ScenePtr cand;
-    st = rebuild_like(ctx, sc, h_poses, (sc->flags & ~split_mask) | (cells[k] << 12), cand);
+    st = rebuild_like(ctx, sc, h_poses, flags[k], cand);
     if (st == AGS_ERR_OUT_OF_MEMORY) continue;  // this setting does not fit beside the scene: skip it
     if (st != AGS_OK) return st;
     float ms = 0.0f;
     if ((st = time_render(ctx, cand.get(), spec, poses, depth, seg, repeats, &ms)) != AGS_OK) return st;
     if (ms < best_ms) {  // keep the faster BVH at once, so at most two are held during tuning
       best_ms = ms;
-      best = cells[k];
+      best = flags[k];
       adopt(sc, cand, false);
     }
   }
-  *best_cells = best;
+  *best_flags = best;
+  return AGS_OK;
+  AGS_API_END
+}
+
+ags_status ags_autotune_build(ags_context* ctx, ags_scene* sc, const ags_sensor_spec* spec, const float* poses,
+                              float* depth, int32_t* seg, const uint32_t* cells, int32_t n_cells, int32_t repeats,
+                              uint32_t* best_cells) {
+  AGS_API_BEGIN
+  if (!ctx || !sc) return invalid("ctx or scene is NULL");
+  if (sc->objects) return invalid("splitting tuning needs a single-level scene");
+  if (!best_cells || (n_cells > 0 && !cells)) return invalid("NULL pointer argument");
+  if (n_cells < 0 || n_cells > 64) return invalid("n_cells must be in [0, 64]");
+  for (int32_t k = 0; k < n_cells; ++k)
+    if (cells[k] > 255u) return invalid("split cell counts must be in [0, 255]");
+  // the scene's flags with each listed splitting setting
+  const uint32_t split_mask = 0xFFu << 12;
+  std::vector<uint32_t> cand((size_t)n_cells);
+  for (int32_t k = 0; k < n_cells; ++k) cand[k] = (sc->flags & ~split_mask) | (cells[k] << 12);
+  uint32_t best = 0;
+  ags_status st = ags_autotune_build_flags(ctx, sc, spec, poses, depth, seg, cand.data(), n_cells, repeats, &best);
+  if (st != AGS_OK) return st;
+  *best_cells = (best >> 12) & 0xFFu;
   return AGS_OK;
   AGS_API_END
 }

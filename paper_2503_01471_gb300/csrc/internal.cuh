@@ -231,7 +231,7 @@ struct DevBufs {
 ags_status build_ploc(const uint64_t* keys, uint32_t* vals, int32_t R, int key_shift, const int32_t* env_ref_off,
                       int32_t E, const Box* ref_box, Box* leaf_box, int32_t* left, int32_t* right, int32_t* first,
                       int32_t* last, Box* inner_box, std::vector<int32_t>& roots, cudaStream_t s,
-                      uint32_t* choice = nullptr, int leaf_max = 2);
+                      uint32_t* choice = nullptr, int leaf_max = 2, int radius = 16);
 
 // build.cu: world vertices v' = R(q) v + p of every sub-mesh (float-float, as the scene build)
 ags_status transform_vertices(const float* base_dev, int32_t V, const int32_t* sub_vert_off_dev, int32_t J,

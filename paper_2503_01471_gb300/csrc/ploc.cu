@@ -9,7 +9,9 @@
 // every cluster finds the cluster within `kRadius` positions (same
 // environment) whose union box has the smallest surface area; mutual nearest
 // pairs merge into a new inner node; the survivors are compacted in order.
-// Rounds repeat until each environment is one cluster. The tree is then laid
+// Rounds repeat until each environment is one cluster. The search radius is a
+// build option (16 by default; 32, 64 or 128): a wider search finds better
+// pairs at a proportional cost per round. The tree is then laid
 // out for the wide-node collapse: leaves reordered depth-first so that every
 // subtree covers a contiguous range of positions (first/last), as in a
 // Morton radix tree.
@@ -19,7 +21,6 @@ namespace ags {
 namespace {
 
 constexpr int kPlocThreads = 256;
-constexpr int kRadius = 16;
 
 __device__ __forceinline__ Box box_join(const Box& a, const Box& b) {
   return {fminf(a.lox, b.lox), fminf(a.loy, b.loy), fminf(a.loz, b.loz),
@@ -44,6 +45,7 @@ __global__ void k_ploc_init(const uint64_t* __restrict__ keys, const uint32_t* _
 // Nearest neighbour of each cluster among the kRadius positions on either
 // side in the same environment, by the surface area of the union box; ties
 // go to the smaller position, so the globally closest pair is always mutual.
+template <int kRadius>
 __global__ void __launch_bounds__(kPlocThreads) k_ploc_nn(const Box* __restrict__ c_box,
                                                           const int32_t* __restrict__ c_env, int32_t n,
                                                           int32_t* __restrict__ nn) {
@@ -272,7 +274,11 @@ int blocks_of(int64_t n, int t) { return (int)((n + t - 1) / t); }
 ags_status build_ploc(const uint64_t* keys, uint32_t* vals, int32_t R, int key_shift, const int32_t* env_ref_off,
                       int32_t E, const Box* ref_box, Box* leaf_box, int32_t* left, int32_t* right, int32_t* first,
                       int32_t* last, Box* inner_box, std::vector<int32_t>& roots, cudaStream_t s,
-                      uint32_t* choice, int leaf_max) {
+                      uint32_t* choice, int leaf_max, int radius) {
+  if (radius != 16 && radius != 32 && radius != 64 && radius != 128) {
+    set_error("clustering radius must be 16, 32, 64 or 128");
+    return AGS_ERR_INVALID_ARG;
+  }
   NvtxRange range("ags clustering");
   roots.assign(E, -1);
   if (R <= 0) return AGS_OK;
@@ -314,7 +320,11 @@ ags_status build_ploc(const uint64_t* keys, uint32_t* vals, int32_t R, int key_s
       set_error("clustering did not terminate");
       return AGS_ERR_CUDA;
     }
-    k_ploc_nn<<<blocks_of(n, kPlocThreads), kPlocThreads, 0, s>>>(c_box[cur], c_env[cur], n, nn);
+    const int nb = blocks_of(n, kPlocThreads);
+    if (radius == 16) k_ploc_nn<16><<<nb, kPlocThreads, 0, s>>>(c_box[cur], c_env[cur], n, nn);
+    else if (radius == 32) k_ploc_nn<32><<<nb, kPlocThreads, 0, s>>>(c_box[cur], c_env[cur], n, nn);
+    else if (radius == 64) k_ploc_nn<64><<<nb, kPlocThreads, 0, s>>>(c_box[cur], c_env[cur], n, nn);
+    else k_ploc_nn<128><<<nb, kPlocThreads, 0, s>>>(c_box[cur], c_env[cur], n, nn);
     k_ploc_flag<<<blocks_of(n, 256), 256, 0, s>>>(nn, n, flag);
     AGS_CHECK(cudaGetLastError());
     AGS_CHECK(exclusive_scan(flag, n, d_tot, scan_tmp, s));

@@ -57,6 +57,7 @@ def test_binding_constants_match_the_header():
     for name, val in consts.items():
         assert getattr(ags, name) == val, name
     assert ags.AGS_LEAF_SIZE(3) == 3 << 8 and ags.AGS_SPLIT_CELLS(64) == 64 << 12
+    assert [ags.AGS_CLUSTER_RADIUS(r) for r in (16, 32, 64, 128)] == [0, 1 << 23, 2 << 23, 3 << 23]
 
 
 def test_struct_layouts_match_the_header():
@@ -110,6 +111,8 @@ int main(void) {{
   printf("%d %d %d %d %d %d %d %d\\n", (int)sizeof(ags_submesh), (int)sizeof(ags_env_mesh),
          (int)sizeof(ags_sensor_spec), (int)sizeof(ags_hit_channels), (int)sizeof(ags_stereo),
          (int)sizeof(ags_render_options), (int)sizeof(ags_launch_config), (int)sizeof(ags_server_config));
+  printf("%u %u %u %u\\n", (unsigned)AGS_CLUSTER_RADIUS(16), (unsigned)AGS_CLUSTER_RADIUS(32),
+         (unsigned)AGS_CLUSTER_RADIUS(64), (unsigned)AGS_CLUSTER_RADIUS(128));
   return 0;
 }}
 """)
@@ -126,6 +129,8 @@ int main(void) {{
     assert [int(x) for x in out[2:10]] == [ctypes.sizeof(t) for t in (
         ags.ags_submesh, ags.ags_env_mesh, ags.ags_sensor_spec, ags.ags_hit_channels, ags.ags_stereo,
         ags.ags_render_options, ags.ags_launch_config, ags.ags_server_config)]
+    # the header's macros encode as the binding's helpers do
+    assert [int(x) for x in out[10:14]] == [ags.AGS_CLUSTER_RADIUS(r) for r in (16, 32, 64, 128)]
     if not torch.cuda.is_available():
         assert int(out[1]) != 0  # no device here: an error status
 

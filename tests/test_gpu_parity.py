@@ -327,6 +327,9 @@ def test_bit_exact_across_bvh_variants(ctx):
     # the greedy collapse instead of the least-cost slots
     variants += [ags.AGS_BUILD_GREEDY_COLLAPSE, ags.AGS_BUILD_GREEDY_COLLAPSE | ags.AGS_LEAF_SIZE(4),
                  ags.AGS_LEAF_SIZE(4) | ags.AGS_BVH_FP16]
+    # wider clustering searches
+    variants += [ags.AGS_CLUSTER_RADIUS(32), ags.AGS_CLUSTER_RADIUS(64) | ags.AGS_SPLIT_CELLS(64),
+                 ags.AGS_CLUSTER_RADIUS(128) | ags.AGS_BVH_Q8]
     for flags in variants:
         scene = ags.ags_scene_build(ctx, batch, flags)
         try:
@@ -891,6 +894,16 @@ def test_build_tuning_keeps_results_and_updates(ctx):
         assert np.array_equal(d1, d0) and np.array_equal(s1, s0)
         with pytest.raises(ags.AgsError):
             ags.ags_autotune_build(ctx, scene, spec, p, d, sg, (300,), 1)
+        # whole build settings: splitting, clustering radius, node format and leaf size at once
+        cands = [ags.AGS_CLUSTER_RADIUS(64), ags.AGS_CLUSTER_RADIUS(32) | ags.AGS_SPLIT_CELLS(32),
+                 ags.AGS_BVH_FP16 | ags.AGS_LEAF_SIZE(3), ags.AGS_BUILD_LBVH]
+        flags = ags.ags_autotune_build_flags(ctx, scene, spec, p, d, sg, cands, 1)
+        assert flags in cands or (flags >> 12) & 0xFF in (0, 1, 16, 48)
+        d2, s2 = render(ctx, scene, spec, poses[0])
+        assert np.array_equal(d2, d0) and np.array_equal(s2, s0)
+        for bad in ([1 << 25], [ags.AGS_BUILD_INSTANCED], [7]):
+            with pytest.raises(ags.AgsError):
+                ags.ags_autotune_build_flags(ctx, scene, spec, p, d, sg, bad, 1)
         rng = np.random.default_rng(23)
         new = batch.poses.copy()
         new[:, :3] += rng.normal(0, 0.2, (new.shape[0], 3)).astype(np.float32)
@@ -1094,7 +1107,8 @@ def test_bvh_structure_of_every_variant(ctx):
     variants = [0, ags.AGS_BVH_FP16, ags.AGS_BVH_Q8, ags.AGS_LEAF_SIZE(1), ags.AGS_LEAF_SIZE(4),
                 ags.AGS_SPLIT_CELLS(1), ags.AGS_SPLIT_CELLS(64), ags.AGS_BUILD_LBVH,
                 ags.AGS_BUILD_LBVH | ags.AGS_BVH_Q8 | ags.AGS_LEAF_SIZE(3), ags.AGS_BUILD_INSTANCED,
-                ags.AGS_BUILD_GREEDY_COLLAPSE, ags.AGS_LEAF_SIZE(3) | ags.AGS_SPLIT_CELLS(64)]
+                ags.AGS_BUILD_GREEDY_COLLAPSE, ags.AGS_LEAF_SIZE(3) | ags.AGS_SPLIT_CELLS(64),
+                ags.AGS_CLUSTER_RADIUS(32), ags.AGS_CLUSTER_RADIUS(128) | ags.AGS_LEAF_SIZE(1)]
     for flags in variants:
         scene = ags.ags_scene_build(ctx, batch, flags)
         try:
