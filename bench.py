@@ -858,15 +858,18 @@ def bench_ours(args, rank, world, local):
     tuned = None
     split_cells = (args.build_flags >> 12) & 0xFF
     cluster_radius = 16 << ((args.build_flags >> 23) & 3)
+    leaf_size = (args.build_flags >> 8) & 0xF or 2
     if not args.no_autotune:  # untimed set-up, like the scene build
         if args.workload == "forest":
             # long LiDAR rays through dense trees gain from finer reference splitting and a wider clustering
             # search; rooms keep the defaults
             split_cells = ags.ags_autotune_build(ctx, scene, spec, poses_d[0], depth, seg, (16, 32, 48, 64), 2)
             base = (args.build_flags & ~(0xFF << 12) & ~ags.AGS_CLUSTER_RADIUS(128)) | ags.AGS_SPLIT_CELLS(split_cells)
-            best = ags.ags_autotune_build_flags(ctx, scene, spec, poses_d[0], depth, seg,
-                                                [base | ags.AGS_CLUSTER_RADIUS(r) for r in (32, 64)], 2)
+            cands = [base | ags.AGS_CLUSTER_RADIUS(r) for r in (32, 64)]
+            cands += [base | ags.AGS_LEAF_SIZE(1) | ags.AGS_CLUSTER_RADIUS(r) for r in (16, 64)]
+            best = ags.ags_autotune_build_flags(ctx, scene, spec, poses_d[0], depth, seg, cands, 3)
             cluster_radius = 16 << ((best >> 23) & 3)
+            leaf_size = (best >> 8) & 0xF or 2
         tuned = ags.ags_autotune(ctx, scene, spec, poses_d[0], depth, seg, 2).as_dict()
     for i in range(args.warmup):
         step(i)
@@ -1004,7 +1007,7 @@ def bench_ours(args, rank, world, local):
                    "tris_per_gpu": n_tris, "rays_per_step": rays_per_step * world, "walk_steps": walk,
                    "l2": "not flushed: per step the resident BVHs and the outputs exceed the 129 MB L2",
                    "bvh_bytes": ags.ags_scene_stats(scene)[2], "build_flags": args.build_flags,
-                   "split_cells": split_cells or 16, "cluster_radius": cluster_radius,
+                   "split_cells": split_cells or 16, "cluster_radius": cluster_radius, "leaf_size": leaf_size,
                    "parallelism": f"env-sharded x{world}, no collective on the data path"},
         "roofline": lead,
         "roofline_hbm_algorithmic": algorithmic,
