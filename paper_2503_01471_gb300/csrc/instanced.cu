@@ -228,6 +228,7 @@ ags_status object_parts(ags_context* ctx, ags_scene* sc, const float* poses_h) {
     for (int64_t j = sc->env_sub_off[e]; j < sc->env_sub_off[e + 1]; ++j) env_area[j] = box_area(u);
   }
   std::vector<WideNode> roots(std::max<int32_t>(J, 1));
+  std::vector<int32_t> root_of(std::max<int32_t>(J, 1), -1);
   if (J > 0) {
     DevBufs tmp;
     WideNode* d_roots = nullptr;
@@ -236,12 +237,10 @@ ags_status object_parts(ags_context* ctx, ags_scene* sc, const float* poses_h) {
                                                       sc->objects->d.env_root, J, sc->objects->n_nodes, d_roots);
     AGS_CHECK(cudaGetLastError());
     AGS_CHECK(cudaMemcpyAsync(roots.data(), d_roots, (size_t)J * sizeof(WideNode), cudaMemcpyDeviceToHost, s));
+    AGS_CHECK(cudaMemcpyAsync(root_of.data(), sc->objects->d.env_root, (size_t)J * sizeof(int32_t),
+                              cudaMemcpyDeviceToHost, s));
     AGS_CHECK(cudaStreamSynchronize(s));
   }
-  std::vector<int32_t> root_of(std::max<int32_t>(J, 1), -1);
-  if (J > 0)
-    AGS_CHECK(cudaMemcpy(root_of.data(), sc->objects->d.env_root, (size_t)J * sizeof(int32_t),
-                         cudaMemcpyDeviceToHost));
   sc->h_parts.clear();
   sc->h_part_off.assign((size_t)J + 1, 0);
   for (int32_t j = 0; j < J; ++j) {
