@@ -69,6 +69,50 @@ def test_lidar_forests_full_size(ctx):
         ags.ags_scene_destroy(scene)
 
 
+def test_two_level_rooms_full_size(ctx):
+    """The dynamic workload's two-level scene at full size: 1024 rooms x 270x480 (31k objects, the rooms'
+    roots opened into the top level), before and after every obstacle moves; sampled rays against the oracle
+    of the moved scene, and every ray against the single-level scene of the same poses (same segment where
+    both hit; depths within the tolerance)."""
+    batch, spec, poses = S.obstacle_rooms(1024, steps=1)
+    E = batch.n_envs
+    p = torch.as_tensor(poses[0]).cuda()
+    rng = np.random.default_rng(35)
+    cur = batch.poses.copy()
+    movable = np.ones(cur.shape[0], bool)
+    movable[batch.env_sub[:-1]] = False
+    two = ags.ags_scene_build(ctx, batch, ags.AGS_BUILD_INSTANCED)
+    try:
+        for step in range(2):
+            if step:
+                cur[movable, :3] += rng.normal(0, 0.05, (int(movable.sum()), 3)).astype(np.float32)
+                q = cur[movable, 3:] + rng.normal(0, 0.025, (int(movable.sum()), 4)).astype(np.float32)
+                cur[movable, 3:] = q / np.linalg.norm(q, axis=1, keepdims=True)
+                ags.ags_scene_update_poses(ctx, two, cur, ags.AGS_UPDATE_REBUILD)
+            moved = S.SceneBatch(batch.vertices, batch.indices, batch.sub_vert, batch.sub_tri, batch.sub_seg,
+                                 batch.env_sub, cur.copy())
+            d = torch.empty((E, spec.height, spec.width), device="cuda")
+            s = torch.empty((E, spec.height, spec.width), dtype=torch.int32, device="cuda")
+            ags.ags_render(ctx, two, spec, p, d, s)
+            ags.ags_stream_status(ctx)
+            depth, seg = d.cpu().numpy(), s.cpu().numpy()
+            every_ray(depth, seg, spec)
+            one = ags.ags_scene_build(ctx, moved)
+            try:
+                ags.ags_render(ctx, one, spec, p, d, s)
+                ags.ags_stream_status(ctx)
+                d1, s1 = d.cpu().numpy(), s.cpu().numpy()
+            finally:
+                ags.ags_scene_destroy(one)
+            assert (s1 == seg).mean() > 0.9999
+            both = (s1 >= 0) & (s1 == seg)
+            assert (np.abs(d1[both] - depth[both]) <= 2 * (1e-5 * d1[both] + 1e-6)).mean() > 0.9999
+            envs = sorted(set([0, E - 1] + list(rng.choice(E, 6, replace=False))))
+            sampled_parity(moved, spec, poses[0], depth, seg, envs, 64, rng, f"two-level 1024 rooms, step {step}")
+    finally:
+        ags.ags_scene_destroy(two)
+
+
 def test_precision_full_size(ctx):
     """4096 rooms x 135x240 with float32, float16 and 8-bit child bounds: outputs bit-identical, sampled rays
     within the tolerance of the oracle."""
